@@ -1,0 +1,327 @@
+"""ctypes front-end of the FP64 CPU oracle (``lbmib_oracle.c``).
+
+Test infrastructure only: the test-suite, the smoke check and the CPU-baseline leg
+of ``bench.py`` import this module. The GPU library never does, and this module
+imports nothing from the GPU package.
+
+Every function states the equation of Coclite et al. (arXiv:1903.03356) that it
+evaluates; the C source carries the readings of the paper that the oracle takes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbmib_oracle.c")
+_LIB = os.path.join(_HERE, "liblbmib_oracle.so")
+
+CFLAGS = ["-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11", "-D_DEFAULT_SOURCE"]
+
+
+def build_library(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C11, no FMA contraction) if it is stale."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build_library())
+        _declare(_lib)
+    return _lib
+
+
+class Lattice(C.Structure):
+    """Lattice description: size, y-boundary, wall velocities, tau, body force."""
+
+    _fields_ = [
+        ("nx", C.c_int),
+        ("ny", C.c_int),
+        ("walls", C.c_int),
+        ("u_bottom", C.c_double),
+        ("u_top", C.c_double),
+        ("tau", C.c_double),
+        ("gx", C.c_double),
+        ("gy", C.c_double),
+    ]
+
+    @property
+    def N(self) -> int:
+        return self.nx * self.ny
+
+
+def lattice(nx, ny, tau, walls=False, u_bottom=0.0, u_top=0.0, gx=0.0, gy=0.0) -> Lattice:
+    return Lattice(int(nx), int(ny), int(bool(walls)), float(u_bottom), float(u_top),
+                   float(tau), float(gx), float(gy))
+
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_LP = C.POINTER(Lattice)
+
+
+def _declare(L):
+    vp = C.c_void_p
+    sig = {
+        "orc_feq": (None, [C.c_double, C.c_double, C.c_double, _dp]),
+        "orc_macros": (None, [_LP, _dp, vp, _dp, _dp, _dp]),
+        "orc_collide_stream": (None, [_LP, _dp, vp, _dp]),
+        "orc_init_equilibrium": (None, [_LP, vp, vp, vp, _dp]),
+        "orc_mls": (C.c_int, [_LP, C.c_double, C.c_double, _ip, _ip, _dp, _dp, _dp]),
+        "orc_interp": (C.c_int, [_LP, _dp, vp, C.c_double, C.c_double, _dp]),
+        "orc_interp_scalar": (C.c_int, [_LP, _dp, C.c_double, C.c_double, _dp]),
+        "orc_spread": (C.c_int, [_LP, C.c_double, C.c_double, C.c_double, C.c_double,
+                                 C.c_double, _dp]),
+        "orc_tractions": (C.c_int, [_LP, _dp, vp, _dp, C.c_int, _dp]),
+        "orc_area": (C.c_double, [_dp, C.c_int]),
+        "orc_perimeter": (C.c_double, [_dp, C.c_int]),
+        "orc_membrane_reference": (None, [_dp, C.c_int, _dp, _dp, _dp]),
+        "orc_membrane_energy": (C.c_double, [_dp, C.c_int, _dp, _dp, C.c_double, C.c_double,
+                                             C.c_double, C.c_double]),
+        "orc_membrane_force": (None, [_dp, C.c_int, _dp, _dp, C.c_double, C.c_double,
+                                      C.c_double, C.c_double, _dp]),
+        "orc_observables": (None, [_dp, C.c_int, _dp]),
+        "orc_kinematic_advance": (None, [C.c_int, _dp, _dp, _dp, C.c_int, _dp]),
+        "orc_dynamic_advance": (None, [C.c_int, _dp, _dp, _dp, _dp, C.c_double, _dp, _dp]),
+        "orc_sim_create": (vp, [_LP]),
+        "orc_sim_destroy": (None, [vp]),
+        "orc_sim_init_fields": (None, [vp, vp, vp, vp]),
+        "orc_sim_populations": (C.POINTER(C.c_double), [vp]),
+        "orc_sim_force_field": (C.POINTER(C.c_double), [vp]),
+        "orc_sim_add_capsule": (C.c_int, [vp, _dp, C.c_int, C.c_double, C.c_double, C.c_double,
+                                          C.c_double]),
+        "orc_sim_step": (C.c_int, [vp, C.c_longlong, C.c_int]),
+        "orc_sim_set_capsule_positions": (C.c_int, [vp, C.c_int, _dp]),
+        "orc_sim_read_fields": (None, [vp, _dp, _dp, _dp]),
+        "orc_sim_read_capsule": (C.c_int, [vp, C.c_int, vp, vp, vp, vp]),
+        "orc_sim_observables": (C.c_int, [vp, C.c_int, _dp]),
+        "orc_sim_step_count": (C.c_longlong, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ----------------------------------------------------------------------------------
+# Lattice Boltzmann (Section 2.1, Eq. 1-7)
+# ----------------------------------------------------------------------------------
+def feq(rho: float, ux: float, uy: float) -> np.ndarray:
+    """Eq. 2 equilibrium populations at one node."""
+    out = np.zeros(9)
+    lib().orc_feq(rho, ux, uy, out)
+    return out
+
+
+def init_equilibrium(L: Lattice, rho=None, ux=None, uy=None) -> np.ndarray:
+    """Populations (9, ny, nx) at the Eq. 2 equilibrium of the given fields."""
+    f = np.zeros((9, L.ny, L.nx))
+    args = [None if a is None else _f64(a) for a in (rho, ux, uy)]
+    lib().orc_init_equilibrium(C.byref(L), *[_ptr(a) for a in args], f)
+    return f
+
+
+def macros(L: Lattice, f: np.ndarray, fib: Optional[np.ndarray] = None):
+    """Eq. 6-7: density and velocity with half of the total body force."""
+    rho = np.zeros((L.ny, L.nx)); ux = np.zeros_like(rho); uy = np.zeros_like(rho)
+    fib = None if fib is None else _f64(fib)
+    lib().orc_macros(C.byref(L), _f64(f), _ptr(fib), rho, ux, uy)
+    return rho, ux, uy
+
+
+def collide_stream(L: Lattice, f: np.ndarray, fib: Optional[np.ndarray] = None) -> np.ndarray:
+    """Eq. 4-5: one forced BGK collision plus streaming with bounce-back walls."""
+    out = np.zeros((9, L.ny, L.nx))
+    fib = None if fib is None else _f64(fib)
+    lib().orc_collide_stream(C.byref(L), _f64(f), _ptr(fib), out)
+    return out
+
+
+# ----------------------------------------------------------------------------------
+# MLS transfer (Eq. 8-9)
+# ----------------------------------------------------------------------------------
+def mls(L: Lattice, X: float, Y: float):
+    """Shape functions phi_k and gradient weights at (X, Y): (ix, iy, phi, gx, gy, status)."""
+    ix = np.zeros(9, np.int32); iy = np.zeros(9, np.int32)
+    phi = np.zeros(9); gx = np.zeros(9); gy = np.zeros(9)
+    st = lib().orc_mls(C.byref(L), float(X), float(Y), ix, iy, phi, gx, gy)
+    return ix, iy, phi, gx, gy, st
+
+
+def interp(L: Lattice, f: np.ndarray, fib: Optional[np.ndarray], X: float, Y: float):
+    """Eq. 8 at (X, Y): (ux, uy, rho, p, dux/dx, dux/dy, duy/dx, duy/dy), status."""
+    out = np.zeros(8)
+    fib = None if fib is None else _f64(fib)
+    st = lib().orc_interp(C.byref(L), _f64(f), _ptr(fib), float(X), float(Y), out)
+    return out, st
+
+
+def interp_scalar(L: Lattice, v: np.ndarray, X: float, Y: float) -> Tuple[float, int]:
+    out = np.zeros(1)
+    st = lib().orc_interp_scalar(C.byref(L), _f64(v), float(X), float(Y), out)
+    return float(out[0]), st
+
+
+def spread(L: Lattice, X, Y, Fx, Fy, c, fib: np.ndarray) -> int:
+    """Step 3 / step iii: fib (2, ny, nx) += c phi_k F at the marker's support."""
+    assert fib.dtype == np.float64 and fib.flags.c_contiguous
+    return lib().orc_spread(C.byref(L), float(X), float(Y), float(Fx), float(Fy), float(c), fib)
+
+
+def tractions(L: Lattice, f: np.ndarray, fib: Optional[np.ndarray], xy: np.ndarray):
+    """Eq. 15-16 nodal shares of the element tractions of a ring: (Fext (n, 2), status)."""
+    xy = _f64(xy).reshape(-1)
+    out = np.zeros_like(xy)
+    fib = None if fib is None else _f64(fib)
+    st = lib().orc_tractions(C.byref(L), _f64(f), _ptr(fib), xy, xy.size // 2, out)
+    return out.reshape(-1, 2), st
+
+
+# ----------------------------------------------------------------------------------
+# Membrane (Eq. 10-14) and observables
+# ----------------------------------------------------------------------------------
+def area(xy: np.ndarray) -> float:
+    xy = _f64(xy); return lib().orc_area(xy, xy.size // 2)
+
+
+def perimeter(xy: np.ndarray) -> float:
+    xy = _f64(xy); return lib().orc_perimeter(xy, xy.size // 2)
+
+
+def membrane_reference(xy: np.ndarray):
+    xy = _f64(xy); n = xy.size // 2
+    L0 = np.zeros(n); th0 = np.zeros(n); A0 = np.zeros(1)
+    lib().orc_membrane_reference(xy, n, L0, th0, A0)
+    return L0, th0, float(A0[0])
+
+
+def membrane_energy(xy, L0, th0, A0, ks, kb, ka) -> float:
+    xy = _f64(xy)
+    return lib().orc_membrane_energy(xy, xy.size // 2, _f64(L0), _f64(th0), A0, ks, kb, ka)
+
+
+def membrane_force(xy, L0, th0, A0, ks, kb, ka) -> np.ndarray:
+    xy = _f64(xy); F = np.zeros_like(xy)
+    lib().orc_membrane_force(xy, xy.size // 2, _f64(L0), _f64(th0), A0, ks, kb, ka, F)
+    return F
+
+
+def observables(xy: np.ndarray) -> np.ndarray:
+    """(area, perimeter, D, xc, yc, Sw, inclination, lambda_max)."""
+    xy = _f64(xy); out = np.zeros(8)
+    lib().orc_observables(xy, xy.size // 2, out)
+    return out
+
+
+def kinematic_advance(X, Xm1, xdot, first: bool) -> np.ndarray:
+    """Eq. 25 (forward Euler when first)."""
+    X = _f64(X); out = np.zeros_like(X)
+    lib().orc_kinematic_advance(X.size, X, _f64(Xm1), _f64(xdot), int(first), out)
+    return out
+
+
+def dynamic_advance(X, Xm1, xdot0, Ftot, m):
+    """Eq. 23-24: (X^{n+1}, u_v^{n+1})."""
+    X = _f64(X); Xn = np.zeros_like(X); uv = np.zeros_like(X)
+    lib().orc_dynamic_advance(X.size, X, _f64(Xm1), _f64(xdot0), _f64(Ftot), float(m), Xn, uv)
+    return Xn, uv
+
+
+# ----------------------------------------------------------------------------------
+# Whole simulation
+# ----------------------------------------------------------------------------------
+KINEMATIC = 0
+DYNAMIC = 1
+
+
+class Sim:
+    """Lattice plus capsules stepped with the Kinematic (Section 2.4) or Dynamic
+    (Section 2.3) scheme."""
+
+    def __init__(self, L: Lattice):
+        self.L = L
+        self._h = lib().orc_sim_create(C.byref(L))
+        self._n = []
+
+    def close(self):
+        if self._h:
+            lib().orc_sim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_fields(self, rho=None, ux=None, uy=None):
+        args = [None if a is None else _f64(a) for a in (rho, ux, uy)]
+        self._keep = args
+        lib().orc_sim_init_fields(self._h, *[_ptr(a) for a in args])
+
+    def add_capsule(self, xy, ks, kb, ka, mass) -> int:
+        xy = _f64(xy).reshape(-1)
+        n = xy.size // 2
+        cid = lib().orc_sim_add_capsule(self._h, xy, n, ks, kb, ka, mass)
+        self._n.append(n)
+        return cid
+
+    def set_positions(self, cid: int, xy):
+        """Start capsule cid at positions xy (its stress-free shape is unchanged)."""
+        lib().orc_sim_set_capsule_positions(self._h, cid, _f64(xy).reshape(-1))
+
+    def step(self, n: int, scheme: int) -> int:
+        return lib().orc_sim_step(self._h, int(n), int(scheme))
+
+    @property
+    def step_count(self) -> int:
+        return lib().orc_sim_step_count(self._h)
+
+    def populations(self) -> np.ndarray:
+        p = lib().orc_sim_populations(self._h)
+        return np.ctypeslib.as_array(p, shape=(9, self.L.ny, self.L.nx)).copy()
+
+    def set_populations(self, f: np.ndarray):
+        p = lib().orc_sim_populations(self._h)
+        np.ctypeslib.as_array(p, shape=(9, self.L.ny, self.L.nx))[...] = f
+
+    def force_field(self) -> np.ndarray:
+        p = lib().orc_sim_force_field(self._h)
+        return np.ctypeslib.as_array(p, shape=(2, self.L.ny, self.L.nx)).copy()
+
+    def read_fields(self):
+        rho = np.zeros((self.L.ny, self.L.nx)); ux = np.zeros_like(rho); uy = np.zeros_like(rho)
+        lib().orc_sim_read_fields(self._h, rho, ux, uy)
+        return rho, ux, uy
+
+    def read_capsule(self, cid: int):
+        n = self._n[cid]
+        xy = np.zeros(2 * n); vel = np.zeros(2 * n); fi = np.zeros(2 * n); fe = np.zeros(2 * n)
+        lib().orc_sim_read_capsule(self._h, cid, _ptr(xy), _ptr(vel), _ptr(fi), _ptr(fe))
+        return xy, vel, fi, fe
+
+    def observables(self, cid: int) -> np.ndarray:
+        """(area, perimeter, D, xc, yc, Sw, inclination, delta_p)."""
+        out = np.zeros(8)
+        lib().orc_sim_observables(self._h, cid, out)
+        return out
