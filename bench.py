@@ -1,0 +1,296 @@
+"""Benchmark of one coupled LBM-IB time step on GB300 (MLUPS and HBM roofline).
+
+A step is one pass of the whole hot path: spread, lattice update (collide-stream),
+forced-node patch, interpolation, tractions, membrane forces and node update
+(Coclite et al., arXiv:1903.03356, Section 2.3-2.4). Default workload: a 16384 x 8192
+Poiseuille channel (1.34e8 lattice nodes, far above L2) holding 16384 biconcave
+capsules of 128 vertices (the capsule density of the 4096 x 512 precision workload),
+Dynamic IB, FP32 shifted storage.
+
+Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle instead, on a
+bounded sample of the same workload (the CPU baseline arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1903_03356_gb300 import workloads as W  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--nx", type=int, default=16384)
+    p.add_argument("--ny", type=int, default=8192)
+    p.add_argument("--storage", default="fp32", choices=["fp64", "fp32", "fp16"])
+    p.add_argument("--scheme", default="dynamic", choices=["dynamic", "kinematic"])
+    p.add_argument("--no-capsules", action="store_true", help="lattice update only")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--extra", default="", help="comma list: fp64,fp16,kinematic extra measurements")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def make_case(a):
+    scheme = W.DYNAMIC if a.scheme == "dynamic" else W.KINEMATIC
+    if a.no_capsules:
+        return W.Case("poiseuille_lattice", a.nx, a.ny, 0.7, True,
+                      gx=W.poiseuille_force(0.7, 0.02, a.ny), init="parabola", scheme=scheme)
+    return W.roofline_lattice(nx=a.nx, ny=a.ny, scheme=scheme, seed=0)
+
+
+def workload_name(a, case):
+    caps = f"{len(case.capsules)}x{case.capsules[0].xy.shape[0] if case.capsules else 0}"
+    return f"poiseuille-biconcave-{a.nx}x{a.ny}-{caps}-{a.scheme}-{a.storage}"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if len(s) > 5 + k and s[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def dist_setup(n):
+    if n <= 1 and "WORLD_SIZE" not in os.environ:
+        return 0, 1, None
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(n)))
+    backend = "nccl" if os.environ.get("LBMIB_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+    dist.init_process_group(backend)
+    return rank, world, dist
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(a, seconds: float):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload: a
+    2048 x 512 slab of the same channel with the same capsule density."""
+    import oracle as o
+    nx, ny = 2048, 512
+    scheme = W.DYNAMIC if a.scheme == "dynamic" else W.KINEMATIC
+    if a.no_capsules:
+        case = W.Case("slab", nx, ny, 0.7, True, gx=W.poiseuille_force(0.7, 0.02, a.ny), init="parabola")
+    else:
+        case = W.poiseuille_biconcave(nx=nx, ny=ny, count=(nx * ny) // 8192, seed=0, scheme=scheme,
+                                      placement="grid")
+    L = o.lattice(nx, ny, 0.7, True, gx=case.gx)
+    s = o.Sim(L)
+    s.init_fields(*case.fields())
+    for c in case.capsules:
+        s.add_capsule(c.xy, c.ks, c.kb, c.ka, c.mass)
+    s.step(1, scheme)  # start-up step, untimed
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < seconds:
+        s.step(1, scheme)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": nx * ny * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{nx}x{ny} slab, {len(case.capsules)} capsules, {steps} steps, FP64, single thread"}
+
+
+def run_reference(a):
+    rank, world, dist = dist_setup(a.gpus)
+    if rank != 0:
+        return
+    per = max(1.0, a.cpu_seconds / max(1, a.steps + a.warmup))
+    base = cpu_baseline(a, per * max(1, a.steps))
+    line = {"impl": "reference", "metric": "LBM-IB MLUPS (coupled step)", "value": base["value"],
+            "unit": "MLUPS", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"poiseuille-biconcave-{a.nx}x{a.ny} (oracle sample)"},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(a):
+    import torch
+
+    rank, world, dist = dist_setup(a.gpus)
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    from paper_1903_03356_gb300 import lbmib as L
+
+    case = make_case(a)
+    scheme = L.DYNAMIC if a.scheme == "dynamic" else L.KINEMATIC
+    N = a.nx * a.ny
+    t_setup = time.perf_counter()
+    ctx = L.from_case(case, storage=a.storage)
+    setup_s = time.perf_counter() - t_setup
+    stream = ctx.stream
+
+    # warm-up (graph capture, clocks ramp); inputs are far larger than L2
+    ctx.set_option(L.OPT_TIMING, 1)
+    ctx.step(a.warmup, scheme)
+    ctx.sync()
+    ctx.kernel_time(reset=True)
+    launches0 = ctx.launch_count
+
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(dev) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        start.record(stream)
+        ctx.step(a.steps, scheme)
+        end.record(stream)
+        torch.cuda.synchronize()
+    elapsed_ms = start.elapsed_time(end)
+    ctx.sync()
+    k1_ms, k1_n = ctx.kernel_time(reset=True)
+    launches = ctx.launch_count - launches0
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, torch.device("cuda", dev))
+
+    mlups = world * N * a.steps / (elapsed_ms / 1e3) / 1e6
+    hbm, src = peaks()
+    bpu = ctx.bytes_per_update
+    k1_avg_ms = k1_ms / max(1, k1_n)
+    achieved = bpu * N / (k1_avg_ms / 1e3) / 1e9
+
+    line = {
+        "metric": "LBM-IB MLUPS (coupled step) and % of HBM roofline",
+        "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": elapsed_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32"}[a.storage],
+        "data": "synthetic",
+        "config": {"workload": workload_name(a, case), "nx": a.nx, "ny": a.ny,
+                   "capsules": len(case.capsules), "markers": case.n_nodes, "scheme": a.scheme,
+                   "storage": a.storage, "tau": case.tau,
+                   "l2": "inputs larger than L2 (populations 2 x %.1f GB)" % (9 * N * bpu / 18 / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "kernel": "k_collide_stream", "bytes_per_update": bpu,
+                     "kernel_ms": k1_avg_ms, "kernel_share": k1_ms / elapsed_ms,
+                     "peak_source": src},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "setup_s": setup_s,
+    }
+
+    if not a.no_e2e:
+        line["e2e"] = e2e_run(a, case, L, scheme, dev)
+    if rank == 0 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a, a.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def e2e_run(a, case, L, scheme, dev):
+    """Same metric through the public API with host buffers. Timed: the fields copied
+    in from pinned host memory (lbmib_init_fields), the steps (lbmib_step), and the
+    fields plus every capsule's observables read back into pinned host memory."""
+    import torch
+
+    N = a.nx * a.ny
+    rho, ux, uy = case.fields()
+    pin = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (rho, ux, uy)]
+    out = [torch.empty((a.ny, a.nx), dtype=torch.float64).pin_memory() for _ in range(3)]
+    ncap = len(case.capsules)
+    obs = torch.empty((max(ncap, 1), 8), dtype=torch.float64).pin_memory()
+    ctx = L.from_case(case, storage=a.storage)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L.lbmib_init_fields(ctx.h, *[p.numpy() for p in pin])
+    L.lbmib_step(ctx.h, a.steps, scheme)
+    L.lbmib_read_fields(ctx.h, *[o.numpy() for o in out])
+    if ncap:
+        L.lbmib_observables_all(ctx.h, obs.numpy())
+    L.lbmib_sync(ctx.h)
+    dt = time.perf_counter() - t0
+    ctx.close()
+    h2d = 3 * N * 8
+    d2h = 3 * N * 8 + 8 * 8 * ncap
+    return {"value": N * a.steps / dt / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": h2d / a.steps, "d2h_bytes_per_step": d2h / a.steps,
+            "note": "init_fields + step + read_fields + observables_all, host-pinned buffers"}
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * lbmib.h - C ABI of the GB300 LBM-IB library.
+ *
+ * The library advances one time step of the combined lattice Boltzmann / immersed
+ * boundary method of Coclite et al., "Kinematic and Dynamic Forcing Strategies for
+ * Predicting the Transport of Inertial Capsules via a combined Lattice Boltzmann -
+ * Immersed Boundary Method" (arXiv:1903.03356):
+ *   - D2Q9 BGK lattice update with a body-force term (Section 2.1-2.2, Eq. 1-7),
+ *   - moving-least-squares interpolation and spreading between the lattice and the
+ *     membrane vertices (Section 2.2, Eq. 8-9; Section 2.3 step 3; Section 2.4 step iii),
+ *   - membrane stretch, bending and area forces (Section 2.2.1, Eq. 10-14),
+ *   - hydrodynamic tractions from normal probes (Section 2.2.2, Eq. 15-16),
+ *   - the Kinematic scheme (Section 2.4, steps i-viii, Eq. 25) or the Dynamic scheme
+ *     (Section 2.3.2, steps 1-8, Eq. 21-24).
+ *
+ * Conventions shared by every call
+ *   Units dx = dt = 1, rho_0 = 1, c_s^2 = 1/3, nu = (tau - 1/2)/3. Lattice node (i, j)
+ *   sits at (x, y) = (i, j); fields are row-major ny x nx (index j * nx + i). x is
+ *   periodic. With walls, half-way bounce-back walls sit at y = -1/2 and y = ny - 1/2
+ *   and move along x with the given velocities. Capsule rings are counter-clockwise;
+ *   coordinate arrays interleave x and y (2n doubles).
+ *
+ *   Memory: the library never allocates device memory. The caller allocates one
+ *   device arena of lbmib_arena_bytes() bytes (at least 256-byte aligned) and keeps it
+ *   alive until lbmib_destroy(). Host pointers passed to any call belong to the caller
+ *   and are only read or written during the call. The context itself is host memory
+ *   owned by the library.
+ *
+ *   Ordering: all device work is issued on the CUDA stream given to lbmib_create (NULL
+ *   means the legacy default stream). lbmib_step only enqueues work; read calls
+ *   synchronise that stream.
+ *
+ *   Errors: every call returns an lbmib_status; lbmib_last_error() gives a message.
+ *   Device-side conditions (a support leaving the channel, an unstable velocity) are
+ *   recorded in a sticky status word and reported by the next synchronising call.
+ */
+#ifndef LBMIB_H
+#define LBMIB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbmib_ctx lbmib_ctx;
+
+typedef enum {
+    LBMIB_OK = 0,
+    LBMIB_ERR_ARG = 1,      /* invalid argument (sizes, ids, NULL where not allowed)  */
+    LBMIB_ERR_OOM = 2,      /* arena too small or capacity exceeded                   */
+    LBMIB_ERR_CUDA = 3,     /* a CUDA call failed; the message names it               */
+    LBMIB_ERR_UNSTABLE = 4, /* |u| > 0.3 or a NaN in the lattice (sticky)             */
+    LBMIB_ERR_SUPPORT = 5,  /* an MLS support or probe left the channel (sticky)      */
+    LBMIB_ERR_TIMEOUT = 6,  /* a bounded device wait gave up (sticky)                 */
+    LBMIB_ERR_STATE = 7     /* call not valid in the current state                    */
+} lbmib_status;
+
+/* Storage of the lattice populations. Populations are stored shifted by their rest
+ * weights (f_i - w_i). FP64 computes in double; FP32 and FP16 compute the collision in
+ * float (FP16 storage keeps the shifted value times a power-of-two scale). Membrane
+ * vertices, their velocities and forces are double in every mode. */
+typedef enum { LBMIB_FP64 = 0, LBMIB_FP32 = 1, LBMIB_FP16 = 2 } lbmib_storage;
+
+/* Coupling scheme of a step: Kinematic IB (Section 2.4) or Dynamic IB (Section 2.3). */
+typedef enum { LBMIB_KINEMATIC = 0, LBMIB_DYNAMIC = 1 } lbmib_scheme;
+
+typedef struct {
+    int nx, ny;             /* lattice size, each >= 3                                */
+    int walls;              /* 0: periodic in y; 1: moving bounce-back walls in y      */
+    double tau;             /* BGK relaxation time (Eq. 1), > 0.5                      */
+    double u_bottom;        /* x-velocity of the wall at y = -1/2                     */
+    double u_top;           /* x-velocity of the wall at y = ny - 1/2                 */
+    double gx, gy;          /* uniform body-force density (added to f_ib, Eq. 5)      */
+    lbmib_storage storage;
+    int max_capsules;       /* capacity for capsules                                  */
+    int max_nodes;          /* capacity for membrane vertices over all capsules       */
+} lbmib_config;
+
+/* Device arena size (bytes) for a configuration; 0 if the configuration is invalid. */
+size_t lbmib_arena_bytes(const lbmib_config* cfg);
+
+/* Create a context over the caller's device arena. cuda_stream is a cudaStream_t (or
+ * NULL). The fluid starts at rest (rho = 1, u = 0). *out receives the context. */
+lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_bytes,
+                          void* cuda_stream, lbmib_ctx** out);
+
+/* Release the context's host memory and CUDA graphs (the arena stays the caller's). */
+void lbmib_destroy(lbmib_ctx* ctx);
+
+/* Message of the last failing call on this context (never NULL). */
+const char* lbmib_last_error(const lbmib_ctx* ctx);
+
+/* Set the fluid to the Eq. 2 equilibrium of the given host fields (ny*nx doubles each;
+ * NULL means rho = 1 or u = 0). Clears the immersed-boundary force field. */
+lbmib_status lbmib_init_fields(lbmib_ctx* ctx, const double* rho, const double* ux,
+                               const double* uy);
+
+/* Add a capsule: xy (2n doubles, host) is its stress-free shape and initial position
+ * (Section 2.2.1: reference lengths, angles and area are taken from it). k_s, k_b, k_a
+ * are the stretch (Eq. 10), bending (Eq. 12) and area (Eq. 14) constants; node_mass is
+ * the per-vertex mass m_v (Eq. 21). n must be in [3, 1024]. *id_out gets its id. */
+lbmib_status lbmib_add_capsule(lbmib_ctx* ctx, const double* xy, int n, double k_s,
+                               double k_b, double k_a, double node_mass, int* id_out);
+
+/* Move capsule id to positions xy (2n doubles, host) without changing its stress-free
+ * shape; its time history restarts (the next step is a start-up step). */
+lbmib_status lbmib_set_capsule_positions(lbmib_ctx* ctx, int id, const double* xy);
+
+/* Advance nsteps time steps with the given scheme (enqueued, asynchronous). A capsule's
+ * first step after being added starts its history: Kinematic uses forward Euler,
+ * Dynamic sets u_v = I(u) and X^{-1} = X^0 - u_v. */
+lbmib_status lbmib_step(lbmib_ctx* ctx, long long nsteps, lbmib_scheme scheme);
+
+/* Wait for the stream and report any sticky device status. */
+lbmib_status lbmib_sync(lbmib_ctx* ctx);
+
+/* Fluid fields at the current time into host arrays (ny*nx doubles each, any may be
+ * NULL): rho (Eq. 6) and u (Eq. 7) with half of the body force plus the last spread
+ * immersed-boundary force. Synchronises. */
+lbmib_status lbmib_read_fields(lbmib_ctx* ctx, double* rho, double* ux, double* uy);
+
+/* Pre-collision populations f_i at the current time (unshifted), host array of
+ * 9*ny*nx doubles ordered [i][j][x]. Synchronises. */
+lbmib_status lbmib_read_populations(lbmib_ctx* ctx, double* f);
+
+/* Last spread immersed-boundary force field f_ib (without the uniform body force),
+ * host arrays of ny*nx doubles (either may be NULL). Synchronises. */
+lbmib_status lbmib_read_force_field(lbmib_ctx* ctx, double* fx, double* fy);
+
+/* Capsule state into host arrays of 2n doubles (any may be NULL): positions X^n,
+ * node velocities (Kinematic: last interpolated velocity; Dynamic: u_v of Eq. 24),
+ * the last internal forces F^int (Eq. 22) and external forces F^ext (Eq. 15-16). */
+lbmib_status lbmib_read_capsule(lbmib_ctx* ctx, int id, double* xy, double* vel,
+                                double* fint, double* fext);
+
+/* Observables of capsule id (Section 3.1-3.2): out = {area, perimeter, Taylor D,
+ * centroid x, centroid y, swelling ratio Sw, inclination of the major axis,
+ * relative perimeter change delta_p}. D comes from the eigenvalues of the area
+ * second-moment tensor. Synchronises. */
+lbmib_status lbmib_observables(lbmib_ctx* ctx, int id, double out[8]);
+
+/* Observables of every capsule: out (8 * capsule count doubles, host) in the order of
+ * lbmib_observables, capsule by capsule. Synchronises. */
+lbmib_status lbmib_observables_all(lbmib_ctx* ctx, double* out);
+
+/* MLS interpolation (Eq. 8) of the current fluid at n host points xy (2n doubles):
+ * out (8n doubles, host) = {ux, uy, rho, p, dux/dx, dux/dy, duy/dx, duy/dy} per point.
+ * n <= max_nodes. Synchronises. */
+lbmib_status lbmib_interpolate(lbmib_ctx* ctx, const double* xy, int n, double* out);
+
+/* Checkpoint: lbmib_state_bytes() gives the size of a snapshot of the populations,
+ * the force fields and all capsule state; lbmib_save_state() writes it into a host
+ * buffer of that size and lbmib_load_state() restores it into a context created with
+ * the same configuration. Both synchronise. */
+size_t lbmib_state_bytes(const lbmib_ctx* ctx);
+lbmib_status lbmib_save_state(lbmib_ctx* ctx, void* host_buf, size_t bytes);
+lbmib_status lbmib_load_state(lbmib_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* Options (lbmib_set_option):
+ *   LBMIB_OPT_GRAPHS        1 (default): replay steps from captured CUDA graphs;
+ *                           0: launch kernels directly.
+ *   LBMIB_OPT_TIMING        1: record CUDA events around every lattice-update launch
+ *                           (forces direct launches); read with lbmib_kernel_time.
+ *   LBMIB_OPT_GRAPH_STEPS   steps per captured graph (default 16).
+ *   LBMIB_OPT_FP16_SCALE    log2 of the FP16 storage scale (default 10).
+ *   LBMIB_OPT_LATTICE_VARIANT launch shape of the lattice-update kernel: bits 0-11 the
+ *                           block size (64..512, multiple of 32; default 256), bit 16
+ *                           streaming loads, bit 17 streaming stores. Results do not
+ *                           depend on it; only speed does.                          */
+enum {
+    LBMIB_OPT_GRAPHS = 1,
+    LBMIB_OPT_TIMING = 2,
+    LBMIB_OPT_GRAPH_STEPS = 3,
+    LBMIB_OPT_FP16_SCALE = 4,
+    LBMIB_OPT_LATTICE_VARIANT = 5
+};
+lbmib_status lbmib_set_option(lbmib_ctx* ctx, int option, long long value);
+
+/* Timing of the lattice-update kernel (collide-stream, Eq. 4) since the last reset,
+ * measured with CUDA events on the context stream while LBMIB_OPT_TIMING is on:
+ * total milliseconds and launch count. reset != 0 clears the record. Synchronises. */
+lbmib_status lbmib_kernel_time(lbmib_ctx* ctx, double* total_ms, long long* launches,
+                               int reset);
+
+/* Number of kernels this context has launched (graph replays count their kernels). */
+long long lbmib_launch_count(const lbmib_ctx* ctx);
+
+/* Bytes the lattice-update kernel must move per lattice update: 18 populations of the
+ * storage type (9 read, 9 written). */
+double lbmib_bytes_per_update(const lbmib_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMIB_H */

@@ -1,0 +1,726 @@
+// C ABI of the LBM-IB library (declared in include/lbmib.h): context, arena layout,
+// step orchestration with CUDA-graph replay, read-back and checkpoints.
+//
+// One coupled step (Coclite et al., arXiv:1903.03356) is enqueued as
+//   Dynamic   (Section 2.3.2): force+spread (steps 1-3) | collide-stream (4-6) |
+//             forced-node patch | per-capsule update (7-8)
+//   Kinematic (Section 2.4):   force+spread (i-iii) | collide-stream (iv-vi) |
+//             forced-node patch | advance (vii-viii)
+// The collide-stream kernel applies only the uniform body force; the patch redoes the
+// collision of the few nodes in the support of a marker with the spread force, so the
+// hot loop stays at 18 population transfers per lattice update. Two force buffers
+// alternate: a step spreads into one while interpolation reads the last spread force
+// from the other; the patch of a step clears the older buffer at its touched cells.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbmib.h"
+#include "lbmib_kernels.cuh"
+
+using namespace lbmib;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxRing = 1024;
+
+inline size_t up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t storage_bytes(lbmib_storage s) { return s == LBMIB_FP64 ? 8 : (s == LBMIB_FP32 ? 4 : 2); }
+
+struct Layout {
+    size_t pops[2], fib[2], mark, list[2], ctr, scratch;
+    size_t X, Xm1, uv, Fint, Fext, L0, c0, s0, age, capid, caps, obs, pts, pts_out;
+    size_t total;
+    int pitch;
+    long long plane;
+};
+
+bool valid_config(const lbmib_config* c) {
+    return c && c->nx >= 3 && c->ny >= 3 && c->tau > 0.5 && c->max_capsules >= 0 && c->max_nodes >= 0 &&
+           (c->storage == LBMIB_FP64 || c->storage == LBMIB_FP32 || c->storage == LBMIB_FP16) &&
+           (long long)c->nx * c->ny < (1LL << 31) && c->max_nodes <= (1 << 26);
+}
+
+Layout make_layout(const lbmib_config* c) {
+    Layout L{};
+    const size_t s = storage_bytes(c->storage);
+    L.pitch = (int)up((size_t)c->nx, 128 / s);
+    L.plane = (long long)c->ny * L.pitch;
+    const size_t N = (size_t)c->nx * c->ny;
+    const size_t M = (size_t)(c->max_nodes > 0 ? c->max_nodes : 1);
+    const size_t K = (size_t)(c->max_capsules > 0 ? c->max_capsules : 1);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = up(o + bytes, kAlign); return r; };
+    L.pops[0] = take(9 * (size_t)L.plane * s);
+    L.pops[1] = take(9 * (size_t)L.plane * s);
+    L.fib[0] = take(2 * N * sizeof(double));
+    L.fib[1] = take(2 * N * sizeof(double));
+    L.mark = take(N * sizeof(int));
+    L.list[0] = take(9 * M * sizeof(int));
+    L.list[1] = take(9 * M * sizeof(int));
+    L.ctr = take(sizeof(DevCounters));
+    L.scratch = take(3 * N * sizeof(double));
+    L.X = take(M * sizeof(double2));
+    L.Xm1 = take(M * sizeof(double2));
+    L.uv = take(M * sizeof(double2));
+    L.Fint = take(M * sizeof(double2));
+    L.Fext = take(M * sizeof(double2));
+    L.L0 = take(M * sizeof(double));
+    L.c0 = take(M * sizeof(double));
+    L.s0 = take(M * sizeof(double));
+    L.age = take(M * sizeof(int));
+    L.capid = take(M * sizeof(int));
+    L.caps = take(K * sizeof(CapsuleParams));
+    L.obs = take(8 * K * sizeof(double));
+    L.pts = take(M * sizeof(double2));
+    L.pts_out = take(8 * M * sizeof(double));
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+struct lbmib_ctx {
+    lbmib_config cfg{};
+    Layout lay{};
+    Lat L{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    char* arena = nullptr;
+    void* pops[2]{};
+    double* fib[2]{};
+    int* mark = nullptr;
+    int* list[2]{};
+    DevCounters* ctr = nullptr;
+    double* scratch = nullptr;
+    Nodes nd{};
+    CapsuleParams* d_caps = nullptr;
+    double* obs = nullptr;
+    double2* pts = nullptr;
+    double* pts_out = nullptr;
+    std::vector<CapsuleParams> caps;
+    int max_n = 0;
+    int cur = 0;      // population buffer holding the latest post-collision state
+    int cur_fib = 0;  // force buffer holding the last spread force
+    long long steps = 0;
+    long long launches = 0;
+    // options
+    bool use_graphs = true;
+    bool timing = false;
+    int graph_steps = 16;
+    int lattice_variant = 256;
+    // graphs keyed by (scheme, cur, cur_fib)
+    cudaGraphExec_t graphs[2][2][2]{};
+    int graph_len[2][2][2]{};
+    // timing
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+    size_t ev_used = 0;
+    double timed_ms = 0.0;
+    long long timed_launches = 0;
+    std::string err;
+};
+
+namespace {
+
+lbmib_status fail(lbmib_ctx* c, lbmib_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+lbmib_status cuda_fail(lbmib_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, LBMIB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LBMIB_CUDA(ctx, call)                                      \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+void drop_graphs(lbmib_ctx* c) {
+    for (auto& a : c->graphs)
+        for (auto& b : a)
+            for (auto& g : b)
+                if (g) {
+                    cudaGraphExecDestroy(g);
+                    g = nullptr;
+                }
+}
+
+// Enqueue one coupled step on stream s, advancing (cur, cur_fib).
+void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cudaStream_t s, bool timed) {
+    const Lat& L = c->L;
+    const int ncaps = (int)c->caps.size();
+    const void* src = c->pops[cur];
+    void* dst = c->pops[1 - cur];
+    const int fc = 1 - cur_fib;  // buffer spread into this step
+    const int fp = cur_fib;      // last spread force
+    unsigned* status = &c->ctr->status;
+    const int list_cap = 9 * (c->cfg.max_nodes > 0 ? c->cfg.max_nodes : 1);
+    Spread sp{c->fib[fc], c->mark, c->list[fc], &c->ctr->count[fc], &c->ctr->step_stamp, list_cap, status};
+    const lbmib_storage st = c->cfg.storage;
+    if (ncaps > 0) {
+        if (scheme == LBMIB_DYNAMIC) {
+            if (st == LBMIB_FP64)
+                launch_dyn_force_spread<double>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, sp, status, s);
+            else if (st == LBMIB_FP32)
+                launch_dyn_force_spread<float>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, sp, status, s);
+            else
+                launch_dyn_force_spread<__half>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, sp, status, s);
+        } else {
+            launch_kin_force_spread(L, c->nd, ncaps, c->max_n, sp, status, st == LBMIB_FP64, s);
+        }
+        c->launches++;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timed) {
+        if (c->ev_used == c->ev_pool.size()) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            c->ev_pool.push_back({a, b});
+        }
+        e0 = c->ev_pool[c->ev_used].first;
+        e1 = c->ev_pool[c->ev_used].second;
+        c->ev_used++;
+        cudaEventRecord(e0, s);
+    }
+    if (st == LBMIB_FP64) launch_collide_stream<double>(src, dst, L, status, c->lattice_variant, s);
+    else if (st == LBMIB_FP32) launch_collide_stream<float>(src, dst, L, status, c->lattice_variant, s);
+    else launch_collide_stream<__half>(src, dst, L, status, c->lattice_variant, s);
+    c->launches++;
+    if (timed) cudaEventRecord(e1, s);
+    if (ncaps > 0) {
+        const int cap = list_cap;
+        if (st == LBMIB_FP64)
+            launch_patch<double>(src, dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->ctr, fc, cap, s);
+        else if (st == LBMIB_FP32)
+            launch_patch<float>(src, dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->ctr, fc, cap, s);
+        else
+            launch_patch<__half>(src, dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->ctr, fc, cap, s);
+        int* reset = &c->ctr->count[fp];
+        if (scheme == LBMIB_DYNAMIC) {
+            if (st == LBMIB_FP64) launch_dyn_update<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, reset, status, s);
+            else if (st == LBMIB_FP32) launch_dyn_update<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, reset, status, s);
+            else launch_dyn_update<__half>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, reset, status, s);
+        } else {
+            if (st == LBMIB_FP64) launch_kin_advance<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, reset, status, s);
+            else if (st == LBMIB_FP32) launch_kin_advance<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, reset, status, s);
+            else launch_kin_advance<__half>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, reset, status, s);
+        }
+        c->launches += 2;
+        cur_fib = fc;
+    }
+    cur = 1 - cur;
+}
+
+int kernels_per_step(const lbmib_ctx* c) { return c->caps.empty() ? 1 : 4; }
+
+lbmib_status capture(lbmib_ctx* c, lbmib_scheme scheme, int cur, int cur_fib, int len, cudaGraphExec_t* out) {
+    LBMIB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const long long launches = c->launches;
+    for (int k = 0; k < len; k++) enqueue_step(c, scheme, cur, cur_fib, c->cap_stream, false);
+    c->launches = launches;  // capture does not launch
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    return LBMIB_OK;
+}
+
+lbmib_status device_status(lbmib_ctx* c) {
+    LBMIB_CUDA(c, cudaStreamSynchronize(c->stream));
+    unsigned st = 0;
+    LBMIB_CUDA(c, cudaMemcpy(&st, &c->ctr->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (st & kStatUnstable) return fail(c, LBMIB_ERR_UNSTABLE, "unstable lattice: |u| > 0.3 or NaN");
+    if (st & kStatSupport) return fail(c, LBMIB_ERR_SUPPORT, "an MLS support or probe left the channel");
+    if (st & kStatTimeout) return fail(c, LBMIB_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (st & (kStatList | kStatCell | kStatRing))
+        return fail(c, LBMIB_ERR_STATE, "device bookkeeping check failed (status bits " + std::to_string(st) + ")");
+    return LBMIB_OK;
+}
+
+template <typename F>
+void by_storage(lbmib_storage st, F&& f) {
+    if (st == LBMIB_FP64) f(double{});
+    else if (st == LBMIB_FP32) f(float{});
+    else f(__half{});
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbmib_arena_bytes(const lbmib_config* cfg) {
+    if (!valid_config(cfg)) return 0;
+    return make_layout(cfg).total;
+}
+
+lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_bytes, void* cuda_stream,
+                          lbmib_ctx** out) {
+    if (!out) return LBMIB_ERR_ARG;
+    *out = nullptr;
+    if (!valid_config(cfg)) return LBMIB_ERR_ARG;
+    const Layout lay = make_layout(cfg);
+    if (!d_arena || ((uintptr_t)d_arena % kAlign) != 0) return LBMIB_ERR_ARG;
+    if (arena_bytes < lay.total) return LBMIB_ERR_OOM;
+    lbmib_ctx* c = new lbmib_ctx();
+    c->cfg = *cfg;
+    c->lay = lay;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->arena = (char*)d_arena;
+    char* a = c->arena;
+    c->pops[0] = a + lay.pops[0];
+    c->pops[1] = a + lay.pops[1];
+    c->fib[0] = (double*)(a + lay.fib[0]);
+    c->fib[1] = (double*)(a + lay.fib[1]);
+    c->mark = (int*)(a + lay.mark);
+    c->list[0] = (int*)(a + lay.list[0]);
+    c->list[1] = (int*)(a + lay.list[1]);
+    c->ctr = (DevCounters*)(a + lay.ctr);
+    c->scratch = (double*)(a + lay.scratch);
+    c->nd.X = (double2*)(a + lay.X);
+    c->nd.Xm1 = (double2*)(a + lay.Xm1);
+    c->nd.uv = (double2*)(a + lay.uv);
+    c->nd.Fint = (double2*)(a + lay.Fint);
+    c->nd.Fext = (double2*)(a + lay.Fext);
+    c->nd.L0 = (double*)(a + lay.L0);
+    c->nd.c0 = (double*)(a + lay.c0);
+    c->nd.s0 = (double*)(a + lay.s0);
+    c->nd.age = (int*)(a + lay.age);
+    c->nd.capid = (int*)(a + lay.capid);
+    c->d_caps = (CapsuleParams*)(a + lay.caps);
+    c->nd.caps = c->d_caps;
+    c->nd.count = 0;
+    c->obs = (double*)(a + lay.obs);
+    c->pts = (double2*)(a + lay.pts);
+    c->pts_out = (double*)(a + lay.pts_out);
+
+    Lat& L = c->L;
+    L.nx = cfg->nx;
+    L.ny = cfg->ny;
+    L.pitch = lay.pitch;
+    L.plane = lay.plane;
+    L.walls = cfg->walls ? 1 : 0;
+    L.tau = cfg->tau;
+    L.omega = 1.0 / cfg->tau;
+    L.ub = cfg->walls ? cfg->u_bottom : 0.0;
+    L.ut = cfg->walls ? cfg->u_top : 0.0;
+    L.gx = cfg->gx;
+    L.gy = cfg->gy;
+    L.scale = cfg->storage == LBMIB_FP16 ? 1024.0f : 1.0f;
+    L.inv_scale = 1.0f / L.scale;
+    L.nu = (cfg->tau - 0.5) / 3.0;
+
+    cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete c;
+        return LBMIB_ERR_CUDA;
+    }
+    set_capsule_smem_limits(kMaxRing);
+    const size_t N = (size_t)cfg->nx * cfg->ny;
+    e = cudaMemsetAsync(c->fib[0], 0, 2 * N * sizeof(double), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->fib[1], 0, 2 * N * sizeof(double), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->mark, 0, N * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(c->cap_stream);
+        delete c;
+        return LBMIB_ERR_CUDA;
+    }
+    by_storage(cfg->storage, [&](auto tag) {
+        using S = decltype(tag);
+        launch_init<S>(c->pops[0], c->L, nullptr, nullptr, nullptr, c->stream);
+    });
+    c->launches++;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(c->cap_stream);
+        delete c;
+        return LBMIB_ERR_CUDA;
+    }
+    *out = c;
+    return LBMIB_OK;
+}
+
+void lbmib_destroy(lbmib_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    for (auto& p : c->ev_pool) {
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+const char* lbmib_last_error(const lbmib_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+lbmib_status lbmib_init_fields(lbmib_ctx* c, const double* rho, const double* ux, const double* uy) {
+    if (!c) return LBMIB_ERR_ARG;
+    const size_t N = (size_t)c->cfg.nx * c->cfg.ny;
+    double* d[3] = {c->scratch, c->scratch + N, c->scratch + 2 * N};
+    const double* h[3] = {rho, ux, uy};
+    for (int k = 0; k < 3; k++)
+        if (h[k]) LBMIB_CUDA(c, cudaMemcpyAsync(d[k], h[k], N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    by_storage(c->cfg.storage, [&](auto tag) {
+        using S = decltype(tag);
+        launch_init<S>(c->pops[c->cur], c->L, rho ? d[0] : nullptr, ux ? d[1] : nullptr, uy ? d[2] : nullptr,
+                       c->stream);
+    });
+    c->launches++;
+    LBMIB_CUDA(c, cudaMemsetAsync(c->fib[0], 0, 2 * N * sizeof(double), c->stream));
+    LBMIB_CUDA(c, cudaMemsetAsync(c->fib[1], 0, 2 * N * sizeof(double), c->stream));
+    LBMIB_CUDA(c, cudaMemsetAsync(c->ctr->count, 0, sizeof(c->ctr->count), c->stream));
+    LBMIB_CUDA(c, cudaGetLastError());
+    LBMIB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBMIB_OK;
+}
+
+static void ring_reference(const double* xy, int n, std::vector<double>& L0, std::vector<double>& c0,
+                           std::vector<double>& s0, double& A0, double& P0) {
+    L0.resize(n);
+    c0.resize(n);
+    s0.resize(n);
+    double a2 = 0.0, per = 0.0;
+    for (int v = 0; v < n; v++) {
+        const int r = (v + 1) % n, l = (v + n - 1) % n;
+        const double dx = xy[2 * r] - xy[2 * v], dy = xy[2 * r + 1] - xy[2 * v + 1];
+        L0[v] = std::sqrt(dx * dx + dy * dy);
+        per += L0[v];
+        const double ax = xy[2 * v] - xy[2 * l], ay = xy[2 * v + 1] - xy[2 * l + 1];
+        const double nrm = std::sqrt((ax * ax + ay * ay) * (dx * dx + dy * dy));
+        c0[v] = (ax * dx + ay * dy) / nrm;  // cos(theta_0)
+        s0[v] = (ax * dy - ay * dx) / nrm;  // sin(theta_0)
+        a2 += (xy[2 * v] - xy[0]) * (xy[2 * r + 1] - xy[1]) - (xy[2 * r] - xy[0]) * (xy[2 * v + 1] - xy[1]);
+    }
+    A0 = 0.5 * a2;
+    P0 = per;
+}
+
+lbmib_status lbmib_add_capsule(lbmib_ctx* c, const double* xy, int n, double ks, double kb, double ka,
+                               double node_mass, int* id_out) {
+    if (!c) return LBMIB_ERR_ARG;
+    if (!xy || n < 3 || n > kMaxRing || !(node_mass > 0.0)) return fail(c, LBMIB_ERR_ARG, "bad capsule arguments");
+    if ((int)c->caps.size() >= c->cfg.max_capsules || c->nd.count + n > c->cfg.max_nodes)
+        return fail(c, LBMIB_ERR_OOM, "capsule capacity exceeded");
+    std::vector<double> L0, c0, s0;
+    double A0, P0;
+    ring_reference(xy, n, L0, c0, s0, A0, P0);
+    if (!(A0 > 0.0)) return fail(c, LBMIB_ERR_ARG, "capsule ring must be counter-clockwise");
+    CapsuleParams P{c->nd.count, n, ks, kb, ka, node_mass, A0, P0};
+    const int off = c->nd.count;
+    const int id = (int)c->caps.size();
+    std::vector<double2> zero(n, make_double2(0.0, 0.0));
+    std::vector<int> zi(n, 0), cid(n, id);
+    cudaStream_t s = c->stream;
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.X + off, xy, n * sizeof(double2), cudaMemcpyHostToDevice, s));
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.Xm1 + off, xy, n * sizeof(double2), cudaMemcpyHostToDevice, s));
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.uv + off, zero.data(), n * sizeof(double2), cudaMemcpyHostToDevice, s));
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.Fint + off, zero.data(), n * sizeof(double2), cudaMemcpyHostToDevice, s));
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.Fext + off, zero.data(), n * sizeof(double2), cudaMemcpyHostToDevice, s));
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.L0 + off, L0.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.c0 + off, c0.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.s0 + off, s0.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.age + off, zi.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.capid + off, cid.data(), n * sizeof(int), cudaMemcpyHostToDevice, s));
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->d_caps + id, &P, sizeof(P), cudaMemcpyHostToDevice, s));
+    LBMIB_CUDA(c, cudaStreamSynchronize(s));  // host staging vectors go out of scope
+    c->caps.push_back(P);
+    c->nd.count += n;
+    if (n > c->max_n) c->max_n = n;
+    drop_graphs(c);  // launch shapes changed
+    if (id_out) *id_out = id;
+    return LBMIB_OK;
+}
+
+lbmib_status lbmib_set_capsule_positions(lbmib_ctx* c, int id, const double* xy) {
+    if (!c || !xy || id < 0 || id >= (int)c->caps.size()) return LBMIB_ERR_ARG;
+    const CapsuleParams& P = c->caps[id];
+    std::vector<int> zi(P.n, 0);
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.X + P.off, xy, P.n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.Xm1 + P.off, xy, P.n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.age + P.off, zi.data(), P.n * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    LBMIB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBMIB_OK;
+}
+
+lbmib_status lbmib_step(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme) {
+    if (!c || nsteps < 0 || (scheme != LBMIB_KINEMATIC && scheme != LBMIB_DYNAMIC)) return LBMIB_ERR_ARG;
+    const int sc = scheme == LBMIB_DYNAMIC ? 1 : 0;
+    if (c->timing || !c->use_graphs) {
+        for (long long k = 0; k < nsteps; k++) enqueue_step(c, scheme, c->cur, c->cur_fib, c->stream, c->timing);
+    } else {
+        const int G = c->graph_steps > 0 ? c->graph_steps : 1;
+        long long left = nsteps;
+        while (left >= G) {
+            cudaGraphExec_t& g = c->graphs[sc][c->cur][c->cur_fib];
+            if (g && c->graph_len[sc][c->cur][c->cur_fib] != G) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+            if (!g) {
+                lbmib_status st = capture(c, scheme, c->cur, c->cur_fib, G, &g);
+                if (st != LBMIB_OK) return st;
+                c->graph_len[sc][c->cur][c->cur_fib] = G;
+            }
+            LBMIB_CUDA(c, cudaGraphLaunch(g, c->stream));
+            c->launches += (long long)G * kernels_per_step(c);
+            // advance the host copy of the buffer parities by G steps
+            for (int k = 0; k < G; k++) {
+                if (!c->caps.empty()) c->cur_fib = 1 - c->cur_fib;
+                c->cur = 1 - c->cur;
+            }
+            left -= G;
+        }
+        for (long long k = 0; k < left; k++) enqueue_step(c, scheme, c->cur, c->cur_fib, c->stream, false);
+    }
+    c->steps += nsteps;
+    LBMIB_CUDA(c, cudaGetLastError());
+    return LBMIB_OK;
+}
+
+lbmib_status lbmib_sync(lbmib_ctx* c) {
+    if (!c) return LBMIB_ERR_ARG;
+    return device_status(c);
+}
+
+lbmib_status lbmib_read_fields(lbmib_ctx* c, double* rho, double* ux, double* uy) {
+    if (!c) return LBMIB_ERR_ARG;
+    const size_t N = (size_t)c->cfg.nx * c->cfg.ny;
+    by_storage(c->cfg.storage, [&](auto tag) {
+        using S = decltype(tag);
+        launch_macros<S>(c->pops[c->cur], c->L, c->fib[c->cur_fib], c->scratch, c->scratch + N,
+                         c->scratch + 2 * N, c->stream);
+    });
+    c->launches++;
+    LBMIB_CUDA(c, cudaGetLastError());
+    double* h[3] = {rho, ux, uy};
+    for (int k = 0; k < 3; k++)
+        if (h[k])
+            LBMIB_CUDA(c, cudaMemcpyAsync(h[k], c->scratch + k * N, N * sizeof(double), cudaMemcpyDeviceToHost,
+                                          c->stream));
+    return device_status(c);
+}
+
+lbmib_status lbmib_read_populations(lbmib_ctx* c, double* f) {
+    if (!c || !f) return LBMIB_ERR_ARG;
+    const size_t N = (size_t)c->cfg.nx * c->cfg.ny;
+    for (int i0 = 0; i0 < 9; i0 += 3) {
+        by_storage(c->cfg.storage, [&](auto tag) {
+            using S = decltype(tag);
+            launch_populations<S>(c->pops[c->cur], c->L, i0, c->scratch, c->stream);
+        });
+        c->launches++;
+        LBMIB_CUDA(c, cudaGetLastError());
+        LBMIB_CUDA(c, cudaMemcpyAsync(f + i0 * N, c->scratch, 3 * N * sizeof(double), cudaMemcpyDeviceToHost,
+                                      c->stream));
+        LBMIB_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return device_status(c);
+}
+
+lbmib_status lbmib_read_force_field(lbmib_ctx* c, double* fx, double* fy) {
+    if (!c) return LBMIB_ERR_ARG;
+    const size_t N = (size_t)c->cfg.nx * c->cfg.ny;
+    if (fx) LBMIB_CUDA(c, cudaMemcpyAsync(fx, c->fib[c->cur_fib], N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (fy)
+        LBMIB_CUDA(c, cudaMemcpyAsync(fy, c->fib[c->cur_fib] + N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return device_status(c);
+}
+
+lbmib_status lbmib_read_capsule(lbmib_ctx* c, int id, double* xy, double* vel, double* fint, double* fext) {
+    if (!c || id < 0 || id >= (int)c->caps.size()) return LBMIB_ERR_ARG;
+    const CapsuleParams& P = c->caps[id];
+    const size_t b = P.n * sizeof(double2);
+    if (xy) LBMIB_CUDA(c, cudaMemcpyAsync(xy, c->nd.X + P.off, b, cudaMemcpyDeviceToHost, c->stream));
+    if (vel) LBMIB_CUDA(c, cudaMemcpyAsync(vel, c->nd.uv + P.off, b, cudaMemcpyDeviceToHost, c->stream));
+    if (fint) LBMIB_CUDA(c, cudaMemcpyAsync(fint, c->nd.Fint + P.off, b, cudaMemcpyDeviceToHost, c->stream));
+    if (fext) LBMIB_CUDA(c, cudaMemcpyAsync(fext, c->nd.Fext + P.off, b, cudaMemcpyDeviceToHost, c->stream));
+    return device_status(c);
+}
+
+lbmib_status lbmib_observables(lbmib_ctx* c, int id, double out[8]) {
+    if (!c || !out || id < 0 || id >= (int)c->caps.size()) return LBMIB_ERR_ARG;
+    launch_observables(c->nd, (int)c->caps.size(), c->max_n, c->obs, c->stream);
+    c->launches++;
+    LBMIB_CUDA(c, cudaGetLastError());
+    LBMIB_CUDA(c, cudaMemcpyAsync(out, c->obs + 8 * id, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return device_status(c);
+}
+
+lbmib_status lbmib_observables_all(lbmib_ctx* c, double* out) {
+    if (!c || !out) return LBMIB_ERR_ARG;
+    const int k = (int)c->caps.size();
+    if (k == 0) return LBMIB_OK;
+    launch_observables(c->nd, k, c->max_n, c->obs, c->stream);
+    c->launches++;
+    LBMIB_CUDA(c, cudaGetLastError());
+    LBMIB_CUDA(c, cudaMemcpyAsync(out, c->obs, 8 * (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return device_status(c);
+}
+
+lbmib_status lbmib_interpolate(lbmib_ctx* c, const double* xy, int n, double* out) {
+    if (!c || !xy || !out || n < 0 || n > c->cfg.max_nodes) return LBMIB_ERR_ARG;
+    if (n == 0) return LBMIB_OK;
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->pts, xy, n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    by_storage(c->cfg.storage, [&](auto tag) {
+        using S = decltype(tag);
+        launch_interp_points<S>(c->pops[c->cur], c->L, c->fib[c->cur_fib], c->pts, n, c->pts_out,
+                                &c->ctr->status, c->stream);
+    });
+    c->launches++;
+    LBMIB_CUDA(c, cudaGetLastError());
+    LBMIB_CUDA(c, cudaMemcpyAsync(out, c->pts_out, 8 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return device_status(c);
+}
+
+// Snapshot: header | populations (latest post-collision) | last spread force | its
+// touched-cell list | node arrays. Parities are normalised on load.
+struct SnapHeader {
+    char magic[8];
+    int nx, ny, storage, ncaps, nnodes, count;
+    long long steps;
+};
+
+size_t lbmib_state_bytes(const lbmib_ctx* c) {
+    if (!c) return 0;
+    const size_t N = (size_t)c->cfg.nx * c->cfg.ny;
+    const size_t M = (size_t)c->nd.count;
+    return sizeof(SnapHeader) + 9 * (size_t)c->L.plane * storage_bytes(c->cfg.storage) + 2 * N * sizeof(double) +
+           9 * (M > 0 ? M : 1) * sizeof(int) + M * (5 * sizeof(double2) + sizeof(int));
+}
+
+lbmib_status lbmib_save_state(lbmib_ctx* c, void* buf, size_t bytes) {
+    if (!c || !buf || bytes < lbmib_state_bytes(c)) return LBMIB_ERR_ARG;
+    LBMIB_CUDA(c, cudaStreamSynchronize(c->stream));
+    const size_t N = (size_t)c->cfg.nx * c->cfg.ny;
+    const size_t M = (size_t)c->nd.count;
+    SnapHeader h{};
+    memcpy(h.magic, "LBMIBv1", 8);
+    h.nx = c->cfg.nx;
+    h.ny = c->cfg.ny;
+    h.storage = c->cfg.storage;
+    h.ncaps = (int)c->caps.size();
+    h.nnodes = (int)M;
+    LBMIB_CUDA(c, cudaMemcpy(&h.count, &c->ctr->count[c->cur_fib], sizeof(int), cudaMemcpyDeviceToHost));
+    h.steps = c->steps;
+    char* p = (char*)buf;
+    memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    const size_t pb = 9 * (size_t)c->L.plane * storage_bytes(c->cfg.storage);
+    LBMIB_CUDA(c, cudaMemcpy(p, c->pops[c->cur], pb, cudaMemcpyDeviceToHost));
+    p += pb;
+    LBMIB_CUDA(c, cudaMemcpy(p, c->fib[c->cur_fib], 2 * N * sizeof(double), cudaMemcpyDeviceToHost));
+    p += 2 * N * sizeof(double);
+    const size_t lb = 9 * (M > 0 ? M : 1) * sizeof(int);
+    LBMIB_CUDA(c, cudaMemcpy(p, c->list[c->cur_fib], lb, cudaMemcpyDeviceToHost));
+    p += lb;
+    double2* arrs[5] = {c->nd.X, c->nd.Xm1, c->nd.uv, c->nd.Fint, c->nd.Fext};
+    for (auto* a : arrs) {
+        LBMIB_CUDA(c, cudaMemcpy(p, a, M * sizeof(double2), cudaMemcpyDeviceToHost));
+        p += M * sizeof(double2);
+    }
+    LBMIB_CUDA(c, cudaMemcpy(p, c->nd.age, M * sizeof(int), cudaMemcpyDeviceToHost));
+    return device_status(c);
+}
+
+lbmib_status lbmib_load_state(lbmib_ctx* c, const void* buf, size_t bytes) {
+    if (!c || !buf || bytes < sizeof(SnapHeader)) return LBMIB_ERR_ARG;
+    SnapHeader h;
+    memcpy(&h, buf, sizeof(h));
+    const size_t N = (size_t)c->cfg.nx * c->cfg.ny;
+    const size_t M = (size_t)c->nd.count;
+    if (memcmp(h.magic, "LBMIBv1", 8) != 0 || h.nx != c->cfg.nx || h.ny != c->cfg.ny ||
+        h.storage != (int)c->cfg.storage || h.ncaps != (int)c->caps.size() || h.nnodes != (int)M ||
+        bytes < lbmib_state_bytes(c))
+        return fail(c, LBMIB_ERR_STATE, "snapshot does not match this context");
+    LBMIB_CUDA(c, cudaStreamSynchronize(c->stream));
+    const char* p = (const char*)buf + sizeof(h);
+    c->cur = 0;
+    c->cur_fib = 0;
+    const size_t pb = 9 * (size_t)c->L.plane * storage_bytes(c->cfg.storage);
+    LBMIB_CUDA(c, cudaMemcpy(c->pops[0], p, pb, cudaMemcpyHostToDevice));
+    p += pb;
+    LBMIB_CUDA(c, cudaMemset(c->fib[1], 0, 2 * N * sizeof(double)));
+    LBMIB_CUDA(c, cudaMemcpy(c->fib[0], p, 2 * N * sizeof(double), cudaMemcpyHostToDevice));
+    p += 2 * N * sizeof(double);
+    const size_t lb = 9 * (M > 0 ? M : 1) * sizeof(int);
+    LBMIB_CUDA(c, cudaMemcpy(c->list[0], p, lb, cudaMemcpyHostToDevice));
+    p += lb;
+    double2* arrs[5] = {c->nd.X, c->nd.Xm1, c->nd.uv, c->nd.Fint, c->nd.Fext};
+    for (auto* a : arrs) {
+        LBMIB_CUDA(c, cudaMemcpy(a, p, M * sizeof(double2), cudaMemcpyHostToDevice));
+        p += M * sizeof(double2);
+    }
+    LBMIB_CUDA(c, cudaMemcpy(c->nd.age, p, M * sizeof(int), cudaMemcpyHostToDevice));
+    // fresh stamps: no cell carries a stamp that a coming step will use
+    LBMIB_CUDA(c, cudaMemset(c->mark, 0, N * sizeof(int)));
+    DevCounters ctr{};
+    ctr.count[0] = h.count;
+    LBMIB_CUDA(c, cudaMemcpy(c->ctr, &ctr, sizeof(ctr), cudaMemcpyHostToDevice));
+    c->steps = h.steps;
+    drop_graphs(c);
+    return LBMIB_OK;
+}
+
+lbmib_status lbmib_set_option(lbmib_ctx* c, int option, long long value) {
+    if (!c) return LBMIB_ERR_ARG;
+    switch (option) {
+        case LBMIB_OPT_GRAPHS: c->use_graphs = value != 0; break;
+        case LBMIB_OPT_TIMING: c->timing = value != 0; break;
+        case LBMIB_OPT_GRAPH_STEPS:
+            if (value < 1 || value > 4096) return fail(c, LBMIB_ERR_ARG, "graph steps out of range");
+            c->graph_steps = (int)value;
+            drop_graphs(c);
+            break;
+        case LBMIB_OPT_FP16_SCALE:
+            if (value < 0 || value > 14) return fail(c, LBMIB_ERR_ARG, "FP16 scale exponent out of range");
+            if (c->cfg.storage == LBMIB_FP16) {
+                c->L.scale = (float)std::ldexp(1.0, (int)value);
+                c->L.inv_scale = 1.0f / c->L.scale;
+                drop_graphs(c);
+            }
+            break;
+        case LBMIB_OPT_LATTICE_VARIANT:
+            c->lattice_variant = (int)value;
+            drop_graphs(c);
+            break;
+        default: return fail(c, LBMIB_ERR_ARG, "unknown option");
+    }
+    return LBMIB_OK;
+}
+
+lbmib_status lbmib_kernel_time(lbmib_ctx* c, double* total_ms, long long* launches, int reset) {
+    if (!c) return LBMIB_ERR_ARG;
+    LBMIB_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (size_t k = 0; k < c->ev_used; k++) {
+        float ms = 0.0f;
+        LBMIB_CUDA(c, cudaEventElapsedTime(&ms, c->ev_pool[k].first, c->ev_pool[k].second));
+        c->timed_ms += ms;
+        c->timed_launches++;
+    }
+    c->ev_used = 0;
+    if (total_ms) *total_ms = c->timed_ms;
+    if (launches) *launches = c->timed_launches;
+    if (reset) {
+        c->timed_ms = 0.0;
+        c->timed_launches = 0;
+    }
+    return LBMIB_OK;
+}
+
+long long lbmib_launch_count(const lbmib_ctx* c) { return c ? c->launches : 0; }
+
+double lbmib_bytes_per_update(const lbmib_ctx* c) {
+    return c ? 18.0 * (double)storage_bytes(c->cfg.storage) : 0.0;
+}
+
+}  // extern "C"

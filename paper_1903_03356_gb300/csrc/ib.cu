@@ -1,0 +1,617 @@
+// Immersed-boundary kernels: MLS interpolation and spreading (Eq. 8-9, Section 2.3
+// step 3, Section 2.4 step iii), membrane forces (Eq. 10-14), hydrodynamic tractions
+// (Eq. 15-16), and the node updates of the Dynamic (Eq. 21-24) and Kinematic (Eq. 25)
+// schemes. Coclite et al., arXiv:1903.03356.
+//
+// Every kernel here runs one CTA per capsule. The CTA stages its ring in shared memory,
+// takes the bounding box of the ring (plus the reach of the supports, and of the
+// probes when it needs them) and fills a shared tile with the lattice moments of every
+// node in the box once (nine pulls per node). Node and probe interpolations then read
+// that tile instead of re-gathering 81 populations each, and the spread accumulates
+// into a shared force tile that is flushed once per touched node (one global atomic
+// per node instead of one per marker and support point). A capsule whose box does not
+// fit the tile budget takes the same path with global pulls and global atomics.
+// Positions, velocities, forces, reference lengths and the MLS reciprocals are double
+// in every storage mode; in FP32/FP16 modes the weights and weighted sums are float.
+#include "lbmib_kernels.cuh"
+
+namespace lbmib {
+
+// Shared-memory view of one capsule (sized by the largest ring of the launch).
+struct CapSmem {
+    double2* X;     // vertex positions
+    double2* ext;   // external force of element v (v -> v+1), Eq. 15-16
+    double2* xd;    // interpolated velocity at vertex v
+    double* sst;    // stretch factor of element v: -k_s (l - l_0) / l  (Eq. 11)
+    double* bs;     // k_b sin(theta_v - theta_v0) at vertex v            (Eq. 13)
+    double2* bdl;   // d(theta_v)/dX_{v-1}
+    double2* bdr;   // d(theta_v)/dX_{v+1}
+    double* red;    // reduction scratch (32 * 8 doubles)
+    unsigned char* tile;  // moment / force tile
+};
+
+static size_t ring_smem_bytes(int max_n) {
+    return (size_t)max_n * (5 * sizeof(double2) + 2 * sizeof(double)) + 32 * 8 * sizeof(double);
+}
+
+size_t capsule_smem_bytes(int max_n) { return ring_smem_bytes(max_n); }
+
+__device__ __forceinline__ CapSmem carve(unsigned char* base, int max_n) {
+    CapSmem s;
+    s.X = reinterpret_cast<double2*>(base);
+    s.ext = s.X + max_n;
+    s.xd = s.ext + max_n;
+    s.bdl = s.xd + max_n;
+    s.bdr = s.bdl + max_n;
+    s.sst = reinterpret_cast<double*>(s.bdr + max_n);
+    s.bs = s.sst + max_n;
+    s.red = s.bs + max_n;
+    s.tile = reinterpret_cast<unsigned char*>(s.red + 32 * 8);
+    return s;
+}
+
+// Reduction of K doubles over the block (blockDim.x a multiple of 32, <= 1024); MIN
+// selects minimum instead of sum. Every thread receives the results.
+template <int K, bool MIN>
+__device__ void block_reduce(double (&v)[K], double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++)
+        for (int o = 16; o > 0; o >>= 1) {
+            const double t = __shfl_xor_sync(0xffffffffu, v[k], o);
+            v[k] = MIN ? fmin(v[k], t) : v[k] + t;
+        }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; k++) red[warp * K + k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        double t = red[k];
+        for (int w = 1; w < nw; w++) t = MIN ? fmin(t, red[w * K + k]) : t + red[w * K + k];
+        v[k] = t;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+
+// ---------------------------------------------------------------------------------
+// Capsule tile: lattice moments (and, for the spread, force accumulators) of every node
+// in the bounding box of the ring widened by `margin` nodes.
+// ---------------------------------------------------------------------------------
+template <typename C>
+struct Tile {
+    int x0, y0, w, h;   // origin (unwrapped lattice coordinates) and extent
+    bool use;           // the box fits the tile budget
+    C* drho;
+    C* ux;
+    C* uy;
+    double* fx;
+    double* fy;
+
+    __device__ __forceinline__ int index(int x, int y) const { return (y - y0) * w + (x - x0); }
+    // the 3x3 support centred on (cx, cy) lies inside the tile
+    __device__ __forceinline__ bool holds(int cx, int cy) const {
+        return use && cx - 1 >= x0 && cx + 1 < x0 + w && cy - 1 >= y0 && cy + 1 < y0 + h;
+    }
+};
+
+// Bounding box of the staged ring and the tile layout. Collective (all threads).
+template <typename C>
+__device__ Tile<C> make_tile(const CapSmem& sm, int n, int margin, int tile_cells, bool moments, bool forces) {
+    double r[4] = {1e300, 1e300, 1e300, 1e300};  // min x, min y, -max x, -max y
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const double2 X = sm.X[v];
+        r[0] = fmin(r[0], X.x);
+        r[1] = fmin(r[1], X.y);
+        r[2] = fmin(r[2], -X.x);
+        r[3] = fmin(r[3], -X.y);
+    }
+    block_reduce<4, true>(r, sm.red);
+    Tile<C> t;
+    const bool sane = fabs(r[0]) < 1e9 && fabs(r[1]) < 1e9 && fabs(r[2]) < 1e9 && fabs(r[3]) < 1e9;
+    t.x0 = sane ? (int)floor(r[0]) - margin : 0;
+    t.y0 = sane ? (int)floor(r[1]) - margin : 0;
+    const long long w = sane ? (long long)floor(-r[2]) + 1 + margin - t.x0 + 1 : 1LL << 30;
+    const long long h = sane ? (long long)floor(-r[3]) + 1 + margin - t.y0 + 1 : 1LL << 30;
+    t.use = sane && w * h <= tile_cells;
+    t.w = t.use ? (int)w : 0;
+    t.h = t.use ? (int)h : 0;
+    unsigned char* p = sm.tile;
+    t.drho = t.ux = t.uy = nullptr;
+    t.fx = t.fy = nullptr;
+    if (forces) {
+        t.fx = reinterpret_cast<double*>(p);
+        t.fy = t.fx + tile_cells;
+        p += 2 * sizeof(double) * (size_t)tile_cells;
+    }
+    if (moments) {
+        t.drho = reinterpret_cast<C*>(p);
+        t.ux = t.drho + tile_cells;
+        t.uy = t.ux + tile_cells;
+    }
+    return t;
+}
+
+// Fill the moment tile from the populations (nine pulls per node, row by row).
+template <typename S>
+__device__ void fill_moments(Tile<typename St<S>::C>& t, const S* __restrict__ src, const Lat& L,
+                             const double* __restrict__ fib) {
+    using C = typename St<S>::C;
+    const int cells = t.w * t.h;
+    for (int k = threadIdx.x; k < cells; k += blockDim.x) {
+        const int j = k / t.w, i = k - j * t.w;
+        const Mom<C> m = node_moments<S>(src, L, fib, wrapi(t.x0 + i, L.nx), support_row(L, t.y0 + j));
+        t.drho[k] = m.drho;
+        t.ux[k] = m.ux;
+        t.uy[k] = m.uy;
+    }
+}
+
+template <typename C>
+__device__ void zero_forces(Tile<C>& t) {
+    const int cells = t.w * t.h;
+    for (int k = threadIdx.x; k < cells; k += blockDim.x) {
+        t.fx[k] = 0.0;
+        t.fy[k] = 0.0;
+    }
+}
+
+__device__ __forceinline__ void touch(const Spread& sp, int cell, int stamp) {
+    if (atomicExch(&sp.mark[cell], stamp) != stamp) {
+        const int p = atomicAdd(sp.count, 1);
+        if (p < sp.capacity) sp.list[p] = cell;
+        else atomicOr(sp.status, kStatList);
+    }
+}
+
+// Add the force tile to the lattice force field and record the touched nodes.
+template <typename C>
+__device__ void flush_forces(const Tile<C>& t, const Lat& L, const Spread& sp, int stamp) {
+    const long long N = (long long)L.nx * L.ny;
+    const int cells = t.w * t.h;
+    for (int k = threadIdx.x; k < cells; k += blockDim.x) {
+        const double fx = t.fx[k], fy = t.fy[k];
+        if (fx == 0.0 && fy == 0.0) continue;
+        const int j = k / t.w, i = k - j * t.w;
+        const int cell = support_row(L, t.y0 + j) * L.nx + wrapi(t.x0 + i, L.nx);
+        atomicAdd(sp.fib + cell, fx);
+        atomicAdd(sp.fib + N + cell, fy);
+        touch(sp, cell, stamp);
+    }
+}
+
+// Interpolation (Eq. 8) at (X, Y) from the tile, or from the populations when the
+// capsule has no tile.
+template <typename S, bool GRAD>
+__device__ __forceinline__ bool interp_at(const Tile<typename St<S>::C>& t, const S* __restrict__ src, const Lat& L,
+                                          const double* __restrict__ fib, double X, double Y, Interp& o) {
+    using C = typename St<S>::C;
+    if (!t.use) return mls_interp<S, GRAD>(src, L, fib, X, Y, o);
+    const MlsW<C> m = mls_setup<C>(L, X, Y);
+    if (!t.holds(m.cx, m.cy)) {
+        // only a runaway point (already moved to the origin) can leave the box: flag it
+        mls_interp<S, GRAD>(src, L, fib, X, Y, o);
+        return false;
+    }
+    mls_apply<C, GRAD>(m, [&](int a, int b) {
+        const int k = t.index(m.cx + a - 1, m.cy + b - 1);
+        Mom<C> q;
+        q.drho = t.drho[k];
+        q.ux = t.ux[k];
+        q.uy = t.uy[k];
+        return q;
+    }, o);
+    return m.ok;
+}
+
+// Spread c * F at (X, Y) (step 3 / step iii): into the force tile, or straight into the
+// lattice field when the capsule has no tile.
+template <typename C>
+__device__ __forceinline__ bool spread_at(Tile<C>& t, const Lat& L, const Spread& sp, int stamp, double X, double Y,
+                                          double Fx, double Fy, double c) {
+    const MlsW<C> m = mls_setup<C>(L, X, Y);
+    const long long N = (long long)L.nx * L.ny;
+    const bool in_tile = t.holds(m.cx, m.cy);
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const double w = c * m.phi(a, b);
+            if (in_tile) {
+                const int k = t.index(m.cx + a - 1, m.cy + b - 1);
+                atomicAdd(t.fx + k, w * Fx);
+                atomicAdd(t.fy + k, w * Fy);
+            } else {
+                const int cell = support_row(L, m.cy + b - 1) * L.nx + wrapi(m.cx + a - 1, L.nx);
+                atomicAdd(sp.fib + cell, w * Fx);
+                atomicAdd(sp.fib + N + cell, w * Fy);
+                touch(sp, cell, stamp);
+            }
+        }
+    }
+    return m.ok && (in_tile || !t.use);
+}
+
+// Per-element stretch factor and per-vertex bending terms of vertex/element v, and
+// this vertex's contribution to twice the enclosed area (Green's theorem, about X_0).
+__device__ __forceinline__ double ring_terms(const CapSmem& sm, const CapsuleParams& P, const Nodes& nd, int v) {
+    const int n = P.n;
+    const double2 Xv = sm.X[v], Xr = sm.X[v + 1 == n ? 0 : v + 1], Xl = sm.X[v == 0 ? n - 1 : v - 1];
+    // Eq. 11: element v joins v and v+1
+    const double2 d = Xr - Xv;
+    const double len = sqrt(d.x * d.x + d.y * d.y);
+    sm.sst[v] = -P.ks * (len - nd.L0[P.off + v]) / len;
+    // Eq. 13 as F = -k_b sin(theta - theta_0) d(theta)/dX with theta the signed turning
+    // angle at v; sin(theta - theta_0) from the cross and dot products and theta_0's
+    // stored cosine and sine.
+    const double2 a = Xv - Xl, b = d;
+    const double a2 = a.x * a.x + a.y * a.y, b2 = b.x * b.x + b.y * b.y;
+    const double cr = a.x * b.y - a.y * b.x, dt = a.x * b.x + a.y * b.y;
+    const double rn = 1.0 / sqrt(a2 * b2);
+    const double sdiff = (cr * nd.c0[P.off + v] - dt * nd.s0[P.off + v]) * rn;
+    sm.bs[v] = P.kb * sdiff;
+    sm.bdl[v] = make_double2(-a.y / a2, a.x / a2);
+    sm.bdr[v] = make_double2(-b.y / b2, b.x / b2);
+    const double2 X0 = sm.X[0];
+    return (Xv.x - X0.x) * (Xr.y - X0.y) - (Xr.x - X0.x) * (Xv.y - X0.y);
+}
+
+// Internal force on vertex v (Eq. 22: stretch + bending + area) from the staged terms.
+__device__ __forceinline__ double2 node_internal_force(const CapSmem& sm, const CapsuleParams& P, int v, double A) {
+    const int n = P.n;
+    const int vl = v == 0 ? n - 1 : v - 1, vr = v + 1 == n ? 0 : v + 1;
+    const double2 Xv = sm.X[v], Xl = sm.X[vl], Xr = sm.X[vr];
+    double2 F = sm.sst[v] * (Xv - Xr);           // element v, this vertex first
+    F = F + (-sm.sst[vl]) * (Xl - Xv);           // element v-1, this vertex second
+    F = F + sm.bs[v] * (sm.bdl[v] + sm.bdr[v]);  // own bending angle
+    F = F + (-sm.bs[vr]) * sm.bdl[vr];           // as left neighbour of v+1
+    F = F + (-sm.bs[vl]) * sm.bdr[vl];           // as right neighbour of v-1
+    // Eq. 14: F^a_l = k_a (1 - A/A0) p_ref (dy, -dx) for element l, half to each end
+    const double fa = P.ka * (1.0 - A / P.A0) * (1.0 / 3.0) * 0.5;
+    const double2 dr = Xr - Xv, dl = Xv - Xl;
+    F.x += fa * (dr.y + dl.y);
+    F.y -= fa * (dr.x + dl.x);
+    return F;
+}
+
+// Load the CTA's capsule; false (after flagging) when its parameters are out of range.
+__device__ __forceinline__ bool load_ring(const Nodes& nd, const CapSmem& sm, int max_n, CapsuleParams& P,
+                                          unsigned* status) {
+    P = nd.caps[blockIdx.x];
+    if (P.n < 3 || P.n > max_n || P.off < 0 || P.off + P.n > nd.count) {
+        if (threadIdx.x == 0) atomicOr(status, kStatRing);
+        return false;
+    }
+    for (int v = threadIdx.x; v < P.n; v += blockDim.x) sm.X[v] = nd.X[P.off + v];
+    __syncthreads();
+    return true;
+}
+
+// ---------------------------------------------------------------------------------
+// Dynamic IB (Section 2.3.2), steps 1-3: U = I(u^n) with half of the last spread
+// force, F_l = u_v - U, spread with c_l = (l_left + l_right)/2. First step of a vertex:
+// u_v = U and X^{-1} = X^0 - U.
+// ---------------------------------------------------------------------------------
+template <typename S>
+__global__ void __launch_bounds__(128) k_dyn_force_spread(const S* __restrict__ src, Lat L,
+                                                          const double* __restrict__ fib_prev, Nodes nd, int max_n,
+                                                          int tile_cells, Spread sp, unsigned* status) {
+    using C = typename St<S>::C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CapSmem sm = carve(smem, max_n);
+    CapsuleParams P;
+    if (!load_ring(nd, sm, max_n, P, status)) return;
+    const int n = P.n, off = P.off;
+    Tile<C> t = make_tile<C>(sm, n, 1, tile_cells, true, true);
+    if (t.use) {
+        fill_moments<S>(t, src, L, fib_prev);
+        zero_forces<C>(t);
+    }
+    __syncthreads();
+    const int stamp = *sp.stamp + 1;
+    bool ok = true;
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const double2 Xv = sm.X[v];
+        const double2 Xl = sm.X[v == 0 ? n - 1 : v - 1], Xr = sm.X[v + 1 == n ? 0 : v + 1];
+        Interp o;
+        ok &= interp_at<S, false>(t, src, L, fib_prev, Xv.x, Xv.y, o);
+        double2 uv = nd.uv[off + v];
+        if (nd.age[off + v] == 0) {
+            uv = make_double2(o.ux, o.uy);
+            nd.uv[off + v] = uv;
+            nd.Xm1[off + v] = Xv - uv;
+        }
+        const double2 dl = Xv - Xl, dr = Xr - Xv;
+        const double cl = 0.5 * (sqrt(dl.x * dl.x + dl.y * dl.y) + sqrt(dr.x * dr.x + dr.y * dr.y));
+        ok &= spread_at<C>(t, L, sp, stamp, Xv.x, Xv.y, uv.x - o.ux, uv.y - o.uy, cl);
+    }
+    __syncthreads();
+    if (t.use) flush_forces<C>(t, L, sp, stamp);
+    if (!ok) atomicOr(status, kStatSupport);
+}
+
+// Dynamic IB steps 5-8 for one capsule per CTA: xdot_0 = I(u^{n+1}) at X^n, probe
+// tractions (Eq. 15-16), internal forces (Eq. 11, 13, 14), Verlet position (Eq. 23) and
+// BDF2 velocity (Eq. 24).
+template <typename S>
+__global__ void __launch_bounds__(128) k_dyn_update(const S* __restrict__ dst, Lat L,
+                                                    const double* __restrict__ fib, Nodes nd, int max_n,
+                                                    int tile_cells, int* reset_count, unsigned* status) {
+    using C = typename St<S>::C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CapSmem sm = carve(smem, max_n);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && reset_count) *reset_count = 0;
+    CapsuleParams P;
+    if (!load_ring(nd, sm, max_n, P, status)) return;
+    const int n = P.n, off = P.off;
+    Tile<C> t = make_tile<C>(sm, n, 3, tile_cells, true, false);
+    if (t.use) fill_moments<S>(t, dst, L, fib);
+    __syncthreads();
+    bool ok = true;
+    double area2[1] = {0.0};
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const double2 Xv = sm.X[v], Xr = sm.X[v + 1 == n ? 0 : v + 1];
+        Interp o;
+        ok &= interp_at<S, false>(t, dst, L, fib, Xv.x, Xv.y, o);
+        sm.xd[v] = make_double2(o.ux, o.uy);
+        // element v: probes at the centroid +/- 1.2 n+ (Section 2.2.2)
+        const double2 d = Xr - Xv;
+        const double len = sqrt(d.x * d.x + d.y * d.y);
+        const double npx = d.y / len, npy = -d.x / len;
+        const double cx = 0.5 * (Xv.x + Xr.x), cy = 0.5 * (Xv.y + Xr.y);
+        Interp op, om;
+        ok &= interp_at<S, true>(t, dst, L, fib, cx + 1.2 * npx, cy + 1.2 * npy, op);
+        ok &= interp_at<S, true>(t, dst, L, fib, cx - 1.2 * npx, cy - 1.2 * npy, om);
+        // tau = rho nu (grad u + grad u^T) at each probe; Eq. 15 + Eq. 16
+        const double mp = op.rho * L.nu, mm = om.rho * L.nu;
+        const double txx = 2.0 * (mp * op.dudx - mm * om.dudx);
+        const double tyy = 2.0 * (mp * op.dvdy - mm * om.dvdy);
+        const double txy = mp * (op.dudy + op.dvdx) - mm * (om.dudy + om.dvdx);
+        const double dp = op.p - om.p;
+        sm.ext[v] = make_double2((-dp * npx + txx * npx + txy * npy) * len,
+                                 (-dp * npy + txy * npx + tyy * npy) * len);
+        area2[0] += ring_terms(sm, P, nd, v);
+    }
+    block_reduce<1, false>(area2, sm.red);
+    const double A = 0.5 * area2[0];
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const int vl = v == 0 ? n - 1 : v - 1;
+        const double2 Fi = node_internal_force(sm, P, v, A);
+        const double2 Fe = 0.5 * (sm.ext[v] + sm.ext[vl]);
+        const double2 Xv = sm.X[v];
+        const double2 Xm = nd.Xm1[off + v];
+        const double2 xd = sm.xd[v];
+        const double hm = 0.5 / P.m;
+        const double2 Xn = make_double2(Xv.x + xd.x + hm * (Fi.x + Fe.x), Xv.y + xd.y + hm * (Fi.y + Fe.y));
+        nd.uv[off + v] = make_double2(1.5 * Xn.x - 2.0 * Xv.x + 0.5 * Xm.x, 1.5 * Xn.y - 2.0 * Xv.y + 0.5 * Xm.y);
+        nd.Xm1[off + v] = Xv;
+        nd.X[off + v] = Xn;
+        nd.Fint[off + v] = Fi;
+        nd.Fext[off + v] = Fe;
+        nd.age[off + v] += 1;
+    }
+    if (!ok) atomicOr(status, kStatSupport);
+}
+
+// ---------------------------------------------------------------------------------
+// Kinematic IB (Section 2.4), steps i-iii: internal forces at X^n (Eq. 11, 13, 14) and
+// their spread with c_v = 1.
+// ---------------------------------------------------------------------------------
+template <typename C>
+__global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int max_n, int tile_cells, Spread sp,
+                                                          unsigned* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CapSmem sm = carve(smem, max_n);
+    CapsuleParams P;
+    if (!load_ring(nd, sm, max_n, P, status)) return;
+    const int n = P.n, off = P.off;
+    Tile<C> t = make_tile<C>(sm, n, 1, tile_cells, false, true);
+    if (t.use) zero_forces<C>(t);
+    double area2[1] = {0.0};
+    for (int v = threadIdx.x; v < n; v += blockDim.x) area2[0] += ring_terms(sm, P, nd, v);
+    block_reduce<1, false>(area2, sm.red);  // also orders the tile zeroing before the spread
+    const double A = 0.5 * area2[0];
+    const int stamp = *sp.stamp + 1;
+    bool ok = true;
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const double2 F = node_internal_force(sm, P, v, A);
+        nd.Fint[off + v] = F;
+        nd.Fext[off + v] = make_double2(0.0, 0.0);
+        ok &= spread_at<C>(t, L, sp, stamp, sm.X[v].x, sm.X[v].y, F.x, F.y, 1.0);
+    }
+    __syncthreads();
+    if (t.use) flush_forces<C>(t, L, sp, stamp);
+    if (!ok) atomicOr(status, kStatSupport);
+}
+
+// Kinematic IB steps vii-viii: xdot = I(u^{n+1}) at X^n with half the spread force,
+// X^{n+1} = 2/3 (2 X^n - X^{n-1}/2 + xdot) (Eq. 25); forward Euler on a first step.
+template <typename S>
+__global__ void __launch_bounds__(128) k_kin_advance(const S* __restrict__ dst, Lat L,
+                                                     const double* __restrict__ fib, Nodes nd, int max_n,
+                                                     int tile_cells, int* reset_count, unsigned* status) {
+    using C = typename St<S>::C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CapSmem sm = carve(smem, max_n);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && reset_count) *reset_count = 0;
+    CapsuleParams P;
+    if (!load_ring(nd, sm, max_n, P, status)) return;
+    const int n = P.n, off = P.off;
+    Tile<C> t = make_tile<C>(sm, n, 1, tile_cells, true, false);
+    if (t.use) fill_moments<S>(t, dst, L, fib);
+    __syncthreads();
+    bool ok = true;
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const double2 Xv = sm.X[v];
+        Interp o;
+        ok &= interp_at<S, false>(t, dst, L, fib, Xv.x, Xv.y, o);
+        double2 Xn;
+        if (nd.age[off + v] == 0) {
+            Xn = make_double2(Xv.x + o.ux, Xv.y + o.uy);
+        } else {
+            const double2 Xm = nd.Xm1[off + v];
+            Xn = make_double2((2.0 / 3.0) * (2.0 * Xv.x - 0.5 * Xm.x + o.ux),
+                              (2.0 / 3.0) * (2.0 * Xv.y - 0.5 * Xm.y + o.uy));
+        }
+        nd.Xm1[off + v] = Xv;
+        nd.X[off + v] = Xn;
+        nd.uv[off + v] = make_double2(o.ux, o.uy);
+        nd.age[off + v] += 1;
+    }
+    if (!ok) atomicOr(status, kStatSupport);
+}
+
+// Observables of every capsule (Section 3.1-3.2): area, perimeter, Taylor D, centroid,
+// swelling ratio, inclination, relative perimeter change.
+__global__ void __launch_bounds__(128) k_observables(Nodes nd, int max_n, double* out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CapSmem sm = carve(smem, max_n);
+    const CapsuleParams P = nd.caps[blockIdx.x];
+    const int n = P.n, off = P.off;
+    if (n < 3 || off < 0 || off + n > nd.count) return;
+    const double2 X0 = nd.X[off];
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};  // 2A, sx, sy, sxx, syy, sxy, perimeter
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double2 a = nd.X[off + i] - X0, b = nd.X[off + (i + 1 == n ? 0 : i + 1)] - X0;
+        const double c = a.x * b.y - b.x * a.y;
+        s[0] += c;
+        s[1] += (a.x + b.x) * c;
+        s[2] += (a.y + b.y) * c;
+        s[3] += (a.x * a.x + a.x * b.x + b.x * b.x) * c;
+        s[4] += (a.y * a.y + a.y * b.y + b.y * b.y) * c;
+        s[5] += (a.x * b.y + 2.0 * a.x * a.y + 2.0 * b.x * b.y + b.x * a.y) * c;
+        s[6] += sqrt((b.x - a.x) * (b.x - a.x) + (b.y - a.y) * (b.y - a.y));
+    }
+    block_reduce<7, false>(s, sm.red);
+    if (threadIdx.x == 0) {
+        const double A = 0.5 * s[0];
+        const double cx = s[1] / (6.0 * A), cy = s[2] / (6.0 * A);
+        const double Ixx = s[3] / 12.0 - A * cx * cx;
+        const double Iyy = s[4] / 12.0 - A * cy * cy;
+        const double Ixy = s[5] / 24.0 - A * cx * cy;
+        const double mid = 0.5 * (Ixx + Iyy);
+        const double dd = sqrt(0.25 * (Ixx - Iyy) * (Ixx - Iyy) + Ixy * Ixy);
+        const double lmax = (mid + dd) / A, lmin = (mid - dd) / A;
+        const double a = 2.0 * sqrt(lmax), b = 2.0 * sqrt(lmin > 0.0 ? lmin : 0.0);
+        const double Pm = s[6];
+        double* o = out + 8 * blockIdx.x;
+        o[0] = A;
+        o[1] = Pm;
+        o[2] = (a - b) / (a + b);
+        o[3] = cx + X0.x;
+        o[4] = cy + X0.y;
+        o[5] = A / (Pm * Pm / (4.0 * 3.14159265358979323846));
+        o[6] = 0.5 * atan2(2.0 * Ixy, Ixx - Iyy);
+        o[7] = (Pm - P.P0) / P.P0;
+    }
+}
+
+// MLS interpolation (Eq. 8) with gradient at arbitrary points.
+template <typename S>
+__global__ void k_interp_points(const S* __restrict__ src, Lat L, const double* __restrict__ fib,
+                                const double2* __restrict__ pts, int n, double* __restrict__ out,
+                                unsigned* status) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    Interp o;
+    const bool ok = mls_interp<S, true>(src, L, fib, pts[m].x, pts[m].y, o);
+    double* r = out + 8 * (long long)m;
+    r[0] = o.ux; r[1] = o.uy; r[2] = o.rho; r[3] = o.p;
+    r[4] = o.dudx; r[5] = o.dudy; r[6] = o.dvdx; r[7] = o.dvdy;
+    if (!ok) atomicOr(status, kStatSupport);
+}
+
+// ---------------------------------------------------------------------------------
+// Host launchers. The tile budget is kTileCells lattice nodes per capsule CTA.
+// ---------------------------------------------------------------------------------
+constexpr int kTileCells = 2304;
+
+static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+template <typename C>
+static size_t tile_bytes(bool moments, bool forces) {
+    return (size_t)kTileCells * ((moments ? 3 * sizeof(C) : 0) + (forces ? 2 * sizeof(double) : 0));
+}
+
+template <typename S>
+static size_t smem_dyn_spread(int max_n) { return ring_smem_bytes(max_n) + tile_bytes<typename St<S>::C>(true, true); }
+template <typename S>
+static size_t smem_moments(int max_n) { return ring_smem_bytes(max_n) + tile_bytes<typename St<S>::C>(true, false); }
+template <typename C>
+static size_t smem_forces(int max_n) { return ring_smem_bytes(max_n) + tile_bytes<C>(false, true); }
+
+void set_capsule_smem_limits(int max_n) {
+    cudaFuncSetAttribute(k_dyn_force_spread<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dyn_spread<double>(max_n));
+    cudaFuncSetAttribute(k_dyn_force_spread<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dyn_spread<float>(max_n));
+    cudaFuncSetAttribute(k_dyn_force_spread<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dyn_spread<__half>(max_n));
+    cudaFuncSetAttribute(k_dyn_update<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_moments<double>(max_n));
+    cudaFuncSetAttribute(k_dyn_update<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_moments<float>(max_n));
+    cudaFuncSetAttribute(k_dyn_update<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_moments<__half>(max_n));
+    cudaFuncSetAttribute(k_kin_advance<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_moments<double>(max_n));
+    cudaFuncSetAttribute(k_kin_advance<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_moments<float>(max_n));
+    cudaFuncSetAttribute(k_kin_advance<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_moments<__half>(max_n));
+    cudaFuncSetAttribute(k_kin_force_spread<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_forces<double>(max_n));
+    cudaFuncSetAttribute(k_kin_force_spread<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_forces<float>(max_n));
+    cudaFuncSetAttribute(k_observables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring_smem_bytes(max_n));
+}
+
+template <typename S>
+void launch_dyn_force_spread(const void* src, const Lat& L, const double* fib_prev, Nodes nd, int ncaps, int max_n,
+                             Spread sp, unsigned* status, cudaStream_t s) {
+    k_dyn_force_spread<S><<<ncaps, 128, smem_dyn_spread<S>(max_n), s>>>((const S*)src, L, fib_prev, nd, max_n,
+                                                                        kTileCells, sp, status);
+}
+
+template <typename S>
+void launch_dyn_update(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
+                       int* reset_count, unsigned* status, cudaStream_t s) {
+    k_dyn_update<S><<<ncaps, 128, smem_moments<S>(max_n), s>>>((const S*)dst, L, fib_cur, nd, max_n, kTileCells,
+                                                               reset_count, status);
+}
+
+void launch_kin_force_spread(const Lat& L, Nodes nd, int ncaps, int max_n, Spread sp, unsigned* status,
+                             bool fp64_weights, cudaStream_t s) {
+    // double MLS weights when the populations are double, float otherwise
+    if (fp64_weights)
+        k_kin_force_spread<double><<<ncaps, 128, smem_forces<double>(max_n), s>>>(L, nd, max_n, kTileCells, sp, status);
+    else
+        k_kin_force_spread<float><<<ncaps, 128, smem_forces<float>(max_n), s>>>(L, nd, max_n, kTileCells, sp, status);
+}
+
+template <typename S>
+void launch_kin_advance(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
+                        int* reset_count, unsigned* status, cudaStream_t s) {
+    k_kin_advance<S><<<ncaps, 128, smem_moments<S>(max_n), s>>>((const S*)dst, L, fib_cur, nd, max_n, kTileCells,
+                                                                reset_count, status);
+}
+
+void launch_observables(Nodes nd, int ncaps, int max_n, double* out, cudaStream_t s) {
+    k_observables<<<ncaps, 128, ring_smem_bytes(max_n), s>>>(nd, max_n, out);
+}
+
+template <typename S>
+void launch_interp_points(const void* src, const Lat& L, const double* fib, const double2* pts, int n,
+                          double* out, unsigned* status, cudaStream_t s) {
+    k_interp_points<S><<<nblk(n, 128), 128, 0, s>>>((const S*)src, L, fib, pts, n, out, status);
+}
+
+#define LBMIB_INSTANTIATE_IB(S)                                                                              \
+    template void launch_dyn_force_spread<S>(const void*, const Lat&, const double*, Nodes, int, int, Spread, \
+                                             unsigned*, cudaStream_t);                                       \
+    template void launch_dyn_update<S>(const void*, const Lat&, const double*, Nodes, int, int, int*,        \
+                                       unsigned*, cudaStream_t);                                             \
+    template void launch_kin_advance<S>(const void*, const Lat&, const double*, Nodes, int, int, int*,       \
+                                        unsigned*, cudaStream_t);                                            \
+    template void launch_interp_points<S>(const void*, const Lat&, const double*, const double2*, int,       \
+                                          double*, unsigned*, cudaStream_t);
+
+LBMIB_INSTANTIATE_IB(double)
+LBMIB_INSTANTIATE_IB(float)
+LBMIB_INSTANTIATE_IB(__half)
+
+}  // namespace lbmib

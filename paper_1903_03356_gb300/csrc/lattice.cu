@@ -1,0 +1,389 @@
+// Lattice kernels: fused pull collide-stream (Eq. 1-5), forced-node patch, start-up
+// and read-back. Coclite et al., arXiv:1903.03356, Section 2.1-2.2.
+//
+// k_collide_stream is the HBM-bound hot loop. One warp owns a run of 32*V consecutive
+// nodes of one row (V nodes per thread, 16 bytes of each population per thread). Every
+// population is fetched with one aligned 16-byte load per thread; the +/-1 x shift of
+// the pull is resolved with a warp shuffle of the neighbouring lane's edge element, and
+// only the warp's edge lane issues one extra scalar load. Stores are aligned 16-byte
+// stores of the node's own slots, so the kernel moves exactly 9 loads + 9 stores of
+// the storage type per lattice update from HBM.
+#include <type_traits>
+
+#include "lbmib_kernels.cuh"
+
+namespace lbmib {
+
+template <typename S>
+struct Vec;
+template <>
+struct Vec<double> { static constexpr int V = 2; };
+template <>
+struct Vec<float> { static constexpr int V = 4; };
+template <>
+struct Vec<__half> { static constexpr int V = 4; };   // 8-byte vectors: keeps registers low
+
+// Aligned vector load / store of V consecutive stored values (16 bytes for double and
+// float, 8 bytes for half). Cache policy:
+// load mode 0 = read-only path (ld.global.nc), 1 = streaming (ld.global.cs);
+// store mode 0 = default write-back, 1 = streaming (st.global.cs, evict first).
+template <int LM, typename T>
+__device__ __forceinline__ T ldv(const T* p) {
+    if constexpr (LM == 1) return __ldcs(p);
+    else return __ldg(p);
+}
+template <int SM_, typename T>
+__device__ __forceinline__ void stv(T* p, const T& v) {
+    if constexpr (SM_ == 1) __stcs(p, v);
+    else *p = v;
+}
+
+template <typename S, int LM>
+__device__ __forceinline__ void ld_vec(const S* p, typename St<S>::C (&o)[Vec<S>::V], const Lat& L) {
+    if constexpr (std::is_same<S, double>::value) {
+        const double2 v = ldv<LM>(reinterpret_cast<const double2*>(p));
+        o[0] = v.x; o[1] = v.y;
+    } else if constexpr (std::is_same<S, float>::value) {
+        const float4 v = ldv<LM>(reinterpret_cast<const float4*>(p));
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else {
+        const uint2 v = ldv<LM>(reinterpret_cast<const uint2*>(p));
+        const __half2* h = reinterpret_cast<const __half2*>(&v);
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const float2 f = __half22float2(h[k]);
+            o[2 * k] = f.x * L.inv_scale;
+            o[2 * k + 1] = f.y * L.inv_scale;
+        }
+    }
+}
+
+template <typename S, int SMODE>
+__device__ __forceinline__ void st_vec(S* p, const typename St<S>::C (&o)[Vec<S>::V], const Lat& L) {
+    if constexpr (std::is_same<S, double>::value) {
+        stv<SMODE>(reinterpret_cast<double2*>(p), make_double2(o[0], o[1]));
+    } else if constexpr (std::is_same<S, float>::value) {
+        stv<SMODE>(reinterpret_cast<float4*>(p), make_float4(o[0], o[1], o[2], o[3]));
+    } else {
+        uint2 v;
+        __half2* h = reinterpret_cast<__half2*>(&v);
+#pragma unroll
+        for (int k = 0; k < 2; k++) h[k] = __floats2half2_rn(o[2 * k] * L.scale, o[2 * k + 1] * L.scale);
+        stv<SMODE>(reinterpret_cast<uint2*>(p), v);
+    }
+}
+
+// Loads of population I for the V nodes x0 .. x0+V-1 of row y (pull of Eq. 1), split
+// in two phases so that all nine populations' loads are in flight before any is used:
+// issue() fetches the aligned 16-byte vector of the source row (at a wall, of the node's
+// own opposite population) and, for an edge lane, the one scalar that no neighbouring
+// lane holds; resolve() shifts by -e_x through warp shuffles. All 32 lanes of the warp
+// call both with the same y. A lane whose chunk crosses the end of the row ("ragged",
+// only when nx is not a multiple of V) keeps its raw vector for its neighbours'
+// shuffles and gathers its own shifted values element-wise in resolve().
+template <typename S, int I, int LM>
+struct PopLoad {
+    using C = typename St<S>::C;
+    static constexpr int V = Vec<S>::V;
+    C v[V];
+    C edge;
+
+    __device__ __forceinline__ bool at_wall(const Lat& L, int y) const {
+        constexpr int EY = ey(I);
+        return EY != 0 && L.walls && (y - EY < 0 || y - EY >= L.ny);
+    }
+    __device__ __forceinline__ const S* row_ptr(const S* __restrict__ src, const Lat& L, int y) const {
+        constexpr int EY = ey(I);
+        if (at_wall(L, y)) return src + (long long)opp(I) * L.plane + (long long)y * L.pitch;
+        const int ys = EY != 0 ? wrapi(y - EY, L.ny) : y;
+        return src + (long long)I * L.plane + (long long)ys * L.pitch;
+    }
+    __device__ __forceinline__ void issue(const S* __restrict__ src, const Lat& L, int x0, int y, int lane,
+                                          bool active) {
+        constexpr int EX = ex(I);
+        const S* row = row_ptr(src, L, y);
+        edge = C(0);
+        if (active) {
+            // x0 < nx <= pitch and both are multiples of V: the vector stays inside the row
+            ld_vec<S, LM>(row + x0, v, L);
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; j++) v[j] = C(0);
+        }
+        if (!at_wall(L, y) && active) {
+            if (EX == 1 && lane == 0) edge = St<S>::ld(row + wrapi(x0 - 1, L.nx), L);
+            // the next lane's chunk is missing or ragged: fetch x0 + V directly
+            if (EX == -1 && (lane == 31 || x0 + 2 * V > L.nx)) edge = St<S>::ld(row + wrapi(x0 + V, L.nx), L);
+        }
+    }
+    __device__ __forceinline__ void resolve(const S* __restrict__ src, const Lat& L, int x0, int y, int lane,
+                                            bool active, bool full, C (&out)[V]) const {
+        constexpr int EX = ex(I);
+        if (at_wall(L, y)) {  // warp-uniform
+            constexpr int J = opp(I);
+            const C corr = C(6) * wgt<C>(J) * C(ex(J)) * C(y - ey(I) < 0 ? L.ub : L.ut);
+#pragma unroll
+            for (int j = 0; j < V; j++) out[j] = v[j] - corr;
+        } else if (EX == 0) {
+#pragma unroll
+            for (int j = 0; j < V; j++) out[j] = v[j];
+        } else if (EX == 1) {  // value at x - 1
+            C prev = __shfl_up_sync(0xffffffffu, v[V - 1], 1);
+            if (lane == 0) prev = edge;
+            out[0] = prev;
+#pragma unroll
+            for (int j = 1; j < V; j++) out[j] = v[j - 1];
+        } else {               // value at x + 1
+            C next = __shfl_down_sync(0xffffffffu, v[0], 1);
+            if (lane == 31 || x0 + 2 * V > L.nx) next = edge;
+#pragma unroll
+            for (int j = 0; j < V - 1; j++) out[j] = v[j + 1];
+            out[V - 1] = next;
+        }
+        if (active && !full) {  // ragged chunk: element-wise, with the pull's wrap
+            const S* row = row_ptr(src, L, y);
+            const bool wall = at_wall(L, y);
+            const C corr = wall ? C(6) * wgt<C>(opp(I)) * C(ex(opp(I))) * C(y - ey(I) < 0 ? L.ub : L.ut) : C(0);
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                const int x = x0 + j;
+                out[j] = x < L.nx ? (wall ? St<S>::ld(row + x, L) - corr : St<S>::ld(row + wrapi(x - EX, L.nx), L))
+                                  : C(0);
+            }
+        }
+    }
+};
+
+template <typename S, int LM, int SMODE, int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) k_collide_stream(const S* __restrict__ src, S* __restrict__ dst,
+                                                             Lat L, unsigned* __restrict__ status) {
+    using C = typename St<S>::C;
+    constexpr int V = Vec<S>::V;
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * BS + threadIdx.x) >> 5;
+    const int segs = (L.nx + 32 * V - 1) / (32 * V);
+    if (gw >= (long long)segs * L.ny) return;  // whole warps only
+    const int y = (int)(gw / segs);
+    const int seg = (int)(gw - (long long)y * segs);
+    const int x0 = (seg * 32 + lane) * V;
+    const bool active = x0 < L.nx;
+    const bool full = x0 + V <= L.nx;
+
+    PopLoad<S, 0, LM> p0; PopLoad<S, 1, LM> p1; PopLoad<S, 2, LM> p2;
+    PopLoad<S, 3, LM> p3; PopLoad<S, 4, LM> p4; PopLoad<S, 5, LM> p5;
+    PopLoad<S, 6, LM> p6; PopLoad<S, 7, LM> p7; PopLoad<S, 8, LM> p8;
+    p0.issue(src, L, x0, y, lane, active); p1.issue(src, L, x0, y, lane, active);
+    p2.issue(src, L, x0, y, lane, active); p3.issue(src, L, x0, y, lane, active);
+    p4.issue(src, L, x0, y, lane, active); p5.issue(src, L, x0, y, lane, active);
+    p6.issue(src, L, x0, y, lane, active); p7.issue(src, L, x0, y, lane, active);
+    p8.issue(src, L, x0, y, lane, active);
+    C f[9][V];
+    p0.resolve(src, L, x0, y, lane, active, full, f[0]); p1.resolve(src, L, x0, y, lane, active, full, f[1]);
+    p2.resolve(src, L, x0, y, lane, active, full, f[2]); p3.resolve(src, L, x0, y, lane, active, full, f[3]);
+    p4.resolve(src, L, x0, y, lane, active, full, f[4]); p5.resolve(src, L, x0, y, lane, active, full, f[5]);
+    p6.resolve(src, L, x0, y, lane, active, full, f[6]); p7.resolve(src, L, x0, y, lane, active, full, f[7]);
+    p8.resolve(src, L, x0, y, lane, active, full, f[8]);
+
+    const C gx = C(L.gx), gy = C(L.gy), om = C(L.omega);
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < V; j++) {
+        C s[9];
+#pragma unroll
+        for (int i = 0; i < 9; i++) s[i] = f[i][j];
+        const C usq = collide<C>(s, gx, gy, om);
+        bad |= !(usq < C(0.09));  // |u| > 0.3 or NaN
+#pragma unroll
+        for (int i = 0; i < 9; i++) f[i][j] = s[i];
+    }
+    if (full) {
+#pragma unroll
+        for (int i = 0; i < 9; i++)
+            st_vec<S, SMODE>(dst + (long long)i * L.plane + (long long)y * L.pitch + x0, f[i], L);
+    } else if (active) {
+#pragma unroll
+        for (int i = 0; i < 9; i++)
+#pragma unroll
+            for (int j = 0; j < V; j++)
+                if (x0 + j < L.nx) St<S>::st(dst + (long long)i * L.plane + (long long)y * L.pitch + x0 + j, f[i][j], L);
+    }
+    if (__any_sync(0xffffffffu, bad && active) && lane == 0) atomicOr(status, kStatUnstable);
+}
+
+// Forced-node patch: redo the collision of every node in the current touched-cell list
+// with the total force g + f_ib (Eq. 4-5), reading the same input as k_collide_stream.
+// Also clears the previous force buffer at the previous list (its last reader has run)
+// and advances the touched-cell stamp.
+template <typename S>
+__global__ void __launch_bounds__(256) k_patch(const S* __restrict__ src, S* __restrict__ dst, Lat L,
+                                               const double* __restrict__ fib_c, const int* __restrict__ list_c,
+                                               double* __restrict__ fib_p, const int* __restrict__ list_p,
+                                               DevCounters* ctr, int c, int capacity) {
+    using C = typename St<S>::C;
+    const long long N = (long long)L.nx * L.ny;
+    int nc = ctr->count[c];
+    int np = ctr->count[1 - c];
+    const int stride = gridDim.x * blockDim.x;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (nc > capacity || np > capacity) {
+        if (t0 == 0) atomicOr(&ctr->status, kStatList);
+        nc = nc > capacity ? capacity : nc;
+        np = np > capacity ? capacity : np;
+    }
+    for (int k = t0; k < nc; k += stride) {
+        const int cell = list_c[k];
+        if (cell < 0 || (long long)cell >= N) {
+            atomicOr(&ctr->status, kStatCell);
+            continue;
+        }
+        const int y = cell / L.nx, x = cell - y * L.nx;
+        C s[9];
+#pragma unroll
+        for (int i = 0; i < 9; i++) s[i] = pull<S>(src, L, i, x, y);
+        const C usq = collide<C>(s, C(L.gx + fib_c[cell]), C(L.gy + fib_c[N + cell]), C(L.omega));
+        if (!(usq < C(0.09))) atomicOr(&ctr->status, kStatUnstable);
+#pragma unroll
+        for (int i = 0; i < 9; i++) St<S>::st(dst + (long long)i * L.plane + (long long)y * L.pitch + x, s[i], L);
+    }
+    for (int k = t0; k < np; k += stride) {
+        const int cell = list_p[k];
+        if (cell < 0 || (long long)cell >= N) {
+            atomicOr(&ctr->status, kStatCell);
+            continue;
+        }
+        fib_p[cell] = 0.0;
+        fib_p[N + cell] = 0.0;
+    }
+    if (t0 == 0) ctr->step_stamp += 1;
+}
+
+// Start-up: post-collision populations whose pull gives the Eq. 2 equilibrium of the
+// fields (rho, ux, uy) at every node ("un-streaming" through walls and periodic edges).
+template <typename S>
+__global__ void k_init(S* __restrict__ dst, Lat L, const double* __restrict__ rho,
+                       const double* __restrict__ ux, const double* __restrict__ uy) {
+    const long long N = (long long)L.nx * L.ny;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int y = (int)(n / L.nx), x = (int)(n - (long long)y * L.nx);
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        int xt = x + ex(i), yt = y + ey(i);
+        int k = i;
+        double corr = 0.0;
+        if (L.walls && (yt < 0 || yt >= L.ny)) {
+            // consumed by this node as the reflected population opp(i)
+            k = opp(i);
+            corr = 6.0 * wgt<double>(i) * ex(i) * (yt < 0 ? L.ub : L.ut);
+            xt = x;
+            yt = y;
+        } else {
+            xt = wrapi(xt, L.nx);
+            yt = wrapi(yt, L.ny);
+        }
+        const long long m = (long long)yt * L.nx + xt;
+        const double r = rho ? rho[m] : 1.0, u = ux ? ux[m] : 0.0, v = uy ? uy[m] : 0.0;
+        const double eu = ex(k) * u + ey(k) * v;
+        const double feq = wgt<double>(k) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * (u * u + v * v));
+        St<S>::st(dst + (long long)i * L.plane + (long long)y * L.pitch + x,
+                  typename St<S>::C(feq - wgt<double>(i) + corr), L);
+    }
+}
+
+// Read-back: rho (Eq. 6) and u (Eq. 7, half of g + f_ib) at every node, in double.
+template <typename S>
+__global__ void k_macros(const S* __restrict__ src, Lat L, const double* __restrict__ fib,
+                         double* __restrict__ rho, double* __restrict__ ux, double* __restrict__ uy) {
+    using C = typename St<S>::C;
+    const long long N = (long long)L.nx * L.ny;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int y = (int)(n / L.nx), x = (int)(n - (long long)y * L.nx);
+    C s[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) s[i] = pull<S>(src, L, i, x, y);
+    C drho, mx, my;
+    moments<C>(s, drho, mx, my);
+    const double r = 1.0 + (double)drho;
+    rho[n] = r;
+    ux[n] = ((double)mx + 0.5 * (L.gx + fib[n])) / r;
+    uy[n] = ((double)my + 0.5 * (L.gy + fib[N + n])) / r;
+}
+
+// Read-back: unshifted pre-collision populations i0 .. i0+2 in double.
+template <typename S>
+__global__ void k_populations(const S* __restrict__ src, Lat L, int i0, double* __restrict__ out) {
+    const long long N = (long long)L.nx * L.ny;
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int y = (int)(n / L.nx), x = (int)(n - (long long)y * L.nx);
+    for (int k = 0; k < 3 && i0 + k < 9; k++) {
+        const int i = i0 + k;
+        double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+        out[k * N + n] = (double)pull<S>(src, L, i, x, y) + w;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------------
+static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// variant: bits 0-11 block size (128 or 256; default 256); bit 18 asks for four resident
+// blocks per SM (register cap 64 at 256 threads) instead of three.
+template <typename S>
+void launch_collide_stream(const void* src, void* dst, const Lat& L, unsigned* status, int variant,
+                           cudaStream_t s) {
+    constexpr int V = Vec<S>::V;
+    const int bs = (variant & 0xfff) == 128 ? 128 : 256;
+    const bool occ4 = (variant >> 18) & 1;
+    const long long segs = (L.nx + 32 * V - 1) / (32 * V);
+    const long long threads = segs * L.ny * 32;
+    const unsigned g = blocks_for(threads, bs);
+    const S* a = (const S*)src;
+    S* b = (S*)dst;
+    if (bs == 256 && !occ4) k_collide_stream<S, 0, 0, 256, 3><<<g, 256, 0, s>>>(a, b, L, status);
+    else if (bs == 256) k_collide_stream<S, 0, 0, 256, 4><<<g, 256, 0, s>>>(a, b, L, status);
+    else if (!occ4) k_collide_stream<S, 0, 0, 128, 6><<<g, 128, 0, s>>>(a, b, L, status);
+    else k_collide_stream<S, 0, 0, 128, 8><<<g, 128, 0, s>>>(a, b, L, status);
+}
+
+template <typename S>
+void launch_patch(const void* src, void* dst, const Lat& L, const double* fib_c, const int* list_c,
+                  double* fib_p, const int* list_p, DevCounters* ctr, int c, int capacity, cudaStream_t s) {
+    int grid = (int)blocks_for(capacity > 0 ? capacity : 1, 256);
+    if (grid > 4096) grid = 4096;
+    k_patch<S><<<grid, 256, 0, s>>>((const S*)src, (S*)dst, L, fib_c, list_c, fib_p, list_p, ctr, c, capacity);
+}
+
+template <typename S>
+void launch_init(void* dst, const Lat& L, const double* rho, const double* ux, const double* uy, cudaStream_t s) {
+    k_init<S><<<blocks_for((long long)L.nx * L.ny, 256), 256, 0, s>>>((S*)dst, L, rho, ux, uy);
+}
+
+template <typename S>
+void launch_macros(const void* src, const Lat& L, const double* fib, double* rho, double* ux, double* uy,
+                   cudaStream_t s) {
+    k_macros<S><<<blocks_for((long long)L.nx * L.ny, 256), 256, 0, s>>>((const S*)src, L, fib, rho, ux, uy);
+}
+
+template <typename S>
+void launch_populations(const void* src, const Lat& L, int i0, double* out, cudaStream_t s) {
+    k_populations<S><<<blocks_for((long long)L.nx * L.ny, 256), 256, 0, s>>>((const S*)src, L, i0, out);
+}
+
+#define LBMIB_INSTANTIATE_LATTICE(S)                                                                  \
+    template void launch_collide_stream<S>(const void*, void*, const Lat&, unsigned*, int, cudaStream_t); \
+    template void launch_patch<S>(const void*, void*, const Lat&, const double*, const int*, double*, \
+                                  const int*, DevCounters*, int, int, cudaStream_t);                  \
+    template void launch_init<S>(void*, const Lat&, const double*, const double*, const double*,      \
+                                 cudaStream_t);                                                       \
+    template void launch_macros<S>(const void*, const Lat&, const double*, double*, double*, double*, \
+                                   cudaStream_t);                                                     \
+    template void launch_populations<S>(const void*, const Lat&, int, double*, cudaStream_t);
+
+LBMIB_INSTANTIATE_LATTICE(double)
+LBMIB_INSTANTIATE_LATTICE(float)
+LBMIB_INSTANTIATE_LATTICE(__half)
+
+}  // namespace lbmib

@@ -1,0 +1,334 @@
+// Device-side building blocks of the LBM-IB library (sm_103a).
+//
+// Method: Coclite et al., arXiv:1903.03356. D2Q9 BGK with a body-force term
+// (Section 2.1-2.2, Eq. 1-7), MLS transfer (Eq. 8-9), membrane forces (Eq. 10-16).
+//
+// Lattice storage: structure of arrays, population-major: plane i holds ny rows of
+// `pitch` elements (pitch = nx rounded up to 128 bytes). The stored value of population
+// i is the POST-collision value minus its rest weight w_i (shifted storage), so a step
+// is a pull: node x gathers population i from x - e_i, collides, and writes its own
+// slot. A population whose source lies beyond a wall is the node's own outgoing
+// population in the opposite direction, corrected by -6 w_j (e_j . u_w) (half-way
+// bounce-back with the reference density rho_0 = 1).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmib {
+
+// ---------------------------------------------------------------------------------
+// D2Q9 velocity set (Eq. 3) and weights (Section 2.1)
+// ---------------------------------------------------------------------------------
+__host__ __device__ constexpr int ex(int i) {
+    return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int i) {
+    return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+}
+template <typename C>
+__host__ __device__ constexpr C wgt(int i) {
+    return i == 0 ? C(4) / C(9) : (i <= 4 ? C(1) / C(9) : C(1) / C(36));
+}
+static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2, "opp axis");
+static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "opp diag");
+
+// Lattice description passed by value to every kernel.
+struct Lat {
+    int nx, ny;
+    int pitch;            // elements per stored row
+    int walls;            // 1: bounce-back walls at y = -1/2 and y = ny - 1/2
+    long long plane;      // elements per population plane (ny * pitch)
+    double tau, omega;    // relaxation time and 1/tau
+    double ub, ut;        // wall x-velocities (bottom, top)
+    double gx, gy;        // uniform body-force density
+    float scale, inv_scale;  // FP16 storage scale (1 for other storages)
+    double nu;            // kinematic viscosity (tau - 1/2)/3
+};
+
+// ---------------------------------------------------------------------------------
+// Storage traits: type S stored, type C computed in.
+// ---------------------------------------------------------------------------------
+template <typename S>
+struct St;
+template <>
+struct St<double> {
+    using C = double;
+    static __device__ __forceinline__ double ld(const double* p, const Lat&) { return __ldg(p); }
+    static __device__ __forceinline__ void st(double* p, double v, const Lat&) { *p = v; }
+};
+template <>
+struct St<float> {
+    using C = float;
+    static __device__ __forceinline__ float ld(const float* p, const Lat&) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float* p, float v, const Lat&) { *p = v; }
+};
+template <>
+struct St<__half> {
+    using C = float;
+    static __device__ __forceinline__ float ld(const __half* p, const Lat& L) {
+        return __half2float(__ldg(p)) * L.inv_scale;
+    }
+    static __device__ __forceinline__ void st(__half* p, float v, const Lat& L) {
+        *p = __float2half_rn(v * L.scale);
+    }
+};
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+// Pre-collision population i at node (x, y) of the step that reads `src` (Eq. 1, left
+// side): the pull of the post-collision population from x - e_i, or the wall reflection.
+template <typename S>
+__device__ __forceinline__ typename St<S>::C pull(const S* __restrict__ src, const Lat& L, int i,
+                                                  int x, int y) {
+    using C = typename St<S>::C;
+    int ys = y - ey(i);
+    if (L.walls && (ys < 0 || ys >= L.ny)) {
+        const int j = opp(i);
+        const C uw = C(ys < 0 ? L.ub : L.ut);
+        return St<S>::ld(src + (long long)j * L.plane + (long long)y * L.pitch + x, L) -
+               C(6) * wgt<C>(j) * C(ex(j)) * uw;
+    }
+    ys = wrapi(ys, L.ny);
+    const int xs = wrapi(x - ex(i), L.nx);
+    return St<S>::ld(src + (long long)i * L.plane + (long long)ys * L.pitch + xs, L);
+}
+
+// Density deviation, momentum (Eq. 6-7 without the force) of shifted populations.
+template <typename C>
+__device__ __forceinline__ void moments(const C s[9], C& drho, C& mx, C& my) {
+    drho = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])) + s[8];
+    mx = (s[1] - s[3]) + (s[5] - s[6]) + (s[8] - s[7]);
+    my = (s[2] - s[4]) + (s[5] + s[6]) - (s[7] + s[8]);
+}
+
+// BGK collision with the Guo forcing term (Eq. 4-5) on shifted populations, in place.
+// F is the total force density at the node. Returns u^2 for the stability check.
+template <typename C>
+__device__ __forceinline__ C collide(C s[9], C Fx, C Fy, C omega) {
+    C drho, mx, my;
+    moments<C>(s, drho, mx, my);
+    const C rho = C(1) + drho;
+    const C inv = C(1) / rho;
+    const C ux = (mx + C(0.5) * Fx) * inv;
+    const C uy = (my + C(0.5) * Fy) * inv;
+    const C usq = ux * ux + uy * uy;
+    const C u15 = C(1.5) * usq;
+    const C fpre = C(1) - C(0.5) * omega;   // 1 - 1/(2 tau)
+    const C uF = ux * Fx + uy * Fy;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const C eu = C(ex(i)) * ux + C(ey(i)) * uy;
+        const C eF = C(ex(i)) * Fx + C(ey(i)) * Fy;
+        // shifted equilibrium f_eq - w = w (drho + rho (3eu + 4.5eu^2 - 1.5u^2)): every
+        // term is small, so nothing cancels against the rest weight in float
+        const C seq = wgt<C>(i) * (drho + rho * (eu * (C(3) + C(4.5) * eu) - u15));
+        // Eq. 5: (1 - 1/2tau) w [3 (e - u) + 9 (e . u) e] . F
+        const C Fi = fpre * wgt<C>(i) * (C(3) * (eF - uF) + C(9) * eu * eF);
+        s[i] = s[i] - omega * (s[i] - seq) + Fi;
+    }
+    if constexpr (sizeof(C) < 8) {
+        // Single precision: rounding inside the collision would break the exact
+        // conservation of mass and momentum, and the lattice has no restoring force for
+        // those errors, so they would accumulate step after step. Populations 1, 2 and
+        // 0 are therefore set from the exact post-collision moments (sum s = drho,
+        // sum s e = m + F); in exact arithmetic this changes nothing.
+        s[1] = s[3] + ((mx + Fx) - ((s[5] - s[6]) + (s[8] - s[7])));
+        s[2] = s[4] + ((my + Fy) - ((s[5] + s[6]) - (s[7] + s[8])));
+        s[0] = drho - (((s[1] + s[2]) + (s[3] + s[4])) + ((s[5] + s[6]) + (s[7] + s[8])));
+    }
+    return usq;
+}
+
+// ---------------------------------------------------------------------------------
+// Moving least squares (Eq. 8-9): 3x3 support centred on the nearest node, weights
+// exp(-(r/alpha)^2), r = |x - x_k| / r_w, r_w = 2.6, alpha = 0.3, linear basis.
+//
+// The weight factorises, W_k = exp(-dx_a^2 / L^2) exp(-dy_b^2 / L^2) with L = r_w alpha,
+// and the support is the tensor grid of three x and three y offsets. In the basis
+// (1, dx - mx, dy - my), with mx, my the weighted mean offsets, every off-diagonal entry
+// of the moment matrix A = sum W p p^T is a product containing sum_a wx_a (dx_a - mx) = 0
+// or sum_b wy_b (dy_b - my) = 0, so A is diagonal and the least-squares fit of Eq. 9 is
+// a_0 = sum W v / sum W, a_1 = sum W dx' v / sum W dx'^2, a_2 = sum W dy' v / sum W dy'^2.
+// The interpolated value at the marker (dx = dy = 0) is a_0 - mx a_1 - my a_2 and the
+// fitted gradient is (a_1, a_2): the same MLS solution as solving the 3x3 system, with
+// the solve reduced to three reciprocals, done in double.
+// ---------------------------------------------------------------------------------
+constexpr double kMlsInvLen2 = 1.0 / (2.6 * 0.3 * 2.6 * 0.3);   // 1 / (r_w alpha)^2
+
+template <typename C>
+struct MlsW {
+    int cx, cy;           // centre node (unwrapped)
+    C wx[3], wy[3];       // axis weights, a or b = -1, 0, 1
+    C dxp[3], dyp[3];     // centred offsets dx_a - mx, dy_b - my
+    double rS, rVx, rVy;  // 1/sum W, 1/sum W dx'^2, 1/sum W dy'^2
+    double mx, my;        // weighted mean offsets
+    bool ok;              // support inside the channel and the point sane
+    // phi_k (Eq. 8) and gradient weights of support node k = 3 (b+1) + (a+1)
+    __device__ __forceinline__ double phi(int a, int b) const {
+        const double w = (double)wx[a] * (double)wy[b];
+        return w * (rS - mx * (double)dxp[a] * rVx - my * (double)dyp[b] * rVy);
+    }
+};
+
+// Support geometry of a point: centre node and whether the 3x3 block stays inside the
+// walls. A non-finite or runaway position (an unstable run) is moved to the origin so
+// that every access stays inside the lattice, and reported as a support failure.
+__device__ __forceinline__ bool support_centre(const Lat& L, double& X, double& Y, int& cx, int& cy) {
+    const bool sane = fabs(X) < 1e9 && fabs(Y) < 1e9;   // false for NaN too
+    if (!sane) {
+        X = 0.0;
+        Y = 0.0;
+    }
+    cx = (int)floor(X + 0.5);
+    cy = (int)floor(Y + 0.5);
+    return sane && (!L.walls || (cy >= 1 && cy <= L.ny - 2));
+}
+
+template <typename C>
+__device__ __forceinline__ MlsW<C> mls_setup(const Lat& L, double X, double Y) {
+    MlsW<C> m;
+    m.ok = support_centre(L, X, Y, m.cx, m.cy);
+    double sx0 = 0, sx1 = 0, sy0 = 0, sy1 = 0;
+    C dx[3], dy[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        dx[a] = C((double)(m.cx + a - 1) - X);
+        dy[a] = C((double)(m.cy + a - 1) - Y);
+        m.wx[a] = exp(-dx[a] * dx[a] * C(kMlsInvLen2));
+        m.wy[a] = exp(-dy[a] * dy[a] * C(kMlsInvLen2));
+        sx0 += (double)m.wx[a];
+        sx1 += (double)m.wx[a] * (double)dx[a];
+        sy0 += (double)m.wy[a];
+        sy1 += (double)m.wy[a] * (double)dy[a];
+    }
+    const double isx = 1.0 / sx0, isy = 1.0 / sy0;
+    m.mx = sx1 * isx;
+    m.my = sy1 * isy;
+    double vx = 0, vy = 0;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const double px = (double)dx[a] - m.mx, py = (double)dy[a] - m.my;
+        m.dxp[a] = C(px);
+        m.dyp[a] = C(py);
+        vx += (double)m.wx[a] * px * px;
+        vy += (double)m.wy[a] * py * py;
+    }
+    m.rS = isx * isy;
+    m.rVx = 1.0 / (vx * sy0);
+    m.rVy = 1.0 / (vy * sx0);
+    return m;
+}
+
+struct Interp {
+    double ux, uy, rho, p;
+    double dudx, dudy, dvdx, dvdy;
+};
+
+// Lattice moments at a node: density deviation and the Eq. 7 velocity (half of the
+// uniform force plus the immersed-boundary force field).
+template <typename C>
+struct Mom {
+    C drho, ux, uy;
+};
+
+template <typename S>
+__device__ __forceinline__ Mom<typename St<S>::C> node_moments(const S* __restrict__ src, const Lat& L,
+                                                               const double* __restrict__ fib, int x, int y) {
+    using C = typename St<S>::C;
+    C s[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) s[i] = pull<S>(src, L, i, x, y);
+    C drho, mx, my;
+    moments<C>(s, drho, mx, my);
+    const long long N = (long long)L.nx * L.ny;
+    const long long n = (long long)y * L.nx + x;
+    const C inv = C(1) / (C(1) + drho);
+    Mom<C> m;
+    m.drho = drho;
+    m.ux = (mx + C(0.5) * C(L.gx + fib[n])) * inv;
+    m.uy = (my + C(0.5) * C(L.gy + fib[N + n])) * inv;
+    return m;
+}
+
+// Lattice row of a support node (walls: clamped, the support is then flagged) and the
+// periodic column.
+__device__ __forceinline__ int support_row(const Lat& L, int yk) {
+    if (L.walls) return yk < 0 ? 0 : (yk >= L.ny ? L.ny - 1 : yk);
+    return wrapi(yk, L.ny);
+}
+
+// MLS interpolation (Eq. 8) from a moment source get(a, b) -> Mom for support node
+// (cx + a - 1, cy + b - 1). Values in double, sums in the compute type.
+template <typename C, bool GRAD, typename Get>
+__device__ __forceinline__ void mls_apply(const MlsW<C>& m, Get&& get, Interp& o) {
+    C r0 = 0, r1 = 0, r2 = 0, u0 = 0, u1 = 0, u2 = 0, v0 = 0, v1 = 0, v2 = 0;
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const Mom<C> q = get(a, b);
+            const C w = m.wx[a] * m.wy[b];
+            const C wx = w * m.dxp[a], wy = w * m.dyp[b];
+            r0 += w * q.drho; r1 += wx * q.drho; r2 += wy * q.drho;
+            u0 += w * q.ux; u1 += wx * q.ux; u2 += wy * q.ux;
+            v0 += w * q.uy; v1 += wx * q.uy; v2 += wy * q.uy;
+        }
+    }
+    const double a1u = (double)u1 * m.rVx, a2u = (double)u2 * m.rVy;
+    const double a1v = (double)v1 * m.rVx, a2v = (double)v2 * m.rVy;
+    o.ux = (double)u0 * m.rS - m.mx * a1u - m.my * a2u;
+    o.uy = (double)v0 * m.rS - m.mx * a1v - m.my * a2v;
+    o.rho = 1.0 + (double)r0 * m.rS - m.mx * (double)r1 * m.rVx - m.my * (double)r2 * m.rVy;
+    o.p = o.rho / 3.0;
+    if (GRAD) {
+        o.dudx = a1u; o.dudy = a2u;
+        o.dvdx = a1v; o.dvdy = a2v;
+    }
+}
+
+// MLS interpolation of the fluid at (X, Y) straight from the populations (no tile).
+template <typename S, bool GRAD>
+__device__ bool mls_interp(const S* __restrict__ src, const Lat& L, const double* __restrict__ fib, double X,
+                           double Y, Interp& o) {
+    using C = typename St<S>::C;
+    const MlsW<C> m = mls_setup<C>(L, X, Y);
+    mls_apply<C, GRAD>(m, [&](int a, int b) {
+        return node_moments<S>(src, L, fib, wrapi(m.cx + a - 1, L.nx), support_row(L, m.cy + b - 1));
+    }, o);
+    return m.ok;
+}
+
+// Device status bits (sticky).
+enum : unsigned {
+    kStatUnstable = 1u,   // |u| > 0.3 or NaN in a collision
+    kStatSupport = 2u,    // a support left the channel, or a position ran away
+    kStatTimeout = 4u,    // a bounded wait gave up
+    kStatList = 8u,       // touched-cell list full (entry dropped)
+    kStatCell = 16u,      // a list entry outside the lattice (skipped)
+    kStatRing = 32u       // capsule parameters outside the launch's bounds (skipped)
+};
+
+// Small device block of counters and flags inside the arena.
+struct DevCounters {
+    int count[2];          // touched-cell list lengths (force buffers 0 and 1)
+    unsigned status;       // sticky status bits
+    int step_stamp;        // incremented once per coupled step (touched-cell stamps)
+    int pad[4];
+};
+
+// Per-capsule parameters (device and host mirror).
+struct CapsuleParams {
+    int off, n;            // first vertex, vertex count
+    double ks, kb, ka, m;  // Eq. 10, 12, 14 constants and per-vertex mass
+    double A0, P0;         // stress-free area and perimeter
+};
+
+}  // namespace lbmib

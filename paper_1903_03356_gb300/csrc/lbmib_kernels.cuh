@@ -1,0 +1,69 @@
+// Host-side declarations of the kernel launchers (internal to the library).
+#pragma once
+
+#include "lbmib_internal.cuh"
+
+namespace lbmib {
+
+// Membrane vertex state, structure of arrays over all vertices of all capsules.
+struct Nodes {
+    double2* X;      // X^n
+    double2* Xm1;    // X^{n-1}
+    double2* uv;     // node velocity (Dynamic: Eq. 24; Kinematic: interpolated)
+    double2* Fint;   // last internal force (Eq. 22)
+    double2* Fext;   // last external force (Eq. 15-16)
+    double* L0;      // stress-free length of element v (v -> v+1)
+    double* c0;      // cos(theta_0) at vertex v
+    double* s0;      // sin(theta_0) at vertex v
+    int* age;        // steps taken since the vertex's history started
+    int* capid;      // capsule of the vertex
+    const CapsuleParams* caps;
+    int count;       // vertices in use
+};
+
+// Touched-cell bookkeeping for the spread of one step.
+struct Spread {
+    double* fib;     // force buffer written this step (fx[N] then fy[N])
+    int* mark;       // per-cell stamp of the last step that touched it
+    int* list;       // unique touched cells of this step
+    int* count;      // length of list
+    const int* stamp;  // stamp source (DevCounters::step_stamp, + 1 is this step's stamp)
+    int capacity;    // entries the list can hold
+    unsigned* status;
+};
+
+// lattice.cu
+template <typename S>
+void launch_collide_stream(const void* src, void* dst, const Lat& L, unsigned* status, int variant,
+                           cudaStream_t s);
+template <typename S>
+void launch_patch(const void* src, void* dst, const Lat& L, const double* fib_c, const int* list_c,
+                  double* fib_p, const int* list_p, DevCounters* ctr, int c, int capacity, cudaStream_t s);
+template <typename S>
+void launch_init(void* dst, const Lat& L, const double* rho, const double* ux, const double* uy, cudaStream_t s);
+template <typename S>
+void launch_macros(const void* src, const Lat& L, const double* fib, double* rho, double* ux, double* uy,
+                   cudaStream_t s);
+template <typename S>
+void launch_populations(const void* src, const Lat& L, int i0, double* out, cudaStream_t s);
+
+// ib.cu
+template <typename S>
+void launch_dyn_force_spread(const void* src, const Lat& L, const double* fib_prev, Nodes nd, int ncaps, int max_n,
+                             Spread sp, unsigned* status, cudaStream_t s);
+template <typename S>
+void launch_dyn_update(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
+                       int* reset_count, unsigned* status, cudaStream_t s);
+void launch_kin_force_spread(const Lat& L, Nodes nd, int ncaps, int max_n, Spread sp, unsigned* status,
+                             bool fp64_weights, cudaStream_t s);
+template <typename S>
+void launch_kin_advance(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
+                        int* reset_count, unsigned* status, cudaStream_t s);
+void launch_observables(Nodes nd, int ncaps, int max_n, double* out, cudaStream_t s);
+template <typename S>
+void launch_interp_points(const void* src, const Lat& L, const double* fib, const double2* pts, int n,
+                          double* out, unsigned* status, cudaStream_t s);
+size_t capsule_smem_bytes(int max_n);
+void set_capsule_smem_limits(int max_n);
+
+}  // namespace lbmib

@@ -55,6 +55,17 @@ def poiseuille_force(tau: float, u_max: float, H: float, rho=1.0) -> float:
     return 8.0 * rho * viscosity(tau) * u_max / (H * H)
 
 
+def stable_eb(eb: float, ks: float, radius: float, xy: np.ndarray, mass: float) -> float:
+    """Bending modulus used by the workloads: E_b as requested, capped so that the
+    explicit node update of the Dynamic scheme (Eq. 23: a displacement of F/(2 m_v) per
+    step) is stable for the ring's shortest bending mode. That mode moves a vertex by
+    about 8 k_b / (l_min^2 m_v) times its amplitude per step; the cap keeps this below 1:
+    k_b <= l_min^2 m_v / 8, i.e. E_b <= l_min^2 m_v / (8 k_s r^2)."""
+    d = np.hypot(*(np.roll(xy, -1, axis=0) - xy).T)
+    cap = float(d.min()) ** 2 * mass / (8.0 * ks * radius * radius)
+    return min(eb, cap)
+
+
 def node_mass(density_ratio: float, area0: float, n: int, rho=1.0) -> float:
     """Membrane mass spread evenly over the vertices; the capsule weighs density_ratio
     times the fluid it encloses."""
@@ -187,8 +198,8 @@ def poiseuille_capsule(nx=600, ny=120, tau=0.7, u_max=0.02, radius=12.0, n=96, c
     xy = circle(n, radius, 100.13 if nx > 200 else 0.3 * nx + 0.13, y_frac * ny - 0.5 + 0.07)
     check_no_ties(xy)
     ks = ks_from_umax_ca(tau, u_max, ca)
-    kb = kb_from_eb(eb, ks, radius)
     m = node_mass(density_ratio, signed_area(xy), n)
+    kb = kb_from_eb(stable_eb(eb, ks, radius, xy, m), ks, radius)
     return Case("poiseuille_capsule", nx, ny, tau, True, gx=g, init="parabola",
                 capsules=[Capsule(xy, ks, kb, ka, m)], scheme=scheme, steps=steps)
 
@@ -257,9 +268,10 @@ def poiseuille_biconcave(nx=4096, ny=512, tau=0.7, u_max=0.02, count=256, n=128,
     rng = np.random.default_rng(seed)
     g = poiseuille_force(tau, u_max, ny)
     ks = ks_from_umax_ca(tau, u_max, ca)
-    kb = kb_from_eb(eb, ks, a)
     place = _place_biconcave if placement == "reject" else _place_biconcave_grid
     shapes = place(rng, nx, ny, count, a, n)
+    m0 = node_mass(density_ratio, signed_area(shapes[0]), n)
+    kb = kb_from_eb(stable_eb(eb, ks, a, shapes[0], m0), ks, a)
     caps = []
     for xy in shapes:
         m = node_mass(density_ratio, signed_area(xy), n)

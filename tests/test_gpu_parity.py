@@ -1,0 +1,228 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 CPU oracle on the
+same seeded inputs.
+
+Tolerances: FP64 storage, velocity within 1e-10 relative max-norm after 1000 steps;
+FP32 storage, within 1e-5; capsule Taylor deformation within 1e-4 absolute (FP32).
+Sizes span several warps per row, ragged row ends (nx not a multiple of the vector
+width) and multiple rows of capsules.
+"""
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_1903_03356_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_03356_gb300 import lbmib
+    return lbmib
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def oracle_sim(case):
+    L = o.lattice(case.nx, case.ny, case.tau, case.walls, case.u_bottom, case.u_top, case.gx, case.gy)
+    s = o.Sim(L)
+    s.init_fields(*case.fields())
+    for c in case.capsules:
+        s.add_capsule(c.xy, c.ks, c.kb, c.ka, c.mass)
+    return s
+
+
+def random_fields(nx, ny, seed, amp=0.01):
+    rng = np.random.default_rng(seed)
+    rho = 1 + amp * rng.standard_normal((ny, nx))
+    ux = amp * rng.standard_normal((ny, nx))
+    uy = amp * rng.standard_normal((ny, nx))
+    return rho, ux, uy
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+@pytest.mark.parametrize("nx,ny,walls,ub,ut,gx,gy", [
+    (67, 45, True, -0.01, 0.02, 2e-6, -1e-6),      # moving walls, ragged rows
+    (130, 40, False, 0.0, 0.0, 2e-5, -1e-5),       # periodic, force-driven, two warps per row
+    (257, 33, True, 0.015, -0.015, 0.0, 0.0),      # Couette-like, ragged rows
+])
+def test_lattice_update_matches_oracle(L, storage, nx, ny, walls, ub, ut, gx, gy):
+    # a sustained flow (walls or body force) with a seeded perturbation on top: the
+    # relative error is measured against a velocity scale that does not decay away
+    case = W.Case("lattice", nx, ny, 0.7, walls, ub, ut, gx=gx, gy=gy)
+    rho, ux, uy = random_fields(nx, ny, 3, amp=0.005)
+    ctx = L.from_case(case, storage=storage)
+    ctx.init_fields(rho, ux, uy)
+    s = oracle_sim(case)
+    s.init_fields(rho, ux, uy)
+    ctx.step(1000)
+    s.step(1000, o.KINEMATIC)
+    r_g, u_g, v_g = ctx.read_fields()
+    r_o, u_o, v_o = s.read_fields()
+    vel_g, vel_o = np.stack([u_g, v_g]), np.stack([u_o, v_o])
+    err = rel(vel_g, vel_o)
+    print(f"{storage} {nx}x{ny}: velocity rel err {err:.3e}")
+    assert err < TOL[storage]
+    assert np.abs(r_g - r_o).max() < (1e-12 if storage == "fp64" else 1e-6)
+
+
+def test_populations_after_one_step_match_oracle(L):
+    case = W.Case("lattice", 37, 21, 0.83, True, 0.013, -0.021, gx=1e-5, gy=3e-6)
+    rho, ux, uy = random_fields(37, 21, 4, amp=0.03)
+    ctx = L.from_case(case, storage="fp64")
+    ctx.init_fields(rho, ux, uy)
+    f0 = ctx.read_populations()
+    np.testing.assert_allclose(f0, o.init_equilibrium(o.lattice(37, 21, 0.83, True, 0.013, -0.021,
+                                                                1e-5, 3e-6), rho, ux, uy), atol=1e-15)
+    ctx.step(1)
+    Lo = o.lattice(37, 21, 0.83, True, 0.013, -0.021, 1e-5, 3e-6)
+    np.testing.assert_allclose(ctx.read_populations(), o.collide_stream(Lo, f0), atol=2e-16)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_interpolation_matches_oracle(L, storage):
+    case = W.Case("lattice", 48, 40, 0.8, True, -0.01, 0.01, gx=1e-5)
+    rho, ux, uy = random_fields(48, 40, 5, amp=0.02)
+    ctx = L.from_case(case, storage=storage, extra_nodes=64)
+    ctx.init_fields(rho, ux, uy)
+    ctx.step(3)
+    s = oracle_sim(case)
+    s.init_fields(rho, ux, uy)
+    s.step(3, o.KINEMATIC)
+    rng = np.random.default_rng(6)
+    pts = np.stack([rng.uniform(-5, 53, 64), rng.uniform(1.6, 37.4, 64)], 1)
+    got = ctx.interpolate(pts)
+    f = s.populations()
+    exp = np.array([o.interp(s.L, f, s.force_field(), x, y)[0] for x, y in pts])
+    tol = 1e-13 if storage == "fp64" else 2e-6
+    np.testing.assert_allclose(got[:, :4], exp[:, :4], atol=tol)
+    np.testing.assert_allclose(got[:, 4:], exp[:, 4:], atol=tol * 10)
+
+
+def _capsule_case(scheme, nx=100, ny=100):
+    if scheme == o.KINEMATIC:
+        return W.shear_capsule(nx=nx, ny=ny, ca=1e-3, scheme=o.KINEMATIC)
+    # near the centre line: inside the Dynamic scheme's stable window for > 1500 steps
+    return W.poiseuille_capsule(nx=160, ny=64, radius=8.0, n=48, ca=1e-2, y_frac=0.45, scheme=o.DYNAMIC)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+@pytest.mark.parametrize("scheme", [o.KINEMATIC, o.DYNAMIC])
+def test_coupled_step_matches_oracle(L, storage, scheme):
+    case = _capsule_case(scheme)
+    ctx = L.from_case(case, storage=storage)
+    s = oracle_sim(case)
+    T = 1000
+    ctx.step(T, scheme)
+    assert s.step(T, scheme) == 0
+    r_g, u_g, v_g = ctx.read_fields()
+    r_o, u_o, v_o = s.read_fields()
+    err = rel(np.stack([u_g, v_g]), np.stack([u_o, v_o]))
+    print(f"{storage} scheme {scheme}: velocity rel err {err:.3e}")
+    assert err < TOL[storage]
+    xy_g, vel_g, fi_g, fe_g = ctx.read_capsule(0)
+    xy_o, vel_o, fi_o, fe_o = s.read_capsule(0)
+    assert np.abs(xy_g - xy_o).max() < (1e-9 if storage == "fp64" else 1e-4)
+    ob_g, ob_o = ctx.observables(0), s.observables(0)
+    assert abs(ob_g[2] - ob_o[2]) < (1e-10 if storage == "fp64" else 1e-4)    # Taylor D
+    if storage == "fp64":
+        np.testing.assert_allclose(fi_g, fi_o, atol=1e-12 * max(1.0, np.abs(fi_o).max()))
+        np.testing.assert_allclose(fe_g, fe_o, atol=1e-12)
+        np.testing.assert_allclose(ob_g, ob_o, rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_many_biconcave_capsules_match_oracle(L, storage):
+    case = W.poiseuille_biconcave(nx=300, ny=96, count=6, n=64, seed=0, scheme=o.DYNAMIC)
+    ctx = L.from_case(case, storage=storage)
+    s = oracle_sim(case)
+    ctx.step(200, o.DYNAMIC)
+    assert s.step(200, o.DYNAMIC) == 0
+    _, u_g, v_g = ctx.read_fields()
+    _, u_o, v_o = s.read_fields()
+    assert rel(np.stack([u_g, v_g]), np.stack([u_o, v_o])) < TOL[storage]
+    for k in range(len(case.capsules)):
+        assert np.abs(ctx.read_capsule(k)[0] - s.read_capsule(k)[0]).max() < (1e-9 if storage == "fp64" else 1e-4)
+        assert abs(ctx.observables(k)[2] - s.observables(k)[2]) < (1e-10 if storage == "fp64" else 1e-4)
+
+
+def test_fp16_storage_error_is_reported(L):
+    # FP16 storage is lossy by design; its error against the oracle is measured, with a
+    # loose sanity bound only.
+    case = _capsule_case(o.KINEMATIC)
+    ctx = L.from_case(case, storage="fp16")
+    s = oracle_sim(case)
+    ctx.step(200, o.KINEMATIC)
+    s.step(200, o.KINEMATIC)
+    _, u_g, v_g = ctx.read_fields()
+    _, u_o, v_o = s.read_fields()
+    err = rel(np.stack([u_g, v_g]), np.stack([u_o, v_o]))
+    print(f"fp16 relative velocity error after 200 steps: {err:.3e}")
+    assert err < 5e-2
+
+
+def test_graph_replay_equals_direct_launches(L):
+    case = _capsule_case(o.DYNAMIC)
+    a = L.from_case(case, storage="fp64")
+    b = L.from_case(case, storage="fp64")
+    b.set_option(L.OPT_GRAPHS, 0)
+    a.set_option(L.OPT_GRAPH_STEPS, 8)
+    a.step(37, o.DYNAMIC)
+    b.step(37, o.DYNAMIC)
+    np.testing.assert_allclose(a.read_fields()[1], b.read_fields()[1], atol=1e-15)
+    np.testing.assert_allclose(a.read_capsule(0)[0], b.read_capsule(0)[0], atol=1e-12)
+
+
+def test_checkpoint_restart_matches_a_straight_run(L):
+    case = _capsule_case(o.DYNAMIC)
+    a = L.from_case(case, storage="fp64")
+    a.step(50, o.DYNAMIC)
+    snap = a.save_state()
+    a.step(50, o.DYNAMIC)
+    b = L.from_case(case, storage="fp64")
+    b.load_state(snap)
+    b.step(50, o.DYNAMIC)
+    np.testing.assert_allclose(b.read_fields()[1], a.read_fields()[1], atol=1e-14)
+    np.testing.assert_allclose(b.read_capsule(0)[0], a.read_capsule(0)[0], atol=1e-12)
+
+
+def test_support_leaving_the_channel_is_reported(L):
+    case = W.Case("wall", 40, 30, 0.7, True)
+    ctx = L.from_case(case, storage="fp32", extra_nodes=24, extra_capsules=1)
+    ctx.add_capsule(W.circle(24, 5.0, 20.2, 5.3), 0.2, 0.01, 0.0, 3.0)
+    ctx.step(1, o.KINEMATIC)
+    with pytest.raises(L.LbmibError) as e:
+        ctx.sync()
+    assert e.value.status == L.ERR_SUPPORT
+
+
+def test_unstable_velocity_is_reported(L):
+    case = W.Case("fast", 32, 32, 0.6, False)
+    ctx = L.from_case(case, storage="fp32")
+    ctx.init_fields(None, np.full((32, 32), 0.4), None)
+    ctx.step(1)
+    with pytest.raises(L.LbmibError) as e:
+        ctx.sync()
+    assert e.value.status == L.ERR_UNSTABLE
+
+
+@pytest.mark.parametrize("scheme", [o.KINEMATIC, o.DYNAMIC])
+def test_capsule_larger_than_the_tile_takes_the_global_path(L, scheme):
+    # radius 26: the bounding box (about 58 x 58 nodes) exceeds the per-capsule tile, so
+    # the kernels gather and spread through global memory; results are the same
+    case = W.shear_capsule(nx=96, ny=96, radius=26.0, n=160, ca=1e-2, scheme=scheme)
+    ctx = L.from_case(case, storage="fp64")
+    s = oracle_sim(case)
+    ctx.step(300, scheme)
+    assert s.step(300, scheme) == 0
+    _, u_g, v_g = ctx.read_fields()
+    _, u_o, v_o = s.read_fields()
+    assert rel(np.stack([u_g, v_g]), np.stack([u_o, v_o])) < 1e-10
+    assert np.abs(ctx.read_capsule(0)[0] - s.read_capsule(0)[0]).max() < 1e-9
