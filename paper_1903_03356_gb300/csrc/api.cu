@@ -104,6 +104,8 @@ struct lbmib_ctx {
     double* pts_out = nullptr;
     std::vector<CapsuleParams> caps;
     int max_n = 0;
+    double max_extent = 0.0;  // largest reference diameter of a capsule
+    int tile_cells = 256;     // per-capsule shared tile budget
     int cur = 0;      // population buffer holding the latest post-collision state
     int cur_fib = 0;  // force buffer holding the last spread force
     long long steps = 0;
@@ -166,13 +168,13 @@ void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
     if (ncaps > 0) {
         if (scheme == LBMIB_DYNAMIC) {
             if (st == LBMIB_FP64)
-                launch_dyn_force_spread<double>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, sp, status, s);
+                launch_dyn_force_spread<double>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->tile_cells, sp, status, s);
             else if (st == LBMIB_FP32)
-                launch_dyn_force_spread<float>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, sp, status, s);
+                launch_dyn_force_spread<float>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->tile_cells, sp, status, s);
             else
-                launch_dyn_force_spread<__half>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, sp, status, s);
+                launch_dyn_force_spread<__half>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->tile_cells, sp, status, s);
         } else {
-            launch_kin_force_spread(L, c->nd, ncaps, c->max_n, sp, status, st == LBMIB_FP64, s);
+            launch_kin_force_spread(L, c->nd, ncaps, c->max_n, c->tile_cells, sp, status, st == LBMIB_FP64, s);
         }
         c->launches++;
     }
@@ -204,13 +206,13 @@ void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
             launch_patch<__half>(src, dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->ctr, fc, cap, s);
         int* reset = &c->ctr->count[fp];
         if (scheme == LBMIB_DYNAMIC) {
-            if (st == LBMIB_FP64) launch_dyn_update<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, reset, status, s);
-            else if (st == LBMIB_FP32) launch_dyn_update<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, reset, status, s);
-            else launch_dyn_update<__half>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, reset, status, s);
+            if (st == LBMIB_FP64) launch_dyn_update<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, reset, status, s);
+            else if (st == LBMIB_FP32) launch_dyn_update<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, reset, status, s);
+            else launch_dyn_update<__half>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, reset, status, s);
         } else {
-            if (st == LBMIB_FP64) launch_kin_advance<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, reset, status, s);
-            else if (st == LBMIB_FP32) launch_kin_advance<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, reset, status, s);
-            else launch_kin_advance<__half>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, reset, status, s);
+            if (st == LBMIB_FP64) launch_kin_advance<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, reset, status, s);
+            else if (st == LBMIB_FP32) launch_kin_advance<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, reset, status, s);
+            else launch_kin_advance<__half>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, reset, status, s);
         }
         c->launches += 2;
         cur_fib = fc;
@@ -317,13 +319,18 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     L.scale = cfg->storage == LBMIB_FP16 ? 1024.0f : 1.0f;
     L.inv_scale = 1.0f / L.scale;
     L.nu = (cfg->tau - 0.5) / 3.0;
+    L.gxf = (float)L.gx;
+    L.gyf = (float)L.gy;
+    L.omegaf = (float)L.omega;
+    L.ubf = (float)L.ub;
+    L.utf = (float)L.ut;
 
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete c;
         return LBMIB_ERR_CUDA;
     }
-    set_capsule_smem_limits(kMaxRing);
+    set_capsule_smem_limits(1, c->tile_cells);
     const size_t N = (size_t)cfg->nx * cfg->ny;
     e = cudaMemsetAsync(c->fib[0], 0, 2 * N * sizeof(double), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->fib[1], 0, 2 * N * sizeof(double), c->stream);
@@ -436,6 +443,17 @@ lbmib_status lbmib_add_capsule(lbmib_ctx* c, const double* xy, int n, double ks,
     c->caps.push_back(P);
     c->nd.count += n;
     if (n > c->max_n) c->max_n = n;
+    // reference extent: the diagonal of the bounding box (an upper bound of the diameter,
+    // so any rotation of the ring fits a square of this side)
+    double x0 = xy[0], x1 = xy[0], y0 = xy[1], y1 = xy[1];
+    for (int a = 1; a < n; a++) {
+        x0 = std::fmin(x0, xy[2 * a]); x1 = std::fmax(x1, xy[2 * a]);
+        y0 = std::fmin(y0, xy[2 * a + 1]); y1 = std::fmax(y1, xy[2 * a + 1]);
+    }
+    const double ext = std::hypot(x1 - x0, y1 - y0);
+    if (ext > c->max_extent) c->max_extent = ext;
+    c->tile_cells = tile_budget(c->max_n, c->max_extent);
+    set_capsule_smem_limits(c->max_n, c->tile_cells);
     drop_graphs(c);  // launch shapes changed
     if (id_out) *id_out = id;
     return LBMIB_OK;

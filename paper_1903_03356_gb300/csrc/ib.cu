@@ -90,8 +90,9 @@ struct Tile {
     C* drho;
     C* ux;
     C* uy;
-    double* fx;
-    double* fy;
+    C* fx;              // force accumulators (compute type)
+    C* fy;
+    int* cells;         // scratch for the flush (aliases the moment arrays)
 
     __device__ __forceinline__ int index(int x, int y) const { return (y - y0) * w + (x - x0); }
     // the 3x3 support centred on (cx, cy) lies inside the tile
@@ -124,10 +125,12 @@ __device__ Tile<C> make_tile(const CapSmem& sm, int n, int margin, int tile_cell
     unsigned char* p = sm.tile;
     t.drho = t.ux = t.uy = nullptr;
     t.fx = t.fy = nullptr;
+    t.cells = reinterpret_cast<int*>(p);
     if (forces) {
-        t.fx = reinterpret_cast<double*>(p);
+        t.fx = reinterpret_cast<C*>(p);
         t.fy = t.fx + tile_cells;
-        p += 2 * sizeof(double) * (size_t)tile_cells;
+        p += 2 * sizeof(C) * (size_t)tile_cells;
+        t.cells = reinterpret_cast<int*>(p);   // behind the accumulators
     }
     if (moments) {
         t.drho = reinterpret_cast<C*>(p);
@@ -156,8 +159,8 @@ template <typename C>
 __device__ void zero_forces(Tile<C>& t) {
     const int cells = t.w * t.h;
     for (int k = threadIdx.x; k < cells; k += blockDim.x) {
-        t.fx[k] = 0.0;
-        t.fy[k] = 0.0;
+        t.fx[k] = C(0);
+        t.fy[k] = C(0);
     }
 }
 
@@ -169,19 +172,34 @@ __device__ __forceinline__ void touch(const Spread& sp, int cell, int stamp) {
     }
 }
 
-// Add the force tile to the lattice force field and record the touched nodes.
+// Add the force tile to the lattice force field and record the touched nodes. The
+// nodes new to this step's list are collected in shared memory first and appended with
+// one global reservation per capsule, so that the list counter is not a hot spot.
+// Collective (all threads); the moment arrays are dead by now and hold the scratch.
 template <typename C>
-__device__ void flush_forces(const Tile<C>& t, const Lat& L, const Spread& sp, int stamp) {
+__device__ void flush_forces(const Tile<C>& t, const Lat& L, const Spread& sp, int stamp, int* s_count) {
     const long long N = (long long)L.nx * L.ny;
     const int cells = t.w * t.h;
+    if (threadIdx.x == 0) *s_count = 0;
+    __syncthreads();
     for (int k = threadIdx.x; k < cells; k += blockDim.x) {
-        const double fx = t.fx[k], fy = t.fy[k];
+        const double fx = (double)t.fx[k], fy = (double)t.fy[k];
         if (fx == 0.0 && fy == 0.0) continue;
         const int j = k / t.w, i = k - j * t.w;
         const int cell = support_row(L, t.y0 + j) * L.nx + wrapi(t.x0 + i, L.nx);
         atomicAdd(sp.fib + cell, fx);
         atomicAdd(sp.fib + N + cell, fy);
-        touch(sp, cell, stamp);
+        if (atomicExch(&sp.mark[cell], stamp) != stamp) t.cells[atomicAdd(s_count, 1)] = cell;
+    }
+    __syncthreads();
+    const int nnew = *s_count;
+    __shared__ int s_base;
+    if (threadIdx.x == 0) s_base = nnew > 0 ? atomicAdd(sp.count, nnew) : 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < nnew; k += blockDim.x) {
+        const int p = s_base + k;
+        if (p < sp.capacity) sp.list[p] = t.cells[k];
+        else atomicOr(sp.status, kStatList);
     }
 }
 
@@ -221,11 +239,11 @@ __device__ __forceinline__ bool spread_at(Tile<C>& t, const Lat& L, const Spread
     for (int b = 0; b < 3; b++) {
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            const double w = c * m.phi(a, b);
+            const double w = c * (double)m.phi(a, b);
             if (in_tile) {
                 const int k = t.index(m.cx + a - 1, m.cy + b - 1);
-                atomicAdd(t.fx + k, w * Fx);
-                atomicAdd(t.fy + k, w * Fy);
+                atomicAdd(t.fx + k, C(w * Fx));
+                atomicAdd(t.fy + k, C(w * Fy));
             } else {
                 const int cell = support_row(L, m.cy + b - 1) * L.nx + wrapi(m.cx + a - 1, L.nx);
                 atomicAdd(sp.fib + cell, w * Fx);
@@ -242,21 +260,20 @@ __device__ __forceinline__ bool spread_at(Tile<C>& t, const Lat& L, const Spread
 __device__ __forceinline__ double ring_terms(const CapSmem& sm, const CapsuleParams& P, const Nodes& nd, int v) {
     const int n = P.n;
     const double2 Xv = sm.X[v], Xr = sm.X[v + 1 == n ? 0 : v + 1], Xl = sm.X[v == 0 ? n - 1 : v - 1];
-    // Eq. 11: element v joins v and v+1
-    const double2 d = Xr - Xv;
-    const double len = sqrt(d.x * d.x + d.y * d.y);
-    sm.sst[v] = -P.ks * (len - nd.L0[P.off + v]) / len;
+    const double2 a = Xv - Xl, b = Xr - Xv;   // incoming edge, outgoing edge (element v)
+    const double a2 = a.x * a.x + a.y * a.y, b2 = b.x * b.x + b.y * b.y;
+    const double ra = rsqrt(a2), rb = rsqrt(b2);   // 1/|a|, 1/|b|
+    // Eq. 11: element v joins v and v+1, length |b|
+    sm.sst[v] = -P.ks * (b2 * rb - nd.L0[P.off + v]) * rb;
     // Eq. 13 as F = -k_b sin(theta - theta_0) d(theta)/dX with theta the signed turning
     // angle at v; sin(theta - theta_0) from the cross and dot products and theta_0's
     // stored cosine and sine.
-    const double2 a = Xv - Xl, b = d;
-    const double a2 = a.x * a.x + a.y * a.y, b2 = b.x * b.x + b.y * b.y;
     const double cr = a.x * b.y - a.y * b.x, dt = a.x * b.x + a.y * b.y;
-    const double rn = 1.0 / sqrt(a2 * b2);
-    const double sdiff = (cr * nd.c0[P.off + v] - dt * nd.s0[P.off + v]) * rn;
+    const double sdiff = (cr * nd.c0[P.off + v] - dt * nd.s0[P.off + v]) * (ra * rb);
     sm.bs[v] = P.kb * sdiff;
-    sm.bdl[v] = make_double2(-a.y / a2, a.x / a2);
-    sm.bdr[v] = make_double2(-b.y / b2, b.x / b2);
+    const double ia2 = ra * ra, ib2 = rb * rb;
+    sm.bdl[v] = make_double2(-a.y * ia2, a.x * ia2);
+    sm.bdr[v] = make_double2(-b.y * ib2, b.x * ib2);
     const double2 X0 = sm.X[0];
     return (Xv.x - X0.x) * (Xr.y - X0.y) - (Xr.x - X0.x) * (Xv.y - X0.y);
 }
@@ -331,7 +348,7 @@ __global__ void __launch_bounds__(128) k_dyn_force_spread(const S* __restrict__ 
         ok &= spread_at<C>(t, L, sp, stamp, Xv.x, Xv.y, uv.x - o.ux, uv.y - o.uy, cl);
     }
     __syncthreads();
-    if (t.use) flush_forces<C>(t, L, sp, stamp);
+    if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
     if (!ok) atomicOr(status, kStatSupport);
 }
 
@@ -425,7 +442,7 @@ __global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int m
         ok &= spread_at<C>(t, L, sp, stamp, sm.X[v].x, sm.X[v].y, F.x, F.y, 1.0);
     }
     __syncthreads();
-    if (t.use) flush_forces<C>(t, L, sp, stamp);
+    if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
     if (!ok) atomicOr(status, kStatSupport);
 }
 
@@ -527,67 +544,91 @@ __global__ void k_interp_points(const S* __restrict__ src, Lat L, const double* 
 }
 
 // ---------------------------------------------------------------------------------
-// Host launchers. The tile budget is kTileCells lattice nodes per capsule CTA.
+// Host launchers. `tile_cells` is the per-capsule tile budget chosen by the host from
+// the capsules' reference extent (tile_budget()).
 // ---------------------------------------------------------------------------------
-constexpr int kTileCells = 2304;
-
 static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// keep well clear of the 227 KB opt-in limit (static shared variables come on top)
+constexpr size_t kSmemLimit = 200 * 1024;
+
 template <typename C>
-static size_t tile_bytes(bool moments, bool forces) {
-    return (size_t)kTileCells * ((moments ? 3 * sizeof(C) : 0) + (forces ? 2 * sizeof(double) : 0));
+static size_t tile_bytes(int cells, bool moments, bool forces) {
+    // the flush scratch (one int per cell) lives in the moment arrays or behind the
+    // force accumulators
+    const size_t m = moments ? 3 * sizeof(C) : 0;
+    const size_t f = forces ? 2 * sizeof(C) + (moments ? 0 : sizeof(int)) : 0;
+    return (size_t)cells * (m + f);
 }
 
-template <typename S>
-static size_t smem_dyn_spread(int max_n) { return ring_smem_bytes(max_n) + tile_bytes<typename St<S>::C>(true, true); }
-template <typename S>
-static size_t smem_moments(int max_n) { return ring_smem_bytes(max_n) + tile_bytes<typename St<S>::C>(true, false); }
 template <typename C>
-static size_t smem_forces(int max_n) { return ring_smem_bytes(max_n) + tile_bytes<C>(false, true); }
+static size_t smem_bytes(int max_n, int cells, bool moments, bool forces) {
+    return ring_smem_bytes(max_n) + tile_bytes<C>(cells, moments, forces);
+}
 
-void set_capsule_smem_limits(int max_n) {
-    cudaFuncSetAttribute(k_dyn_force_spread<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dyn_spread<double>(max_n));
-    cudaFuncSetAttribute(k_dyn_force_spread<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dyn_spread<float>(max_n));
-    cudaFuncSetAttribute(k_dyn_force_spread<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dyn_spread<__half>(max_n));
-    cudaFuncSetAttribute(k_dyn_update<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_moments<double>(max_n));
-    cudaFuncSetAttribute(k_dyn_update<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_moments<float>(max_n));
-    cudaFuncSetAttribute(k_dyn_update<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_moments<__half>(max_n));
-    cudaFuncSetAttribute(k_kin_advance<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_moments<double>(max_n));
-    cudaFuncSetAttribute(k_kin_advance<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_moments<float>(max_n));
-    cudaFuncSetAttribute(k_kin_advance<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_moments<__half>(max_n));
-    cudaFuncSetAttribute(k_kin_force_spread<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_forces<double>(max_n));
-    cudaFuncSetAttribute(k_kin_force_spread<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_forces<float>(max_n));
+int tile_budget(int max_n, double extent) {
+    // any rotation of the reference ring, probes and supports (3 nodes each side), and
+    // room for deformation
+    const double side = extent + 8.0;
+    long long cells = (long long)(1.5 * side * side);
+    if (cells < 256) cells = 256;
+    const size_t free_b = kSmemLimit - ring_smem_bytes(max_n);
+    const long long cap = (long long)(free_b / (3 * sizeof(double) + 2 * sizeof(double)));
+    if (cells > cap) cells = cap;
+    return (int)cells;
+}
+
+void set_capsule_smem_limits(int max_n, int cells) {
+#define LBMIB_SMEM(K, C, M, F) \
+    cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<C>(max_n, cells, M, F))
+    LBMIB_SMEM(k_dyn_force_spread<double>, double, true, true);
+    LBMIB_SMEM(k_dyn_force_spread<float>, float, true, true);
+    LBMIB_SMEM(k_dyn_force_spread<__half>, float, true, true);
+    LBMIB_SMEM(k_dyn_update<double>, double, true, false);
+    LBMIB_SMEM(k_dyn_update<float>, float, true, false);
+    LBMIB_SMEM(k_dyn_update<__half>, float, true, false);
+    LBMIB_SMEM(k_kin_advance<double>, double, true, false);
+    LBMIB_SMEM(k_kin_advance<float>, float, true, false);
+    LBMIB_SMEM(k_kin_advance<__half>, float, true, false);
+    LBMIB_SMEM(k_kin_force_spread<double>, double, false, true);
+    LBMIB_SMEM(k_kin_force_spread<float>, float, false, true);
+#undef LBMIB_SMEM
     cudaFuncSetAttribute(k_observables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring_smem_bytes(max_n));
 }
 
 template <typename S>
 void launch_dyn_force_spread(const void* src, const Lat& L, const double* fib_prev, Nodes nd, int ncaps, int max_n,
-                             Spread sp, unsigned* status, cudaStream_t s) {
-    k_dyn_force_spread<S><<<ncaps, 128, smem_dyn_spread<S>(max_n), s>>>((const S*)src, L, fib_prev, nd, max_n,
-                                                                        kTileCells, sp, status);
+                             int cells, Spread sp, unsigned* status, cudaStream_t s) {
+    using C = typename St<S>::C;
+    k_dyn_force_spread<S><<<ncaps, 128, smem_bytes<C>(max_n, cells, true, true), s>>>(
+        (const S*)src, L, fib_prev, nd, max_n, cells, sp, status);
 }
 
 template <typename S>
 void launch_dyn_update(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
-                       int* reset_count, unsigned* status, cudaStream_t s) {
-    k_dyn_update<S><<<ncaps, 128, smem_moments<S>(max_n), s>>>((const S*)dst, L, fib_cur, nd, max_n, kTileCells,
-                                                               reset_count, status);
+                       int cells, int* reset_count, unsigned* status, cudaStream_t s) {
+    using C = typename St<S>::C;
+    k_dyn_update<S><<<ncaps, 128, smem_bytes<C>(max_n, cells, true, false), s>>>(
+        (const S*)dst, L, fib_cur, nd, max_n, cells, reset_count, status);
 }
 
-void launch_kin_force_spread(const Lat& L, Nodes nd, int ncaps, int max_n, Spread sp, unsigned* status,
+void launch_kin_force_spread(const Lat& L, Nodes nd, int ncaps, int max_n, int cells, Spread sp, unsigned* status,
                              bool fp64_weights, cudaStream_t s) {
     // double MLS weights when the populations are double, float otherwise
     if (fp64_weights)
-        k_kin_force_spread<double><<<ncaps, 128, smem_forces<double>(max_n), s>>>(L, nd, max_n, kTileCells, sp, status);
+        k_kin_force_spread<double><<<ncaps, 128, smem_bytes<double>(max_n, cells, false, true), s>>>(
+            L, nd, max_n, cells, sp, status);
     else
-        k_kin_force_spread<float><<<ncaps, 128, smem_forces<float>(max_n), s>>>(L, nd, max_n, kTileCells, sp, status);
+        k_kin_force_spread<float><<<ncaps, 128, smem_bytes<float>(max_n, cells, false, true), s>>>(
+            L, nd, max_n, cells, sp, status);
 }
 
 template <typename S>
 void launch_kin_advance(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
-                        int* reset_count, unsigned* status, cudaStream_t s) {
-    k_kin_advance<S><<<ncaps, 128, smem_moments<S>(max_n), s>>>((const S*)dst, L, fib_cur, nd, max_n, kTileCells,
-                                                                reset_count, status);
+                        int cells, int* reset_count, unsigned* status, cudaStream_t s) {
+    using C = typename St<S>::C;
+    k_kin_advance<S><<<ncaps, 128, smem_bytes<C>(max_n, cells, true, false), s>>>(
+        (const S*)dst, L, fib_cur, nd, max_n, cells, reset_count, status);
 }
 
 void launch_observables(Nodes nd, int ncaps, int max_n, double* out, cudaStream_t s) {
@@ -601,11 +642,11 @@ void launch_interp_points(const void* src, const Lat& L, const double* fib, cons
 }
 
 #define LBMIB_INSTANTIATE_IB(S)                                                                              \
-    template void launch_dyn_force_spread<S>(const void*, const Lat&, const double*, Nodes, int, int, Spread, \
-                                             unsigned*, cudaStream_t);                                       \
-    template void launch_dyn_update<S>(const void*, const Lat&, const double*, Nodes, int, int, int*,        \
+    template void launch_dyn_force_spread<S>(const void*, const Lat&, const double*, Nodes, int, int, int,   \
+                                             Spread, unsigned*, cudaStream_t);                               \
+    template void launch_dyn_update<S>(const void*, const Lat&, const double*, Nodes, int, int, int, int*,   \
                                        unsigned*, cudaStream_t);                                             \
-    template void launch_kin_advance<S>(const void*, const Lat&, const double*, Nodes, int, int, int*,       \
+    template void launch_kin_advance<S>(const void*, const Lat&, const double*, Nodes, int, int, int, int*,  \
                                         unsigned*, cudaStream_t);                                            \
     template void launch_interp_points<S>(const void*, const Lat&, const double*, const double2*, int,       \
                                           double*, unsigned*, cudaStream_t);

@@ -121,7 +121,8 @@ struct PopLoad {
         constexpr int EX = ex(I);
         if (at_wall(L, y)) {  // warp-uniform
             constexpr int J = opp(I);
-            const C corr = C(6) * wgt<C>(J) * C(ex(J)) * C(y - ey(I) < 0 ? L.ub : L.ut);
+            const C uw = y - ey(I) < 0 ? lat_c<C>(L.ub, L.ubf) : lat_c<C>(L.ut, L.utf);
+            const C corr = C(6) * wgt<C>(J) * C(ex(J)) * uw;
 #pragma unroll
             for (int j = 0; j < V; j++) out[j] = v[j] - corr;
         } else if (EX == 0) {
@@ -143,7 +144,8 @@ struct PopLoad {
         if (active && !full) {  // ragged chunk: element-wise, with the pull's wrap
             const S* row = row_ptr(src, L, y);
             const bool wall = at_wall(L, y);
-            const C corr = wall ? C(6) * wgt<C>(opp(I)) * C(ex(opp(I))) * C(y - ey(I) < 0 ? L.ub : L.ut) : C(0);
+            const C uw = y - ey(I) < 0 ? lat_c<C>(L.ub, L.ubf) : lat_c<C>(L.ut, L.utf);
+            const C corr = wall ? C(6) * wgt<C>(opp(I)) * C(ex(opp(I))) * uw : C(0);
 #pragma unroll
             for (int j = 0; j < V; j++) {
                 const int x = x0 + j;
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(BS, MINB) k_collide_stream(const S* __restrict
     p6.resolve(src, L, x0, y, lane, active, full, f[6]); p7.resolve(src, L, x0, y, lane, active, full, f[7]);
     p8.resolve(src, L, x0, y, lane, active, full, f[8]);
 
-    const C gx = C(L.gx), gy = C(L.gy), om = C(L.omega);
+    const C gx = lat_c<C>(L.gx, L.gxf), gy = lat_c<C>(L.gy, L.gyf), om = lat_c<C>(L.omega, L.omegaf);
     bool bad = false;
 #pragma unroll
     for (int j = 0; j < V; j++) {

@@ -48,7 +48,17 @@ struct Lat {
     double gx, gy;        // uniform body-force density
     float scale, inv_scale;  // FP16 storage scale (1 for other storages)
     double nu;            // kinematic viscosity (tau - 1/2)/3
+    // float copies for single-precision kernels (a double-to-float conversion in every
+    // thread would occupy GB300's narrow FP64 pipe)
+    float gxf, gyf, omegaf, ubf, utf;
 };
+
+// Lattice constant in the compute type C.
+template <typename C>
+__device__ __forceinline__ C lat_c(double d, float f) {
+    if constexpr (sizeof(C) == 8) return d;
+    else return f;
+}
 
 // ---------------------------------------------------------------------------------
 // Storage traits: type S stored, type C computed in.
@@ -92,7 +102,7 @@ __device__ __forceinline__ typename St<S>::C pull(const S* __restrict__ src, con
     int ys = y - ey(i);
     if (L.walls && (ys < 0 || ys >= L.ny)) {
         const int j = opp(i);
-        const C uw = C(ys < 0 ? L.ub : L.ut);
+        const C uw = ys < 0 ? lat_c<C>(L.ub, L.ubf) : lat_c<C>(L.ut, L.utf);
         return St<S>::ld(src + (long long)j * L.plane + (long long)y * L.pitch + x, L) -
                C(6) * wgt<C>(j) * C(ex(j)) * uw;
     }
@@ -168,13 +178,12 @@ struct MlsW {
     int cx, cy;           // centre node (unwrapped)
     C wx[3], wy[3];       // axis weights, a or b = -1, 0, 1
     C dxp[3], dyp[3];     // centred offsets dx_a - mx, dy_b - my
-    double rS, rVx, rVy;  // 1/sum W, 1/sum W dx'^2, 1/sum W dy'^2
-    double mx, my;        // weighted mean offsets
+    C k0, kx, ky;         // value weights: phi_ab = wx_a wy_b (k0 + kx dxp_a + ky dyp_b)
+    C gx, gy;             // gradient weights: wx_a wy_b dxp_a gx, wx_a wy_b dyp_b gy
     bool ok;              // support inside the channel and the point sane
-    // phi_k (Eq. 8) and gradient weights of support node k = 3 (b+1) + (a+1)
-    __device__ __forceinline__ double phi(int a, int b) const {
-        const double w = (double)wx[a] * (double)wy[b];
-        return w * (rS - mx * (double)dxp[a] * rVx - my * (double)dyp[b] * rVy);
+    // phi_k (Eq. 8) of support node (cx + a - 1, cy + b - 1)
+    __device__ __forceinline__ C phi(int a, int b) const {
+        return wx[a] * wy[b] * (k0 + kx * dxp[a] + ky * dyp[b]);
     }
 };
 
@@ -192,38 +201,55 @@ __device__ __forceinline__ bool support_centre(const Lat& L, double& X, double& 
     return sane && (!L.walls || (cy >= 1 && cy <= L.ny - 2));
 }
 
+// Double reciprocal of a value known to lie well inside float range (the MLS weight
+// sums and variances, between about 0.05 and 10): a float seed refined by two Newton
+// steps r <- r (2 - x r), each of which doubles the number of correct bits (24 -> 48 ->
+// full double precision).
+__device__ __forceinline__ double rcp_bounded(double x) {
+    double r = (double)__frcp_rn((float)x);
+    r = r * (2.0 - x * r);
+    r = r * (2.0 - x * r);
+    return r;
+}
+
+// Shape functions of the point (X, Y). The offsets of the support from the point are
+// formed in double (positions are double) and then held in the compute type; weights,
+// sums and the application are in the compute type; the solve (three reciprocals and
+// the weighted means) is in double.
 template <typename C>
 __device__ __forceinline__ MlsW<C> mls_setup(const Lat& L, double X, double Y) {
     MlsW<C> m;
     m.ok = support_centre(L, X, Y, m.cx, m.cy);
-    double sx0 = 0, sx1 = 0, sy0 = 0, sy1 = 0;
-    C dx[3], dy[3];
+    const C d0x = C((double)m.cx - X), d0y = C((double)m.cy - Y);   // in [-1/2, 1/2]
+    C dx[3], dy[3], sx0 = 0, sx1 = 0, sy0 = 0, sy1 = 0;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        dx[a] = C((double)(m.cx + a - 1) - X);
-        dy[a] = C((double)(m.cy + a - 1) - Y);
+        dx[a] = d0x + C(a - 1);
+        dy[a] = d0y + C(a - 1);
         m.wx[a] = exp(-dx[a] * dx[a] * C(kMlsInvLen2));
         m.wy[a] = exp(-dy[a] * dy[a] * C(kMlsInvLen2));
-        sx0 += (double)m.wx[a];
-        sx1 += (double)m.wx[a] * (double)dx[a];
-        sy0 += (double)m.wy[a];
-        sy1 += (double)m.wy[a] * (double)dy[a];
+        sx0 += m.wx[a];
+        sx1 += m.wx[a] * dx[a];
+        sy0 += m.wy[a];
+        sy1 += m.wy[a] * dy[a];
     }
-    const double isx = 1.0 / sx0, isy = 1.0 / sy0;
-    m.mx = sx1 * isx;
-    m.my = sy1 * isy;
-    double vx = 0, vy = 0;
+    const double isx = rcp_bounded((double)sx0), isy = rcp_bounded((double)sy0);
+    const double mx = (double)sx1 * isx, my = (double)sy1 * isy;
+    C vx = 0, vy = 0;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        const double px = (double)dx[a] - m.mx, py = (double)dy[a] - m.my;
-        m.dxp[a] = C(px);
-        m.dyp[a] = C(py);
-        vx += (double)m.wx[a] * px * px;
-        vy += (double)m.wy[a] * py * py;
+        m.dxp[a] = C((double)dx[a] - mx);
+        m.dyp[a] = C((double)dy[a] - my);
+        vx += m.wx[a] * m.dxp[a] * m.dxp[a];
+        vy += m.wy[a] * m.dyp[a] * m.dyp[a];
     }
-    m.rS = isx * isy;
-    m.rVx = 1.0 / (vx * sy0);
-    m.rVy = 1.0 / (vy * sx0);
+    const double rVx = rcp_bounded((double)vx) * isy;   // 1 / sum W dx'^2
+    const double rVy = rcp_bounded((double)vy) * isx;   // 1 / sum W dy'^2
+    m.k0 = C(isx * isy);
+    m.kx = C(-mx * rVx);
+    m.ky = C(-my * rVy);
+    m.gx = C(rVx);
+    m.gy = C(rVy);
     return m;
 }
 
@@ -282,15 +308,13 @@ __device__ __forceinline__ void mls_apply(const MlsW<C>& m, Get&& get, Interp& o
             v0 += w * q.uy; v1 += wx * q.uy; v2 += wy * q.uy;
         }
     }
-    const double a1u = (double)u1 * m.rVx, a2u = (double)u2 * m.rVy;
-    const double a1v = (double)v1 * m.rVx, a2v = (double)v2 * m.rVy;
-    o.ux = (double)u0 * m.rS - m.mx * a1u - m.my * a2u;
-    o.uy = (double)v0 * m.rS - m.mx * a1v - m.my * a2v;
-    o.rho = 1.0 + (double)r0 * m.rS - m.mx * (double)r1 * m.rVx - m.my * (double)r2 * m.rVy;
+    o.ux = (double)(m.k0 * u0 + m.kx * u1 + m.ky * u2);
+    o.uy = (double)(m.k0 * v0 + m.kx * v1 + m.ky * v2);
+    o.rho = 1.0 + (double)(m.k0 * r0 + m.kx * r1 + m.ky * r2);
     o.p = o.rho / 3.0;
     if (GRAD) {
-        o.dudx = a1u; o.dudy = a2u;
-        o.dvdx = a1v; o.dvdy = a2v;
+        o.dudx = (double)(m.gx * u1); o.dudy = (double)(m.gy * u2);
+        o.dvdx = (double)(m.gx * v1); o.dvdy = (double)(m.gy * v2);
     }
 }
 

@@ -50,20 +50,21 @@ void launch_populations(const void* src, const Lat& L, int i0, double* out, cuda
 // ib.cu
 template <typename S>
 void launch_dyn_force_spread(const void* src, const Lat& L, const double* fib_prev, Nodes nd, int ncaps, int max_n,
-                             Spread sp, unsigned* status, cudaStream_t s);
+                             int cells, Spread sp, unsigned* status, cudaStream_t s);
 template <typename S>
 void launch_dyn_update(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
-                       int* reset_count, unsigned* status, cudaStream_t s);
-void launch_kin_force_spread(const Lat& L, Nodes nd, int ncaps, int max_n, Spread sp, unsigned* status,
+                       int cells, int* reset_count, unsigned* status, cudaStream_t s);
+void launch_kin_force_spread(const Lat& L, Nodes nd, int ncaps, int max_n, int cells, Spread sp, unsigned* status,
                              bool fp64_weights, cudaStream_t s);
 template <typename S>
 void launch_kin_advance(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
-                        int* reset_count, unsigned* status, cudaStream_t s);
+                        int cells, int* reset_count, unsigned* status, cudaStream_t s);
 void launch_observables(Nodes nd, int ncaps, int max_n, double* out, cudaStream_t s);
 template <typename S>
 void launch_interp_points(const void* src, const Lat& L, const double* fib, const double2* pts, int n,
                           double* out, unsigned* status, cudaStream_t s);
 size_t capsule_smem_bytes(int max_n);
-void set_capsule_smem_limits(int max_n);
+int tile_budget(int max_n, double extent);
+void set_capsule_smem_limits(int max_n, int tile_cells);
 
 }  // namespace lbmib
