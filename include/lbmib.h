@@ -165,9 +165,10 @@ lbmib_status lbmib_load_state(lbmib_ctx* ctx, const void* host_buf, size_t bytes
  *   LBMIB_OPT_GRAPH_STEPS   steps per captured graph (default 16).
  *   LBMIB_OPT_FP16_SCALE    log2 of the FP16 storage scale (default 10).
  *   LBMIB_OPT_LATTICE_VARIANT launch shape of the lattice-update kernel: bits 0-11 the
- *                           block size (64..512, multiple of 32; default 256), bit 16
- *                           streaming loads, bit 17 streaming stores. Results do not
- *                           depend on it; only speed does.                          */
+ *                           block size (128 or 256), bit 18 a register cap that keeps
+ *                           four blocks resident per SM instead of three. Default:
+ *                           128 threads, with the cap for FP32/FP16 storage. Results
+ *                           do not depend on it; only speed does.                   */
 enum {
     LBMIB_OPT_GRAPHS = 1,
     LBMIB_OPT_TIMING = 2,

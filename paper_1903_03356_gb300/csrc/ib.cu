@@ -207,7 +207,8 @@ __device__ void flush_forces(const Tile<C>& t, const Lat& L, const Spread& sp, i
 // capsule has no tile.
 template <typename S, bool GRAD>
 __device__ __forceinline__ bool interp_at(const Tile<typename St<S>::C>& t, const S* __restrict__ src, const Lat& L,
-                                          const double* __restrict__ fib, double X, double Y, Interp& o) {
+                                          const double* __restrict__ fib, double X, double Y,
+                                          InterpT<typename St<S>::C>& o) {
     using C = typename St<S>::C;
     if (!t.use) return mls_interp<S, GRAD>(src, L, fib, X, Y, o);
     const MlsW<C> m = mls_setup<C>(L, X, Y);
@@ -235,16 +236,18 @@ __device__ __forceinline__ bool spread_at(Tile<C>& t, const Lat& L, const Spread
     const MlsW<C> m = mls_setup<C>(L, X, Y);
     const long long N = (long long)L.nx * L.ny;
     const bool in_tile = t.holds(m.cx, m.cy);
+    const C cFx = C(c * Fx), cFy = C(c * Fy);
 #pragma unroll
     for (int b = 0; b < 3; b++) {
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            const double w = c * (double)m.phi(a, b);
+            const C phi = m.phi(a, b);
             if (in_tile) {
                 const int k = t.index(m.cx + a - 1, m.cy + b - 1);
-                atomicAdd(t.fx + k, C(w * Fx));
-                atomicAdd(t.fy + k, C(w * Fy));
+                atomicAdd(t.fx + k, phi * cFx);
+                atomicAdd(t.fy + k, phi * cFy);
             } else {
+                const double w = c * (double)phi;
                 const int cell = support_row(L, m.cy + b - 1) * L.nx + wrapi(m.cx + a - 1, L.nx);
                 atomicAdd(sp.fib + cell, w * Fx);
                 atomicAdd(sp.fib + N + cell, w * Fy);
@@ -330,22 +333,27 @@ __global__ void __launch_bounds__(128) k_dyn_force_spread(const S* __restrict__ 
         zero_forces<C>(t);
     }
     __syncthreads();
+    // element lengths, once per element (c_l of reading R4)
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const double2 d = sm.X[v + 1 == n ? 0 : v + 1] - sm.X[v];
+        sm.sst[v] = sqrt(d.x * d.x + d.y * d.y);
+    }
+    __syncthreads();
     const int stamp = *sp.stamp + 1;
     bool ok = true;
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
         const double2 Xv = sm.X[v];
-        const double2 Xl = sm.X[v == 0 ? n - 1 : v - 1], Xr = sm.X[v + 1 == n ? 0 : v + 1];
-        Interp o;
+        InterpT<C> o;
         ok &= interp_at<S, false>(t, src, L, fib_prev, Xv.x, Xv.y, o);
+        const double Ux = (double)o.ux, Uy = (double)o.uy;
         double2 uv = nd.uv[off + v];
         if (nd.age[off + v] == 0) {
-            uv = make_double2(o.ux, o.uy);
+            uv = make_double2(Ux, Uy);
             nd.uv[off + v] = uv;
             nd.Xm1[off + v] = Xv - uv;
         }
-        const double2 dl = Xv - Xl, dr = Xr - Xv;
-        const double cl = 0.5 * (sqrt(dl.x * dl.x + dl.y * dl.y) + sqrt(dr.x * dr.x + dr.y * dr.y));
-        ok &= spread_at<C>(t, L, sp, stamp, Xv.x, Xv.y, uv.x - o.ux, uv.y - o.uy, cl);
+        const double cl = 0.5 * (sm.sst[v == 0 ? n - 1 : v - 1] + sm.sst[v]);
+        ok &= spread_at<C>(t, L, sp, stamp, Xv.x, Xv.y, uv.x - Ux, uv.y - Uy, cl);
     }
     __syncthreads();
     if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
@@ -371,27 +379,31 @@ __global__ void __launch_bounds__(128) k_dyn_update(const S* __restrict__ dst, L
     __syncthreads();
     bool ok = true;
     double area2[1] = {0.0};
+    const C nu = C(L.nu);
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
         const double2 Xv = sm.X[v], Xr = sm.X[v + 1 == n ? 0 : v + 1];
-        Interp o;
+        InterpT<C> o;
         ok &= interp_at<S, false>(t, dst, L, fib, Xv.x, Xv.y, o);
-        sm.xd[v] = make_double2(o.ux, o.uy);
+        sm.xd[v] = make_double2((double)o.ux, (double)o.uy);
         // element v: probes at the centroid +/- 1.2 n+ (Section 2.2.2)
         const double2 d = Xr - Xv;
-        const double len = sqrt(d.x * d.x + d.y * d.y);
-        const double npx = d.y / len, npy = -d.x / len;
+        const double rl = rsqrt(d.x * d.x + d.y * d.y);
+        const double npx = d.y * rl, npy = -d.x * rl;
         const double cx = 0.5 * (Xv.x + Xr.x), cy = 0.5 * (Xv.y + Xr.y);
-        Interp op, om;
+        InterpT<C> op, om;
         ok &= interp_at<S, true>(t, dst, L, fib, cx + 1.2 * npx, cy + 1.2 * npy, op);
         ok &= interp_at<S, true>(t, dst, L, fib, cx - 1.2 * npx, cy - 1.2 * npy, om);
-        // tau = rho nu (grad u + grad u^T) at each probe; Eq. 15 + Eq. 16
-        const double mp = op.rho * L.nu, mm = om.rho * L.nu;
-        const double txx = 2.0 * (mp * op.dudx - mm * om.dudx);
-        const double tyy = 2.0 * (mp * op.dvdy - mm * om.dvdy);
-        const double txy = mp * (op.dudy + op.dvdx) - mm * (om.dudy + om.dvdx);
-        const double dp = op.p - om.p;
-        sm.ext[v] = make_double2((-dp * npx + txx * npx + txy * npy) * len,
-                                 (-dp * npy + txy * npx + tyy * npy) * len);
+        // tau = rho nu (grad u + grad u^T) at each probe; Eq. 15 + Eq. 16 (per unit
+        // length, then times the element length)
+        const C mp = op.rho * nu, mm = om.rho * nu;
+        const C txx = C(2) * (mp * op.dudx - mm * om.dudx);
+        const C tyy = C(2) * (mp * op.dvdy - mm * om.dvdy);
+        const C txy = mp * (op.dudy + op.dvdx) - mm * (om.dudy + om.dvdx);
+        const C dp = op.p - om.p;
+        const C nx = C(npx), ny = C(npy);
+        const double len = (d.x * d.x + d.y * d.y) * rl;
+        sm.ext[v] = make_double2((double)(-dp * nx + txx * nx + txy * ny) * len,
+                                 (double)(-dp * ny + txy * nx + tyy * ny) * len);
         area2[0] += ring_terms(sm, P, nd, v);
     }
     block_reduce<1, false>(area2, sm.red);
@@ -465,19 +477,20 @@ __global__ void __launch_bounds__(128) k_kin_advance(const S* __restrict__ dst, 
     bool ok = true;
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
         const double2 Xv = sm.X[v];
-        Interp o;
+        InterpT<C> o;
         ok &= interp_at<S, false>(t, dst, L, fib, Xv.x, Xv.y, o);
+        const double Ux = (double)o.ux, Uy = (double)o.uy;
         double2 Xn;
         if (nd.age[off + v] == 0) {
-            Xn = make_double2(Xv.x + o.ux, Xv.y + o.uy);
+            Xn = make_double2(Xv.x + Ux, Xv.y + Uy);
         } else {
             const double2 Xm = nd.Xm1[off + v];
-            Xn = make_double2((2.0 / 3.0) * (2.0 * Xv.x - 0.5 * Xm.x + o.ux),
-                              (2.0 / 3.0) * (2.0 * Xv.y - 0.5 * Xm.y + o.uy));
+            Xn = make_double2((2.0 / 3.0) * (2.0 * Xv.x - 0.5 * Xm.x + Ux),
+                              (2.0 / 3.0) * (2.0 * Xv.y - 0.5 * Xm.y + Uy));
         }
         nd.Xm1[off + v] = Xv;
         nd.X[off + v] = Xn;
-        nd.uv[off + v] = make_double2(o.ux, o.uy);
+        nd.uv[off + v] = make_double2(Ux, Uy);
         nd.age[off + v] += 1;
     }
     if (!ok) atomicOr(status, kStatSupport);
@@ -535,7 +548,7 @@ __global__ void k_interp_points(const S* __restrict__ src, Lat L, const double* 
                                 unsigned* status) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n) return;
-    Interp o;
+    InterpT<typename St<S>::C> o;
     const bool ok = mls_interp<S, true>(src, L, fib, pts[m].x, pts[m].y, o);
     double* r = out + 8 * (long long)m;
     r[0] = o.ux; r[1] = o.uy; r[2] = o.rho; r[3] = o.p;

@@ -253,10 +253,13 @@ __device__ __forceinline__ MlsW<C> mls_setup(const Lat& L, double X, double Y) {
     return m;
 }
 
-struct Interp {
-    double ux, uy, rho, p;
-    double dudx, dudy, dvdx, dvdy;
+// Interpolated fluid quantities (Eq. 8) in the compute type.
+template <typename C>
+struct InterpT {
+    C ux, uy, rho, p;
+    C dudx, dudy, dvdx, dvdy;
 };
+using Interp = InterpT<double>;
 
 // Lattice moments at a node: density deviation and the Eq. 7 velocity (half of the
 // uniform force plus the immersed-boundary force field).
@@ -294,7 +297,7 @@ __device__ __forceinline__ int support_row(const Lat& L, int yk) {
 // MLS interpolation (Eq. 8) from a moment source get(a, b) -> Mom for support node
 // (cx + a - 1, cy + b - 1). Values in double, sums in the compute type.
 template <typename C, bool GRAD, typename Get>
-__device__ __forceinline__ void mls_apply(const MlsW<C>& m, Get&& get, Interp& o) {
+__device__ __forceinline__ void mls_apply(const MlsW<C>& m, Get&& get, InterpT<C>& o) {
     C r0 = 0, r1 = 0, r2 = 0, u0 = 0, u1 = 0, u2 = 0, v0 = 0, v1 = 0, v2 = 0;
 #pragma unroll
     for (int b = 0; b < 3; b++) {
@@ -308,20 +311,20 @@ __device__ __forceinline__ void mls_apply(const MlsW<C>& m, Get&& get, Interp& o
             v0 += w * q.uy; v1 += wx * q.uy; v2 += wy * q.uy;
         }
     }
-    o.ux = (double)(m.k0 * u0 + m.kx * u1 + m.ky * u2);
-    o.uy = (double)(m.k0 * v0 + m.kx * v1 + m.ky * v2);
-    o.rho = 1.0 + (double)(m.k0 * r0 + m.kx * r1 + m.ky * r2);
-    o.p = o.rho / 3.0;
+    o.ux = m.k0 * u0 + m.kx * u1 + m.ky * u2;
+    o.uy = m.k0 * v0 + m.kx * v1 + m.ky * v2;
+    o.rho = C(1) + (m.k0 * r0 + m.kx * r1 + m.ky * r2);
+    o.p = o.rho * C(1.0 / 3.0);
     if (GRAD) {
-        o.dudx = (double)(m.gx * u1); o.dudy = (double)(m.gy * u2);
-        o.dvdx = (double)(m.gx * v1); o.dvdy = (double)(m.gy * v2);
+        o.dudx = m.gx * u1; o.dudy = m.gy * u2;
+        o.dvdx = m.gx * v1; o.dvdy = m.gy * v2;
     }
 }
 
 // MLS interpolation of the fluid at (X, Y) straight from the populations (no tile).
 template <typename S, bool GRAD>
 __device__ bool mls_interp(const S* __restrict__ src, const Lat& L, const double* __restrict__ fib, double X,
-                           double Y, Interp& o) {
+                           double Y, InterpT<typename St<S>::C>& o) {
     using C = typename St<S>::C;
     const MlsW<C> m = mls_setup<C>(L, X, Y);
     mls_apply<C, GRAD>(m, [&](int a, int b) {
