@@ -149,6 +149,21 @@ lbmib_status lbmib_observables_all(lbmib_ctx* ctx, double* out);
  * n <= max_nodes. Synchronises. */
 lbmib_status lbmib_interpolate(lbmib_ctx* ctx, const double* xy, int n, double* out);
 
+/* Same as lbmib_interpolate, for callers that cannot allocate device memory at the time
+ * of the call: code running while a stream is being captured into a CUDA graph (where
+ * cudaMalloc is not allowed), callbacks on real-time loops that must not trigger the
+ * implicit synchronisation of an allocation, or hosts whose device memory belongs to
+ * another framework's allocator. The paper has no counterpart; this is a library
+ * convenience. The call allocates nothing: the device staging of the points and results
+ * lives in a static array of the library, sized for 16384 points (1.25 MiB held on every
+ * device that loads the library until the process exits). n > 16384 is rejected with
+ * LBMIB_ERR_ARG. The first call on a device resolves the array's device address (with
+ * the context's device made current for that moment); make that first call before any
+ * stream capture. Every call on a device shares the one array and its contents persist
+ * between calls, so calls whose device work overlaps (several streams, or several
+ * host threads) race: serialise them. Synchronises. */
+lbmib_status lbmib_interpolate_noalloc(lbmib_ctx* ctx, const double* xy, int n, double* out);
+
 /* Checkpoint: lbmib_state_bytes() gives the size of a snapshot of the populations,
  * the force fields and all capsule state; lbmib_save_state() writes it into a host
  * buffer of that size and lbmib_load_state() restores it into a context created with

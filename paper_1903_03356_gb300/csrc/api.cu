@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -85,6 +86,7 @@ Layout make_layout(const lbmib_config* c) {
 }  // namespace
 
 struct lbmib_ctx {
+    int device = 0;  // the device that holds the arena
     lbmib_config cfg{};
     Layout lay{};
     Lat L{};
@@ -257,6 +259,21 @@ void by_storage(lbmib_storage st, F&& f) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------------
+// Staging memory of lbmib_interpolate_noalloc: a file-scope device array, so that the
+// call needs no allocation by anyone. Every device that loads the library holds it
+// (1.25 MiB) until the process exits. In host code the name g_noalloc_interp is only a
+// stand-in for the symbol; the device address comes from cudaGetSymbolAddress, taken
+// once per device with that device current and cached in g_noalloc_addr.
+// ---------------------------------------------------------------------------------
+namespace {
+constexpr int kNoallocMaxPoints = 16384;
+constexpr int kNoallocMaxDevices = 64;
+static __device__ __align__(256) double g_noalloc_interp[kNoallocMaxPoints * 10];  // 2 in + 8 out per point
+double* g_noalloc_addr[kNoallocMaxDevices] = {};
+std::mutex g_noalloc_mu;
+}  // namespace
+
 extern "C" {
 
 size_t lbmib_arena_bytes(const lbmib_config* cfg) {
@@ -274,6 +291,14 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     if (arena_bytes < lay.total) return LBMIB_ERR_OOM;
     lbmib_ctx* c = new lbmib_ctx();
     c->cfg = *cfg;
+    {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, d_arena) == cudaSuccess && pa.type == cudaMemoryTypeDevice)
+            c->device = pa.device;
+        else
+            cudaGetDevice(&c->device);
+        cudaGetLastError();  // clear a non-sticky error from the attribute query
+    }
     c->lay = lay;
     c->stream = (cudaStream_t)cuda_stream;
     c->arena = (char*)d_arena;
@@ -600,6 +625,44 @@ lbmib_status lbmib_interpolate(lbmib_ctx* c, const double* xy, int n, double* ou
     c->launches++;
     LBMIB_CUDA(c, cudaGetLastError());
     LBMIB_CUDA(c, cudaMemcpyAsync(out, c->pts_out, 8 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return device_status(c);
+}
+
+lbmib_status lbmib_interpolate_noalloc(lbmib_ctx* c, const double* xy, int n, double* out) {
+    if (!c || !xy || !out || n < 0) return LBMIB_ERR_ARG;
+    if (n > kNoallocMaxPoints)
+        return fail(c, LBMIB_ERR_ARG, "lbmib_interpolate_noalloc: n exceeds the static staging limit of 16384 points");
+    if (n == 0) return LBMIB_OK;
+    if (c->device < 0 || c->device >= kNoallocMaxDevices)
+        return fail(c, LBMIB_ERR_ARG, "lbmib_interpolate_noalloc: device ordinal beyond the supported range");
+    double* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        base = g_noalloc_addr[c->device];
+        if (!base) {
+            // first call on this device: resolve the array's device address with the
+            // context's device current (restored afterwards)
+            int prev = 0;
+            LBMIB_CUDA(c, cudaGetDevice(&prev));
+            if (prev != c->device) LBMIB_CUDA(c, cudaSetDevice(c->device));
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_interp);
+            if (prev != c->device) cudaSetDevice(prev);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetSymbolAddress(g_noalloc_interp)");
+            g_noalloc_addr[c->device] = base = static_cast<double*>(p);
+        }
+    }
+    double2* pts = reinterpret_cast<double2*>(base);
+    double* res = base + 2 * kNoallocMaxPoints;
+    LBMIB_CUDA(c, cudaMemcpyAsync(pts, xy, n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    by_storage(c->cfg.storage, [&](auto tag) {
+        using S = decltype(tag);
+        launch_interp_points<S>(c->pops[c->cur], c->L, c->fib[c->cur_fib], pts, n, res, &c->ctr->status,
+                                c->stream);
+    });
+    c->launches++;
+    LBMIB_CUDA(c, cudaGetLastError());
+    LBMIB_CUDA(c, cudaMemcpyAsync(out, res, 8 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     return device_status(c);
 }
 

@@ -67,6 +67,7 @@ _SIGS = {
     "lbmib_observables": (C.c_int, [_vp, C.c_int, _vp]),
     "lbmib_observables_all": (C.c_int, [_vp, _vp]),
     "lbmib_interpolate": (C.c_int, [_vp, _vp, C.c_int, _vp]),
+    "lbmib_interpolate_noalloc": (C.c_int, [_vp, _vp, C.c_int, _vp]),
     "lbmib_state_bytes": (C.c_size_t, [_vp]),
     "lbmib_save_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "lbmib_load_state": (C.c_int, [_vp, _vp, C.c_size_t]),
@@ -166,6 +167,10 @@ def lbmib_observables_all(h, out):
 
 def lbmib_interpolate(h, xy, out):
     _check(h, _lib.lbmib_interpolate(h, _p(xy), xy.size // 2, _p(out)))
+
+
+def lbmib_interpolate_noalloc(h, xy, out):
+    _check(h, _lib.lbmib_interpolate_noalloc(h, _p(xy), xy.size // 2, _p(out)))
 
 
 def lbmib_state_bytes(h) -> int:
@@ -290,6 +295,13 @@ class Context:
         xy = _f64(xy).reshape(-1)
         out = np.empty(4 * xy.size)
         lbmib_interpolate(self.h, xy, out)
+        return out.reshape(-1, 8)
+
+    def interpolate_noalloc(self, xy) -> np.ndarray:
+        """lbmib_interpolate through the library's static staging (no allocation)."""
+        xy = _f64(xy).reshape(-1)
+        out = np.empty(4 * xy.size)
+        lbmib_interpolate_noalloc(self.h, xy, out)
         return out.reshape(-1, 8)
 
     def save_state(self) -> np.ndarray:
