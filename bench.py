@@ -29,6 +29,12 @@ from paper_1903_03356_gb300 import workloads as W  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+METRIC = "LBM-IB MLUPS (coupled step) and % of HBM roofline"
+
+# DRAM bytes (read + write) per lattice update of k_collide_stream from one ncu capture of
+# the current kernel (see profiles/k_collide_stream_*.md); scaled to a full launch by the
+# number of updates. None where no capture of the current kernel exists.
+MEASURED_TRAFFIC_PER_UPDATE = {"fp32": (302.058752e6 + 252.157696e6) / (4096 * 2048), "fp64": None, "fp16": None}
 
 
 def parse():
@@ -138,6 +144,13 @@ def max_over_ranks(value: float, dist, device=None) -> float:
     return float(t.item())
 
 
+def job_throughput(units_per_rank: float, elapsed_ms: float, world: int, dist, device=None):
+    """Whole-job rate of N independent replicas (no data-path collective): all ranks'
+    units over the slowest rank's time. Returns (units per second, slowest ms)."""
+    slowest = max_over_ranks(elapsed_ms, dist, device)
+    return world * units_per_rank / (slowest / 1e3), slowest
+
+
 def cpu_baseline(a, seconds: float):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload: a
     2048 x 512 slab of the same channel with the same capsule density."""
@@ -166,18 +179,24 @@ def cpu_baseline(a, seconds: float):
 
 
 def run_reference(a):
-    rank, world, dist = dist_setup(a.gpus)
+    """The CPU baseline arm: the FP64 oracle as it stands, on a bounded sample of the
+    same workload (there is no reference code; the paper describes a method). Under
+    torchrun only rank 0 runs it."""
+    rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per = max(1.0, a.cpu_seconds / max(1, a.steps + a.warmup))
-    base = cpu_baseline(a, per * max(1, a.steps))
-    line = {"impl": "reference", "metric": "LBM-IB MLUPS (coupled step)", "value": base["value"],
-            "unit": "MLUPS", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"poiseuille-biconcave-{a.nx}x{a.ny} (oracle sample)"},
+    per_step_budget = a.cpu_seconds / max(1, a.steps)
+    base = cpu_baseline(a, max(1.0, per_step_budget * a.steps))
+    case_name = f"poiseuille-biconcave-{a.nx}x{a.ny}-{(a.nx * a.ny) // 8192}x128-{a.scheme}-{a.storage}"
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "MLUPS",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": a.nx * a.ny / (base["value"] * 1e6) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": case_name, "nx": a.nx, "ny": a.ny, "scheme": a.scheme,
+                       "storage": a.storage, "sample": base["sample"]},
             "cpu_baseline": base,
-            "e2e": {"value": base["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": base["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -217,16 +236,15 @@ def run_gpu(a):
     ctx.sync()
     k1_ms, k1_n = ctx.kernel_time(reset=True)
     launches = ctx.launch_count - launches0
-    elapsed_ms = max_over_ranks(elapsed_ms, dist, torch.device("cuda", dev))
-
-    mlups = world * N * a.steps / (elapsed_ms / 1e3) / 1e6
+    rate, elapsed_ms = job_throughput(N * a.steps, elapsed_ms, world, dist, torch.device("cuda", dev))
+    mlups = rate / 1e6
     hbm, src = peaks()
     bpu = ctx.bytes_per_update
     k1_avg_ms = k1_ms / max(1, k1_n)
     achieved = bpu * N / (k1_avg_ms / 1e3) / 1e9
 
     line = {
-        "metric": "LBM-IB MLUPS (coupled step) and % of HBM roofline",
+        "metric": METRIC,
         "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": elapsed_ms / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32"}[a.storage],
@@ -236,7 +254,9 @@ def run_gpu(a):
                    "storage": a.storage, "tau": case.tau,
                    "l2": "inputs larger than L2 (populations 2 x %.1f GB)" % (9 * N * bpu / 18 / 1e9)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
+                     "frac": achieved / hbm,
+                     "traffic": (MEASURED_TRAFFIC_PER_UPDATE[a.storage] * N
+                                 if MEASURED_TRAFFIC_PER_UPDATE[a.storage] else None),
                      "kernel": "k_collide_stream", "bytes_per_update": bpu,
                      "kernel_ms": k1_avg_ms, "kernel_share": k1_ms / elapsed_ms,
                      "peak_source": src},

@@ -480,8 +480,11 @@ lbmib_status lbmib_add_capsule(lbmib_ctx* c, const double* xy, int n, double ks,
     }
     const double ext = std::hypot(x1 - x0, y1 - y0);
     if (ext > c->max_extent) c->max_extent = ext;
-    c->tile_cells = tile_budget(c->max_n, c->max_extent);
-    set_capsule_smem_limits(c->max_n, c->tile_cells);
+    const int cells = tile_budget(c->max_n, c->max_extent);
+    if (cells != c->tile_cells || n == c->max_n) {
+        c->tile_cells = cells;
+        set_capsule_smem_limits(c->max_n, c->tile_cells);
+    }
     drop_graphs(c);  // launch shapes changed
     if (id_out) *id_out = id;
     return LBMIB_OK;

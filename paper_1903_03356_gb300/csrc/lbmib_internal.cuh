@@ -61,7 +61,9 @@ __device__ __forceinline__ C lat_c(double d, float f) {
 }
 
 // ---------------------------------------------------------------------------------
-// Storage traits: type S stored, type C computed in.
+// Storage traits: type S stored, type C computed in. ld goes through the read-only
+// (non-coherent) path and is only for data the kernel never writes; ldc is a plain
+// load for kernels that read populations they wrote earlier in the same launch.
 // ---------------------------------------------------------------------------------
 template <typename S>
 struct St;
@@ -69,12 +71,14 @@ template <>
 struct St<double> {
     using C = double;
     static __device__ __forceinline__ double ld(const double* p, const Lat&) { return __ldg(p); }
+    static __device__ __forceinline__ double ldc(const double* p, const Lat&) { return *p; }
     static __device__ __forceinline__ void st(double* p, double v, const Lat&) { *p = v; }
 };
 template <>
 struct St<float> {
     using C = float;
     static __device__ __forceinline__ float ld(const float* p, const Lat&) { return __ldg(p); }
+    static __device__ __forceinline__ float ldc(const float* p, const Lat&) { return *p; }
     static __device__ __forceinline__ void st(float* p, float v, const Lat&) { *p = v; }
 };
 template <>
@@ -82,6 +86,9 @@ struct St<__half> {
     using C = float;
     static __device__ __forceinline__ float ld(const __half* p, const Lat& L) {
         return __half2float(__ldg(p)) * L.inv_scale;
+    }
+    static __device__ __forceinline__ float ldc(const __half* p, const Lat& L) {
+        return __half2float(*p) * L.inv_scale;
     }
     static __device__ __forceinline__ void st(__half* p, float v, const Lat& L) {
         *p = __float2half_rn(v * L.scale);
@@ -95,20 +102,21 @@ __device__ __forceinline__ int wrapi(int a, int n) {
 
 // Pre-collision population i at node (x, y) of the step that reads `src` (Eq. 1, left
 // side): the pull of the post-collision population from x - e_i, or the wall reflection.
-template <typename S>
+// NC selects the read-only load path (src not written during the launch).
+template <typename S, bool NC = true>
 __device__ __forceinline__ typename St<S>::C pull(const S* __restrict__ src, const Lat& L, int i,
                                                   int x, int y) {
     using C = typename St<S>::C;
     int ys = y - ey(i);
+    auto ld = [&](const S* p) { return NC ? St<S>::ld(p, L) : St<S>::ldc(p, L); };
     if (L.walls && (ys < 0 || ys >= L.ny)) {
         const int j = opp(i);
         const C uw = ys < 0 ? lat_c<C>(L.ub, L.ubf) : lat_c<C>(L.ut, L.utf);
-        return St<S>::ld(src + (long long)j * L.plane + (long long)y * L.pitch + x, L) -
-               C(6) * wgt<C>(j) * C(ex(j)) * uw;
+        return ld(src + (long long)j * L.plane + (long long)y * L.pitch + x) - C(6) * wgt<C>(j) * C(ex(j)) * uw;
     }
     ys = wrapi(ys, L.ny);
     const int xs = wrapi(x - ex(i), L.nx);
-    return St<S>::ld(src + (long long)i * L.plane + (long long)ys * L.pitch + xs, L);
+    return ld(src + (long long)i * L.plane + (long long)ys * L.pitch + xs);
 }
 
 // Density deviation, momentum (Eq. 6-7 without the force) of shifted populations.

@@ -1,0 +1,182 @@
+// Device helpers shared by the immersed-boundary kernels (ib.cu) and the batched
+// persistent kernel (batch.cu): the shared-memory view of one capsule, block
+// reductions, the capsule tile, and the membrane force terms (Eq. 10-14).
+#pragma once
+
+#include "lbmib_kernels.cuh"
+
+namespace lbmib {
+
+// Shared-memory view of one capsule (sized by the largest ring of the launch).
+struct CapSmem {
+    double2* X;     // vertex positions
+    double2* ext;   // external force of element v (v -> v+1), Eq. 15-16
+    double2* xd;    // interpolated velocity at vertex v
+    double* sst;    // stretch factor of element v: -k_s (l - l_0) / l  (Eq. 11)
+    double* bs;     // k_b sin(theta_v - theta_v0) at vertex v            (Eq. 13)
+    double2* bdl;   // d(theta_v)/dX_{v-1}
+    double2* bdr;   // d(theta_v)/dX_{v+1}
+    double* red;    // reduction scratch (32 * 8 doubles)
+    unsigned char* tile;  // moment / force tile
+};
+
+inline size_t ring_smem_bytes(int max_n) {
+    return (size_t)max_n * (5 * sizeof(double2) + 2 * sizeof(double)) + 32 * 8 * sizeof(double);
+}
+
+__device__ __forceinline__ CapSmem carve(unsigned char* base, int max_n) {
+    CapSmem s;
+    s.X = reinterpret_cast<double2*>(base);
+    s.ext = s.X + max_n;
+    s.xd = s.ext + max_n;
+    s.bdl = s.xd + max_n;
+    s.bdr = s.bdl + max_n;
+    s.sst = reinterpret_cast<double*>(s.bdr + max_n);
+    s.bs = s.sst + max_n;
+    s.red = s.bs + max_n;
+    s.tile = reinterpret_cast<unsigned char*>(s.red + 32 * 8);
+    return s;
+}
+
+// Reduction of K doubles over the block (blockDim.x a multiple of 32, <= 1024); MIN
+// selects minimum instead of sum. Every thread receives the results.
+template <int K, bool MIN>
+__device__ void block_reduce(double (&v)[K], double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++)
+        for (int o = 16; o > 0; o >>= 1) {
+            const double t = __shfl_xor_sync(0xffffffffu, v[k], o);
+            v[k] = MIN ? fmin(v[k], t) : v[k] + t;
+        }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; k++) red[warp * K + k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        double t = red[k];
+        for (int w = 1; w < nw; w++) t = MIN ? fmin(t, red[w * K + k]) : t + red[w * K + k];
+        v[k] = t;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+
+// ---------------------------------------------------------------------------------
+// Capsule tile: lattice moments (and, for the spread, force accumulators) of every node
+// in the bounding box of the ring widened by `margin` nodes.
+// ---------------------------------------------------------------------------------
+template <typename C>
+struct Tile {
+    int x0, y0, w, h;   // origin (unwrapped lattice coordinates) and extent
+    bool use;           // the box fits the tile budget
+    C* drho;
+    C* ux;
+    C* uy;
+    C* fx;              // force accumulators (compute type)
+    C* fy;
+    int* cells;         // scratch for the flush (aliases the moment arrays)
+
+    __device__ __forceinline__ int index(int x, int y) const { return (y - y0) * w + (x - x0); }
+    // the 3x3 support centred on (cx, cy) lies inside the tile
+    __device__ __forceinline__ bool holds(int cx, int cy) const {
+        return use && cx - 1 >= x0 && cx + 1 < x0 + w && cy - 1 >= y0 && cy + 1 < y0 + h;
+    }
+};
+
+// Bounding box of the staged ring and the tile layout. Collective (all threads).
+template <typename C>
+__device__ Tile<C> make_tile(const CapSmem& sm, int n, int margin, int tile_cells, bool moments, bool forces) {
+    double r[4] = {1e300, 1e300, 1e300, 1e300};  // min x, min y, -max x, -max y
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const double2 X = sm.X[v];
+        r[0] = fmin(r[0], X.x);
+        r[1] = fmin(r[1], X.y);
+        r[2] = fmin(r[2], -X.x);
+        r[3] = fmin(r[3], -X.y);
+    }
+    block_reduce<4, true>(r, sm.red);
+    Tile<C> t;
+    const bool sane = fabs(r[0]) < 1e9 && fabs(r[1]) < 1e9 && fabs(r[2]) < 1e9 && fabs(r[3]) < 1e9;
+    t.x0 = sane ? (int)floor(r[0]) - margin : 0;
+    t.y0 = sane ? (int)floor(r[1]) - margin : 0;
+    const long long w = sane ? (long long)floor(-r[2]) + 1 + margin - t.x0 + 1 : 1LL << 30;
+    const long long h = sane ? (long long)floor(-r[3]) + 1 + margin - t.y0 + 1 : 1LL << 30;
+    t.use = sane && w * h <= tile_cells;
+    t.w = t.use ? (int)w : 0;
+    t.h = t.use ? (int)h : 0;
+    unsigned char* p = sm.tile;
+    t.drho = t.ux = t.uy = nullptr;
+    t.fx = t.fy = nullptr;
+    t.cells = reinterpret_cast<int*>(p);
+    if (forces) {
+        t.fx = reinterpret_cast<C*>(p);
+        t.fy = t.fx + tile_cells;
+        p += 2 * sizeof(C) * (size_t)tile_cells;
+        t.cells = reinterpret_cast<int*>(p);   // behind the accumulators
+    }
+    if (moments) {
+        t.drho = reinterpret_cast<C*>(p);
+        t.ux = t.drho + tile_cells;
+        t.uy = t.ux + tile_cells;
+    }
+    return t;
+}
+
+// Zero the force accumulators of a tile (collective; callers order it before use).
+template <typename C>
+__device__ void zero_forces(Tile<C>& t) {
+    const int cells = t.w * t.h;
+    for (int k = threadIdx.x; k < cells; k += blockDim.x) {
+        t.fx[k] = C(0);
+        t.fy[k] = C(0);
+    }
+}
+
+// Per-element stretch factor and per-vertex bending terms of vertex/element v, and
+// this vertex's contribution to twice the enclosed area (Green's theorem, about X_0).
+__device__ __forceinline__ double ring_terms(const CapSmem& sm, const CapsuleParams& P, const Nodes& nd, int v) {
+    const int n = P.n;
+    const double2 Xv = sm.X[v], Xr = sm.X[v + 1 == n ? 0 : v + 1], Xl = sm.X[v == 0 ? n - 1 : v - 1];
+    const double2 a = Xv - Xl, b = Xr - Xv;   // incoming edge, outgoing edge (element v)
+    const double a2 = a.x * a.x + a.y * a.y, b2 = b.x * b.x + b.y * b.y;
+    const double ra = rsqrt(a2), rb = rsqrt(b2);   // 1/|a|, 1/|b|
+    // Eq. 11: element v joins v and v+1, length |b|
+    sm.sst[v] = -P.ks * (b2 * rb - nd.L0[P.off + v]) * rb;
+    // Eq. 13 as F = -k_b sin(theta - theta_0) d(theta)/dX with theta the signed turning
+    // angle at v; sin(theta - theta_0) from the cross and dot products and theta_0's
+    // stored cosine and sine.
+    const double cr = a.x * b.y - a.y * b.x, dt = a.x * b.x + a.y * b.y;
+    const double sdiff = (cr * nd.c0[P.off + v] - dt * nd.s0[P.off + v]) * (ra * rb);
+    sm.bs[v] = P.kb * sdiff;
+    const double ia2 = ra * ra, ib2 = rb * rb;
+    sm.bdl[v] = make_double2(-a.y * ia2, a.x * ia2);
+    sm.bdr[v] = make_double2(-b.y * ib2, b.x * ib2);
+    const double2 X0 = sm.X[0];
+    return (Xv.x - X0.x) * (Xr.y - X0.y) - (Xr.x - X0.x) * (Xv.y - X0.y);
+}
+
+// Internal force on vertex v (Eq. 22: stretch + bending + area) from the staged terms.
+__device__ __forceinline__ double2 node_internal_force(const CapSmem& sm, const CapsuleParams& P, int v, double A) {
+    const int n = P.n;
+    const int vl = v == 0 ? n - 1 : v - 1, vr = v + 1 == n ? 0 : v + 1;
+    const double2 Xv = sm.X[v], Xl = sm.X[vl], Xr = sm.X[vr];
+    double2 F = sm.sst[v] * (Xv - Xr);           // element v, this vertex first
+    F = F + (-sm.sst[vl]) * (Xl - Xv);           // element v-1, this vertex second
+    F = F + sm.bs[v] * (sm.bdl[v] + sm.bdr[v]);  // own bending angle
+    F = F + (-sm.bs[vr]) * sm.bdl[vr];           // as left neighbour of v+1
+    F = F + (-sm.bs[vl]) * sm.bdr[vl];           // as right neighbour of v-1
+    // Eq. 14: F^a_l = k_a (1 - A/A0) p_ref (dy, -dx) for element l, half to each end
+    const double fa = P.ka * (1.0 - A / P.A0) * (1.0 / 3.0) * 0.5;
+    const double2 dr = Xr - Xv, dl = Xv - Xl;
+    F.x += fa * (dr.y + dl.y);
+    F.y -= fa * (dr.x + dl.x);
+    return F;
+}
+
+}  // namespace lbmib

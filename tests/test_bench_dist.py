@@ -1,0 +1,54 @@
+"""Host logic of bench.py's multi-GPU replicas, run as two gloo ranks on the CPU.
+
+With N GPUs the benchmark runs N independent replicas (the lattice is not split; there
+is no data-path collective): the job rate is all ranks' units over the slowest rank's
+time, taken with an all-reduce MAX.
+"""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    elapsed = [120.0, 150.0][rank]        # the second rank is slower
+    rate, slowest = bench.job_throughput(1e6, elapsed, world, dist, torch.device("cpu"))
+    q.put((rank, rate, slowest))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replica_throughput_uses_the_slowest_rank():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, rate, slowest in res:
+        assert slowest == 150.0
+        assert abs(rate - 2 * 1e6 / 0.150) < 1e-6
+
+
+def test_single_process_needs_no_process_group():
+    import bench
+    rate, slowest = bench.job_throughput(5e5, 250.0, 1, None)
+    assert slowest == 250.0 and abs(rate - 2e6) < 1e-9
