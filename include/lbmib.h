@@ -206,6 +206,74 @@ long long lbmib_launch_count(const lbmib_ctx* ctx);
  * storage type (9 read, 9 written). */
 double lbmib_bytes_per_update(const lbmib_ctx* ctx);
 
+/* ---------------------------------------------------------------------------------
+ * Batched persistent launch: many independent cases, each its own small lattice with at
+ * most one capsule, advanced together by the Kinematic scheme (Section 2.4, steps
+ * i-viii, Eq. 25) in one kernel launch per lbmib_batch_step call. Every case follows
+ * exactly the single-context step of LBMIB_KINEMATIC; cases never interact.
+ *
+ * A case's capsule must stay inside a shared-memory tile sized from its initial ring
+ * (largest bounding-box side + 8 nodes, squared, times 1.5); a capsule that outgrows it,
+ * or whose tile would wrap onto itself on a periodic lattice, stops moving and raises
+ * LBMIB_ERR_SUPPORT at the next synchronising call.
+ * --------------------------------------------------------------------------------- */
+typedef struct lbmib_batch lbmib_batch;
+
+typedef struct {
+    int nx, ny;             /* lattice size, each >= 3, nx * ny < 2^31               */
+    int walls;              /* as lbmib_config                                        */
+    double tau;             /* > 0.5                                                  */
+    double u_bottom, u_top; /* wall x-velocities (ignored without walls)              */
+    double gx, gy;          /* uniform body-force density                             */
+    const double* rho;      /* initial fields, host, nx*ny row-major; NULL = rest     */
+    const double* ux;       /*   (rho 1, u 0); read during lbmib_batch_create only    */
+    const double* uy;
+    const double* xy;       /* capsule ring, 2n interleaved, counter-clockwise; it is */
+    int n;                  /*   also the stress-free shape. n = 0: no capsule,       */
+    double k_s, k_b, k_a;   /*   else 3 <= n <= 1024. Constants of Eq. 10, 12, 14.    */
+    double node_mass;       /* > 0 when n > 0 (unused by the Kinematic scheme)        */
+} lbmib_case;
+
+/* Device arena size (bytes) for a batch; 0 if a case or the storage is invalid. */
+size_t lbmib_batch_arena_bytes(const lbmib_case* cases, int ncases, lbmib_storage storage);
+
+/* Create a batch over caller-owned device memory (as lbmib_create): copies the case
+ * table and initial state (populations at equilibrium with the given fields, Section
+ * 2.1). autotune_steps > 0 times each candidate launch shape (256, 512 or 1024 threads
+ * per CTA, from one CTA per SM up to as many as fit) for that many steps, keeps the
+ * fastest and restarts every case from its initial state; 0 uses 512 threads with as
+ * many CTAs as fit. Synchronises.
+ * Errors: LBMIB_ERR_ARG (a case invalid, a ring clockwise, arena misaligned),
+ * LBMIB_ERR_OOM (arena too small), LBMIB_ERR_CUDA. */
+lbmib_status lbmib_batch_create(const lbmib_case* cases, int ncases, lbmib_storage storage,
+                                void* d_arena, size_t arena_bytes, void* cuda_stream,
+                                int autotune_steps, lbmib_batch** out);
+void lbmib_batch_destroy(lbmib_batch* batch);
+const char* lbmib_batch_last_error(const lbmib_batch* batch);
+
+/* Advance every case by nsteps (0 <= nsteps < 2^30) with one persistent launch
+ * (replayed from a CUDA graph captured for this nsteps). Enqueues only. */
+lbmib_status lbmib_batch_step(lbmib_batch* batch, long long nsteps);
+
+/* Wait for the batch stream; report sticky device conditions (LBMIB_ERR_UNSTABLE,
+ * LBMIB_ERR_SUPPORT). */
+lbmib_status lbmib_batch_sync(lbmib_batch* batch);
+
+/* Populations of case c (unshifted f_i, host double [9][ny][nx]). Synchronises. */
+lbmib_status lbmib_batch_read_populations(lbmib_batch* batch, int c, double* f);
+
+/* Vertex positions and last interpolated velocities of case c (2n each, NULL to skip;
+ * nothing is written when the case has no capsule). Synchronises. */
+lbmib_status lbmib_batch_read_capsule(lbmib_batch* batch, int c, double* xy, double* vel);
+
+/* Observables of every case's capsule (host double [ncases][8], layout of
+ * lbmib_observables_all; rows of cases without a capsule are zero). Synchronises. */
+lbmib_status lbmib_batch_observables(lbmib_batch* batch, double* out);
+
+/* Launch shape in use: threads per CTA, resident CTAs, tile cells per CTA. */
+lbmib_status lbmib_batch_config(const lbmib_batch* batch, int* threads, int* grid,
+                                int* tile_cells);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,6 +43,17 @@ class lbmib_config(C.Structure):
     ]
 
 
+class lbmib_case(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("walls", C.c_int),
+        ("tau", C.c_double), ("u_bottom", C.c_double), ("u_top", C.c_double),
+        ("gx", C.c_double), ("gy", C.c_double),
+        ("rho", C.c_void_p), ("ux", C.c_void_p), ("uy", C.c_void_p),
+        ("xy", C.c_void_p), ("n", C.c_int),
+        ("k_s", C.c_double), ("k_b", C.c_double), ("k_a", C.c_double), ("node_mass", C.c_double),
+    ]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is not built; run __graft_entry__.build() (nvcc, sm_103a)")
 
@@ -75,6 +86,16 @@ _SIGS = {
     "lbmib_kernel_time": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
     "lbmib_launch_count": (C.c_longlong, [_vp]),
     "lbmib_bytes_per_update": (C.c_double, [_vp]),
+    "lbmib_batch_arena_bytes": (C.c_size_t, [_vp, C.c_int, C.c_int]),
+    "lbmib_batch_create": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.c_size_t, _vp, C.c_int, C.POINTER(_vp)]),
+    "lbmib_batch_destroy": (None, [_vp]),
+    "lbmib_batch_last_error": (C.c_char_p, [_vp]),
+    "lbmib_batch_step": (C.c_int, [_vp, C.c_longlong]),
+    "lbmib_batch_sync": (C.c_int, [_vp]),
+    "lbmib_batch_read_populations": (C.c_int, [_vp, C.c_int, _vp]),
+    "lbmib_batch_read_capsule": (C.c_int, [_vp, C.c_int, _vp, _vp]),
+    "lbmib_batch_observables": (C.c_int, [_vp, _vp]),
+    "lbmib_batch_config": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -202,6 +223,58 @@ def lbmib_launch_count(h) -> int:
 
 def lbmib_bytes_per_update(h) -> float:
     return float(_lib.lbmib_bytes_per_update(h))
+
+
+def lbmib_batch_arena_bytes(cases, ncases: int, storage: int) -> int:
+    return int(_lib.lbmib_batch_arena_bytes(C.cast(cases, C.c_void_p), int(ncases), int(storage)))
+
+
+def lbmib_batch_create(cases, ncases, storage, d_arena, arena_bytes, cuda_stream, autotune_steps) -> int:
+    h = C.c_void_p()
+    st = _lib.lbmib_batch_create(C.cast(cases, C.c_void_p), int(ncases), int(storage), C.c_void_p(d_arena),
+                                 arena_bytes, C.c_void_p(cuda_stream), int(autotune_steps), C.byref(h))
+    if st != OK:
+        raise LbmibError(st, "lbmib_batch_create failed")
+    return h.value
+
+
+def lbmib_batch_destroy(h) -> None:
+    _lib.lbmib_batch_destroy(h)
+
+
+def lbmib_batch_last_error(h) -> str:
+    return _lib.lbmib_batch_last_error(h).decode()
+
+
+def _bcheck(h, st):
+    if st != OK:
+        raise LbmibError(st, lbmib_batch_last_error(h))
+
+
+def lbmib_batch_step(h, nsteps: int):
+    _bcheck(h, _lib.lbmib_batch_step(h, int(nsteps)))
+
+
+def lbmib_batch_sync(h):
+    _bcheck(h, _lib.lbmib_batch_sync(h))
+
+
+def lbmib_batch_read_populations(h, c, f):
+    _bcheck(h, _lib.lbmib_batch_read_populations(h, int(c), _p(f)))
+
+
+def lbmib_batch_read_capsule(h, c, xy, vel):
+    _bcheck(h, _lib.lbmib_batch_read_capsule(h, int(c), _p(xy), _p(vel)))
+
+
+def lbmib_batch_observables(h, out):
+    _bcheck(h, _lib.lbmib_batch_observables(h, _p(out)))
+
+
+def lbmib_batch_config(h):
+    t, g, c = C.c_int(), C.c_int(), C.c_int()
+    _bcheck(h, _lib.lbmib_batch_config(h, C.byref(t), C.byref(g), C.byref(c)))
+    return t.value, g.value, c.value
 
 
 # ---- convenience wrapper ---------------------------------------------------------------
@@ -336,3 +409,84 @@ def from_case(case, storage="fp64", extra_nodes=0, extra_capsules=0, **kw) -> Co
     for c in case.capsules:
         ctx.add_capsule(c.xy, c.ks, c.kb, c.ka, c.mass)
     return ctx
+
+
+class Batch:
+    """Independent cases (``workloads.Case`` with at most one capsule each) advanced by
+    the Kinematic scheme in one persistent launch; device memory from torch."""
+
+    def __init__(self, cases, storage="fp32", autotune_steps=0, device=None, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("the LBM-IB library needs a CUDA device")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        self.shapes = [(c.nx, c.ny) for c in cases]
+        self._n = []
+        keep = []                       # host arrays referenced by the case table
+        table = (lbmib_case * len(cases))()
+        for k, case in enumerate(cases):
+            if len(case.capsules) > 1:
+                raise ValueError("a batched case holds at most one capsule")
+            rho, ux, uy = (_f64(a) for a in case.fields())
+            keep += [rho, ux, uy]
+            t = table[k]
+            t.nx, t.ny, t.walls = case.nx, case.ny, int(bool(case.walls))
+            t.tau, t.u_bottom, t.u_top, t.gx, t.gy = case.tau, case.u_bottom, case.u_top, case.gx, case.gy
+            t.rho, t.ux, t.uy = rho.ctypes.data, ux.ctypes.data, uy.ctypes.data
+            if case.capsules:
+                cap = case.capsules[0]
+                xy = _f64(cap.xy).reshape(-1)
+                keep.append(xy)
+                t.xy, t.n = xy.ctypes.data, xy.size // 2
+                t.k_s, t.k_b, t.k_a, t.node_mass = cap.ks, cap.kb, cap.ka, cap.mass
+            self._n.append(int(t.n))
+        nbytes = lbmib_batch_arena_bytes(table, len(cases), self.storage)
+        if nbytes == 0:
+            raise LbmibError(ERR_ARG, "invalid batch")
+        self.arena = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            self.h = lbmib_batch_create(table, len(cases), self.storage, self.arena.data_ptr(), nbytes,
+                                        self.stream.cuda_stream, autotune_steps)
+        del keep
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbmib_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, nsteps: int):
+        lbmib_batch_step(self.h, nsteps)
+
+    def sync(self):
+        lbmib_batch_sync(self.h)
+
+    def read_populations(self, c: int) -> np.ndarray:
+        nx, ny = self.shapes[c]
+        f = np.empty((9, ny, nx))
+        lbmib_batch_read_populations(self.h, c, f)
+        return f
+
+    def read_capsule(self, c: int):
+        n = self._n[c]
+        xy, vel = np.empty(2 * n), np.empty(2 * n)
+        lbmib_batch_read_capsule(self.h, c, xy, vel)
+        return xy, vel
+
+    def observables(self) -> np.ndarray:
+        out = np.empty((len(self.shapes), 8))
+        lbmib_batch_observables(self.h, out)
+        return out
+
+    @property
+    def config(self):
+        """(threads per CTA, resident CTAs, tile cells)"""
+        return lbmib_batch_config(self.h)

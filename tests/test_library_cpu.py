@@ -120,3 +120,48 @@ def test_batch_cases_follow_their_recipe():
         n = c.capsules[0].xy.shape[0]
         assert n in W.BATCH_NODES
         assert W.signed_area(c.capsules[0].xy) > 0
+
+
+def _batch_table(L, cases):
+    keep, table = [], (L.lbmib_case * len(cases))()
+    for k, case in enumerate(cases):
+        t = table[k]
+        t.nx, t.ny, t.walls, t.tau = case.nx, case.ny, int(case.walls), case.tau
+        t.u_bottom, t.u_top = case.u_bottom, case.u_top
+        if case.capsules:
+            xy = np.ascontiguousarray(case.capsules[0].xy, dtype=np.float64).reshape(-1)
+            keep.append(xy)
+            t.xy, t.n = xy.ctypes.data, xy.size // 2
+            cap = case.capsules[0]
+            t.k_s, t.k_b, t.k_a, t.node_mass = cap.ks, cap.kb, cap.ka, cap.mass
+    return table, keep
+
+
+def test_batch_arena_sizing_and_rejection_are_host_logic():
+    from paper_1903_03356_gb300 import lbmib as L
+    cases = W.batch_cases(count=16, seed=1, steps=1)
+    table, keep = _batch_table(L, cases)
+    fp32 = L.lbmib_batch_arena_bytes(table, 16, L.FP32)
+    fp16 = L.lbmib_batch_arena_bytes(table, 16, L.FP16)
+    fp64 = L.lbmib_batch_arena_bytes(table, 16, L.FP64)
+    assert fp64 > fp32 > fp16 > 0
+    # two population buffers of 9 planes per case, rows padded to 128 bytes
+    pops = sum(2 * 9 * c.ny * ((c.nx * 4 + 127) // 128 * 128) for c in cases)
+    assert fp32 >= pops
+    assert L.lbmib_batch_arena_bytes(table, 16, 5) == 0
+    assert L.lbmib_batch_arena_bytes(table, 0, L.FP32) == 0
+    table[3].tau = 0.5
+    assert L.lbmib_batch_arena_bytes(table, 16, L.FP32) == 0
+    table[3].tau = 0.8
+    table[5].n = 2
+    assert L.lbmib_batch_arena_bytes(table, 16, L.FP32) == 0
+    table[5].n = 0                   # a case without a capsule is valid
+    assert L.lbmib_batch_arena_bytes(table, 16, L.FP32) > 0
+    h = C.c_void_p()
+    create = L._lib.lbmib_batch_create
+    assert create(C.cast(table, C.c_void_p), 16, L.FP32, None, 1 << 30, None, 0, C.byref(h)) == L.ERR_ARG
+    assert create(C.cast(table, C.c_void_p), 16, L.FP32, C.c_void_p(4096 + 16), 1 << 34, None, 0,
+                  C.byref(h)) == L.ERR_ARG
+    assert create(C.cast(table, C.c_void_p), 16, L.FP32, C.c_void_p(4096), 64, None, 0,
+                  C.byref(h)) == L.ERR_OOM
+    assert h.value is None
