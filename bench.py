@@ -51,7 +51,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--extra", default="", help="comma list: fp64,fp16,kinematic extra measurements")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the batched-launch and adjoint measurements that follow the main line")
+    p.add_argument("--batch-steps", type=int, default=3000, help="steps per case of the batched workload")
     return p.parse_args()
 
 
@@ -267,11 +269,102 @@ def run_gpu(a):
 
     if not a.no_e2e:
         line["e2e"] = e2e_run(a, case, L, scheme, dev)
+    if rank == 0 and not a.no_extras:
+        ctx.close()
+        line["batched"] = batched_run(L, a.batch_steps)
+        line["adjoint"] = adjoint_run(L, a.storage)
     if rank == 0 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, a.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def batched_run(L, steps):
+    """512 independent shear-flow capsule cases (seed 1, uneven sizes and capillary
+    numbers) in one persistent launch, FP32, `steps` steps each; against the same cases
+    run one after another through single-case contexts (a sample of 32 cases, 300 steps
+    each, scaled by lattice updates)."""
+    import torch
+
+    cases = W.batch_cases(count=512, seed=1, steps=steps)
+    lu = sum(c.nx * c.ny for c in cases)
+    b = L.Batch(cases, storage="fp32", autotune_steps=20)
+    threads, grid, cells = b.config
+    s = b.stream
+    b.step(steps)          # graph capture at the timed length, warm-up
+    b.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    b.step(steps)          # one persistent launch
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    b.sync()
+    launches = 1
+    b.close()
+    seq_ms, seq_lu = 0.0, 0
+    for k in range(0, 512, 16):
+        c = cases[k]
+        ctx = L.from_case(c, storage="fp32")
+        ctx.step(300, L.KINEMATIC)
+        ctx.sync()
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        ctx.step(300, L.KINEMATIC)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        seq_ms += e0.elapsed_time(e1)
+        seq_lu += c.nx * c.ny * 300
+        ctx.close()
+    mlups = lu * steps / ms / 1e3
+    seq_mlups = seq_lu / seq_ms / 1e3
+    return {"workload": "512 shear cases, sizes {64..256}^2, Ca in [1e-3, 1e-1], 48-128 vertices, seed 1, "
+                        "Kinematic, FP32",
+            "steps": steps, "ms": ms, "cases_per_s": 512 / (ms / 1e3), "mlups": mlups,
+            "sequential_mlups": seq_mlups, "speedup_vs_sequential": mlups / seq_mlups,
+            "launch": {"threads": threads, "ctas": grid, "tile_cells": cells}, "gpu_launches": launches,
+            "sequential_sample": "32 cases x 300 steps through single-case contexts (CUDA graphs)"}
+
+
+def adjoint_run(L, storage):
+    """Gradient of D(T) with respect to (k_s, k_b, g_x) on the 512 x 128 channel capsule
+    (radius 16, 128 vertices, Ca = 0.02), Kinematic, T = 800 with a checkpoint every 200,
+    against T forward steps of the same context (cost ratio)."""
+    import torch
+
+    case = W.adjoint_capsule(scheme=0, steps=800)
+    T = 800
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx = L.from_case(case, storage=storage)
+    ctx.step(T, L.KINEMATIC)           # warm-up and graph capture
+    ctx.sync()
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    ctx.step(T, L.KINEMATIC)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1)
+    ctx.close()
+    ctx = L.from_case(case, storage=storage)
+    nbytes = L.lbmib_adjoint_workspace_bytes(ctx.h, T, 200)
+    work = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    grad = np.zeros(4)
+    L.lbmib_adjoint(ctx.h, T, L.KINEMATIC, 200, 0, 0, work.data_ptr(), nbytes, grad)   # warm-up
+    ctx.close()
+    ctx = L.from_case(case, storage=storage)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = L.lbmib_adjoint(ctx.h, T, L.KINEMATIC, 200, 0, 0, work.data_ptr(), nbytes, grad)
+    adj_ms = (time.perf_counter() - t0) * 1e3
+    ctx.close()
+    return {"workload": "512x128 channel, radius-16 capsule of 128 vertices, Ca 0.02, Kinematic, " + storage,
+            "steps": T, "ckpt_every": 200, "forward_ms": fwd_ms, "adjoint_ms": adj_ms,
+            "cost_ratio": adj_ms / fwd_ms, "J": J,
+            "grad": {"k_s": grad[0], "k_b": grad[1], "g_x": grad[2]},
+            "workspace_bytes": nbytes,
+            "note": "adjoint_ms: host clock around lbmib_adjoint (forward with checkpoints, recompute, reverse)"}
 
 
 def e2e_run(a, case, L, scheme, dev):

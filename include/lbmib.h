@@ -207,6 +207,39 @@ long long lbmib_launch_count(const lbmib_ctx* ctx);
 double lbmib_bytes_per_update(const lbmib_ctx* ctx);
 
 /* ---------------------------------------------------------------------------------
+ * Adjoint: gradients of a capsule objective J(X^T) after nsteps Kinematic steps
+ * (Section 2.4) from the current state, with respect to k_s and k_b of every capsule
+ * and the uniform body force (gx, gy). The initial state (populations, capsule
+ * positions and history) is held fixed. Computed by a reverse sweep over the exact
+ * discrete step (collision, streaming, MLS interpolation and spreading, membrane
+ * forces, Eq. 25 advance); MLS supports are differentiated as they stand (a vertex
+ * crossing a half-integer line switches support, which the derivative ignores).
+ * --------------------------------------------------------------------------------- */
+enum {
+    LBMIB_OBJ_TAYLOR_D = 0,     /* Taylor deformation D of the capsule (Section 3.1)   */
+    LBMIB_OBJ_CENTROID_Y = 1,   /* centroid y (lateral position in a channel)          */
+    LBMIB_OBJ_CENTROID_X = 2    /* centroid x                                          */
+};
+
+/* Device workspace (bytes) for lbmib_adjoint over nsteps steps with a checkpoint every
+ * ckpt_every steps: ceil(nsteps / ckpt_every) + 1 state checkpoints (none when
+ * ckpt_every >= nsteps), a tape of min(ckpt_every, nsteps) + 1 population buffers and
+ * the adjoint fields. 0 on invalid arguments. */
+size_t lbmib_adjoint_workspace_bytes(const lbmib_ctx* ctx, long long nsteps, int ckpt_every);
+
+/* Run nsteps Kinematic steps from the current state (the context ends nsteps steps
+ * later, as after lbmib_step) and return J at the end (*J, may be NULL) and its gradient
+ * grad[2 * ncapsules + 2] = {dJ/dk_s of each capsule, dJ/dk_b of each capsule,
+ * dJ/dgx, dJ/dgy}. objective: LBMIB_OBJ_*; capsule: whose ring J measures. d_work:
+ * device workspace of lbmib_adjoint_workspace_bytes (256-byte aligned). Segments of
+ * ckpt_every steps are recomputed from their checkpoints during the reverse sweep.
+ * Synchronises. Errors: LBMIB_ERR_ARG (arguments, or scheme other than Kinematic),
+ * LBMIB_ERR_OOM (workspace too small), sticky device conditions of the run. */
+lbmib_status lbmib_adjoint(lbmib_ctx* ctx, long long nsteps, lbmib_scheme scheme,
+                           int ckpt_every, int objective, int capsule, void* d_work,
+                           size_t work_bytes, double* J, double* grad);
+
+/* ---------------------------------------------------------------------------------
  * Batched persistent launch: many independent cases, each its own small lattice with at
  * most one capsule, advanced together by the Kinematic scheme (Section 2.4, steps
  * i-viii, Eq. 25) in one kernel launch per lbmib_batch_step call. Every case follows

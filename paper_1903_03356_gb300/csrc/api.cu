@@ -18,27 +18,10 @@
 #include <string>
 #include <vector>
 
-#include "../../include/lbmib.h"
-#include "lbmib_kernels.cuh"
+#include "ctx.cuh"
 
 using namespace lbmib;
-
 namespace {
-
-constexpr size_t kAlign = 256;
-constexpr int kMaxRing = 1024;
-
-inline size_t up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-size_t storage_bytes(lbmib_storage s) { return s == LBMIB_FP64 ? 8 : (s == LBMIB_FP32 ? 4 : 2); }
-
-struct Layout {
-    size_t pops[2], fib[2], mark, list[2], ctr, scratch;
-    size_t X, Xm1, uv, Fint, Fext, L0, c0, s0, age, capid, caps, obs, pts, pts_out;
-    size_t total;
-    int pitch;
-    long long plane;
-};
 
 bool valid_config(const lbmib_config* c) {
     return c && c->nx >= 3 && c->ny >= 3 && c->tau > 0.5 && c->max_capsules >= 0 && c->max_nodes >= 0 &&
@@ -85,50 +68,7 @@ Layout make_layout(const lbmib_config* c) {
 
 }  // namespace
 
-struct lbmib_ctx {
-    int device = 0;  // the device that holds the arena
-    lbmib_config cfg{};
-    Layout lay{};
-    Lat L{};
-    cudaStream_t stream = nullptr;
-    cudaStream_t cap_stream = nullptr;
-    char* arena = nullptr;
-    void* pops[2]{};
-    double* fib[2]{};
-    int* mark = nullptr;
-    int* list[2]{};
-    DevCounters* ctr = nullptr;
-    double* scratch = nullptr;
-    Nodes nd{};
-    CapsuleParams* d_caps = nullptr;
-    double* obs = nullptr;
-    double2* pts = nullptr;
-    double* pts_out = nullptr;
-    std::vector<CapsuleParams> caps;
-    int max_n = 0;
-    double max_extent = 0.0;  // largest reference diameter of a capsule
-    int tile_cells = 256;     // per-capsule shared tile budget
-    int cur = 0;      // population buffer holding the latest post-collision state
-    int cur_fib = 0;  // force buffer holding the last spread force
-    long long steps = 0;
-    long long launches = 0;
-    // options
-    bool use_graphs = true;
-    bool timing = false;
-    int graph_steps = 16;
-    int lattice_variant = 256;
-    // graphs keyed by (scheme, cur, cur_fib)
-    cudaGraphExec_t graphs[2][2][2]{};
-    int graph_len[2][2][2]{};
-    // timing
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
-    size_t ev_used = 0;
-    double timed_ms = 0.0;
-    long long timed_launches = 0;
-    std::string err;
-};
-
-namespace {
+namespace lbmib {
 
 lbmib_status fail(lbmib_ctx* c, lbmib_status s, const std::string& msg) {
     if (c) c->err = msg;
@@ -139,11 +79,7 @@ lbmib_status cuda_fail(lbmib_ctx* c, cudaError_t e, const char* where) {
     return fail(c, LBMIB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-#define LBMIB_CUDA(ctx, call)                                      \
-    do {                                                           \
-        cudaError_t e_ = (call);                                   \
-        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
-    } while (0)
+
 
 void drop_graphs(lbmib_ctx* c) {
     for (auto& a : c->graphs)
@@ -222,6 +158,22 @@ void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
     cur = 1 - cur;
 }
 
+lbmib_status device_status(lbmib_ctx* c) {
+    LBMIB_CUDA(c, cudaStreamSynchronize(c->stream));
+    unsigned st = 0;
+    LBMIB_CUDA(c, cudaMemcpy(&st, &c->ctr->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (st & kStatUnstable) return fail(c, LBMIB_ERR_UNSTABLE, "unstable lattice: |u| > 0.3 or NaN");
+    if (st & kStatSupport) return fail(c, LBMIB_ERR_SUPPORT, "an MLS support or probe left the channel");
+    if (st & kStatTimeout) return fail(c, LBMIB_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (st & (kStatList | kStatCell | kStatRing))
+        return fail(c, LBMIB_ERR_STATE, "device bookkeeping check failed (status bits " + std::to_string(st) + ")");
+    return LBMIB_OK;
+}
+
+}  // namespace lbmib
+
+namespace {
+
 int kernels_per_step(const lbmib_ctx* c) { return c->caps.empty() ? 1 : 4; }
 
 lbmib_status capture(lbmib_ctx* c, lbmib_scheme scheme, int cur, int cur_fib, int len, cudaGraphExec_t* out) {
@@ -236,25 +188,6 @@ lbmib_status capture(lbmib_ctx* c, lbmib_scheme scheme, int cur, int cur_fib, in
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
     return LBMIB_OK;
-}
-
-lbmib_status device_status(lbmib_ctx* c) {
-    LBMIB_CUDA(c, cudaStreamSynchronize(c->stream));
-    unsigned st = 0;
-    LBMIB_CUDA(c, cudaMemcpy(&st, &c->ctr->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
-    if (st & kStatUnstable) return fail(c, LBMIB_ERR_UNSTABLE, "unstable lattice: |u| > 0.3 or NaN");
-    if (st & kStatSupport) return fail(c, LBMIB_ERR_SUPPORT, "an MLS support or probe left the channel");
-    if (st & kStatTimeout) return fail(c, LBMIB_ERR_TIMEOUT, "a bounded device wait gave up");
-    if (st & (kStatList | kStatCell | kStatRing))
-        return fail(c, LBMIB_ERR_STATE, "device bookkeeping check failed (status bits " + std::to_string(st) + ")");
-    return LBMIB_OK;
-}
-
-template <typename F>
-void by_storage(lbmib_storage st, F&& f) {
-    if (st == LBMIB_FP64) f(double{});
-    else if (st == LBMIB_FP32) f(float{});
-    else f(__half{});
 }
 
 }  // namespace

@@ -1,0 +1,103 @@
+// Private to the library: the context record and the step orchestration shared by the
+// public calls (api.cu) and the reverse sweep (adjoint.cu).
+#pragma once
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/lbmib.h"
+#include "lbmib_kernels.cuh"
+
+namespace lbmib {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxRing = 1024;
+
+inline size_t up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+inline size_t storage_bytes(lbmib_storage s) { return s == LBMIB_FP64 ? 8 : (s == LBMIB_FP32 ? 4 : 2); }
+
+// Offsets of the context's buffers inside the caller's arena.
+struct Layout {
+    size_t pops[2], fib[2], mark, list[2], ctr, scratch;
+    size_t X, Xm1, uv, Fint, Fext, L0, c0, s0, age, capid, caps, obs, pts, pts_out;
+    size_t total;
+    int pitch;
+    long long plane;
+};
+
+}  // namespace lbmib
+
+struct lbmib_ctx {
+    int device = 0;  // the device that holds the arena
+    lbmib_config cfg{};
+    lbmib::Layout lay{};
+    lbmib::Lat L{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    char* arena = nullptr;
+    void* pops[2]{};
+    double* fib[2]{};
+    int* mark = nullptr;
+    int* list[2]{};
+    lbmib::DevCounters* ctr = nullptr;
+    double* scratch = nullptr;
+    lbmib::Nodes nd{};
+    lbmib::CapsuleParams* d_caps = nullptr;
+    double* obs = nullptr;
+    double2* pts = nullptr;
+    double* pts_out = nullptr;
+    std::vector<lbmib::CapsuleParams> caps;
+    int max_n = 0;
+    double max_extent = 0.0;  // largest reference diameter of a capsule
+    int tile_cells = 256;     // per-capsule shared tile budget
+    int cur = 0;      // population buffer holding the latest post-collision state
+    int cur_fib = 0;  // force buffer holding the last spread force
+    long long steps = 0;
+    long long launches = 0;
+    // options
+    bool use_graphs = true;
+    bool timing = false;
+    int graph_steps = 16;
+    int lattice_variant = 256;
+    // graphs keyed by (scheme, cur, cur_fib)
+    cudaGraphExec_t graphs[2][2][2]{};
+    int graph_len[2][2][2]{};
+    // timing
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+    size_t ev_used = 0;
+    double timed_ms = 0.0;
+    long long timed_launches = 0;
+    std::string err;
+};
+
+namespace lbmib {
+
+lbmib_status fail(lbmib_ctx* c, lbmib_status s, const std::string& msg);
+lbmib_status cuda_fail(lbmib_ctx* c, cudaError_t e, const char* where);
+
+#define LBMIB_CUDA(ctx, call)                                              \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return ::lbmib::cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+// Destroy the captured step graphs (after the buffers they name change role).
+void drop_graphs(lbmib_ctx* c);
+
+// Enqueue one coupled step on stream s: populations c->pops[cur] -> c->pops[1 - cur],
+// last spread force c->fib[cur_fib]; advances (cur, cur_fib).
+void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cudaStream_t s, bool timed);
+
+// Synchronise the context stream and translate the sticky device status.
+lbmib_status device_status(lbmib_ctx* c);
+
+template <typename F>
+void by_storage(lbmib_storage st, F&& f) {
+    if (st == LBMIB_FP64) f(double{});
+    else if (st == LBMIB_FP32) f(float{});
+    else f(__half{});
+}
+
+}  // namespace lbmib

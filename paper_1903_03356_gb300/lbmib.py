@@ -23,6 +23,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_UNSTABLE, ERR_SUPPORT, ERR_TIMEOUT, ERR_STAT
 FP64, FP32, FP16 = 0, 1, 2
 KINEMATIC, DYNAMIC = 0, 1
 OPT_GRAPHS, OPT_TIMING, OPT_GRAPH_STEPS, OPT_FP16_SCALE, OPT_LATTICE_VARIANT = 1, 2, 3, 4, 5
+OBJ_TAYLOR_D, OBJ_CENTROID_Y, OBJ_CENTROID_X = 0, 1, 2
 STORAGE = {"fp64": FP64, "fp32": FP32, "fp16": FP16}
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_UNSTABLE",
                 5: "ERR_SUPPORT", 6: "ERR_TIMEOUT", 7: "ERR_STATE"}
@@ -86,6 +87,8 @@ _SIGS = {
     "lbmib_kernel_time": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
     "lbmib_launch_count": (C.c_longlong, [_vp]),
     "lbmib_bytes_per_update": (C.c_double, [_vp]),
+    "lbmib_adjoint_workspace_bytes": (C.c_size_t, [_vp, C.c_longlong, C.c_int]),
+    "lbmib_adjoint": (C.c_int, [_vp, C.c_longlong, C.c_int, C.c_int, C.c_int, C.c_int, _vp, C.c_size_t, _vp, _vp]),
     "lbmib_batch_arena_bytes": (C.c_size_t, [_vp, C.c_int, C.c_int]),
     "lbmib_batch_create": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.c_size_t, _vp, C.c_int, C.POINTER(_vp)]),
     "lbmib_batch_destroy": (None, [_vp]),
@@ -223,6 +226,17 @@ def lbmib_launch_count(h) -> int:
 
 def lbmib_bytes_per_update(h) -> float:
     return float(_lib.lbmib_bytes_per_update(h))
+
+
+def lbmib_adjoint_workspace_bytes(h, nsteps: int, ckpt_every: int) -> int:
+    return int(_lib.lbmib_adjoint_workspace_bytes(h, int(nsteps), int(ckpt_every)))
+
+
+def lbmib_adjoint(h, nsteps, scheme, ckpt_every, objective, capsule, d_work, work_bytes, grad):
+    J = C.c_double()
+    _check(h, _lib.lbmib_adjoint(h, int(nsteps), int(scheme), int(ckpt_every), int(objective), int(capsule),
+                                 C.c_void_p(d_work), int(work_bytes), C.byref(J), _p(grad)))
+    return J.value
 
 
 def lbmib_batch_arena_bytes(cases, ncases: int, storage: int) -> int:
@@ -390,6 +404,21 @@ class Context:
 
     def kernel_time(self, reset=False):
         return lbmib_kernel_time(self.h, reset)
+
+    def adjoint(self, nsteps: int, objective: int = OBJ_TAYLOR_D, capsule: int = 0, ckpt_every: int = 200,
+                scheme: int = KINEMATIC):
+        """Advance nsteps steps and return (J, grad) with grad = {dJ/dk_s per capsule,
+        dJ/dk_b per capsule, dJ/dgx, dJ/dgy}; the workspace is a temporary torch buffer."""
+        import torch
+
+        nbytes = lbmib_adjoint_workspace_bytes(self.h, nsteps, ckpt_every)
+        if nbytes == 0:
+            raise LbmibError(ERR_ARG, "invalid adjoint arguments")
+        work = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        grad = np.zeros(2 * len(self._n) + 2)
+        J = lbmib_adjoint(self.h, nsteps, scheme, ckpt_every, objective, capsule, work.data_ptr(), nbytes, grad)
+        del work
+        return J, grad
 
     @property
     def launch_count(self) -> int:

@@ -291,10 +291,10 @@ def roofline_lattice(nx=16384, ny=8192, scheme=DYNAMIC, seed=0, steps=200) -> Ca
 
 
 def adjoint_capsule(nx=512, ny=128, tau=0.7, u_max=0.02, radius=16.0, n=128, ca=0.02,
-                    eb=0.01, density_ratio=1.0, steps=8000) -> Case:
-    """Circular capsule in Poiseuille flow, Dynamic IB, for gradients of D(T), y_c(T)."""
+                    eb=0.01, density_ratio=1.0, steps=8000, scheme=DYNAMIC) -> Case:
+    """Circular capsule in Poiseuille flow at y = 0.3 H, for gradients of D(T), y_c(T)."""
     c = poiseuille_capsule(nx=nx, ny=ny, tau=tau, u_max=u_max, radius=radius, n=n, ca=ca,
-                           eb=eb, density_ratio=density_ratio, scheme=DYNAMIC, steps=steps)
+                           eb=eb, density_ratio=density_ratio, scheme=scheme, steps=steps)
     c.name = "adjoint_capsule"
     return c
 
