@@ -54,6 +54,11 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched-launch and adjoint measurements that follow the main line")
     p.add_argument("--batch-steps", type=int, default=3000, help="steps per case of the batched workload")
+    p.add_argument("--adjoint-steps", type=int, default=800, help="horizon T of the adjoint measurement")
+    p.add_argument("--batch-autotune", type=int, default=20,
+                   help="steps per candidate launch shape of the batch autotuner (0: default shape)")
+    p.add_argument("--only", default="all", choices=["all", "batched", "adjoint"],
+                   help="batched / adjoint: run only that measurement and print its JSON object")
     return p.parse_args()
 
 
@@ -271,8 +276,8 @@ def run_gpu(a):
         line["e2e"] = e2e_run(a, case, L, scheme, dev)
     if rank == 0 and not a.no_extras:
         ctx.close()
-        line["batched"] = batched_run(L, a.batch_steps)
-        line["adjoint"] = adjoint_run(L, a.storage)
+        line["batched"] = batched_run(L, a.batch_steps, a.batch_autotune)
+        line["adjoint"] = adjoint_run(L, a.storage, a.adjoint_steps)
     if rank == 0 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, a.cpu_seconds)
     if rank == 0:
@@ -280,7 +285,7 @@ def run_gpu(a):
     ctx.close()
 
 
-def batched_run(L, steps):
+def batched_run(L, steps, autotune=20):
     """512 independent shear-flow capsule cases (seed 1, uneven sizes and capillary
     numbers) in one persistent launch, FP32, `steps` steps each; against the same cases
     run one after another through single-case contexts (a sample of 32 cases, 300 steps
@@ -289,7 +294,7 @@ def batched_run(L, steps):
 
     cases = W.batch_cases(count=512, seed=1, steps=steps)
     lu = sum(c.nx * c.ny for c in cases)
-    b = L.Batch(cases, storage="fp32", autotune_steps=20)
+    b = L.Batch(cases, storage="fp32", autotune_steps=autotune)
     threads, grid, cells = b.config
     s = b.stream
     b.step(steps)          # graph capture at the timed length, warm-up
@@ -328,14 +333,13 @@ def batched_run(L, steps):
             "sequential_sample": "32 cases x 300 steps through single-case contexts (CUDA graphs)"}
 
 
-def adjoint_run(L, storage):
+def adjoint_run(L, storage, T=800):
     """Gradient of D(T) with respect to (k_s, k_b, g_x) on the 512 x 128 channel capsule
-    (radius 16, 128 vertices, Ca = 0.02), Kinematic, T = 800 with a checkpoint every 200,
+    (radius 16, 128 vertices, Ca = 0.02), Kinematic, T steps with a checkpoint every 200,
     against T forward steps of the same context (cost ratio)."""
     import torch
 
-    case = W.adjoint_capsule(scheme=0, steps=800)
-    T = 800
+    case = W.adjoint_capsule(scheme=0, steps=T)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ctx = L.from_case(case, storage=storage)
     ctx.step(T, L.KINEMATIC)           # warm-up and graph capture
@@ -401,6 +405,15 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.only != "all":
+        import torch
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_1903_03356_gb300 import lbmib as L
+
+        out = (batched_run(L, a.batch_steps, a.batch_autotune) if a.only == "batched"
+               else adjoint_run(L, a.storage, a.adjoint_steps))
+        print(json.dumps(out), flush=True)
     else:
         run_gpu(a)
 

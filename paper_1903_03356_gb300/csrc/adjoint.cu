@@ -64,6 +64,9 @@ __device__ __forceinline__ Dual dexp(Dual a) {
     return {e, e * a.d};
 }
 __device__ __forceinline__ double vpart(Dual a) { return a.v; }
+__device__ __forceinline__ double vpart(double a) { return a; }
+__device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ double dexp(double a) { return exp(a); }
 
 template <typename T>
 struct P2 {
@@ -78,13 +81,15 @@ __device__ __forceinline__ P2<T> operator-(P2<T> a, P2<T> b) { return {a.x - b.x
 // exp(-d_a^2 / (r_w alpha)^2):
 //   q_a = w_a / S0                    (S0 = sum w, normalised weights)
 //   h_a = q_a - m w_a (d_a - m) / V   (m = sum w d / S0, V = sum w (d - m)^2)
+//   g_a = w_a (d_a - m) / V           (slope of the linear fit)
 // and the 2-D linear-basis shape function is phi_ab = h^x_a q^y_b + q^x_a h^y_b -
-// q^x_a q^y_b (the closed-form MLS solve of the forward kernels written per axis).
+// q^x_a q^y_b, the fitted x-slope weight g^x_a q^y_b and the y-slope weight q^x_a g^y_b
+// (the closed-form MLS solve of the forward kernels written per axis).
 // Evaluated on duals with d(d_a)/dX = -1 they give d(phi)/dX and d(phi)/dY.
 // ---------------------------------------------------------------------------------
 template <typename T>
 struct Axis {
-    T q[3], h[3];
+    T q[3], h[3], g[3];   // normalised weights, linear-fit value weights, slope weights
 };
 
 template <typename T>
@@ -107,6 +112,7 @@ __device__ Axis<T> mls_axis(T d0) {
     for (int a = 0; a < 3; a++) {
         r.q[a] = w[a] / s0;
         r.h[a] = r.q[a] - (m * w[a] * (d[a] - m)) / V;
+        r.g[a] = (w[a] * (d[a] - m)) / V;
     }
     return r;
 }
@@ -185,24 +191,27 @@ __device__ void membrane_parts(int v, int n, GetX X, const double* L0, const dou
 // ---------------------------------------------------------------------------------
 enum { kObjTaylorD = 0, kObjCentroidY = 1, kObjCentroidX = 2 };
 
-template <typename T, typename GetX>
-__device__ T ring_objective(int n, GetX X, int kind) {
-    const P2<T> X0 = X(0);
-    T s[6] = {T{0.0}, T{0.0}, T{0.0}, T{0.0}, T{0.0}, T{0.0}};
-    for (int i = 0; i < n; i++) {
-        const P2<T> a = X(i) - X0, b = X(i + 1 == n ? 0 : i + 1) - X0;
-        const T c = a.x * b.y - b.x * a.y;
-        s[0] = s[0] + c;
-        s[1] = s[1] + (a.x + b.x) * c;
-        s[2] = s[2] + (a.y + b.y) * c;
-        s[3] = s[3] + (a.x * a.x + a.x * b.x + b.x * b.x) * c;
-        s[4] = s[4] + (a.y * a.y + a.y * b.y + b.y * b.y) * c;
-        s[5] = s[5] + (a.x * b.y + 2.0 * (a.x * a.y) + 2.0 * (b.x * b.y) + b.x * a.y) * c;
-    }
+// Contribution of the ring term (a, b) = (X_i - c, X_{i+1} - c) to the six area sums
+// s = {2A, 6A xc, 6A yc, 12 Sxx, 12 Syy, 24 Sxy} (Green's theorem about a fixed point c).
+template <typename T>
+__device__ __forceinline__ void ring_term_sums(P2<T> a, P2<T> b, T (&s)[6]) {
+    const T c = a.x * b.y - b.x * a.y;
+    s[0] = s[0] + c;
+    s[1] = s[1] + (a.x + b.x) * c;
+    s[2] = s[2] + (a.y + b.y) * c;
+    s[3] = s[3] + (a.x * a.x + a.x * b.x + b.x * b.x) * c;
+    s[4] = s[4] + (a.y * a.y + a.y * b.y + b.y * b.y) * c;
+    s[5] = s[5] + (a.x * b.y + 2.0 * (a.x * a.y) + 2.0 * (b.x * b.y) + b.x * a.y) * c;
+}
+
+// The objective from the six sums: centroid (offset by c) or the Taylor deformation
+// from the eigenvalues of the area second-moment tensor about the centroid.
+template <typename T>
+__device__ T objective_from_sums(const T (&s)[6], double2 c, int kind) {
     const T A = 0.5 * s[0];
     const T cx = s[1] / (6.0 * A), cy = s[2] / (6.0 * A);
-    if (kind == kObjCentroidY) return cy + X0.y;
-    if (kind == kObjCentroidX) return cx + X0.x;
+    if (kind == kObjCentroidY) return cy + c.y;
+    if (kind == kObjCentroidX) return cx + c.x;
     const T Ixx = (1.0 / 12.0) * s[3] - A * (cx * cx);
     const T Iyy = (1.0 / 12.0) * s[4] - A * (cy * cy);
     const T Ixy = (1.0 / 24.0) * s[5] - A * (cx * cy);
@@ -214,21 +223,44 @@ __device__ T ring_objective(int n, GetX X, int kind) {
     return (a - b) / (a + b);
 }
 
-// dJ/dX for every vertex of capsule `cap` (one dual evaluation per coordinate), J itself.
+// J and dJ/dX of capsule `cap`. The objectives are invariant under a shift of the ring
+// (the centroid shifts with it), so the sums are taken about the fixed point c = X_0 and
+// dJ/dX_v = sum_k dJ/ds_k ds_k/dX_v, where only the two ring terms that hold X_v
+// depend on it: O(n) work. One block.
 __global__ void k_adj_objective(Nodes nd, int cap, int kind, double2* xc, double* J) {
+    __shared__ double red[32 * 8];
     const CapsuleParams P = nd.caps[cap];
     const int n = P.n;
     const double2* X = nd.X + P.off;
-    for (int j = threadIdx.x; j < 2 * n; j += blockDim.x) {
-        const int vs = j >> 1, comp = j & 1;
-        auto get = [&](int i) {
-            const double2 p = X[i];
-            return P2<Dual>{mk(p.x, i == vs && comp == 0 ? 1.0 : 0.0), mk(p.y, i == vs && comp == 1 ? 1.0 : 0.0)};
-        };
-        const Dual r = ring_objective<Dual>(n, get, kind);
-        if (comp == 0) xc[P.off + vs].x = r.d;
-        else xc[P.off + vs].y = r.d;
-        if (j == 0) *J = r.v;
+    const double2 c = X[0];
+    auto rel = [&](int i) { return P2<double>{X[i].x - c.x, X[i].y - c.y}; };
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) ring_term_sums<double>(rel(i), rel(i + 1 == n ? 0 : i + 1), s);
+    block_reduce<6, false>(s, red);
+    if (threadIdx.x == 0) *J = objective_from_sums<double>(s, c, kind);
+    double dJ[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        Dual sd[6];
+#pragma unroll
+        for (int m = 0; m < 6; m++) sd[m] = mk(s[m], m == k ? 1.0 : 0.0);
+        dJ[k] = objective_from_sums<Dual>(sd, c, kind).d;
+    }
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const P2<double> xl = rel(v == 0 ? n - 1 : v - 1), xv = rel(v), xr = rel(v + 1 == n ? 0 : v + 1);
+        double g[2];
+#pragma unroll
+        for (int comp = 0; comp < 2; comp++) {
+            const P2<Dual> dv{mk(xv.x, comp == 0 ? 1.0 : 0.0), mk(xv.y, comp == 1 ? 1.0 : 0.0)};
+            Dual ds[6] = {mk(0.0), mk(0.0), mk(0.0), mk(0.0), mk(0.0), mk(0.0)};
+            ring_term_sums<Dual>(P2<Dual>{mk(xl.x), mk(xl.y)}, dv, ds);
+            ring_term_sums<Dual>(dv, P2<Dual>{mk(xr.x), mk(xr.y)}, ds);
+            double t = 0.0;
+#pragma unroll
+            for (int k = 0; k < 6; k++) t += dJ[k] * ds[k].d;
+            g[comp] = t;
+        }
+        xc[P.off + v] = make_double2(g[0], g[1]);
     }
 }
 
@@ -236,7 +268,7 @@ __global__ void k_adj_objective(Nodes nd, int cap, int kind, double2* xc, double
 // R0: membrane forces at X^n (saved per vertex) and their spread into the force field.
 // ---------------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_adj_spread(Lat L, Nodes nd, const double2* Xn, int max_n, double2* Fv,
-                                                    double* fib) {
+                                                    Shape* shp, double* fib) {
     extern __shared__ __align__(16) unsigned char smem[];
     const CapSmem sm = carve(smem, max_n);
     const CapsuleParams P = nd.caps[blockIdx.x];
@@ -252,6 +284,7 @@ __global__ void __launch_bounds__(128) k_adj_spread(Lat L, Nodes nd, const doubl
         const double2 F = node_internal_force(sm, P, v, 0.5 * area2[0]);
         Fv[off + v] = F;
         const Shape s = shape_with_derivatives(L, sm.X[v].x, sm.X[v].y);
+        shp[off + v] = s;   // reused by the interpolation and spread transposes
 #pragma unroll
         for (int b = 0; b < 3; b++)
 #pragma unroll
@@ -266,62 +299,69 @@ __global__ void __launch_bounds__(128) k_adj_spread(Lat L, Nodes nd, const doubl
 // ---------------------------------------------------------------------------------
 // R1: transposes of the advance (Eq. 25) and of the interpolation (Eq. 8 with the Eq. 7
 // velocity u_k = (m_k + (g + fib_k)/2) / rho_k at the support nodes). One thread per
-// vertex.
+// (vertex, support node); X-bar of X^n accumulates in xnew (zero on entry), completed
+// by R3.
 // ---------------------------------------------------------------------------------
 template <typename S>
-__global__ void k_adj_interp(Lat L, const S* __restrict__ post1, const double* __restrict__ fib, const double2* Xn,
-                             const int* age0, int nloc, int count, double2* xc, double2* xp,
-                             typename St<S>::C* sbar, double* bbar, double* grad_g, unsigned* status) {
-    using C = typename St<S>::C;
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(288) k_adj_interp(Lat L, const S* __restrict__ post1,
+                                                    const double* __restrict__ fib, const Shape* __restrict__ shp,
+                                                    const int* age0, int nloc, int count, const double2* xc,
+                                                    double2* xp, double2* xnew, double* sbar,
+                                                    double* bbar, double* grad_g, unsigned* status) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = t / 9, k = t - 9 * (t / 9);
     double gsx = 0.0, gsy = 0.0;
     if (v < count) {
         const bool first = age0[v] + nloc == 0;
-        const double2 c = xc[v], p = xp[v];
-        const double kU = first ? 1.0 : 2.0 / 3.0, kX = first ? 1.0 : 4.0 / 3.0;
+        const double2 c = xc[v];
+        const double kU = first ? 1.0 : 2.0 / 3.0;
         const double Ux = kU * c.x, Uy = kU * c.y;
-        double ax = p.x + kX * c.x, ay = p.y + kX * c.y;
-        xp[v] = first ? make_double2(0.0, 0.0) : make_double2(-c.x / 3.0, -c.y / 3.0);
-        const Shape s = shape_with_derivatives(L, Xn[v].x, Xn[v].y);
-        if (!s.ok) atomicOr(status, kStatSupport);
+        if (k == 0) {
+            const double kX = first ? 1.0 : 4.0 / 3.0;
+            const double2 p = xp[v];
+            atomicAdd(&xnew[v].x, p.x + kX * c.x);
+            atomicAdd(&xnew[v].y, p.y + kX * c.y);
+            xp[v] = first ? make_double2(0.0, 0.0) : make_double2(-c.x / 3.0, -c.y / 3.0);
+            if (!shp[v].ok) atomicOr(status, kStatSupport);
+        }
+        const int a = k % 3, b = k / 3;
+        const Shape& s = shp[v];
         const long long N = (long long)L.nx * L.ny;
-#pragma unroll 1
-        for (int b = 0; b < 3; b++)
-#pragma unroll 1
-            for (int a = 0; a < 3; a++) {
-                const int xk = wrapi(s.cx + a - 1, L.nx), yk = support_row(L, s.cy + b - 1);
-                const long long cell = (long long)yk * L.nx + xk;
-                double q[9];
+        const int xk = wrapi(s.cx + a - 1, L.nx), yk = support_row(L, s.cy + b - 1);
+        const long long cell = (long long)yk * L.nx + xk;
+        double q[9];
 #pragma unroll
-                for (int i = 0; i < 9; i++) q[i] = (double)pull<S>(post1, L, i, xk, yk);
-                double drho = 0.0, mx = 0.0, my = 0.0;
+        for (int i = 0; i < 9; i++) q[i] = (double)pull<S>(post1, L, i, xk, yk);
+        double drho = 0.0, mx = 0.0, my = 0.0;
 #pragma unroll
-                for (int i = 0; i < 9; i++) {
-                    drho += q[i];
-                    mx += ex(i) * q[i];
-                    my += ey(i) * q[i];
-                }
-                const double rho = 1.0 + drho;
-                const double ux = (mx + 0.5 * (L.gx + fib[cell])) / rho;
-                const double uy = (my + 0.5 * (L.gy + fib[N + cell])) / rho;
-                const double uU = ux * Ux + uy * Uy;
-                ax += s.px[b][a] * uU;
-                ay += s.py[b][a] * uU;
-                const double cf = s.phi[b][a] / rho;
+        for (int i = 0; i < 9; i++) {
+            drho += q[i];
+            mx += ex(i) * q[i];
+            my += ey(i) * q[i];
+        }
+        const double rho = 1.0 + drho;
+        const double ux = (mx + 0.5 * (L.gx + fib[cell])) / rho;
+        const double uy = (my + 0.5 * (L.gy + fib[N + cell])) / rho;
+        const double uU = ux * Ux + uy * Uy;
+        atomicAdd(&xnew[v].x, s.px[b][a] * uU);
+        atomicAdd(&xnew[v].y, s.py[b][a] * uU);
+        const double cf = s.phi[b][a] / rho;
 #pragma unroll
-                for (int i = 0; i < 9; i++) {
-                    const double g = cf * ((ex(i) - ux) * Ux + (ey(i) - uy) * Uy);
-                    atomicAdd(sbar + (long long)i * N + cell, (C)g);
-                }
-                atomicAdd(bbar + cell, 0.5 * cf * Ux);
-                atomicAdd(bbar + N + cell, 0.5 * cf * Uy);
-                gsx += 0.5 * cf * Ux;
-                gsy += 0.5 * cf * Uy;
-            }
-        xc[v] = make_double2(ax, ay);
+        for (int i = 0; i < 9; i++)
+            atomicAdd(sbar + (long long)i * N + cell, cf * ((ex(i) - ux) * Ux + (ey(i) - uy) * Uy));
+        atomicAdd(bbar + cell, 0.5 * cf * Ux);
+        atomicAdd(bbar + N + cell, 0.5 * cf * Uy);
+        gsx = 0.5 * cf * Ux;
+        gsy = 0.5 * cf * Uy;
     }
-    if (gsx != 0.0) atomicAdd(grad_g, gsx);
-    if (gsy != 0.0) atomicAdd(grad_g + 1, gsy);
+    for (int o = 16; o > 0; o >>= 1) {
+        gsx += __shfl_xor_sync(0xffffffffu, gsx, o);
+        gsy += __shfl_xor_sync(0xffffffffu, gsy, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (gsx != 0.0 || gsy != 0.0)) {
+        atomicAdd(grad_g, gsx);
+        atomicAdd(grad_g + 1, gsy);
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -379,12 +419,10 @@ __device__ __forceinline__ void collide_adjoint(const C s[9], C Fx, C Fy, C omeg
 
 template <typename S>
 __global__ void __launch_bounds__(256) k_adj_lattice(const S* __restrict__ post0, Lat L,
-                                                     const typename St<S>::C* __restrict__ sb_in,
-                                                     typename St<S>::C* __restrict__ sb_out,
-                                                     typename St<S>::C* __restrict__ fbar,
-                                                     const double* __restrict__ fib, double* fib_clear,
-                                                     double* bbar_clear, double* grad_g) {
-    using C = typename St<S>::C;
+                                                     const double* __restrict__ sb_in, double* __restrict__ sb_out,
+                                                     double* __restrict__ fbar, const double* __restrict__ fib,
+                                                     double* fib_clear, double* bbar_clear, double* grad_g) {
+    using C = double;   // adjoint fields are double in every storage mode
     __shared__ double red[2 * 32];
     const long long N = (long long)L.nx * L.ny;
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -403,10 +441,10 @@ __global__ void __launch_bounds__(256) k_adj_lattice(const S* __restrict__ post0
             }
         }
 #pragma unroll
-        for (int i = 0; i < 9; i++) s[i] = pull<S>(post0, L, i, x, y);
-        const C Fx = C(L.gx + fib[node]), Fy = C(L.gy + fib[N + node]);
+        for (int i = 0; i < 9; i++) s[i] = (double)pull<S>(post0, L, i, x, y);
+        const C Fx = L.gx + fib[node], Fy = L.gy + fib[N + node];
         C Fbx, Fby;
-        collide_adjoint<C>(s, Fx, Fy, lat_c<C>(L.omega, L.omegaf), pb, sb, Fbx, Fby);
+        collide_adjoint<C>(s, Fx, Fy, L.omega, pb, sb, Fbx, Fby);
 #pragma unroll
         for (int i = 0; i < 9; i++) sb_out[(long long)i * N + node] = sb[i];
         fbar[node] = Fbx;
@@ -439,49 +477,12 @@ __global__ void __launch_bounds__(256) k_adj_lattice(const S* __restrict__ post0
     }
 }
 
-// ---------------------------------------------------------------------------------
-// R3: spread and membrane transposes, one CTA per capsule.
-//   F-bar_v = sum_k phi_k(X_v) fib-bar_k,  X-bar_v += sum_k grad phi_k (fib-bar_k . F_v)
-//   X-bar_v += d/de F_v(X + e F-bar),      k_s-bar += F-bar . Fs,  k_b-bar += F-bar . Fb
-// with fib-bar = (collision force adjoint) + (interpolation half-force adjoint).
-// ---------------------------------------------------------------------------------
-template <typename C>
-__global__ void __launch_bounds__(128) k_adj_membrane(Lat L, Nodes nd, const double2* Xn, int max_n,
-                                                      const double2* Fv, const C* __restrict__ fbar,
-                                                      const double* __restrict__ bbar, double2* xc, int ncaps,
-                                                      double* grad) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const CapSmem sm = carve(smem, max_n);
-    const int cap = blockIdx.x;
-    const CapsuleParams P = nd.caps[cap];
-    if (P.n < 3 || P.n > max_n) return;
+// Membrane transpose of one capsule (collective): with the vertices in sm.X and F-bar in
+// sm.ext, adds d/de F_v(X + e F-bar) (= (dF/dX)^T F-bar, the Jacobian being symmetric)
+// to sm.xd[v], and F-bar . dF/dk to the k_s and k_b gradients of capsule `cap`.
+__device__ void membrane_transpose(const CapSmem& sm, const CapsuleParams& P, const Nodes& nd, int cap, int ncaps,
+                                   double* grad) {
     const int n = P.n, off = P.off;
-    const long long N = (long long)L.nx * L.ny;
-    for (int v = threadIdx.x; v < n; v += blockDim.x) sm.X[v] = Xn[off + v];
-    __syncthreads();
-    for (int v = threadIdx.x; v < n; v += blockDim.x) {
-        const Shape s = shape_with_derivatives(L, sm.X[v].x, sm.X[v].y);
-        const double2 F = Fv[off + v];
-        double fbx = 0.0, fby = 0.0, gxv = 0.0, gyv = 0.0;
-#pragma unroll
-        for (int b = 0; b < 3; b++)
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                const int cell = support_cell(L, s, a, b);
-                const double tx = (double)fbar[cell] + bbar[cell];
-                const double ty = (double)fbar[N + cell] + bbar[N + cell];
-                fbx += s.phi[b][a] * tx;
-                fby += s.phi[b][a] * ty;
-                const double tF = tx * F.x + ty * F.y;
-                gxv += s.px[b][a] * tF;
-                gyv += s.py[b][a] * tF;
-            }
-        sm.ext[v] = make_double2(fbx, fby);   // F-bar of vertex v
-        const double2 c = xc[off + v];
-        xc[off + v] = make_double2(c.x + gxv, c.y + gyv);
-    }
-    __syncthreads();
-    // area along the direction F-bar
     double ar[2] = {0.0, 0.0};
     auto getd = [&](int k) {
         const double2 p = sm.X[k], t = sm.ext[k];
@@ -502,14 +503,430 @@ __global__ void __launch_bounds__(128) k_adj_membrane(Lat L, Nodes nd, const dou
         const double2 fb = sm.ext[v];
         kk[0] += fb.x * Fs.x.v + fb.y * Fs.y.v;
         kk[1] += fb.x * Fb.x.v + fb.y * Fb.y.v;
-        const double2 c = xc[off + v];
-        xc[off + v] = make_double2(c.x + P.ks * Fs.x.d + P.kb * Fb.x.d + P.ka * Fa.x.d,
-                                   c.y + P.ks * Fs.y.d + P.kb * Fb.y.d + P.ka * Fa.y.d);
+        const double2 c = sm.xd[v];
+        sm.xd[v] = make_double2(c.x + P.ks * Fs.x.d + P.kb * Fb.x.d + P.ka * Fa.x.d,
+                                c.y + P.ks * Fs.y.d + P.kb * Fb.y.d + P.ka * Fa.y.d);
     }
     block_reduce<2, false>(kk, sm.red);
     if (threadIdx.x == 0) {
         grad[cap] += kk[0];
         grad[ncaps + cap] += kk[1];
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// R3: spread and membrane transposes, one CTA per capsule.
+//   F-bar_v = sum_k phi_k(X_v) fib-bar_k,  X-bar_v += sum_k grad phi_k (fib-bar_k . F_v)
+//   X-bar_v += d/de F_v(X + e F-bar),      k_s-bar += F-bar . Fs,  k_b-bar += F-bar . Fb
+// with fib-bar = (collision force adjoint) + (interpolation half-force adjoint).
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_adj_membrane(Lat L, Nodes nd, const double2* Xn, int max_n,
+                                                      const double2* Fv, const Shape* __restrict__ shp,
+                                                      const double* __restrict__ fbar, const double* __restrict__ bbar,
+                                                      double2* xnew, double2* xc, int ncaps, double* grad) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CapSmem sm = carve(smem, max_n);
+    const int cap = blockIdx.x;
+    const CapsuleParams P = nd.caps[cap];
+    if (P.n < 3 || P.n > max_n) return;
+    const int n = P.n, off = P.off;
+    const long long N = (long long)L.nx * L.ny;
+    for (int v = threadIdx.x; v < n; v += blockDim.x) sm.X[v] = Xn[off + v];
+    __syncthreads();
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const Shape& s = shp[off + v];
+        const double2 F = Fv[off + v];
+        double fbx = 0.0, fby = 0.0, gxv = 0.0, gyv = 0.0;
+#pragma unroll
+        for (int b = 0; b < 3; b++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const int cell = support_cell(L, s, a, b);
+                const double tx = fbar[cell] + bbar[cell];
+                const double ty = fbar[N + cell] + bbar[N + cell];
+                fbx += s.phi[b][a] * tx;
+                fby += s.phi[b][a] * ty;
+                const double tF = tx * F.x + ty * F.y;
+                gxv += s.px[b][a] * tF;
+                gyv += s.py[b][a] * tF;
+            }
+        sm.ext[v] = make_double2(fbx, fby);   // F-bar of vertex v
+        const double2 c = xnew[off + v];
+        sm.xd[v] = make_double2(c.x + gxv, c.y + gyv);
+        xnew[off + v] = make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    membrane_transpose(sm, P, nd, cap, ncaps, grad);
+    for (int v = threadIdx.x; v < n; v += blockDim.x) xc[off + v] = sm.xd[v];
+}
+
+// =================================================================================
+// Dynamic scheme (Section 2.3.2, steps 1-8; Eq. 15-16, 21-24). Forward step n:
+//   U1 = I(s^n, fib^{n-1}, X^n)         (first step of a vertex: u_v := U1, X^{n-1} := X^n - U1)
+//   F_l = u_v - U1,  c_l = (l_left + l_right)/2,  fib^n = sum phi(X^n) c_l F_l
+//   post^{n+1} = Coll(s^n, g + fib^n)
+//   U2 = I(s^{n+1}, fib^n, X^n),  F^ext = tractions(s^{n+1}, fib^n, X^n),  F^int = F(X^n)
+//   X^{n+1} = X^n + U2 + (F^int + F^ext) / (2 m)                               (Eq. 23)
+//   u_v^{n+1} = 3/2 X^{n+1} - 2 X^n + 1/2 X^{n-1}                             (Eq. 24)
+// The reverse sweep carries S = dJ/ds^{n+1}, B^n = dJ/dfib^n (from the next step's U1),
+// Xc = dJ/dX^{n+1}, Xm = dJ/dX^n through the X^{n-1} slot and Ub = dJ/du_v^{n+1}.
+// =================================================================================
+
+// MLS density and velocity gradient at probe P from the fields of its 3x3 support
+// (centre fixed), for any scalar type.
+template <typename T>
+struct ProbeVal {
+    T rho, G[2][2];   // G[a][b] = d u_a / d x_b
+};
+
+template <typename T>
+__device__ ProbeVal<T> probe_eval(T Px, T Py, int cx, int cy, const double* drho, const double* ux,
+                                  const double* uy) {
+    const Axis<T> ax = mls_axis<T>(T{(double)cx} - Px), ay = mls_axis<T>(T{(double)cy} - Py);
+    ProbeVal<T> o;
+    o.rho = T{1.0};
+    o.G[0][0] = o.G[0][1] = o.G[1][0] = o.G[1][1] = T{0.0};
+#pragma unroll
+    for (int b = 0; b < 3; b++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const int k = 3 * b + a;
+            const T phi = ax.h[a] * ay.q[b] + ax.q[a] * ay.h[b] - ax.q[a] * ay.q[b];
+            const T gx = ax.g[a] * ay.q[b], gy = ax.q[a] * ay.g[b];
+            o.rho = o.rho + drho[k] * phi;
+            o.G[0][0] = o.G[0][0] + ux[k] * gx;
+            o.G[0][1] = o.G[0][1] + ux[k] * gy;
+            o.G[1][0] = o.G[1][0] + uy[k] * gx;
+            o.G[1][1] = o.G[1][1] + uy[k] * gy;
+        }
+    return o;
+}
+
+// Field samples of the two probes of an element: density deviation and Eq. 7 velocity
+// (with half of g + fib) at the 9 support nodes of each probe.
+struct ProbeFields {
+    int cx[2], cy[2];
+    double f[2][3][9];   // [probe][drho, ux, uy][support]
+};
+
+// Traction of one element (Eq. 15-16): probes at the element centroid +/- 1.2 n with
+// n = (dy, -dx)/l the outward normal of a counter-clockwise ring; p = rho/3,
+// tau = rho nu (G + G^T); F = l (-(p+ - p-) n + (tau+ - tau-) n). Any scalar type.
+template <typename T>
+__device__ P2<T> element_traction(P2<T> X1, P2<T> X2, const ProbeFields& pf, double nu) {
+    const P2<T> d = X2 - X1;
+    const T len = dsqrt(d.x * d.x + d.y * d.y);
+    const P2<T> nn{d.y / len, -(d.x / len)};
+    const P2<T> C{0.5 * (X1.x + X2.x), 0.5 * (X1.y + X2.y)};
+    ProbeVal<T> o[2];
+#pragma unroll
+    for (int s = 0; s < 2; s++) {
+        const double sg = s == 0 ? 1.2 : -1.2;
+        o[s] = probe_eval<T>(C.x + sg * nn.x, C.y + sg * nn.y, pf.cx[s], pf.cy[s], pf.f[s][0], pf.f[s][1],
+                             pf.f[s][2]);
+    }
+    const T dp = (1.0 / 3.0) * (o[0].rho - o[1].rho);
+    const T n_[2] = {nn.x, nn.y};
+    T F[2];
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        T t = -(dp * n_[a]);
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            const T tp = nu * (o[0].rho * (o[0].G[a][b] + o[0].G[b][a]));
+            const T tm = nu * (o[1].rho * (o[1].G[a][b] + o[1].G[b][a]));
+            t = t + (tp - tm) * n_[b];
+        }
+        F[a] = len * t;
+    }
+    return P2<T>{F[0], F[1]};
+}
+
+// DR0: the spread force of step n-1 (and of step n at the first reverse step of a
+// segment) from the taped c_l F_l, and the MLS shapes at X^n.
+__global__ void __launch_bounds__(128) k_adjd_spread(Lat L, Nodes nd, int max_n, const double2* Xn,
+                                                     const double2* Xp, const double2* Flc_n,
+                                                     const double2* Flc_p, double* fib_n, double* fib_p,
+                                                     Shape* shp) {
+    const CapsuleParams P = nd.caps[blockIdx.x];
+    if (P.n < 3 || P.n > max_n) return;
+    const long long N = (long long)L.nx * L.ny;
+    for (int v = threadIdx.x; v < P.n; v += blockDim.x) {
+        const int g = P.off + v;
+        const Shape s = shape_with_derivatives(L, Xn[g].x, Xn[g].y);
+        shp[g] = s;
+        if (fib_n) {
+            const double2 F = Flc_n[g];
+#pragma unroll
+            for (int b = 0; b < 3; b++)
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    const int cell = support_cell(L, s, a, b);
+                    atomicAdd(fib_n + cell, s.phi[b][a] * F.x);
+                    atomicAdd(fib_n + N + cell, s.phi[b][a] * F.y);
+                }
+        }
+        if (fib_p) {
+            const Shape sp = shape_with_derivatives(L, Xp[g].x, Xp[g].y);
+            const double2 F = Flc_p[g];
+#pragma unroll
+            for (int b = 0; b < 3; b++)
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    const int cell = support_cell(L, sp, a, b);
+                    atomicAdd(fib_p + cell, sp.phi[b][a] * F.x);
+                    atomicAdd(fib_p + N + cell, sp.phi[b][a] * F.y);
+                }
+        }
+    }
+}
+
+// Fields (density deviation, Eq. 7 velocity, density) at lattice node (xk, yk).
+template <typename S>
+__device__ __forceinline__ void node_fields(const S* __restrict__ post, const Lat& L, const double* __restrict__ fib,
+                                            int xk, int yk, double& drho, double& ux, double& uy) {
+    const long long N = (long long)L.nx * L.ny;
+    const long long cell = (long long)yk * L.nx + xk;
+    double mx = 0.0, my = 0.0;
+    drho = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const double q = (double)pull<S>(post, L, i, xk, yk);
+        drho += q;
+        mx += ex(i) * q;
+        my += ey(i) * q;
+    }
+    const double rho = 1.0 + drho;
+    ux = (mx + 0.5 * (L.gx + fib[cell])) / rho;
+    uy = (my + 0.5 * (L.gy + fib[N + cell])) / rho;
+}
+
+// Adjoint of the fields at support node `cell`: drho-bar and u-bar into the population
+// adjoint (drho = sum s, u = (m + (g + fib)/2) / rho) and the half-force adjoint.
+__device__ __forceinline__ void inject_fields(const Lat& L, long long cell, double drho_b, double ubx, double uby,
+                                              double ux, double uy, double rho, double* sbar, double* bbar,
+                                              double& gsx, double& gsy) {
+    const long long N = (long long)L.nx * L.ny;
+#pragma unroll
+    for (int i = 0; i < 9; i++)
+        atomicAdd(sbar + (long long)i * N + cell, drho_b + ((ex(i) - ux) * ubx + (ey(i) - uy) * uby) / rho);
+    atomicAdd(bbar + cell, 0.5 * ubx / rho);
+    atomicAdd(bbar + N + cell, 0.5 * uby / rho);
+    gsx += 0.5 * ubx / rho;
+    gsy += 0.5 * uby / rho;
+}
+
+// DR1: transposes of Eq. 24, Eq. 23, the membrane force and the tractions, one CTA per
+// capsule. Writes dJ/dX^n (partial) to xout, U2-bar to u2b, keeps dJ/dX^{n-1} (from
+// Eq. 24) in xm for DR3.
+template <typename S>
+__global__ void __launch_bounds__(128) k_adjd_update(Lat L, Nodes nd, int max_n, const double2* Xn,
+                                                     const S* __restrict__ post1, const double* __restrict__ fib,
+                                                     const double2* xc, double2* xm, const double2* ub,
+                                                     double2* xout, double2* u2b, double* sbar, double* bbar,
+                                                     int ncaps, double* grad, unsigned* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CapSmem sm = carve(smem, max_n);
+    const int cap = blockIdx.x;
+    const CapsuleParams P = nd.caps[cap];
+    if (P.n < 3 || P.n > max_n) return;
+    const int n = P.n, off = P.off;
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const int g = off + v;
+        sm.X[v] = Xn[g];
+        const double2 u = ub[g], c = xc[g];
+        const double2 ct = make_double2(c.x + 1.5 * u.x, c.y + 1.5 * u.y);   // dJ/dX^{n+1} in total
+        u2b[g] = ct;
+        sm.ext[v] = make_double2(ct.x / (2.0 * P.m), ct.y / (2.0 * P.m));       // F^tot-bar
+        const double2 m = xm[g];
+        sm.xd[v] = make_double2(m.x - 2.0 * u.x + ct.x, m.y - 2.0 * u.y + ct.y);
+        xm[g] = make_double2(0.5 * u.x, 0.5 * u.y);                             // dJ/dX^{n-1}
+    }
+    __syncthreads();
+    membrane_transpose(sm, P, nd, cap, ncaps, grad);
+    // tractions: one thread per element, position adjoints of both ends staged in bdl/bdr
+    double gsx = 0.0, gsy = 0.0;
+    bool ok = true;
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+        const int l2 = l + 1 == n ? 0 : l + 1;
+        const double2 X1 = sm.X[l], X2 = sm.X[l2];
+        const double2 fb1 = sm.ext[l], fb2 = sm.ext[l2];
+        const double Fbx = 0.5 * (fb1.x + fb2.x), Fby = 0.5 * (fb1.y + fb2.y);
+        const double dx = X2.x - X1.x, dy = X2.y - X1.y, len = sqrt(dx * dx + dy * dy);
+        const double nx = dy / len, ny = -dx / len;
+        const double Cx = 0.5 * (X1.x + X2.x), Cy = 0.5 * (X1.y + X2.y);
+        ProbeFields pf;
+        long long cells[2][9];
+        double rho_k[2][9];
+        for (int s = 0; s < 2; s++) {
+            const double sg = s == 0 ? 1.2 : -1.2;
+            double Px = Cx + sg * nx, Py = Cy + sg * ny;
+            ok &= support_centre(L, Px, Py, pf.cx[s], pf.cy[s]);
+            for (int b = 0; b < 3; b++)
+                for (int a = 0; a < 3; a++) {
+                    const int k = 3 * b + a;
+                    const int xk = wrapi(pf.cx[s] + a - 1, L.nx), yk = support_row(L, pf.cy[s] + b - 1);
+                    cells[s][k] = (long long)yk * L.nx + xk;
+                    node_fields<S>(post1, L, fib, xk, yk, pf.f[s][0][k], pf.f[s][1][k], pf.f[s][2][k]);
+                    rho_k[s][k] = 1.0 + pf.f[s][0][k];
+                }
+        }
+        // position transpose: four directional derivatives (dual numbers)
+        double e[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const P2<Dual> D1{mk(X1.x, j == 0 ? 1.0 : 0.0), mk(X1.y, j == 1 ? 1.0 : 0.0)};
+            const P2<Dual> D2{mk(X2.x, j == 2 ? 1.0 : 0.0), mk(X2.y, j == 3 ? 1.0 : 0.0)};
+            const P2<Dual> F = element_traction<Dual>(D1, D2, pf, L.nu);
+            e[j] = Fbx * F.x.d + Fby * F.y.d;
+        }
+        sm.bdl[l] = make_double2(e[0], e[1]);    // to vertex l
+        sm.bdr[l] = make_double2(e[2], e[3]);    // to vertex l + 1
+        // field transpose
+        const double nn[2] = {nx, ny}, Fb[2] = {Fbx, Fby};
+        for (int s = 0; s < 2; s++) {
+            const double sgn = s == 0 ? 1.0 : -1.0;
+            const ProbeVal<double> o = probe_eval<double>(Cx + sgn * 1.2 * nx, Cy + sgn * 1.2 * ny, pf.cx[s],
+                                                          pf.cy[s], pf.f[s][0], pf.f[s][1], pf.f[s][2]);
+            // dF/drho and dF/dG of this probe, contracted with F-bar
+            double rho_b = 0.0, Gb[2][2];
+            for (int a = 0; a < 2; a++) {
+                double t = -nn[a] / 3.0;
+                for (int b = 0; b < 2; b++) t += L.nu * (o.G[a][b] + o.G[b][a]) * nn[b];
+                rho_b += Fb[a] * sgn * len * t;
+            }
+            for (int a = 0; a < 2; a++)
+                for (int b = 0; b < 2; b++)
+                    Gb[a][b] = sgn * len * o.rho * L.nu * (Fb[a] * nn[b] + Fb[b] * nn[a]);
+            const Axis<double> ax = mls_axis<double>((double)pf.cx[s] - (Cx + sgn * 1.2 * nx));
+            const Axis<double> ay = mls_axis<double>((double)pf.cy[s] - (Cy + sgn * 1.2 * ny));
+            for (int b = 0; b < 3; b++)
+                for (int a = 0; a < 3; a++) {
+                    const int k = 3 * b + a;
+                    const double phi = ax.h[a] * ay.q[b] + ax.q[a] * ay.h[b] - ax.q[a] * ay.q[b];
+                    const double gx = ax.g[a] * ay.q[b], gy = ax.q[a] * ay.g[b];
+                    const double ubx = Gb[0][0] * gx + Gb[0][1] * gy, uby = Gb[1][0] * gx + Gb[1][1] * gy;
+                    inject_fields(L, cells[s][k], phi * rho_b, ubx, uby, pf.f[s][1][k], pf.f[s][2][k], rho_k[s][k],
+                                  sbar, bbar, gsx, gsy);
+                }
+        }
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const double2 a = sm.bdl[v], b = sm.bdr[v == 0 ? n - 1 : v - 1], c = sm.xd[v];
+        xout[off + v] = make_double2(c.x + a.x + b.x, c.y + a.y + b.y);
+    }
+    double gg[2] = {gsx, gsy};
+    block_reduce<2, false>(gg, sm.red);
+    if (threadIdx.x == 0) {
+        atomicAdd(grad + 2 * ncaps, gg[0]);
+        atomicAdd(grad + 2 * ncaps + 1, gg[1]);
+    }
+    if (!ok) atomicOr(status, kStatSupport);
+}
+
+// Interpolation transpose (Eq. 8, Eq. 7 velocity) of U = I(s, fib, X^n) at every vertex
+// for a given U-bar: one thread per (vertex, support node). Adds to the population
+// adjoint, the half-force adjoint and dJ/dX^n (xout).
+template <typename S>
+__global__ void __launch_bounds__(288) k_adjd_interp(Lat L, const S* __restrict__ post, const double* __restrict__ fib,
+                                                     const Shape* __restrict__ shp, int count, const double2* ubar,
+                                                     double2* xout, double* sbar, double* bbar, double* grad_g) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = t / 9, k = t - 9 * (t / 9);
+    double gsx = 0.0, gsy = 0.0;
+    if (v < count) {
+        const double2 U = ubar[v];
+        const int a = k % 3, b = k / 3;
+        const Shape& s = shp[v];
+        const int xk = wrapi(s.cx + a - 1, L.nx), yk = support_row(L, s.cy + b - 1);
+        double drho, ux, uy;
+        node_fields<S>(post, L, fib, xk, yk, drho, ux, uy);
+        const double uU = ux * U.x + uy * U.y;
+        atomicAdd(&xout[v].x, s.px[b][a] * uU);
+        atomicAdd(&xout[v].y, s.py[b][a] * uU);
+        const double phi = s.phi[b][a];
+        inject_fields(L, (long long)yk * L.nx + xk, 0.0, phi * U.x, phi * U.y, ux, uy, 1.0 + drho, sbar, bbar, gsx,
+                      gsy);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        gsx += __shfl_xor_sync(0xffffffffu, gsx, o);
+        gsy += __shfl_xor_sync(0xffffffffu, gsy, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (gsx != 0.0 || gsy != 0.0)) {
+        atomicAdd(grad_g, gsx);
+        atomicAdd(grad_g + 1, gsy);
+    }
+}
+
+// DR3: spread transpose (with c_l), F_l = u_v - U1 and the start-up rule, one CTA per
+// capsule. Completes dJ/dX^n in xout (except the U1 interpolation, added by the next
+// kernel), writes U1-bar, the new u_v-bar and dJ/dX^{n-1}.
+__global__ void __launch_bounds__(128) k_adjd_forcing(Lat L, Nodes nd, int max_n, const double2* Xn,
+                                                      const double2* Flc, const Shape* __restrict__ shp,
+                                                      const double* __restrict__ fbar, const double* __restrict__ bbar,
+                                                      const int* age0, int nloc, double2* xout, double2* xm,
+                                                      double2* ub, double2* u1b) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CapSmem sm = carve(smem, max_n);
+    const CapsuleParams P = nd.caps[blockIdx.x];
+    if (P.n < 3 || P.n > max_n) return;
+    const int n = P.n, off = P.off;
+    const long long N = (long long)L.nx * L.ny;
+    for (int v = threadIdx.x; v < n; v += blockDim.x) sm.X[v] = Xn[off + v];
+    __syncthreads();
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const int g = off + v;
+        const Shape& s = shp[g];
+        const double2 F = Flc[g];   // c_l F_l
+        double cfx = 0.0, cfy = 0.0, gxv = 0.0, gyv = 0.0;
+#pragma unroll
+        for (int b = 0; b < 3; b++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const int cell = support_cell(L, s, a, b);
+                const double tx = fbar[cell] + bbar[cell], ty = fbar[N + cell] + bbar[N + cell];
+                cfx += s.phi[b][a] * tx;
+                cfy += s.phi[b][a] * ty;
+                const double tF = tx * F.x + ty * F.y;
+                gxv += s.px[b][a] * tF;
+                gyv += s.py[b][a] * tF;
+            }
+        const double2 Xv = sm.X[v], Xl = sm.X[v == 0 ? n - 1 : v - 1], Xr = sm.X[v + 1 == n ? 0 : v + 1];
+        const double ll = sqrt((Xv.x - Xl.x) * (Xv.x - Xl.x) + (Xv.y - Xl.y) * (Xv.y - Xl.y));
+        const double lr = sqrt((Xr.x - Xv.x) * (Xr.x - Xv.x) + (Xr.y - Xv.y) * (Xr.y - Xv.y));
+        const double cl = 0.5 * (ll + lr);
+        // c-bar = F_l . (cF)-bar = (c F_l) . (cF)-bar / c;  F_l-bar = c (cF)-bar
+        sm.sst[v] = (F.x * cfx + F.y * cfy) / cl;
+        sm.ext[v] = make_double2(cl * cfx, cl * cfy);
+        const double2 c = xout[g];
+        sm.xd[v] = make_double2(c.x + gxv, c.y + gyv);
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        const int g = off + v;
+        const int vl = v == 0 ? n - 1 : v - 1, vr = v + 1 == n ? 0 : v + 1;
+        const double2 Xv = sm.X[v], Xl = sm.X[vl], Xr = sm.X[vr];
+        const double dlx = Xv.x - Xl.x, dly = Xv.y - Xl.y, drx = Xr.x - Xv.x, dry = Xr.y - Xv.y;
+        const double ll = sqrt(dlx * dlx + dly * dly), lr = sqrt(drx * drx + dry * dry);
+        // c_u = (l_{u-1} + l_u)/2: X_v gets (d_{v-1}/l_{v-1})(c_v + c_{v-1})/2 - (d_v/l_v)(c_v + c_{v+1})/2
+        const double wl = 0.5 * (sm.sst[v] + sm.sst[vl]) / ll, wr = 0.5 * (sm.sst[v] + sm.sst[vr]) / lr;
+        double2 acc = sm.xd[v];
+        acc.x += wl * dlx - wr * drx;
+        acc.y += wl * dly - wr * dry;
+        const double2 flb = sm.ext[v], xm1 = xm[g];
+        if (age0[g] + nloc == 0) {
+            // start-up: u_v := U1 (F_l = 0 whatever U1 is), X^{n-1} := X^n - U1
+            acc.x += xm1.x;
+            acc.y += xm1.y;
+            u1b[g] = make_double2(-xm1.x, -xm1.y);
+            ub[g] = make_double2(0.0, 0.0);
+            xm[g] = make_double2(0.0, 0.0);
+        } else {
+            u1b[g] = make_double2(-flb.x, -flb.y);
+            ub[g] = flb;   // xm keeps dJ/dX^{n-1}
+        }
+        xout[g] = acc;
     }
 }
 
@@ -526,11 +943,14 @@ namespace {
 struct AdjLayout {
     int K = 0, nseg = 0;
     size_t pb = 0, ckpt = 0;
-    size_t tape_pops = 0, tape_X = 0, age0 = 0, ckpts = 0, sbar[2]{}, fbar = 0, fib[2]{}, bbar[2]{}, xc = 0,
-           xp = 0, fv = 0, grad = 0, J = 0, total = 0;
+    size_t tape_pops = 0, tape_X = 0, tape_flc = 0, tape_fib0 = 0, age0 = 0, ckpts = 0, sbar[2]{}, fbar = 0,
+           fib[3]{}, bbar[3]{}, xc = 0, xp = 0, xnew = 0, xb[2]{}, ub = 0, u1b = 0, u2b = 0, fv = 0, shp = 0,
+           grad = 0, J = 0, total = 0;
 };
 
-size_t comp_bytes(lbmib_storage s) { return s == LBMIB_FP64 ? 8 : 4; }
+// The adjoint fields (population and force adjoints) are double in every storage mode:
+// the body-force gradient sums them over every node and step.
+size_t comp_bytes(lbmib_storage) { return sizeof(double); }
 
 AdjLayout adj_layout(const lbmib_ctx* c, long long T, int K) {
     AdjLayout a;
@@ -546,18 +966,27 @@ AdjLayout adj_layout(const lbmib_ctx* c, long long T, int K) {
     auto take = [&](size_t bytes) { size_t r = o; o = up(o + bytes, kAlign); return r; };
     a.tape_pops = take((size_t)(a.K + 1) * a.pb);
     a.tape_X = take((size_t)(a.K + 1) * M * sizeof(double2));
+    a.tape_flc = take((size_t)(a.K + 1) * M * sizeof(double2));   // Dynamic: c_l F_l per step
+    a.tape_fib0 = take(2 * N * sizeof(double));                    // Dynamic: spread force before the segment
     a.age0 = take(M * sizeof(int));
     a.ckpts = take(a.nseg > 1 ? (size_t)(a.nseg + 1) * a.ckpt : 0);
     a.sbar[0] = take(9 * N * cs);
     a.sbar[1] = take(9 * N * cs);
     a.fbar = take(2 * N * cs);
-    a.fib[0] = take(2 * N * sizeof(double));
-    a.fib[1] = take(2 * N * sizeof(double));
-    a.bbar[0] = take(2 * N * sizeof(double));
-    a.bbar[1] = take(2 * N * sizeof(double));
+    for (int r = 0; r < 3; r++) {
+        a.fib[r] = take(2 * N * sizeof(double));
+        a.bbar[r] = take(2 * N * sizeof(double));
+    }
     a.xc = take(M * sizeof(double2));
+    a.xb[0] = take(M * sizeof(double2));
+    a.xb[1] = take(M * sizeof(double2));
+    a.ub = take(M * sizeof(double2));
+    a.u1b = take(M * sizeof(double2));
+    a.u2b = take(M * sizeof(double2));
     a.xp = take(M * sizeof(double2));
+    a.xnew = take(M * sizeof(double2));
     a.fv = take(M * sizeof(double2));
+    a.shp = take(M * sizeof(Shape));
     a.grad = take((2 * c->caps.size() + 2) * sizeof(double));
     a.J = take(sizeof(double));
     a.total = o;
@@ -624,15 +1053,20 @@ lbmib_status tape_forward(lbmib_ctx* c, lbmib_scheme scheme, int len, char* w, c
     double2* tX = (double2*)(w + a.tape_X);
     LBMIB_CUDA(c, cudaMemcpyAsync(tape, c->pops[c->cur], pbytes, cudaMemcpyDeviceToDevice, s));
     LBMIB_CUDA(c, cudaMemcpyAsync(w + a.age0, c->nd.age, M * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    if (scheme == LBMIB_DYNAMIC)
+        LBMIB_CUDA(c, cudaMemcpyAsync(w + a.tape_fib0, c->fib[c->cur_fib], 2 * (size_t)c->cfg.nx * c->cfg.ny *
+                                      sizeof(double), cudaMemcpyDeviceToDevice, s));
     void* keep0 = c->pops[0];
     void* keep1 = c->pops[1];
     for (int k = 0; k < len; k++) {
         LBMIB_CUDA(c, cudaMemcpyAsync(tX + (size_t)k * M, c->nd.X, M * sizeof(double2), cudaMemcpyDeviceToDevice, s));
         c->pops[0] = tape + (size_t)k * a.pb;
         c->pops[1] = tape + (size_t)(k + 1) * a.pb;
+        if (scheme == LBMIB_DYNAMIC) c->nd.Flc = (double2*)(w + a.tape_flc) + (size_t)k * M;
         int cur = 0;
         enqueue_step(c, scheme, cur, c->cur_fib, s, false);
     }
+    c->nd.Flc = nullptr;
     c->pops[0] = keep0;
     c->pops[1] = keep1;
     LBMIB_CUDA(c, cudaMemcpyAsync(tX + (size_t)len * M, c->nd.X, M * sizeof(double2), cudaMemcpyDeviceToDevice, s));
@@ -645,7 +1079,6 @@ lbmib_status tape_forward(lbmib_ctx* c, lbmib_scheme scheme, int len, char* w, c
 // Reverse sweep of one taped segment: global steps n0 + len - 1 down to n0.
 template <typename S>
 lbmib_status reverse_segment(lbmib_ctx* c, long long n0, int len, char* w, const AdjLayout& a) {
-    using C = typename St<S>::C;
     cudaStream_t s = c->stream;
     const Lat& L = c->L;
     const int ncaps = (int)c->caps.size();
@@ -661,24 +1094,85 @@ lbmib_status reverse_segment(lbmib_ctx* c, long long n0, int len, char* w, const
         const double2* Xn = (const double2*)(w + a.tape_X) + (size_t)k * M;
         double* fib = (double*)(w + a.fib[par]);
         double* bbar = (double*)(w + a.bbar[par]);
-        C* sb_in = (C*)(w + a.sbar[1 - par]);
-        C* sb_out = (C*)(w + a.sbar[par]);
-        C* fbar = (C*)(w + a.fbar);
+        double* sb_in = (double*)(w + a.sbar[1 - par]);
+        double* sb_out = (double*)(w + a.sbar[par]);
+        double* fbar = (double*)(w + a.fbar);
         double2* Fv = (double2*)(w + a.fv);
         double2* xc = (double2*)(w + a.xc);
         double2* xp = (double2*)(w + a.xp);
+        Shape* shp = (Shape*)(w + a.shp);
+        double2* xnew = (double2*)(w + a.xnew);
         if (ncaps > 0) {
-            k_adj_spread<<<ncaps, 128, smem, s>>>(L, c->nd, Xn, c->max_n, Fv, fib);
-            k_adj_interp<S><<<nblk(count, 128), 128, 0, s>>>(L, post1, fib, Xn, (const int*)(w + a.age0), k, count,
-                                                             xc, xp, sb_in, bbar, grad + 2 * ncaps,
-                                                             &c->ctr->status);
+            k_adj_spread<<<ncaps, 128, smem, s>>>(L, c->nd, Xn, c->max_n, Fv, shp, fib);
+            k_adj_interp<S><<<nblk(9LL * count, 288), 288, 0, s>>>(L, post1, fib, shp, (const int*)(w + a.age0), k,
+                                                                   count, xc, xp, xnew, sb_in, bbar,
+                                                                   grad + 2 * ncaps, &c->ctr->status);
         }
         k_adj_lattice<S><<<nblk(N, 256), 256, 0, s>>>(post0, L, sb_in, sb_out, fbar, fib,
                                                        (double*)(w + a.fib[1 - par]),
                                                        (double*)(w + a.bbar[1 - par]), grad + 2 * ncaps);
         if (ncaps > 0)
-            k_adj_membrane<C><<<ncaps, 128, smem, s>>>(L, c->nd, Xn, c->max_n, Fv, fbar, bbar, xc, ncaps, grad);
+            k_adj_membrane<<<ncaps, 128, smem, s>>>(L, c->nd, Xn, c->max_n, Fv, shp, fbar, bbar, xnew, xc,
+                                                       ncaps, grad);
         c->launches += ncaps > 0 ? 4 : 1;
+        LBMIB_CUDA(c, cudaGetLastError());
+    }
+    return LBMIB_OK;
+}
+
+// Reverse sweep of one taped Dynamic segment: global steps n0 + len - 1 down to n0.
+template <typename S>
+lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* w, const AdjLayout& a) {
+    cudaStream_t s = c->stream;
+    const Lat& L = c->L;
+    const int ncaps = (int)c->caps.size();
+    const int count = c->nd.count;
+    const size_t M = (size_t)(count > 0 ? count : 1);
+    const long long N = (long long)L.nx * L.ny;
+    const size_t smem = ring_smem_bytes(c->max_n);
+    double* grad = (double*)(w + a.grad);
+    auto r3 = [](long long n) { return (int)(((n % 3) + 3) % 3); };
+    Shape* shp = (Shape*)(w + a.shp);
+    double* fbar = (double*)(w + a.fbar);
+    double2* xm = (double2*)(w + a.xp);
+    double2* ub = (double2*)(w + a.ub);
+    double2* u1b = (double2*)(w + a.u1b);
+    double2* u2b = (double2*)(w + a.u2b);
+    const int* age0 = (const int*)(w + a.age0);
+    for (int k = len - 1; k >= 0; k--) {
+        const long long n = n0 + k;
+        const int par = (int)(n & 1);
+        const S* post0 = (const S*)(w + a.tape_pops + (size_t)k * a.pb);
+        const S* post1 = (const S*)(w + a.tape_pops + (size_t)(k + 1) * a.pb);
+        const double2* Xn = (const double2*)(w + a.tape_X) + (size_t)k * M;
+        const double2* flc = (const double2*)(w + a.tape_flc);
+        double* fib_n = (double*)(w + a.fib[r3(n)]);
+        double* fib_p = k > 0 ? (double*)(w + a.fib[r3(n - 1)]) : (double*)(w + a.tape_fib0);
+        double* b_n = (double*)(w + a.bbar[r3(n)]);
+        double* b_p = (double*)(w + a.bbar[r3(n - 1)]);
+        double* sb_in = (double*)(w + a.sbar[1 - par]);
+        double* sb_out = (double*)(w + a.sbar[par]);
+        double2* xc = (double2*)(w + a.xb[1 - par]);
+        double2* xout = (double2*)(w + a.xb[par]);
+        if (ncaps > 0) {
+            k_adjd_spread<<<ncaps, 128, 0, s>>>(L, c->nd, c->max_n, Xn, k > 0 ? Xn - M : nullptr,
+                                                flc + (size_t)k * M, k > 0 ? flc + (size_t)(k - 1) * M : nullptr,
+                                                k == len - 1 ? fib_n : nullptr, k > 0 ? fib_p : nullptr, shp);
+            k_adjd_update<S><<<ncaps, 128, smem, s>>>(L, c->nd, c->max_n, Xn, post1, fib_n, xc, xm, ub, xout, u2b,
+                                                      sb_in, b_n, ncaps, grad, &c->ctr->status);
+            k_adjd_interp<S><<<nblk(9LL * count, 288), 288, 0, s>>>(L, post1, fib_n, shp, count, u2b, xout, sb_in,
+                                                                    b_n, grad + 2 * ncaps);
+        }
+        k_adj_lattice<S><<<nblk(N, 256), 256, 0, s>>>(post0, L, sb_in, sb_out, fbar, fib_n,
+                                                       (double*)(w + a.fib[r3(n + 1)]),
+                                                       (double*)(w + a.bbar[r3(n + 1)]), grad + 2 * ncaps);
+        if (ncaps > 0) {
+            k_adjd_forcing<<<ncaps, 128, smem, s>>>(L, c->nd, c->max_n, Xn, flc + (size_t)k * M, shp, fbar, b_n,
+                                                    age0, k, xout, xm, ub, u1b);
+            k_adjd_interp<S><<<nblk(9LL * count, 288), 288, 0, s>>>(L, post0, fib_p, shp, count, u1b, xout, sb_out,
+                                                                    b_p, grad + 2 * ncaps);
+        }
+        c->launches += ncaps > 0 ? 6 : 1;
         LBMIB_CUDA(c, cudaGetLastError());
     }
     return LBMIB_OK;
@@ -699,8 +1193,8 @@ lbmib_status lbmib_adjoint(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme, 
     if (nsteps < 1 || nsteps > (1LL << 30) || ckpt_every < 1 || !d_work || ((uintptr_t)d_work % kAlign) != 0 ||
         objective < 0 || objective > 2 || capsule < 0 || capsule >= (int)c->caps.size() || !grad)
         return fail(c, LBMIB_ERR_ARG, "lbmib_adjoint: invalid argument");
-    if (scheme != LBMIB_KINEMATIC)
-        return fail(c, LBMIB_ERR_ARG, "lbmib_adjoint: the reverse sweep covers the Kinematic scheme");
+    if (scheme != LBMIB_KINEMATIC && scheme != LBMIB_DYNAMIC)
+        return fail(c, LBMIB_ERR_ARG, "lbmib_adjoint: unknown scheme");
     const AdjLayout a = adj_layout(c, nsteps, ckpt_every);
     if (work_bytes < a.total) return fail(c, LBMIB_ERR_OOM, "lbmib_adjoint: workspace too small");
     lbmib_status st = device_status(c);
@@ -708,8 +1202,11 @@ lbmib_status lbmib_adjoint(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme, 
     if (c->max_n > 0) {
         const int sm_bytes = (int)ring_smem_bytes(c->max_n);
         cudaFuncSetAttribute(k_adj_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_bytes);
-        cudaFuncSetAttribute(k_adj_membrane<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_bytes);
-        cudaFuncSetAttribute(k_adj_membrane<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_bytes);
+        cudaFuncSetAttribute(k_adj_membrane, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_bytes);
+        cudaFuncSetAttribute(k_adjd_forcing, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_bytes);
+        cudaFuncSetAttribute(k_adjd_update<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_bytes);
+        cudaFuncSetAttribute(k_adjd_update<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_bytes);
+        cudaFuncSetAttribute(k_adjd_update<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_bytes);
     }
     char* w = (char*)d_work;
     cudaStream_t s = c->stream;
@@ -737,14 +1234,19 @@ lbmib_status lbmib_adjoint(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme, 
     // J and dJ/dX^T
     LBMIB_CUDA(c, cudaMemsetAsync(w + a.xc, 0, M * sizeof(double2), s));
     LBMIB_CUDA(c, cudaMemsetAsync(w + a.xp, 0, M * sizeof(double2), s));
+    LBMIB_CUDA(c, cudaMemsetAsync(w + a.xnew, 0, M * sizeof(double2), s));
+    LBMIB_CUDA(c, cudaMemsetAsync(w + a.ub, 0, M * sizeof(double2), s));
     LBMIB_CUDA(c, cudaMemsetAsync(w + a.sbar[0], 0, 9 * N * cs, s));
     LBMIB_CUDA(c, cudaMemsetAsync(w + a.sbar[1], 0, 9 * N * cs, s));
-    for (int p = 0; p < 2; p++) {
+    for (int p = 0; p < 3; p++) {
         LBMIB_CUDA(c, cudaMemsetAsync(w + a.fib[p], 0, 2 * N * sizeof(double), s));
         LBMIB_CUDA(c, cudaMemsetAsync(w + a.bbar[p], 0, 2 * N * sizeof(double), s));
     }
     LBMIB_CUDA(c, cudaMemsetAsync(w + a.grad, 0, (2 * ncaps + 2) * sizeof(double), s));
-    k_adj_objective<<<1, 256, 0, s>>>(c->nd, capsule, objective, (double2*)(w + a.xc), (double*)(w + a.J));
+    // dJ/dX^T: the Kinematic sweep carries it in xc, the Dynamic one in the X-bar buffer of parity T
+    double2* xT = scheme == LBMIB_KINEMATIC ? (double2*)(w + a.xc) : (double2*)(w + a.xb[nsteps & 1]);
+    LBMIB_CUDA(c, cudaMemsetAsync(xT, 0, M * sizeof(double2), s));
+    k_adj_objective<<<1, 256, 0, s>>>(c->nd, capsule, objective, xT, (double*)(w + a.J));
     c->launches++;
     LBMIB_CUDA(c, cudaGetLastError());
     // reverse sweep, segment by segment
@@ -758,7 +1260,9 @@ lbmib_status lbmib_adjoint(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme, 
         }
         by_storage(c->cfg.storage, [&](auto tag) {
             using S = decltype(tag);
-            if (st == LBMIB_OK) st = reverse_segment<S>(c, n0, len, w, a);
+            if (st != LBMIB_OK) return;
+            st = scheme == LBMIB_KINEMATIC ? reverse_segment<S>(c, n0, len, w, a)
+                                           : reverse_segment_dynamic<S>(c, n0, len, w, a);
         });
         if (st != LBMIB_OK) return st;
     }

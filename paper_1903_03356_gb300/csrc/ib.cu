@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(128) k_dyn_force_spread(const S* __restrict__ 
             nd.Xm1[off + v] = Xv - uv;
         }
         const double cl = 0.5 * (sm.sst[v == 0 ? n - 1 : v - 1] + sm.sst[v]);
+        if (nd.Flc) nd.Flc[off + v] = make_double2(cl * (uv.x - Ux), cl * (uv.y - Uy));
         ok &= spread_at<C>(t, L, sp, stamp, Xv.x, Xv.y, uv.x - Ux, uv.y - Uy, cl);
     }
     __syncthreads();

@@ -19,6 +19,7 @@ struct Nodes {
     int* capid;      // capsule of the vertex
     const CapsuleParams* caps;
     int count;       // vertices in use
+    double2* Flc;    // optional (null): c_l F_l of the last Dynamic spread, per vertex
 };
 
 // Touched-cell bookkeeping for the spread of one step.

@@ -1,4 +1,5 @@
-"""GPU parity of the adjoint (lbmib_adjoint, Kinematic scheme) against the FP64 CPU oracle.
+"""GPU parity of the adjoint (lbmib_adjoint, Kinematic and Dynamic schemes) against the
+FP64 CPU oracle.
 
 The reference gradient is the derivative itself, taken by central finite differences of
 the oracle's forward run, J(p (1 + h)) - J(p (1 - h)) over 2 h p, for k_s, k_b and g_x (an
@@ -34,7 +35,7 @@ def oracle_J(case, T, objective, ks, kb, gx):
     s.init_fields(*case.fields())
     cap = case.capsules[0]
     s.add_capsule(cap.xy, ks, kb, cap.ka, cap.mass)
-    assert s.step(T, o.KINEMATIC) == 0
+    assert s.step(T, case.scheme) == 0
     return s.observables(0)[OBS_INDEX[objective]]
 
 
@@ -74,14 +75,14 @@ def reference(case, key, T, objective):
 
 def gpu_adjoint(L, case, T, objective, storage, ckpt_every):
     ctx = L.from_case(case, storage=storage)
-    J, grad = ctx.adjoint(T, objective=objective, capsule=0, ckpt_every=ckpt_every)
+    J, grad = ctx.adjoint(T, objective=objective, capsule=0, ckpt_every=ckpt_every, scheme=case.scheme)
     return J, {"ks": grad[0], "kb": grad[1], "gx": grad[2]}, ctx
 
 
-def channel_case():
-    # Kinematic capsule off the centre line of a body-force channel: D and y_c both move
+def channel_case(scheme=o.KINEMATIC):
+    # capsule off the centre line of a body-force channel: D and y_c both move
     return W.poiseuille_capsule(nx=96, ny=40, radius=6.0, n=32, ca=2e-2, u_max=0.02, y_frac=0.38,
-                                scheme=o.KINEMATIC, steps=1)
+                                scheme=scheme, steps=1)
 
 
 def shear_case():
@@ -169,7 +170,45 @@ def test_autograd_function_returns_the_adjoint_gradient(L):
     assert gx.grad.item() == pytest.approx(3.0 * grad["gx"], rel=1e-12)
 
 
-def test_adjoint_rejects_the_dynamic_scheme_and_a_small_workspace(L):
+@pytest.mark.parametrize("T", [10, 40])
+@pytest.mark.parametrize("objective", [0, 1])
+def test_dynamic_adjoint_matches_oracle_finite_differences_fp64(L, T, objective):
+    case = channel_case(o.DYNAMIC)
+    ref, unc, J_ref = reference(case, "channel-dynamic", T, objective)
+    J, grad, _ = gpu_adjoint(L, case, T, objective, "fp64", ckpt_every=1000)
+    print(f"Dynamic T={T} objective={objective}: J {J:.12e} oracle {J_ref:.12e}")
+    assert abs(J - J_ref) <= 1e-11 * max(1.0, abs(J_ref))
+    check(grad, ref, unc, 1e-6)
+
+
+def test_dynamic_checkpointed_and_taped_sweeps_agree(L):
+    case = channel_case(o.DYNAMIC)
+    T = 30
+    J1, g1, c1 = gpu_adjoint(L, case, T, 0, "fp64", ckpt_every=1000)
+    J2, g2, c2 = gpu_adjoint(L, case, T, 0, "fp64", ckpt_every=7)
+    assert J1 == pytest.approx(J2, rel=1e-12)
+    for k in g1:
+        assert g1[k] == pytest.approx(g2[k], rel=1e-9)
+    ref = L.from_case(case, storage="fp64")
+    ref.step(T, L.DYNAMIC)
+    for c in (c1, c2):
+        np.testing.assert_allclose(c.read_capsule(0)[0], ref.read_capsule(0)[0], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-6), ("fp32", 1e-4)])
+def test_dynamic_adjoint_on_the_channel_workload(L, storage, tol):
+    # the 512 x 128 channel with the radius-16, 128-vertex capsule at Ca = 0.02 and the
+    # Dynamic scheme, gradients of D over 200 steps with a checkpoint every 50
+    case = W.adjoint_capsule(scheme=o.DYNAMIC, steps=200)
+    T = 200
+    ref, unc, J_ref = reference(case, "workload-dynamic", T, 0)
+    J, grad, _ = gpu_adjoint(L, case, T, 0, storage, ckpt_every=50)
+    print(f"Dynamic {storage}: J {J:.9e} oracle {J_ref:.9e}")
+    assert abs(J - J_ref) <= (1e-9 * abs(J_ref) if storage == "fp64" else 1e-4)
+    check(grad, ref, unc, tol)
+
+
+def test_adjoint_rejects_an_unknown_scheme_and_a_small_workspace(L):
     torch = pytest.importorskip("torch")
     case = channel_case()
     ctx = L.from_case(case, storage="fp64")
@@ -178,7 +217,7 @@ def test_adjoint_rejects_the_dynamic_scheme_and_a_small_workspace(L):
     work = torch.empty(n, dtype=torch.uint8, device="cuda")
     grad = np.zeros(4)
     with pytest.raises(L.LbmibError) as e:
-        L.lbmib_adjoint(ctx.h, 10, L.DYNAMIC, 100, 0, 0, work.data_ptr(), n, grad)
+        L.lbmib_adjoint(ctx.h, 10, 7, 100, 0, 0, work.data_ptr(), n, grad)
     assert e.value.status == L.ERR_ARG
     with pytest.raises(L.LbmibError) as e:
         L.lbmib_adjoint(ctx.h, 10, L.KINEMATIC, 100, 0, 0, work.data_ptr(), n - 256, grad)
