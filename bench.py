@@ -277,7 +277,8 @@ def run_gpu(a):
     if rank == 0 and not a.no_extras:
         ctx.close()
         line["batched"] = batched_run(L, a.batch_steps, a.batch_autotune)
-        line["adjoint"] = adjoint_run(L, a.storage, a.adjoint_steps)
+        line["adjoint"] = {"dynamic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=1),
+                           "kinematic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=0)}
     if rank == 0 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, a.cpu_seconds)
     if rank == 0:
@@ -333,20 +334,20 @@ def batched_run(L, steps, autotune=20):
             "sequential_sample": "32 cases x 300 steps through single-case contexts (CUDA graphs)"}
 
 
-def adjoint_run(L, storage, T=800):
+def adjoint_run(L, storage, T=800, scheme=1):
     """Gradient of D(T) with respect to (k_s, k_b, g_x) on the 512 x 128 channel capsule
-    (radius 16, 128 vertices, Ca = 0.02), Kinematic, T steps with a checkpoint every 200,
-    against T forward steps of the same context (cost ratio)."""
+    (radius 16, 128 vertices, Ca = 0.02), Dynamic (1) or Kinematic (0), T steps with a
+    checkpoint every 200, against T forward steps of the same context (cost ratio)."""
     import torch
 
-    case = W.adjoint_capsule(scheme=0, steps=T)
+    case = W.adjoint_capsule(scheme=scheme, steps=T)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ctx = L.from_case(case, storage=storage)
-    ctx.step(T, L.KINEMATIC)           # warm-up and graph capture
+    ctx.step(T, scheme)           # warm-up and graph capture
     ctx.sync()
     torch.cuda.synchronize()
     e0.record(ctx.stream)
-    ctx.step(T, L.KINEMATIC)
+    ctx.step(T, scheme)
     e1.record(ctx.stream)
     torch.cuda.synchronize()
     fwd_ms = e0.elapsed_time(e1)
@@ -355,15 +356,16 @@ def adjoint_run(L, storage, T=800):
     nbytes = L.lbmib_adjoint_workspace_bytes(ctx.h, T, 200)
     work = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     grad = np.zeros(4)
-    L.lbmib_adjoint(ctx.h, T, L.KINEMATIC, 200, 0, 0, work.data_ptr(), nbytes, grad)   # warm-up
+    L.lbmib_adjoint(ctx.h, T, scheme, 200, 0, 0, work.data_ptr(), nbytes, grad)   # warm-up
     ctx.close()
     ctx = L.from_case(case, storage=storage)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    J = L.lbmib_adjoint(ctx.h, T, L.KINEMATIC, 200, 0, 0, work.data_ptr(), nbytes, grad)
+    J = L.lbmib_adjoint(ctx.h, T, scheme, 200, 0, 0, work.data_ptr(), nbytes, grad)
     adj_ms = (time.perf_counter() - t0) * 1e3
     ctx.close()
-    return {"workload": "512x128 channel, radius-16 capsule of 128 vertices, Ca 0.02, Kinematic, " + storage,
+    return {"workload": "512x128 channel, radius-16 capsule of 128 vertices, Ca 0.02, "
+                        + ("Dynamic" if scheme == 1 else "Kinematic") + ", " + storage,
             "steps": T, "ckpt_every": 200, "forward_ms": fwd_ms, "adjoint_ms": adj_ms,
             "cost_ratio": adj_ms / fwd_ms, "J": J,
             "grad": {"k_s": grad[0], "k_b": grad[1], "g_x": grad[2]},
@@ -412,7 +414,8 @@ def main():
         from paper_1903_03356_gb300 import lbmib as L
 
         out = (batched_run(L, a.batch_steps, a.batch_autotune) if a.only == "batched"
-               else adjoint_run(L, a.storage, a.adjoint_steps))
+               else {"dynamic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=1),
+                     "kinematic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=0)})
         print(json.dumps(out), flush=True)
     else:
         run_gpu(a)

@@ -181,15 +181,24 @@ lbmib_status lbmib_load_state(lbmib_ctx* ctx, const void* host_buf, size_t bytes
  *   LBMIB_OPT_FP16_SCALE    log2 of the FP16 storage scale (default 10).
  *   LBMIB_OPT_LATTICE_VARIANT launch shape of the lattice-update kernel: bits 0-11 the
  *                           block size (128 or 256), bit 18 a register cap that keeps
- *                           four blocks resident per SM instead of three. Default:
- *                           128 threads, with the cap for FP32/FP16 storage. Results
- *                           do not depend on it; only speed does.                   */
+ *                           four blocks resident per SM instead of three, bit 19 (FP16
+ *                           storage) the kernel that moves 8 nodes per thread as packed
+ *                           16-byte vectors. Default: 128 threads, with the cap for
+ *                           FP32/FP16 storage and bit 19 for FP16. Results do not
+ *                           depend on it; only speed does.
+ *   LBMIB_OPT_OVERLAP       1: the immersed-boundary kernels run on a second stream of
+ *                           the library, overlapping the lattice update of the same
+ *                           step (force and spread) and of the next step (node
+ *                           update); 0: every kernel on the context stream; -1
+ *                           (default): on while there are fewer than two capsules per
+ *                           multiprocessor. Results do not depend on it.            */
 enum {
     LBMIB_OPT_GRAPHS = 1,
     LBMIB_OPT_TIMING = 2,
     LBMIB_OPT_GRAPH_STEPS = 3,
     LBMIB_OPT_FP16_SCALE = 4,
-    LBMIB_OPT_LATTICE_VARIANT = 5
+    LBMIB_OPT_LATTICE_VARIANT = 5,
+    LBMIB_OPT_OVERLAP = 6
 };
 lbmib_status lbmib_set_option(lbmib_ctx* ctx, int option, long long value);
 
@@ -207,13 +216,15 @@ long long lbmib_launch_count(const lbmib_ctx* ctx);
 double lbmib_bytes_per_update(const lbmib_ctx* ctx);
 
 /* ---------------------------------------------------------------------------------
- * Adjoint: gradients of a capsule objective J(X^T) after nsteps Kinematic steps
- * (Section 2.4) from the current state, with respect to k_s and k_b of every capsule
- * and the uniform body force (gx, gy). The initial state (populations, capsule
- * positions and history) is held fixed. Computed by a reverse sweep over the exact
- * discrete step (collision, streaming, MLS interpolation and spreading, membrane
- * forces, Eq. 25 advance); MLS supports are differentiated as they stand (a vertex
- * crossing a half-integer line switches support, which the derivative ignores).
+ * Adjoint: gradients of a capsule objective J(X^T) after nsteps steps of either scheme
+ * (Kinematic, Section 2.4; Dynamic, Section 2.3.2) from the current state, with respect
+ * to k_s and k_b of every capsule and the uniform body force (gx, gy). The initial state
+ * (populations, last spread force, capsule positions and history) is held fixed.
+ * Computed by a reverse sweep over the exact discrete step (collision, streaming, MLS
+ * interpolation and spreading, membrane forces, and for the Dynamic scheme the
+ * c_l-weighted forcing, the probe tractions of Eq. 15-16 and the Eq. 23-24 update); MLS
+ * supports are differentiated as they stand (a vertex crossing a half-integer line
+ * switches support, which the derivative ignores).
  * --------------------------------------------------------------------------------- */
 enum {
     LBMIB_OBJ_TAYLOR_D = 0,     /* Taylor deformation D of the capsule (Section 3.1)   */
@@ -227,14 +238,14 @@ enum {
  * the adjoint fields. 0 on invalid arguments. */
 size_t lbmib_adjoint_workspace_bytes(const lbmib_ctx* ctx, long long nsteps, int ckpt_every);
 
-/* Run nsteps Kinematic steps from the current state (the context ends nsteps steps
+/* Run nsteps steps of `scheme` from the current state (the context ends nsteps steps
  * later, as after lbmib_step) and return J at the end (*J, may be NULL) and its gradient
  * grad[2 * ncapsules + 2] = {dJ/dk_s of each capsule, dJ/dk_b of each capsule,
  * dJ/dgx, dJ/dgy}. objective: LBMIB_OBJ_*; capsule: whose ring J measures. d_work:
  * device workspace of lbmib_adjoint_workspace_bytes (256-byte aligned). Segments of
  * ckpt_every steps are recomputed from their checkpoints during the reverse sweep.
- * Synchronises. Errors: LBMIB_ERR_ARG (arguments, or scheme other than Kinematic),
- * LBMIB_ERR_OOM (workspace too small), sticky device conditions of the run. */
+ * Synchronises. Errors: LBMIB_ERR_ARG (arguments, unknown scheme), LBMIB_ERR_OOM
+ * (workspace too small), sticky device conditions of the run. */
 lbmib_status lbmib_adjoint(lbmib_ctx* ctx, long long nsteps, lbmib_scheme scheme,
                            int ckpt_every, int objective, int capsule, void* d_work,
                            size_t work_bytes, double* J, double* grad);

@@ -1,5 +1,5 @@
-"""A capsule objective after T Kinematic steps as a differentiable torch function of the
-membrane constants and the driving force.
+"""A capsule objective after T steps (the case's scheme, Kinematic or Dynamic) as a
+differentiable torch function of the membrane constants and the driving force.
 
 ``CapsuleObjective.apply(k_s, k_b, g_x, case, nsteps, objective, storage, ckpt_every)``
 returns J = D(T) (Taylor deformation) or a centroid coordinate of the case's first
@@ -32,7 +32,8 @@ class CapsuleObjective(torch.autograd.Function):
     @staticmethod
     def forward(fctx, ks, kb, gx, case, nsteps, objective=lbmib.OBJ_TAYLOR_D, storage="fp32", ckpt_every=200):
         c = context_for(case, float(ks), float(kb), float(gx), storage)
-        J, grad = c.adjoint(int(nsteps), objective=objective, capsule=0, ckpt_every=int(ckpt_every))
+        J, grad = c.adjoint(int(nsteps), objective=objective, capsule=0, ckpt_every=int(ckpt_every),
+                            scheme=case.scheme)
         nc = len(case.capsules)
         g = torch.tensor([grad[0], grad[nc], grad[2 * nc]], dtype=torch.float64)
         fctx.save_for_backward(g)

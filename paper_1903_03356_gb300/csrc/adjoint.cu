@@ -1,9 +1,10 @@
-// Adjoint (reverse-mode derivative) of the Kinematic coupled step (Section 2.4, steps
-// i-viii; Eq. 1-14, 25): gradients of a capsule objective J(X^T) (Taylor deformation D
-// or centroid coordinate, Section 3.1) with respect to the membrane constants k_s, k_b
-// of every capsule and the uniform body force g, over T steps from the current state.
+// Adjoint (reverse-mode derivative) of the coupled step: gradients of a capsule objective
+// J(X^T) (Taylor deformation D or centroid coordinate, Section 3.1) with respect to the
+// membrane constants k_s, k_b of every capsule and the uniform body force g, over T
+// steps from the current state, for the Kinematic scheme (Section 2.4, steps i-viii;
+// Eq. 1-14, 25; below) and the Dynamic scheme (Section 2.3.2; further down).
 //
-// Forward step n (populations stored post-collision, s^n = pull(post^n) the streamed
+// Kinematic forward step n (populations stored post-collision, s^n = pull(post^n) the streamed
 // populations that step n collides):
 //   F_v   = F(X^n; k_s, k_b, k_a)                      membrane force (Eq. 11, 13, 14)
 //   fib   = sum_v phi(X^n_v) F_v                       spread (step iii)
@@ -67,6 +68,65 @@ __device__ __forceinline__ double vpart(Dual a) { return a.v; }
 __device__ __forceinline__ double vpart(double a) { return a; }
 __device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ double dexp(double a) { return exp(a); }
+
+// A value with its derivatives along four directions at once (one pass instead of four
+// when the value parts, exponentials included, would be the same in each).
+struct Dual4 {
+    double v, d[4];
+};
+__device__ __forceinline__ Dual4 d4(double v) { return Dual4{v, {0.0, 0.0, 0.0, 0.0}}; }
+__device__ __forceinline__ Dual4 operator+(Dual4 a, Dual4 b) {
+    Dual4 r{a.v + b.v, {}};
+#pragma unroll
+    for (int k = 0; k < 4; k++) r.d[k] = a.d[k] + b.d[k];
+    return r;
+}
+__device__ __forceinline__ Dual4 operator-(Dual4 a, Dual4 b) {
+    Dual4 r{a.v - b.v, {}};
+#pragma unroll
+    for (int k = 0; k < 4; k++) r.d[k] = a.d[k] - b.d[k];
+    return r;
+}
+__device__ __forceinline__ Dual4 operator-(Dual4 a) {
+    Dual4 r{-a.v, {}};
+#pragma unroll
+    for (int k = 0; k < 4; k++) r.d[k] = -a.d[k];
+    return r;
+}
+__device__ __forceinline__ Dual4 operator*(Dual4 a, Dual4 b) {
+    Dual4 r{a.v * b.v, {}};
+#pragma unroll
+    for (int k = 0; k < 4; k++) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+    return r;
+}
+__device__ __forceinline__ Dual4 operator/(Dual4 a, Dual4 b) {
+    const double q = a.v / b.v, ib = 1.0 / b.v;
+    Dual4 r{q, {}};
+#pragma unroll
+    for (int k = 0; k < 4; k++) r.d[k] = (a.d[k] - q * b.d[k]) * ib;
+    return r;
+}
+__device__ __forceinline__ Dual4 operator*(double s, Dual4 a) {
+    Dual4 r{s * a.v, {}};
+#pragma unroll
+    for (int k = 0; k < 4; k++) r.d[k] = s * a.d[k];
+    return r;
+}
+__device__ __forceinline__ Dual4 operator+(Dual4 a, double s) { a.v += s; return a; }
+__device__ __forceinline__ Dual4 dsqrt(Dual4 a) {
+    const double r = sqrt(a.v), h = 0.5 / r;
+    Dual4 o{r, {}};
+#pragma unroll
+    for (int k = 0; k < 4; k++) o.d[k] = a.d[k] * h;
+    return o;
+}
+__device__ __forceinline__ Dual4 dexp(Dual4 a) {
+    const double e = exp(a.v);
+    Dual4 o{e, {}};
+#pragma unroll
+    for (int k = 0; k < 4; k++) o.d[k] = e * a.d[k];
+    return o;
+}
 
 template <typename T>
 struct P2 {
@@ -329,9 +389,11 @@ __global__ void __launch_bounds__(288) k_adj_interp(Lat L, const S* __restrict__
         const long long N = (long long)L.nx * L.ny;
         const int xk = wrapi(s.cx + a - 1, L.nx), yk = support_row(L, s.cy + b - 1);
         const long long cell = (long long)yk * L.nx + xk;
+        typename St<S>::C qc[9];
+        pull_all<S>(post1, L, xk, yk, qc);
         double q[9];
 #pragma unroll
-        for (int i = 0; i < 9; i++) q[i] = (double)pull<S>(post1, L, i, xk, yk);
+        for (int i = 0; i < 9; i++) q[i] = (double)qc[i];
         double drho = 0.0, mx = 0.0, my = 0.0;
 #pragma unroll
         for (int i = 0; i < 9; i++) {
@@ -440,11 +502,41 @@ __global__ void __launch_bounds__(256) k_adj_lattice(const S* __restrict__ post0
                 pb[j] = sb_in[(long long)j * N + (long long)wrapi(ty, L.ny) * L.nx + tx];
             }
         }
-#pragma unroll
-        for (int i = 0; i < 9; i++) s[i] = (double)pull<S>(post0, L, i, x, y);
-        const C Fx = L.gx + fib[node], Fy = L.gy + fib[N + node];
+        typename St<S>::C sc[9];
+        pull_all<S>(post0, L, x, y, sc);
+        const double Fx = L.gx + fib[node], Fy = L.gy + fib[N + node];
         C Fbx, Fby;
-        collide_adjoint<C>(s, Fx, Fy, L.omega, pb, sb, Fbx, Fby);
+        if constexpr (sizeof(typename St<S>::C) == 8) {
+#pragma unroll
+            for (int i = 0; i < 9; i++) s[i] = (double)sc[i];
+            collide_adjoint<double>(s, Fx, Fy, L.omega, pb, sb, Fbx, Fby);
+        } else {
+            // The collision keeps mass (sum of the outgoing populations = sum of the
+            // incoming ones) and momentum up to the force (sum e post = sum e s + F), so
+            // the adjoint modes 1, e_x, e_y pass through it exactly: 1 -> 1 with no force
+            // adjoint, e_x -> e_x with force adjoint (1, 0). Those parts are split off in
+            // double (weighted mean and first moments of p-bar) and only the remainder
+            // goes through the float transpose.
+            double c0 = 0.0, ca = 0.0, cb = 0.0;
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                const double w = wgt<double>(i);
+                c0 += w * pb[i];
+                ca += 3.0 * w * ex(i) * pb[i];
+                cb += 3.0 * w * ey(i) * pb[i];
+            }
+            float sf[9], rf[9], sbf[9], fx, fy;
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                sf[i] = (float)sc[i];
+                rf[i] = (float)(pb[i] - c0 - ca * ex(i) - cb * ey(i));
+            }
+            collide_adjoint<float>(sf, (float)Fx, (float)Fy, L.omegaf, rf, sbf, fx, fy);
+#pragma unroll
+            for (int i = 0; i < 9; i++) sb[i] = c0 + ca * ex(i) + cb * ey(i) + (double)sbf[i];
+            Fbx = ca + (double)fx;
+            Fby = cb + (double)fy;
+        }
 #pragma unroll
         for (int i = 0; i < 9; i++) sb_out[(long long)i * N + node] = sb[i];
         fbar[node] = Fbx;
@@ -602,42 +694,30 @@ __device__ ProbeVal<T> probe_eval(T Px, T Py, int cx, int cy, const double* drho
     return o;
 }
 
-// Field samples of the two probes of an element: density deviation and Eq. 7 velocity
-// (with half of g + fib) at the 9 support nodes of each probe.
-struct ProbeFields {
-    int cx[2], cy[2];
-    double f[2][3][9];   // [probe][drho, ux, uy][support]
-};
-
-// Traction of one element (Eq. 15-16): probes at the element centroid +/- 1.2 n with
-// n = (dy, -dx)/l the outward normal of a counter-clockwise ring; p = rho/3,
-// tau = rho nu (G + G^T); F = l (-(p+ - p-) n + (tau+ - tau-) n). Any scalar type.
+// Part of the traction of one element (Eq. 15-16) that comes from probe s (0: outer,
+// at the centroid + 1.2 n; 1: inner, at - 1.2 n), with n = (dy, -dx)/l the outward normal
+// of a counter-clockwise ring, p = rho/3 and tau = rho nu (G + G^T):
+//   F = l (-(p+ - p-) n + (tau+ - tau-) n) = T_0 - T_1,  T_s = l (-p_s n + tau_s n).
+// Returns (+/-) T_s for fields sampled at the probe's support (centre fixed); any
+// scalar type.
 template <typename T>
-__device__ P2<T> element_traction(P2<T> X1, P2<T> X2, const ProbeFields& pf, double nu) {
+__device__ P2<T> probe_traction(P2<T> X1, P2<T> X2, int s, int cx, int cy, const double* drho, const double* ux,
+                                const double* uy, double nu) {
     const P2<T> d = X2 - X1;
     const T len = dsqrt(d.x * d.x + d.y * d.y);
     const P2<T> nn{d.y / len, -(d.x / len)};
-    const P2<T> C{0.5 * (X1.x + X2.x), 0.5 * (X1.y + X2.y)};
-    ProbeVal<T> o[2];
-#pragma unroll
-    for (int s = 0; s < 2; s++) {
-        const double sg = s == 0 ? 1.2 : -1.2;
-        o[s] = probe_eval<T>(C.x + sg * nn.x, C.y + sg * nn.y, pf.cx[s], pf.cy[s], pf.f[s][0], pf.f[s][1],
-                             pf.f[s][2]);
-    }
-    const T dp = (1.0 / 3.0) * (o[0].rho - o[1].rho);
+    const double sg = s == 0 ? 1.2 : -1.2;
+    const ProbeVal<T> o = probe_eval<T>(0.5 * (X1.x + X2.x) + sg * nn.x, 0.5 * (X1.y + X2.y) + sg * nn.y, cx, cy,
+                                        drho, ux, uy);
+    const T p = (1.0 / 3.0) * o.rho;
     const T n_[2] = {nn.x, nn.y};
     T F[2];
 #pragma unroll
     for (int a = 0; a < 2; a++) {
-        T t = -(dp * n_[a]);
+        T t = -(p * n_[a]);
 #pragma unroll
-        for (int b = 0; b < 2; b++) {
-            const T tp = nu * (o[0].rho * (o[0].G[a][b] + o[0].G[b][a]));
-            const T tm = nu * (o[1].rho * (o[1].G[a][b] + o[1].G[b][a]));
-            t = t + (tp - tm) * n_[b];
-        }
-        F[a] = len * t;
+        for (int b = 0; b < 2; b++) t = t + nu * (o.rho * (o.G[a][b] + o.G[b][a])) * n_[b];
+        F[a] = (s == 0 ? 1.0 : -1.0) * (len * t);
     }
     return P2<T>{F[0], F[1]};
 }
@@ -689,9 +769,11 @@ __device__ __forceinline__ void node_fields(const S* __restrict__ post, const La
     const long long cell = (long long)yk * L.nx + xk;
     double mx = 0.0, my = 0.0;
     drho = 0.0;
+    typename St<S>::C qc[9];
+    pull_all<S>(post, L, xk, yk, qc);
 #pragma unroll
     for (int i = 0; i < 9; i++) {
-        const double q = (double)pull<S>(post, L, i, xk, yk);
+        const double q = (double)qc[i];
         drho += q;
         mx += ex(i) * q;
         my += ey(i) * q;
@@ -716,15 +798,12 @@ __device__ __forceinline__ void inject_fields(const Lat& L, long long cell, doub
     gsy += 0.5 * uby / rho;
 }
 
-// DR1: transposes of Eq. 24, Eq. 23, the membrane force and the tractions, one CTA per
-// capsule. Writes dJ/dX^n (partial) to xout, U2-bar to u2b, keeps dJ/dX^{n-1} (from
-// Eq. 24) in xm for DR3.
-template <typename S>
-__global__ void __launch_bounds__(128) k_adjd_update(Lat L, Nodes nd, int max_n, const double2* Xn,
-                                                     const S* __restrict__ post1, const double* __restrict__ fib,
-                                                     const double2* xc, double2* xm, const double2* ub,
-                                                     double2* xout, double2* u2b, double* sbar, double* bbar,
-                                                     int ncaps, double* grad, unsigned* status) {
+// DR1: transposes of Eq. 24, Eq. 23 and the membrane force, one CTA per capsule. Writes
+// dJ/dX^n (partial) to xout, U2-bar to u2b, F^tot-bar to ftb (for the tractions), and
+// keeps dJ/dX^{n-1} (from Eq. 24) in xm for DR3.
+__global__ void __launch_bounds__(128) k_adjd_update(Nodes nd, int max_n, const double2* Xn, const double2* xc,
+                                                     double2* xm, const double2* ub, double2* xout, double2* u2b,
+                                                     double2* ftb, int ncaps, double* grad) {
     extern __shared__ __align__(16) unsigned char smem[];
     const CapSmem sm = carve(smem, max_n);
     const int cap = blockIdx.x;
@@ -737,90 +816,97 @@ __global__ void __launch_bounds__(128) k_adjd_update(Lat L, Nodes nd, int max_n,
         const double2 u = ub[g], c = xc[g];
         const double2 ct = make_double2(c.x + 1.5 * u.x, c.y + 1.5 * u.y);   // dJ/dX^{n+1} in total
         u2b[g] = ct;
-        sm.ext[v] = make_double2(ct.x / (2.0 * P.m), ct.y / (2.0 * P.m));       // F^tot-bar
+        const double2 fb = make_double2(ct.x / (2.0 * P.m), ct.y / (2.0 * P.m));   // F^tot-bar
+        sm.ext[v] = fb;
+        ftb[g] = fb;
         const double2 m = xm[g];
         sm.xd[v] = make_double2(m.x - 2.0 * u.x + ct.x, m.y - 2.0 * u.y + ct.y);
         xm[g] = make_double2(0.5 * u.x, 0.5 * u.y);                             // dJ/dX^{n-1}
     }
     __syncthreads();
     membrane_transpose(sm, P, nd, cap, ncaps, grad);
-    // tractions: one thread per element, position adjoints of both ends staged in bdl/bdr
+    for (int v = threadIdx.x; v < n; v += blockDim.x) xout[off + v] = sm.xd[v];
+}
+
+// DR1t: transpose of the tractions (Eq. 15-16), one thread per (element, probe). Each
+// end vertex receives half of the element force, so F_l-bar = (F^tot-bar_1 +
+// F^tot-bar_2)/2. The fields enter linearly: density through p and tau, the velocity
+// gradient through tau; the positions through the probe location, normal and length
+// (four directional derivatives with dual numbers).
+template <typename S>
+__global__ void __launch_bounds__(32) k_adjd_tract(Lat L, Nodes nd, int count, const double2* Xn,
+                                                   const S* __restrict__ post1, const double* __restrict__ fib,
+                                                   const double2* ftb, double2* xout, double* sbar, double* bbar,
+                                                   double* grad_g, unsigned* status) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g1 = t >> 1, s = t & 1;
     double gsx = 0.0, gsy = 0.0;
     bool ok = true;
-    for (int l = threadIdx.x; l < n; l += blockDim.x) {
-        const int l2 = l + 1 == n ? 0 : l + 1;
-        const double2 X1 = sm.X[l], X2 = sm.X[l2];
-        const double2 fb1 = sm.ext[l], fb2 = sm.ext[l2];
-        const double Fbx = 0.5 * (fb1.x + fb2.x), Fby = 0.5 * (fb1.y + fb2.y);
+    if (g1 < count) {
+        const CapsuleParams P = nd.caps[nd.capid[g1]];
+        const int v = g1 - P.off;
+        const int g2 = P.off + (v + 1 == P.n ? 0 : v + 1);
+        const double2 X1 = Xn[g1], X2 = Xn[g2];
+        const double2 f1 = ftb[g1], f2 = ftb[g2];
+        const double Fb[2] = {0.5 * (f1.x + f2.x), 0.5 * (f1.y + f2.y)};
         const double dx = X2.x - X1.x, dy = X2.y - X1.y, len = sqrt(dx * dx + dy * dy);
-        const double nx = dy / len, ny = -dx / len;
-        const double Cx = 0.5 * (X1.x + X2.x), Cy = 0.5 * (X1.y + X2.y);
-        ProbeFields pf;
-        long long cells[2][9];
-        double rho_k[2][9];
-        for (int s = 0; s < 2; s++) {
-            const double sg = s == 0 ? 1.2 : -1.2;
-            double Px = Cx + sg * nx, Py = Cy + sg * ny;
-            ok &= support_centre(L, Px, Py, pf.cx[s], pf.cy[s]);
-            for (int b = 0; b < 3; b++)
-                for (int a = 0; a < 3; a++) {
-                    const int k = 3 * b + a;
-                    const int xk = wrapi(pf.cx[s] + a - 1, L.nx), yk = support_row(L, pf.cy[s] + b - 1);
-                    cells[s][k] = (long long)yk * L.nx + xk;
-                    node_fields<S>(post1, L, fib, xk, yk, pf.f[s][0][k], pf.f[s][1][k], pf.f[s][2][k]);
-                    rho_k[s][k] = 1.0 + pf.f[s][0][k];
-                }
-        }
-        // position transpose: four directional derivatives (dual numbers)
+        const double nn[2] = {dy / len, -dx / len};
+        const double sg = s == 0 ? 1.2 : -1.2, sgn = s == 0 ? 1.0 : -1.0;
+        double Px = 0.5 * (X1.x + X2.x) + sg * nn[0], Py = 0.5 * (X1.y + X2.y) + sg * nn[1];
+        int cx, cy;
+        ok = support_centre(L, Px, Py, cx, cy);
+        double drho[9], ux[9], uy[9];
+        long long cells[9];
+#pragma unroll
+        for (int b = 0; b < 3; b++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const int k = 3 * b + a;
+                const int xk = wrapi(cx + a - 1, L.nx), yk = support_row(L, cy + b - 1);
+                cells[k] = (long long)yk * L.nx + xk;
+                node_fields<S>(post1, L, fib, xk, yk, drho[k], ux[k], uy[k]);
+            }
+        // positions: derivatives along the four end coordinates, in one pass
+        Dual4 c1x = d4(X1.x), c1y = d4(X1.y), c2x = d4(X2.x), c2y = d4(X2.y);
+        c1x.d[0] = c1y.d[1] = c2x.d[2] = c2y.d[3] = 1.0;
+        const P2<Dual4> F = probe_traction<Dual4>(P2<Dual4>{c1x, c1y}, P2<Dual4>{c2x, c2y}, s, cx, cy, drho, ux, uy,
+                                                  L.nu);
         double e[4];
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const P2<Dual> D1{mk(X1.x, j == 0 ? 1.0 : 0.0), mk(X1.y, j == 1 ? 1.0 : 0.0)};
-            const P2<Dual> D2{mk(X2.x, j == 2 ? 1.0 : 0.0), mk(X2.y, j == 3 ? 1.0 : 0.0)};
-            const P2<Dual> F = element_traction<Dual>(D1, D2, pf, L.nu);
-            e[j] = Fbx * F.x.d + Fby * F.y.d;
+        for (int j = 0; j < 4; j++) e[j] = Fb[0] * F.x.d[j] + Fb[1] * F.y.d[j];
+        atomicAdd(&xout[g1].x, e[0]);
+        atomicAdd(&xout[g1].y, e[1]);
+        atomicAdd(&xout[g2].x, e[2]);
+        atomicAdd(&xout[g2].y, e[3]);
+        // fields: dT/drho and dT/dG contracted with F_l-bar
+        const ProbeVal<double> o = probe_eval<double>(Px, Py, cx, cy, drho, ux, uy);
+        double rho_b = 0.0, Gb[2][2];
+        for (int a = 0; a < 2; a++) {
+            double tt = -nn[a] / 3.0;
+            for (int b = 0; b < 2; b++) tt += L.nu * (o.G[a][b] + o.G[b][a]) * nn[b];
+            rho_b += Fb[a] * sgn * len * tt;
         }
-        sm.bdl[l] = make_double2(e[0], e[1]);    // to vertex l
-        sm.bdr[l] = make_double2(e[2], e[3]);    // to vertex l + 1
-        // field transpose
-        const double nn[2] = {nx, ny}, Fb[2] = {Fbx, Fby};
-        for (int s = 0; s < 2; s++) {
-            const double sgn = s == 0 ? 1.0 : -1.0;
-            const ProbeVal<double> o = probe_eval<double>(Cx + sgn * 1.2 * nx, Cy + sgn * 1.2 * ny, pf.cx[s],
-                                                          pf.cy[s], pf.f[s][0], pf.f[s][1], pf.f[s][2]);
-            // dF/drho and dF/dG of this probe, contracted with F-bar
-            double rho_b = 0.0, Gb[2][2];
-            for (int a = 0; a < 2; a++) {
-                double t = -nn[a] / 3.0;
-                for (int b = 0; b < 2; b++) t += L.nu * (o.G[a][b] + o.G[b][a]) * nn[b];
-                rho_b += Fb[a] * sgn * len * t;
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2; b++) Gb[a][b] = sgn * len * o.rho * L.nu * (Fb[a] * nn[b] + Fb[b] * nn[a]);
+        const Axis<double> ax = mls_axis<double>((double)cx - Px), ay = mls_axis<double>((double)cy - Py);
+#pragma unroll
+        for (int b = 0; b < 3; b++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const int k = 3 * b + a;
+                const double phi = ax.h[a] * ay.q[b] + ax.q[a] * ay.h[b] - ax.q[a] * ay.q[b];
+                const double gx = ax.g[a] * ay.q[b], gy = ax.q[a] * ay.g[b];
+                inject_fields(L, cells[k], phi * rho_b, Gb[0][0] * gx + Gb[0][1] * gy, Gb[1][0] * gx + Gb[1][1] * gy,
+                              ux[k], uy[k], 1.0 + drho[k], sbar, bbar, gsx, gsy);
             }
-            for (int a = 0; a < 2; a++)
-                for (int b = 0; b < 2; b++)
-                    Gb[a][b] = sgn * len * o.rho * L.nu * (Fb[a] * nn[b] + Fb[b] * nn[a]);
-            const Axis<double> ax = mls_axis<double>((double)pf.cx[s] - (Cx + sgn * 1.2 * nx));
-            const Axis<double> ay = mls_axis<double>((double)pf.cy[s] - (Cy + sgn * 1.2 * ny));
-            for (int b = 0; b < 3; b++)
-                for (int a = 0; a < 3; a++) {
-                    const int k = 3 * b + a;
-                    const double phi = ax.h[a] * ay.q[b] + ax.q[a] * ay.h[b] - ax.q[a] * ay.q[b];
-                    const double gx = ax.g[a] * ay.q[b], gy = ax.q[a] * ay.g[b];
-                    const double ubx = Gb[0][0] * gx + Gb[0][1] * gy, uby = Gb[1][0] * gx + Gb[1][1] * gy;
-                    inject_fields(L, cells[s][k], phi * rho_b, ubx, uby, pf.f[s][1][k], pf.f[s][2][k], rho_k[s][k],
-                                  sbar, bbar, gsx, gsy);
-                }
-        }
     }
-    __syncthreads();
-    for (int v = threadIdx.x; v < n; v += blockDim.x) {
-        const double2 a = sm.bdl[v], b = sm.bdr[v == 0 ? n - 1 : v - 1], c = sm.xd[v];
-        xout[off + v] = make_double2(c.x + a.x + b.x, c.y + a.y + b.y);
+    for (int o = 16; o > 0; o >>= 1) {
+        gsx += __shfl_xor_sync(0xffffffffu, gsx, o);
+        gsy += __shfl_xor_sync(0xffffffffu, gsy, o);
     }
-    double gg[2] = {gsx, gsy};
-    block_reduce<2, false>(gg, sm.red);
-    if (threadIdx.x == 0) {
-        atomicAdd(grad + 2 * ncaps, gg[0]);
-        atomicAdd(grad + 2 * ncaps + 1, gg[1]);
+    if ((threadIdx.x & 31) == 0 && (gsx != 0.0 || gsy != 0.0)) {
+        atomicAdd(grad_g, gsx);
+        atomicAdd(grad_g + 1, gsy);
     }
     if (!ok) atomicOr(status, kStatSupport);
 }
@@ -944,7 +1030,7 @@ struct AdjLayout {
     int K = 0, nseg = 0;
     size_t pb = 0, ckpt = 0;
     size_t tape_pops = 0, tape_X = 0, tape_flc = 0, tape_fib0 = 0, age0 = 0, ckpts = 0, sbar[2]{}, fbar = 0,
-           fib[3]{}, bbar[3]{}, xc = 0, xp = 0, xnew = 0, xb[2]{}, ub = 0, u1b = 0, u2b = 0, fv = 0, shp = 0,
+           fib[3]{}, bbar[3]{}, xc = 0, xp = 0, xnew = 0, xb[2]{}, ub = 0, u1b = 0, u2b = 0, ftb = 0, fv = 0, shp = 0,
            grad = 0, J = 0, total = 0;
 };
 
@@ -983,6 +1069,7 @@ AdjLayout adj_layout(const lbmib_ctx* c, long long T, int K) {
     a.ub = take(M * sizeof(double2));
     a.u1b = take(M * sizeof(double2));
     a.u2b = take(M * sizeof(double2));
+    a.ftb = take(M * sizeof(double2));
     a.xp = take(M * sizeof(double2));
     a.xnew = take(M * sizeof(double2));
     a.fv = take(M * sizeof(double2));
@@ -1058,14 +1145,18 @@ lbmib_status tape_forward(lbmib_ctx* c, lbmib_scheme scheme, int len, char* w, c
                                       sizeof(double), cudaMemcpyDeviceToDevice, s));
     void* keep0 = c->pops[0];
     void* keep1 = c->pops[1];
+    fork_ib(c, s);
     for (int k = 0; k < len; k++) {
-        LBMIB_CUDA(c, cudaMemcpyAsync(tX + (size_t)k * M, c->nd.X, M * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+        // positions before step k: after the previous node update, on the stream that runs it
+        LBMIB_CUDA(c, cudaMemcpyAsync(tX + (size_t)k * M, c->nd.X, M * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                      ib_stream_of(c, s)));
         c->pops[0] = tape + (size_t)k * a.pb;
         c->pops[1] = tape + (size_t)(k + 1) * a.pb;
         if (scheme == LBMIB_DYNAMIC) c->nd.Flc = (double2*)(w + a.tape_flc) + (size_t)k * M;
         int cur = 0;
         enqueue_step(c, scheme, cur, c->cur_fib, s, false);
     }
+    join_ib(c, s);
     c->nd.Flc = nullptr;
     c->pops[0] = keep0;
     c->pops[1] = keep1;
@@ -1158,8 +1249,11 @@ lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* 
             k_adjd_spread<<<ncaps, 128, 0, s>>>(L, c->nd, c->max_n, Xn, k > 0 ? Xn - M : nullptr,
                                                 flc + (size_t)k * M, k > 0 ? flc + (size_t)(k - 1) * M : nullptr,
                                                 k == len - 1 ? fib_n : nullptr, k > 0 ? fib_p : nullptr, shp);
-            k_adjd_update<S><<<ncaps, 128, smem, s>>>(L, c->nd, c->max_n, Xn, post1, fib_n, xc, xm, ub, xout, u2b,
-                                                      sb_in, b_n, ncaps, grad, &c->ctr->status);
+            k_adjd_update<<<ncaps, 128, smem, s>>>(c->nd, c->max_n, Xn, xc, xm, ub, xout, u2b,
+                                                   (double2*)(w + a.ftb), ncaps, grad);
+            k_adjd_tract<S><<<nblk(2LL * count, 32), 32, 0, s>>>(L, c->nd, count, Xn, post1, fib_n,
+                                                                 (const double2*)(w + a.ftb), xout, sb_in, b_n,
+                                                                 grad + 2 * ncaps, &c->ctr->status);
             k_adjd_interp<S><<<nblk(9LL * count, 288), 288, 0, s>>>(L, post1, fib_n, shp, count, u2b, xout, sb_in,
                                                                     b_n, grad + 2 * ncaps);
         }
@@ -1172,7 +1266,7 @@ lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* 
             k_adjd_interp<S><<<nblk(9LL * count, 288), 288, 0, s>>>(L, post0, fib_p, shp, count, u1b, xout, sb_out,
                                                                     b_p, grad + 2 * ncaps);
         }
-        c->launches += ncaps > 0 ? 6 : 1;
+        c->launches += ncaps > 0 ? 7 : 1;
         LBMIB_CUDA(c, cudaGetLastError());
     }
     return LBMIB_OK;
@@ -1204,9 +1298,7 @@ lbmib_status lbmib_adjoint(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme, 
         cudaFuncSetAttribute(k_adj_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_bytes);
         cudaFuncSetAttribute(k_adj_membrane, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_bytes);
         cudaFuncSetAttribute(k_adjd_forcing, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_bytes);
-        cudaFuncSetAttribute(k_adjd_update<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_bytes);
-        cudaFuncSetAttribute(k_adjd_update<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_bytes);
-        cudaFuncSetAttribute(k_adjd_update<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_bytes);
+        cudaFuncSetAttribute(k_adjd_update, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_bytes);
     }
     char* w = (char*)d_work;
     cudaStream_t s = c->stream;

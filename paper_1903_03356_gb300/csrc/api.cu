@@ -58,6 +58,7 @@ Layout make_layout(const lbmib_config* c) {
     L.s0 = take(M * sizeof(double));
     L.age = take(M * sizeof(int));
     L.capid = take(M * sizeof(int));
+    L.mls = take(M * sizeof(MlsW<double>));
     L.caps = take(K * sizeof(CapsuleParams));
     L.obs = take(8 * K * sizeof(double));
     L.pts = take(M * sizeof(double2));
@@ -91,10 +92,41 @@ void drop_graphs(lbmib_ctx* c) {
                 }
 }
 
+// Stream schedule of one step (FS force+spread, CS collide-stream, P patch, U update):
+//   ib stream:      FS(n) ----------+                 +--> U(n) --> FS(n+1) ...
+//   lattice stream: CS(n) ------- wait --> P(n) --+---+--> CS(n+1) ...
+// CS reads only the populations and the uniform force, so it does not wait for FS; P
+// needs both. CS(n+1) needs the patched populations only, so it runs beside U(n) and
+// FS(n+1), which read those populations and write vertices, lists and the other force
+// buffer. The lattice kernel is HBM-bound and the IB kernels FP64- and latency-bound,
+// so the two can share the GPU. Measured on GB300: with few capsules (one CTA each,
+// most SMs idle during the IB kernels) the step time drops by a third; with enough
+// capsules to fill the GPU the IB blocks take registers and warp slots from the lattice
+// kernel, which slows by what the overlap saves. Hence the automatic setting: overlap
+// while the capsules number fewer than two per SM.
+bool overlapped(const lbmib_ctx* c) {
+    if (c->caps.empty() || c->overlap == 0) return false;
+    return c->overlap == 1 || (int)c->caps.size() < 2 * (c->sms > 0 ? c->sms : 1);
+}
+
+void fork_ib(lbmib_ctx* c, cudaStream_t s) {
+    if (!overlapped(c)) return;
+    cudaEventRecord(c->ev_fork, s);
+    cudaStreamWaitEvent(c->ib_stream, c->ev_fork, 0);
+}
+
+void join_ib(lbmib_ctx* c, cudaStream_t s) {
+    if (!overlapped(c)) return;
+    cudaEventRecord(c->ev_join, c->ib_stream);
+    cudaStreamWaitEvent(s, c->ev_join, 0);
+}
+
 // Enqueue one coupled step on stream s, advancing (cur, cur_fib).
-void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cudaStream_t s, bool timed) {
+void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cudaStream_t s_lat, bool timed) {
     const Lat& L = c->L;
     const int ncaps = (int)c->caps.size();
+    const bool ov = overlapped(c);
+    cudaStream_t s = ov ? c->ib_stream : s_lat;   // stream of the immersed-boundary kernels
     const void* src = c->pops[cur];
     void* dst = c->pops[1 - cur];
     const int fc = 1 - cur_fib;  // buffer spread into this step
@@ -115,6 +147,7 @@ void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
             launch_kin_force_spread(L, c->nd, ncaps, c->max_n, c->tile_cells, sp, status, st == LBMIB_FP64, s);
         }
         c->launches++;
+        if (ov) cudaEventRecord(c->ev_spread, s);
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timed) {
@@ -127,21 +160,26 @@ void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
         e0 = c->ev_pool[c->ev_used].first;
         e1 = c->ev_pool[c->ev_used].second;
         c->ev_used++;
-        cudaEventRecord(e0, s);
+        cudaEventRecord(e0, s_lat);
     }
-    if (st == LBMIB_FP64) launch_collide_stream<double>(src, dst, L, status, c->lattice_variant, s);
-    else if (st == LBMIB_FP32) launch_collide_stream<float>(src, dst, L, status, c->lattice_variant, s);
-    else launch_collide_stream<__half>(src, dst, L, status, c->lattice_variant, s);
+    if (st == LBMIB_FP64) launch_collide_stream<double>(src, dst, L, status, c->lattice_variant, s_lat);
+    else if (st == LBMIB_FP32) launch_collide_stream<float>(src, dst, L, status, c->lattice_variant, s_lat);
+    else launch_collide_stream<__half>(src, dst, L, status, c->lattice_variant, s_lat);
     c->launches++;
-    if (timed) cudaEventRecord(e1, s);
+    if (timed) cudaEventRecord(e1, s_lat);
     if (ncaps > 0) {
         const int cap = list_cap;
+        if (ov) cudaStreamWaitEvent(s_lat, c->ev_spread, 0);
         if (st == LBMIB_FP64)
-            launch_patch<double>(src, dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->ctr, fc, cap, s);
+            launch_patch<double>(src, dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->ctr, fc, cap, s_lat);
         else if (st == LBMIB_FP32)
-            launch_patch<float>(src, dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->ctr, fc, cap, s);
+            launch_patch<float>(src, dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->ctr, fc, cap, s_lat);
         else
-            launch_patch<__half>(src, dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->ctr, fc, cap, s);
+            launch_patch<__half>(src, dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->ctr, fc, cap, s_lat);
+        if (ov) {
+            cudaEventRecord(c->ev_patch, s_lat);
+            cudaStreamWaitEvent(s, c->ev_patch, 0);
+        }
         int* reset = &c->ctr->count[fp];
         if (scheme == LBMIB_DYNAMIC) {
             if (st == LBMIB_FP64) launch_dyn_update<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, reset, status, s);
@@ -179,7 +217,9 @@ int kernels_per_step(const lbmib_ctx* c) { return c->caps.empty() ? 1 : 4; }
 lbmib_status capture(lbmib_ctx* c, lbmib_scheme scheme, int cur, int cur_fib, int len, cudaGraphExec_t* out) {
     LBMIB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     const long long launches = c->launches;
+    fork_ib(c, c->cap_stream);
     for (int k = 0; k < len; k++) enqueue_step(c, scheme, cur, cur_fib, c->cap_stream, false);
+    join_ib(c, c->cap_stream);
     c->launches = launches;  // capture does not launch
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
@@ -255,6 +295,7 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     c->nd.s0 = (double*)(a + lay.s0);
     c->nd.age = (int*)(a + lay.age);
     c->nd.capid = (int*)(a + lay.capid);
+    c->nd.mls = a + lay.mls;
     c->d_caps = (CapsuleParams*)(a + lay.caps);
     c->nd.caps = c->d_caps;
     c->nd.count = 0;
@@ -280,15 +321,20 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     // lattice launch shape measured fastest on GB300: 128-thread blocks, and for the
     // single-precision storages a 64-register cap (four resident blocks per SM)
     c->lattice_variant = cfg->storage == LBMIB_FP64 ? 0x80 : (0x80 | (1 << 18));
+    if (cfg->storage == LBMIB_FP16) c->lattice_variant |= 1 << 19;   // packed 16-byte FP16 kernel
     L.gxf = (float)L.gx;
     L.gyf = (float)L.gy;
     L.omegaf = (float)L.omega;
     L.ubf = (float)L.ub;
     L.utf = (float)L.ut;
 
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->ib_stream, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&c->ev_fork, &c->ev_spread, &c->ev_patch, &c->ev_join})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
-        delete c;
+        lbmib_destroy(c);
         return LBMIB_ERR_CUDA;
     }
     set_capsule_smem_limits(1, c->tile_cells);
@@ -298,8 +344,7 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     if (e == cudaSuccess) e = cudaMemsetAsync(c->mark, 0, N * sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream);
     if (e != cudaSuccess) {
-        cudaStreamDestroy(c->cap_stream);
-        delete c;
+        lbmib_destroy(c);
         return LBMIB_ERR_CUDA;
     }
     by_storage(cfg->storage, [&](auto tag) {
@@ -309,8 +354,7 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     c->launches++;
     e = cudaGetLastError();
     if (e != cudaSuccess) {
-        cudaStreamDestroy(c->cap_stream);
-        delete c;
+        lbmib_destroy(c);
         return LBMIB_ERR_CUDA;
     }
     *out = c;
@@ -326,6 +370,12 @@ void lbmib_destroy(lbmib_ctx* c) {
         cudaEventDestroy(p.second);
     }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->ib_stream) {
+        cudaStreamSynchronize(c->ib_stream);
+        cudaStreamDestroy(c->ib_stream);
+    }
+    for (cudaEvent_t ev : {c->ev_fork, c->ev_spread, c->ev_patch, c->ev_join})
+        if (ev) cudaEventDestroy(ev);
     delete c;
 }
 
@@ -438,7 +488,9 @@ lbmib_status lbmib_step(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme) {
     if (!c || nsteps < 0 || (scheme != LBMIB_KINEMATIC && scheme != LBMIB_DYNAMIC)) return LBMIB_ERR_ARG;
     const int sc = scheme == LBMIB_DYNAMIC ? 1 : 0;
     if (c->timing || !c->use_graphs) {
+        fork_ib(c, c->stream);
         for (long long k = 0; k < nsteps; k++) enqueue_step(c, scheme, c->cur, c->cur_fib, c->stream, c->timing);
+        join_ib(c, c->stream);
     } else {
         const int G = c->graph_steps > 0 ? c->graph_steps : 1;
         long long left = nsteps;
@@ -462,7 +514,9 @@ lbmib_status lbmib_step(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme) {
             }
             left -= G;
         }
+        fork_ib(c, c->stream);
         for (long long k = 0; k < left; k++) enqueue_step(c, scheme, c->cur, c->cur_fib, c->stream, false);
+        join_ib(c, c->stream);
     }
     c->steps += nsteps;
     LBMIB_CUDA(c, cudaGetLastError());
@@ -696,6 +750,11 @@ lbmib_status lbmib_set_option(lbmib_ctx* c, int option, long long value) {
     switch (option) {
         case LBMIB_OPT_GRAPHS: c->use_graphs = value != 0; break;
         case LBMIB_OPT_TIMING: c->timing = value != 0; break;
+        case LBMIB_OPT_OVERLAP:
+            if (value < -1 || value > 1) return fail(c, LBMIB_ERR_ARG, "overlap must be -1, 0 or 1");
+            c->overlap = (int)value;
+            drop_graphs(c);
+            break;
         case LBMIB_OPT_GRAPH_STEPS:
             if (value < 1 || value > 4096) return fail(c, LBMIB_ERR_ARG, "graph steps out of range");
             c->graph_steps = (int)value;

@@ -44,35 +44,6 @@ struct BatchDev {
     int ncases;
 };
 
-// Pre-collision populations of node (x, y) (Eq. 1, left side) with explicit neighbour
-// coordinates (no divisions), all nine loads issued before any is used. Plain loads:
-// the case's populations are rewritten by this CTA every step.
-template <typename S>
-__device__ __forceinline__ void pull9(const S* __restrict__ src, const Lat& L, int x, int y,
-                                      typename St<S>::C (&s)[9]) {
-    using C = typename St<S>::C;
-    const int xm = x == 0 ? L.nx - 1 : x - 1, xp = x + 1 == L.nx ? 0 : x + 1;
-    const int ym = y == 0 ? L.ny - 1 : y - 1, yp = y + 1 == L.ny ? 0 : y + 1;
-    const bool lo = L.walls && y == 0, hi = L.walls && y == L.ny - 1;
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        const bool bounce = (ey(i) > 0 && lo) || (ey(i) < 0 && hi);
-        const int sx = ex(i) > 0 ? xm : (ex(i) < 0 ? xp : x);
-        const int sy = ey(i) > 0 ? ym : (ey(i) < 0 ? yp : y);
-        const int k = bounce ? opp(i) : i;
-        s[i] = St<S>::ldc(src + (long long)k * L.plane + (long long)(bounce ? y : sy) * L.pitch + (bounce ? x : sx), L);
-    }
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        const bool bounce = (ey(i) > 0 && lo) || (ey(i) < 0 && hi);
-        if (bounce) {
-            const int j = opp(i);
-            const C uw = ey(i) > 0 ? lat_c<C>(L.ub, L.ubf) : lat_c<C>(L.ut, L.utf);
-            s[i] -= C(6) * wgt<C>(j) * C(ex(j)) * uw;
-        }
-    }
-}
-
 // Force-tile value at lattice node (x, y), or zero when the node is outside the tile.
 // (x0w, y0w): tile origin wrapped into the lattice (y0w unwrapped between walls).
 template <typename C>
@@ -162,7 +133,7 @@ __device__ void run_case(const BatchDev& d, int c, int nsteps, const CapSmem& sm
             int y = (int)threadIdx.x / L.nx, x = (int)threadIdx.x - y * L.nx;
             while (y < L.ny) {
                 C s[9];
-                pull9<S>(src, L, x, y, s);
+                pull_all<S, false>(src, L, x, y, s);   // plain loads: rewritten every step
                 C fx, fy;
                 tile_force<C>(t, L, x0w, y0w, x, y, fx, fy);
                 const C usq = collide<C>(s, gx + fx, gy + fy, om);
@@ -186,7 +157,7 @@ __device__ void run_case(const BatchDev& d, int c, int nsteps, const CapSmem& sm
             for (int k = threadIdx.x; k < cells; k += blockDim.x) {
                 const int j = k / t.w, i = k - j * t.w;
                 C q[9];
-                pull9<S>(dst, L, wrapi(t.x0 + i, L.nx), support_row(L, t.y0 + j), q);
+                pull_all<S, false>(dst, L, wrapi(t.x0 + i, L.nx), support_row(L, t.y0 + j), q);
                 C drho, mx, my;
                 moments<C>(q, drho, mx, my);
                 const C inv = C(1) / (C(1) + drho);

@@ -21,7 +21,7 @@ inline size_t storage_bytes(lbmib_storage s) { return s == LBMIB_FP64 ? 8 : (s =
 // Offsets of the context's buffers inside the caller's arena.
 struct Layout {
     size_t pops[2], fib[2], mark, list[2], ctr, scratch;
-    size_t X, Xm1, uv, Fint, Fext, L0, c0, s0, age, capid, caps, obs, pts, pts_out;
+    size_t X, Xm1, uv, Fint, Fext, L0, c0, s0, age, capid, mls, caps, obs, pts, pts_out;
     size_t total;
     int pitch;
     long long plane;
@@ -36,6 +36,12 @@ struct lbmib_ctx {
     lbmib::Lat L{};
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
+    // Immersed-boundary kernels run on their own stream so that they overlap the lattice
+    // update of the same or the next step (fork/join through these events).
+    cudaStream_t ib_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_spread = nullptr, ev_patch = nullptr, ev_join = nullptr;
+    int overlap = -1;   // 1 on, 0 off, -1 automatic (on while the capsules cannot fill the GPU)
+    int sms = 0;        // multiprocessors of the device
     char* arena = nullptr;
     void* pops[2]{};
     double* fib[2]{};
@@ -87,8 +93,16 @@ lbmib_status cuda_fail(lbmib_ctx* c, cudaError_t e, const char* where);
 void drop_graphs(lbmib_ctx* c);
 
 // Enqueue one coupled step on stream s: populations c->pops[cur] -> c->pops[1 - cur],
-// last spread force c->fib[cur_fib]; advances (cur, cur_fib).
+// last spread force c->fib[cur_fib]; advances (cur, cur_fib). With overlap on, the
+// immersed-boundary kernels go to c->ib_stream: a sequence of steps must be bracketed
+// by fork_ib() and join_ib() on s.
 void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cudaStream_t s, bool timed);
+void fork_ib(lbmib_ctx* c, cudaStream_t s);
+void join_ib(lbmib_ctx* c, cudaStream_t s);
+// Whether the immersed-boundary kernels run on their own stream, and the stream they
+// run on when a step sequence is enqueued on s.
+bool overlapped(const lbmib_ctx* c);
+inline cudaStream_t ib_stream_of(const lbmib_ctx* c, cudaStream_t s) { return overlapped(c) ? c->ib_stream : s; }
 
 // Synchronise the context stream and translate the sticky device status.
 lbmib_status device_status(lbmib_ctx* c);

@@ -73,18 +73,17 @@ __device__ void flush_forces(const Tile<C>& t, const Lat& L, const Spread& sp, i
     }
 }
 
-// Interpolation (Eq. 8) at (X, Y) from the tile, or from the populations when the
-// capsule has no tile.
+// Interpolation (Eq. 8) with the shape functions m from the tile, or from the
+// populations when the capsule has no tile.
 template <typename S, bool GRAD>
-__device__ __forceinline__ bool interp_at(const Tile<typename St<S>::C>& t, const S* __restrict__ src, const Lat& L,
-                                          const double* __restrict__ fib, double X, double Y,
-                                          InterpT<typename St<S>::C>& o) {
+__device__ __forceinline__ bool interp_with(const MlsW<typename St<S>::C>& m, const Tile<typename St<S>::C>& t,
+                                            const S* __restrict__ src, const Lat& L, const double* __restrict__ fib,
+                                            InterpT<typename St<S>::C>& o) {
     using C = typename St<S>::C;
-    if (!t.use) return mls_interp<S, GRAD>(src, L, fib, X, Y, o);
-    const MlsW<C> m = mls_setup<C>(L, X, Y);
+    if (!t.use) return mls_interp_with<S, GRAD>(m, src, L, fib, o);
     if (!t.holds(m.cx, m.cy)) {
         // only a runaway point (already moved to the origin) can leave the box: flag it
-        mls_interp<S, GRAD>(src, L, fib, X, Y, o);
+        mls_interp_with<S, GRAD>(m, src, L, fib, o);
         return false;
     }
     mls_apply<C, GRAD>(m, [&](int a, int b) {
@@ -98,12 +97,20 @@ __device__ __forceinline__ bool interp_at(const Tile<typename St<S>::C>& t, cons
     return m.ok;
 }
 
-// Spread c * F at (X, Y) (step 3 / step iii): into the force tile, or straight into the
-// lattice field when the capsule has no tile.
+// Interpolation (Eq. 8) at (X, Y) from the tile, or from the populations when the
+// capsule has no tile.
+template <typename S, bool GRAD>
+__device__ __forceinline__ bool interp_at(const Tile<typename St<S>::C>& t, const S* __restrict__ src, const Lat& L,
+                                          const double* __restrict__ fib, double X, double Y,
+                                          InterpT<typename St<S>::C>& o) {
+    return interp_with<S, GRAD>(mls_setup<typename St<S>::C>(L, X, Y), t, src, L, fib, o);
+}
+
+// Spread c * F with the shape functions m (step 3 / step iii): into the force tile, or
+// straight into the lattice field when the capsule has no tile.
 template <typename C>
-__device__ __forceinline__ bool spread_at(Tile<C>& t, const Lat& L, const Spread& sp, int stamp, double X, double Y,
-                                          double Fx, double Fy, double c) {
-    const MlsW<C> m = mls_setup<C>(L, X, Y);
+__device__ __forceinline__ bool spread_with(const MlsW<C>& m, Tile<C>& t, const Lat& L, const Spread& sp, int stamp,
+                                            double Fx, double Fy, double c) {
     const long long N = (long long)L.nx * L.ny;
     const bool in_tile = t.holds(m.cx, m.cy);
     const C cFx = C(c * Fx), cFy = C(c * Fy);
@@ -172,8 +179,11 @@ __global__ void __launch_bounds__(128) k_dyn_force_spread(const S* __restrict__ 
     bool ok = true;
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
         const double2 Xv = sm.X[v];
+        // shape functions at X^n: used for U, for the spread, and by this step's update
+        const MlsW<C> m = mls_setup<C>(L, Xv.x, Xv.y);
+        reinterpret_cast<MlsW<C>*>(nd.mls)[off + v] = m;
         InterpT<C> o;
-        ok &= interp_at<S, false>(t, src, L, fib_prev, Xv.x, Xv.y, o);
+        ok &= interp_with<S, false>(m, t, src, L, fib_prev, o);
         const double Ux = (double)o.ux, Uy = (double)o.uy;
         double2 uv = nd.uv[off + v];
         if (nd.age[off + v] == 0) {
@@ -183,7 +193,7 @@ __global__ void __launch_bounds__(128) k_dyn_force_spread(const S* __restrict__ 
         }
         const double cl = 0.5 * (sm.sst[v == 0 ? n - 1 : v - 1] + sm.sst[v]);
         if (nd.Flc) nd.Flc[off + v] = make_double2(cl * (uv.x - Ux), cl * (uv.y - Uy));
-        ok &= spread_at<C>(t, L, sp, stamp, Xv.x, Xv.y, uv.x - Ux, uv.y - Uy, cl);
+        ok &= spread_with<C>(m, t, L, sp, stamp, uv.x - Ux, uv.y - Uy, cl);
     }
     __syncthreads();
     if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
@@ -213,7 +223,7 @@ __global__ void __launch_bounds__(128) k_dyn_update(const S* __restrict__ dst, L
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
         const double2 Xv = sm.X[v], Xr = sm.X[v + 1 == n ? 0 : v + 1];
         InterpT<C> o;
-        ok &= interp_at<S, false>(t, dst, L, fib, Xv.x, Xv.y, o);
+        ok &= interp_with<S, false>(reinterpret_cast<const MlsW<C>*>(nd.mls)[off + v], t, dst, L, fib, o);
         sm.xd[v] = make_double2((double)o.ux, (double)o.uy);
         // element v: probes at the centroid +/- 1.2 n+ (Section 2.2.2)
         const double2 d = Xr - Xv;
@@ -281,7 +291,9 @@ __global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int m
         const double2 F = node_internal_force(sm, P, v, A);
         nd.Fint[off + v] = F;
         nd.Fext[off + v] = make_double2(0.0, 0.0);
-        ok &= spread_at<C>(t, L, sp, stamp, sm.X[v].x, sm.X[v].y, F.x, F.y, 1.0);
+        const MlsW<C> m = mls_setup<C>(L, sm.X[v].x, sm.X[v].y);
+        reinterpret_cast<MlsW<C>*>(nd.mls)[off + v] = m;
+        ok &= spread_with<C>(m, t, L, sp, stamp, F.x, F.y, 1.0);
     }
     __syncthreads();
     if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
@@ -308,7 +320,7 @@ __global__ void __launch_bounds__(128) k_kin_advance(const S* __restrict__ dst, 
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
         const double2 Xv = sm.X[v];
         InterpT<C> o;
-        ok &= interp_at<S, false>(t, dst, L, fib, Xv.x, Xv.y, o);
+        ok &= interp_with<S, false>(reinterpret_cast<const MlsW<C>*>(nd.mls)[off + v], t, dst, L, fib, o);
         const double Ux = (double)o.ux, Uy = (double)o.uy;
         double2 Xn;
         if (nd.age[off + v] == 0) {

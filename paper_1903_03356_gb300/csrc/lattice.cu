@@ -212,6 +212,146 @@ __global__ void __launch_bounds__(BS, MINB) k_collide_stream(const S* __restrict
     if (__any_sync(0xffffffffu, bad && active) && lane == 0) atomicOr(status, kStatUnstable);
 }
 
+// FP16 storage: one warp owns 256 consecutive nodes of a row, 8 per thread, each
+// population fetched with one aligned 16-byte load and kept packed (four half2
+// registers) until its node pair is collided; the results are packed back and stored
+// as 16-byte vectors. This keeps the bytes in flight per thread at the FP32 kernel's
+// (9 x 16 B) without holding 72 floats in registers.
+template <int I>
+struct PopH {
+    __half2 h[4];   // halves of the source row at x0 .. x0+7 (own opposite row at a wall)
+    __half edge;    // the element no neighbouring lane holds
+
+    __device__ __forceinline__ bool at_wall(const Lat& L, int y) const {
+        constexpr int EY = ey(I);
+        return EY != 0 && L.walls && (y - EY < 0 || y - EY >= L.ny);
+    }
+    __device__ __forceinline__ const __half* row_ptr(const __half* __restrict__ src, const Lat& L, int y) const {
+        constexpr int EY = ey(I);
+        if (at_wall(L, y)) return src + (long long)opp(I) * L.plane + (long long)y * L.pitch;
+        const int ys = EY != 0 ? wrapi(y - EY, L.ny) : y;
+        return src + (long long)I * L.plane + (long long)ys * L.pitch;
+    }
+    __device__ __forceinline__ void issue(const __half* __restrict__ src, const Lat& L, int x0, int y, int lane,
+                                          bool active) {
+        constexpr int EX = ex(I);
+        const __half* row = row_ptr(src, L, y);
+        edge = __float2half(0.0f);
+        uint4 raw = make_uint4(0u, 0u, 0u, 0u);
+        // x0 < nx <= pitch, both multiples of 8: the vector stays inside the padded row
+        if (active) raw = __ldg(reinterpret_cast<const uint4*>(row + x0));
+        const __half2* hp = reinterpret_cast<const __half2*>(&raw);
+#pragma unroll
+        for (int k = 0; k < 4; k++) h[k] = hp[k];
+        if (!at_wall(L, y) && active) {
+            if (EX == 1 && lane == 0) edge = __ldg(row + wrapi(x0 - 1, L.nx));
+            if (EX == -1 && (lane == 31 || x0 + 16 > L.nx)) edge = __ldg(row + wrapi(x0 + 8, L.nx));
+        }
+    }
+    __device__ __forceinline__ __half elem(int j) const { return (j & 1) ? __high2half(h[j >> 1]) : __low2half(h[j >> 1]); }
+    // the neighbouring element across the lane boundary (all 32 lanes call this together)
+    __device__ __forceinline__ __half across(const Lat& L, int x0, int lane) const {
+        constexpr int EX = ex(I);
+        if (EX == 1) {
+            const __half p = __shfl_up_sync(0xffffffffu, elem(7), 1);
+            return lane == 0 ? edge : p;
+        }
+        const __half nx = __shfl_down_sync(0xffffffffu, elem(0), 1);
+        return (lane == 31 || x0 + 16 > L.nx) ? edge : nx;
+    }
+};
+
+template <int I>
+__device__ __forceinline__ float pop_value(const PopH<I>& p, __half across, int j, bool wall, float corr,
+                                           float inv_scale) {
+    constexpr int EX = ex(I);
+    __half v;
+    if (wall || EX == 0) v = p.elem(j);
+    else if (EX == 1) v = j == 0 ? across : p.elem(j - 1);
+    else v = j == 7 ? across : p.elem(j + 1);
+    return __half2float(v) * inv_scale - (wall ? corr : 0.0f);
+}
+
+template <int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) k_collide_stream_h(const __half* __restrict__ src,
+                                                               __half* __restrict__ dst, Lat L,
+                                                               unsigned* __restrict__ status) {
+    constexpr int V = 8;
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * BS + threadIdx.x) >> 5;
+    const int segs = (L.nx + 32 * V - 1) / (32 * V);
+    if (gw >= (long long)segs * L.ny) return;   // whole warps only
+    const int y = (int)(gw / segs);
+    const int seg = (int)(gw - (long long)y * segs);
+    const int x0 = (seg * 32 + lane) * V;
+    const bool active = x0 < L.nx;
+    const bool full = x0 + V <= L.nx;
+
+    PopH<0> p0; PopH<1> p1; PopH<2> p2; PopH<3> p3; PopH<4> p4;
+    PopH<5> p5; PopH<6> p6; PopH<7> p7; PopH<8> p8;
+    p0.issue(src, L, x0, y, lane, active); p1.issue(src, L, x0, y, lane, active);
+    p2.issue(src, L, x0, y, lane, active); p3.issue(src, L, x0, y, lane, active);
+    p4.issue(src, L, x0, y, lane, active); p5.issue(src, L, x0, y, lane, active);
+    p6.issue(src, L, x0, y, lane, active); p7.issue(src, L, x0, y, lane, active);
+    p8.issue(src, L, x0, y, lane, active);
+    const __half a1 = p1.across(L, x0, lane), a3 = p3.across(L, x0, lane), a5 = p5.across(L, x0, lane);
+    const __half a6 = p6.across(L, x0, lane), a7 = p7.across(L, x0, lane), a8 = p8.across(L, x0, lane);
+    // wall corrections -6 w_j (e_j . u_w) of the reflected populations (Section 2.1, R2)
+    const bool lo = L.walls && y == 0, hi = L.walls && y == L.ny - 1;
+    const float cw = 6.0f / 36.0f;
+    const float c2 = 0.0f;   // populations 2 and 4 reflect populations without an x component
+    const float c5 = -cw * L.ubf, c6 = cw * L.ubf;   // bottom wall: 5 <- 7 (e_x -1), 6 <- 8 (e_x +1)
+    const float c7 = cw * L.utf, c8 = -cw * L.utf;   // top wall: 7 <- 5 (e_x +1), 8 <- 6 (e_x -1)
+    const float gx = L.gxf, gy = L.gyf, om = L.omegaf, is = L.inv_scale, sc = L.scale;
+    uint4 out[9];
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        float r[2][9];
+#pragma unroll
+        for (int t = 0; t < 2; t++) {
+            const int j = 2 * q + t;
+            float s[9];
+            s[0] = pop_value(p0, a1, j, false, 0.0f, is);
+            s[1] = pop_value(p1, a1, j, false, 0.0f, is);
+            s[2] = pop_value(p2, a1, j, lo, c2, is);
+            s[3] = pop_value(p3, a3, j, false, 0.0f, is);
+            s[4] = pop_value(p4, a1, j, hi, c2, is);
+            s[5] = pop_value(p5, a5, j, lo, c5, is);
+            s[6] = pop_value(p6, a6, j, lo, c6, is);
+            s[7] = pop_value(p7, a7, j, hi, c7, is);
+            s[8] = pop_value(p8, a8, j, hi, c8, is);
+            const float usq = collide<float>(s, gx, gy, om);
+            bad |= !(usq < 0.09f);
+#pragma unroll
+            for (int i = 0; i < 9; i++) r[t][i] = s[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            const __half2 hv = __floats2half2_rn(r[0][i] * sc, r[1][i] * sc);
+            (&out[i].x)[q] = *reinterpret_cast<const unsigned*>(&hv);
+        }
+    }
+    if (full) {
+#pragma unroll
+        for (int i = 0; i < 9; i++)
+            *reinterpret_cast<uint4*>(dst + (long long)i * L.plane + (long long)y * L.pitch + x0) = out[i];
+    } else if (active) {
+        // ragged chunk at the end of a row: element-wise, with the pull's own wrap
+        bad = false;
+        for (int j = 0; j < V && x0 + j < L.nx; j++) {
+            float s[9];
+            pull_all<__half>(src, L, x0 + j, y, s);
+            const float usq = collide<float>(s, gx, gy, om);
+            bad |= !(usq < 0.09f);
+#pragma unroll
+            for (int i = 0; i < 9; i++)
+                St<__half>::st(dst + (long long)i * L.plane + (long long)y * L.pitch + x0 + j, s[i], L);
+        }
+    }
+    if (__any_sync(0xffffffffu, bad && active) && lane == 0) atomicOr(status, kStatUnstable);
+}
+
 // Forced-node patch: redo the collision of every node in the current touched-cell list
 // with the total force g + f_ib (Eq. 4-5), reading the same input as k_collide_stream.
 // Also clears the previous force buffer at the previous list (its last reader has run)
@@ -240,8 +380,7 @@ __global__ void __launch_bounds__(256) k_patch(const S* __restrict__ src, S* __r
         }
         const int y = cell / L.nx, x = cell - y * L.nx;
         C s[9];
-#pragma unroll
-        for (int i = 0; i < 9; i++) s[i] = pull<S>(src, L, i, x, y);
+        pull_all<S>(src, L, x, y, s);
         const C usq = collide<C>(s, C(L.gx + fib_c[cell]), C(L.gy + fib_c[N + cell]), C(L.omega));
         if (!(usq < C(0.09))) atomicOr(&ctr->status, kStatUnstable);
 #pragma unroll
@@ -302,8 +441,7 @@ __global__ void k_macros(const S* __restrict__ src, Lat L, const double* __restr
     if (n >= N) return;
     const int y = (int)(n / L.nx), x = (int)(n - (long long)y * L.nx);
     C s[9];
-#pragma unroll
-    for (int i = 0; i < 9; i++) s[i] = pull<S>(src, L, i, x, y);
+    pull_all<S>(src, L, x, y, s);
     C drho, mx, my;
     moments<C>(s, drho, mx, my);
     const double r = 1.0 + (double)drho;
@@ -344,6 +482,15 @@ void launch_collide_stream(const void* src, void* dst, const Lat& L, unsigned* s
     const unsigned g = blocks_for(threads, bs);
     const S* a = (const S*)src;
     S* b = (S*)dst;
+    if constexpr (std::is_same<S, __half>::value) {
+        if (variant & (1 << 19)) {   // packed 16-byte FP16 kernel, 8 nodes per thread
+            const long long segs8 = (L.nx + 255) / 256;
+            const unsigned g8 = blocks_for(segs8 * L.ny * 32, bs);
+            if (bs == 128) k_collide_stream_h<128, 4><<<g8, 128, 0, s>>>(a, b, L, status);
+            else k_collide_stream_h<256, 2><<<g8, 256, 0, s>>>(a, b, L, status);
+            return;
+        }
+    }
     if (bs == 256 && !occ4) k_collide_stream<S, 0, 0, 256, 3><<<g, 256, 0, s>>>(a, b, L, status);
     else if (bs == 256) k_collide_stream<S, 0, 0, 256, 4><<<g, 256, 0, s>>>(a, b, L, status);
     else if (!occ4) k_collide_stream<S, 0, 0, 128, 6><<<g, 128, 0, s>>>(a, b, L, status);

@@ -119,6 +119,35 @@ __device__ __forceinline__ typename St<S>::C pull(const S* __restrict__ src, con
     return ld(src + (long long)i * L.plane + (long long)ys * L.pitch + xs);
 }
 
+// All nine pre-collision populations of node (x, y), as pull() but with the neighbour
+// coordinates formed by comparisons instead of the periodic wrap's integer division,
+// and every load issued before any is used. NC as for pull().
+template <typename S, bool NC = true>
+__device__ __forceinline__ void pull_all(const S* __restrict__ src, const Lat& L, int x, int y,
+                                         typename St<S>::C (&s)[9]) {
+    using C = typename St<S>::C;
+    const int xm = x == 0 ? L.nx - 1 : x - 1, xp = x + 1 == L.nx ? 0 : x + 1;
+    const int ym = y == 0 ? L.ny - 1 : y - 1, yp = y + 1 == L.ny ? 0 : y + 1;
+    const bool lo = L.walls && y == 0, hi = L.walls && y == L.ny - 1;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const bool bounce = (ey(i) > 0 && lo) || (ey(i) < 0 && hi);
+        const int sx = ex(i) > 0 ? xm : (ex(i) < 0 ? xp : x);
+        const int sy = ey(i) > 0 ? ym : (ey(i) < 0 ? yp : y);
+        const S* p = src + (long long)(bounce ? opp(i) : i) * L.plane + (long long)(bounce ? y : sy) * L.pitch +
+                     (bounce ? x : sx);
+        s[i] = NC ? St<S>::ld(p, L) : St<S>::ldc(p, L);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        if ((ey(i) > 0 && lo) || (ey(i) < 0 && hi)) {
+            const int j = opp(i);
+            const C uw = ey(i) > 0 ? lat_c<C>(L.ub, L.ubf) : lat_c<C>(L.ut, L.utf);
+            s[i] -= C(6) * wgt<C>(j) * C(ex(j)) * uw;
+        }
+    }
+}
+
 // Density deviation, momentum (Eq. 6-7 without the force) of shifted populations.
 template <typename C>
 __device__ __forceinline__ void moments(const C s[9], C& drho, C& mx, C& my) {
@@ -244,10 +273,19 @@ __device__ __forceinline__ MlsW<C> mls_setup(const Lat& L, double X, double Y) {
     const double isx = rcp_bounded((double)sx0), isy = rcp_bounded((double)sy0);
     const double mx = (double)sx1 * isx, my = (double)sy1 * isy;
     C vx = 0, vy = 0;
+    // centred offsets, held in the compute type: for a single-precision C the subtraction
+    // is done in C (its result differs from the rounded double difference by at most
+    // one unit in the last place), which keeps GB300's narrow FP64 pipe for the solve
+    const C mxc = C(mx), myc = C(my);
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        m.dxp[a] = C((double)dx[a] - mx);
-        m.dyp[a] = C((double)dy[a] - my);
+        if constexpr (sizeof(C) == 8) {
+            m.dxp[a] = dx[a] - mx;
+            m.dyp[a] = dy[a] - my;
+        } else {
+            m.dxp[a] = dx[a] - mxc;
+            m.dyp[a] = dy[a] - myc;
+        }
         vx += m.wx[a] * m.dxp[a] * m.dxp[a];
         vy += m.wy[a] * m.dyp[a] * m.dyp[a];
     }
@@ -281,8 +319,7 @@ __device__ __forceinline__ Mom<typename St<S>::C> node_moments(const S* __restri
                                                                const double* __restrict__ fib, int x, int y) {
     using C = typename St<S>::C;
     C s[9];
-#pragma unroll
-    for (int i = 0; i < 9; i++) s[i] = pull<S>(src, L, i, x, y);
+    pull_all<S>(src, L, x, y, s);
     C drho, mx, my;
     moments<C>(s, drho, mx, my);
     const long long N = (long long)L.nx * L.ny;
@@ -329,16 +366,22 @@ __device__ __forceinline__ void mls_apply(const MlsW<C>& m, Get&& get, InterpT<C
     }
 }
 
+// MLS interpolation of the fluid with given shape functions, straight from the
+// populations (no tile).
+template <typename S, bool GRAD>
+__device__ bool mls_interp_with(const MlsW<typename St<S>::C>& m, const S* __restrict__ src, const Lat& L,
+                                const double* __restrict__ fib, InterpT<typename St<S>::C>& o) {
+    mls_apply<typename St<S>::C, GRAD>(m, [&](int a, int b) {
+        return node_moments<S>(src, L, fib, wrapi(m.cx + a - 1, L.nx), support_row(L, m.cy + b - 1));
+    }, o);
+    return m.ok;
+}
+
 // MLS interpolation of the fluid at (X, Y) straight from the populations (no tile).
 template <typename S, bool GRAD>
 __device__ bool mls_interp(const S* __restrict__ src, const Lat& L, const double* __restrict__ fib, double X,
                            double Y, InterpT<typename St<S>::C>& o) {
-    using C = typename St<S>::C;
-    const MlsW<C> m = mls_setup<C>(L, X, Y);
-    mls_apply<C, GRAD>(m, [&](int a, int b) {
-        return node_moments<S>(src, L, fib, wrapi(m.cx + a - 1, L.nx), support_row(L, m.cy + b - 1));
-    }, o);
-    return m.ok;
+    return mls_interp_with<S, GRAD>(mls_setup<typename St<S>::C>(L, X, Y), src, L, fib, o);
 }
 
 // Device status bits (sticky).

@@ -20,6 +20,8 @@ struct Nodes {
     const CapsuleParams* caps;
     int count;       // vertices in use
     double2* Flc;    // optional (null): c_l F_l of the last Dynamic spread, per vertex
+    void* mls;       // MLS shape functions of each vertex at X^n (MlsW of the compute type),
+                     // written by the spread kernels, read by the node update of the step
 };
 
 // Touched-cell bookkeeping for the spread of one step.

@@ -211,6 +211,23 @@ def test_fp16_storage_error_is_reported(L):
     assert err < 5e-2
 
 
+@pytest.mark.parametrize("nx,ny,walls", [(301, 37, True), (512, 20, False), (256, 64, True)])
+def test_packed_fp16_kernel_equals_the_scalar_fp16_kernel(L, nx, ny, walls):
+    # the 8-nodes-per-thread FP16 lattice kernel (default) against the 4-per-thread one:
+    # the same float arithmetic on the same half inputs, so identical bits; ragged rows,
+    # moving walls, periodic rows, a body force
+    case = W.Case("fp16", nx, ny, 0.7, walls, -0.01, 0.02, gx=3e-6, gy=-1e-6)
+    rho, ux, uy = random_fields(nx, ny, 5, amp=0.01)
+    out = []
+    for variant in (0x80 | (1 << 18) | (1 << 19), 0x80 | (1 << 18)):
+        ctx = L.from_case(case, storage="fp16")
+        ctx.set_option(L.OPT_LATTICE_VARIANT, variant)
+        ctx.init_fields(rho, ux, uy)
+        ctx.step(60)
+        out.append(ctx.read_populations())
+    assert np.array_equal(out[0], out[1])
+
+
 def test_graph_replay_equals_direct_launches(L):
     case = _capsule_case(o.DYNAMIC)
     a = L.from_case(case, storage="fp64")
@@ -221,6 +238,25 @@ def test_graph_replay_equals_direct_launches(L):
     b.step(37, o.DYNAMIC)
     np.testing.assert_allclose(a.read_fields()[1], b.read_fields()[1], atol=1e-15)
     np.testing.assert_allclose(a.read_capsule(0)[0], b.read_capsule(0)[0], atol=1e-12)
+
+
+@pytest.mark.parametrize("scheme", [o.KINEMATIC, o.DYNAMIC])
+def test_overlapped_streams_equal_a_single_stream(L, scheme):
+    # the immersed-boundary kernels on their own stream (default) against every kernel on
+    # the context stream, with graphs and with direct launches
+    case = W.poiseuille_biconcave(nx=512, ny=128, count=12, seed=3, scheme=scheme, steps=1)
+    a = L.from_case(case, storage="fp64")
+    a.set_option(L.OPT_OVERLAP, 1)
+    b = L.from_case(case, storage="fp64")
+    b.set_option(L.OPT_OVERLAP, 0)
+    c = L.from_case(case, storage="fp64")
+    c.set_option(L.OPT_OVERLAP, 1)
+    c.set_option(L.OPT_GRAPHS, 0)
+    for ctx in (a, b, c):
+        ctx.step(45, scheme)
+    for ctx in (b, c):
+        np.testing.assert_allclose(ctx.read_populations(), a.read_populations(), rtol=0, atol=1e-13)
+        np.testing.assert_allclose(ctx.observables_all(), a.observables_all(), rtol=1e-12, atol=1e-13)
 
 
 def test_checkpoint_restart_matches_a_straight_run(L):
