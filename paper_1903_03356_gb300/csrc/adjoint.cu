@@ -723,31 +723,37 @@ __device__ P2<T> probe_traction(P2<T> X1, P2<T> X2, int s, int cx, int cy, const
 }
 
 // DR0: the spread force of step n-1 (and of step n at the first reverse step of a
-// segment) from the taped c_l F_l, and the MLS shapes at X^n.
+// segment) from the taped c_l F_l, and the MLS shapes. Shapes at X^n were computed by
+// the previous reverse step (as its X^{n-1}) except at a segment's first reverse step
+// (compute_n); shapes at X^{n-1} are computed here for this step's spread of fib^{n-1}
+// and kept for the next reverse step.
 __global__ void __launch_bounds__(128) k_adjd_spread(Lat L, Nodes nd, int max_n, const double2* Xn,
                                                      const double2* Xp, const double2* Flc_n,
                                                      const double2* Flc_p, double* fib_n, double* fib_p,
-                                                     Shape* shp) {
+                                                     Shape* shp_n, Shape* shp_p, bool compute_n) {
     const CapsuleParams P = nd.caps[blockIdx.x];
     if (P.n < 3 || P.n > max_n) return;
     const long long N = (long long)L.nx * L.ny;
     for (int v = threadIdx.x; v < P.n; v += blockDim.x) {
         const int g = P.off + v;
-        const Shape s = shape_with_derivatives(L, Xn[g].x, Xn[g].y);
-        shp[g] = s;
-        if (fib_n) {
-            const double2 F = Flc_n[g];
+        if (compute_n) {
+            const Shape s = shape_with_derivatives(L, Xn[g].x, Xn[g].y);
+            shp_n[g] = s;
+            if (fib_n) {
+                const double2 F = Flc_n[g];
 #pragma unroll
-            for (int b = 0; b < 3; b++)
+                for (int b = 0; b < 3; b++)
 #pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    const int cell = support_cell(L, s, a, b);
-                    atomicAdd(fib_n + cell, s.phi[b][a] * F.x);
-                    atomicAdd(fib_n + N + cell, s.phi[b][a] * F.y);
-                }
+                    for (int a = 0; a < 3; a++) {
+                        const int cell = support_cell(L, s, a, b);
+                        atomicAdd(fib_n + cell, s.phi[b][a] * F.x);
+                        atomicAdd(fib_n + N + cell, s.phi[b][a] * F.y);
+                    }
+            }
         }
         if (fib_p) {
             const Shape sp = shape_with_derivatives(L, Xp[g].x, Xp[g].y);
+            shp_p[g] = sp;
             const double2 F = Flc_p[g];
 #pragma unroll
             for (int b = 0; b < 3; b++)
@@ -1031,7 +1037,7 @@ struct AdjLayout {
     size_t pb = 0, ckpt = 0;
     size_t tape_pops = 0, tape_X = 0, tape_flc = 0, tape_fib0 = 0, age0 = 0, ckpts = 0, sbar[2]{}, fbar = 0,
            fib[3]{}, bbar[3]{}, xc = 0, xp = 0, xnew = 0, xb[2]{}, ub = 0, u1b = 0, u2b = 0, ftb = 0, fv = 0, shp = 0,
-           grad = 0, J = 0, total = 0;
+           shp1 = 0, grad = 0, J = 0, total = 0;
 };
 
 // The adjoint fields (population and force adjoints) are double in every storage mode:
@@ -1074,6 +1080,7 @@ AdjLayout adj_layout(const lbmib_ctx* c, long long T, int K) {
     a.xnew = take(M * sizeof(double2));
     a.fv = take(M * sizeof(double2));
     a.shp = take(M * sizeof(Shape));
+    a.shp1 = take(M * sizeof(Shape));   // Dynamic: shapes of the other step parity
     a.grad = take((2 * c->caps.size() + 2) * sizeof(double));
     a.J = take(sizeof(double));
     a.total = o;
@@ -1223,7 +1230,7 @@ lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* 
     const size_t smem = ring_smem_bytes(c->max_n);
     double* grad = (double*)(w + a.grad);
     auto r3 = [](long long n) { return (int)(((n % 3) + 3) % 3); };
-    Shape* shp = (Shape*)(w + a.shp);
+    Shape* shps[2] = {(Shape*)(w + a.shp), (Shape*)(w + a.shp1)};   // shapes at X^m in shps[m & 1]
     double* fbar = (double*)(w + a.fbar);
     double2* xm = (double2*)(w + a.xp);
     double2* ub = (double2*)(w + a.ub);
@@ -1245,10 +1252,12 @@ lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* 
         double* sb_out = (double*)(w + a.sbar[par]);
         double2* xc = (double2*)(w + a.xb[1 - par]);
         double2* xout = (double2*)(w + a.xb[par]);
+        Shape* shp = shps[par];
         if (ncaps > 0) {
             k_adjd_spread<<<ncaps, 128, 0, s>>>(L, c->nd, c->max_n, Xn, k > 0 ? Xn - M : nullptr,
                                                 flc + (size_t)k * M, k > 0 ? flc + (size_t)(k - 1) * M : nullptr,
-                                                k == len - 1 ? fib_n : nullptr, k > 0 ? fib_p : nullptr, shp);
+                                                k == len - 1 ? fib_n : nullptr, k > 0 ? fib_p : nullptr, shp,
+                                                shps[1 - par], k == len - 1);
             k_adjd_update<<<ncaps, 128, smem, s>>>(c->nd, c->max_n, Xn, xc, xm, ub, xout, u2b,
                                                    (double2*)(w + a.ftb), ncaps, grad);
             k_adjd_tract<S><<<nblk(2LL * count, 32), 32, 0, s>>>(L, c->nd, count, Xn, post1, fib_n,

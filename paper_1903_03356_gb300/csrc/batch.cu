@@ -44,6 +44,75 @@ struct BatchDev {
     int ncases;
 };
 
+// Two adjacent stored values (x, x + 1; x even, so the pair is aligned) as the compute
+// type. Plain loads and stores: the CTA rewrites its case's populations every step.
+template <typename S>
+__device__ __forceinline__ void ld_pair(const S* p, const Lat& L, typename St<S>::C& a, typename St<S>::C& b) {
+    if constexpr (sizeof(S) == 8) {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        a = v.x;
+        b = v.y;
+    } else if constexpr (sizeof(S) == 4) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        a = v.x;
+        b = v.y;
+    } else {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+        a = v.x * L.inv_scale;
+        b = v.y * L.inv_scale;
+    }
+}
+template <typename S>
+__device__ __forceinline__ void st_pair(S* p, const Lat& L, typename St<S>::C a, typename St<S>::C b) {
+    if constexpr (sizeof(S) == 8) {
+        *reinterpret_cast<double2*>(p) = make_double2(a, b);
+    } else if constexpr (sizeof(S) == 4) {
+        *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    } else {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a * L.scale, b * L.scale);
+    }
+}
+
+// Pre-collision populations of the node pair (x, x + 1) of row y, x even (Eq. 1, left
+// side): one pair load per population, plus one scalar for the populations shifted in x
+// (the value across the pair's edge), all issued before any is used.
+template <typename S>
+__device__ __forceinline__ void pull_pair(const S* __restrict__ src, const Lat& L, int x, int y,
+                                          typename St<S>::C (&s0)[9], typename St<S>::C (&s1)[9]) {
+    using C = typename St<S>::C;
+    const int xm = x == 0 ? L.nx - 1 : x - 1, xp2 = x + 2 >= L.nx ? x + 2 - L.nx : x + 2;
+    const int ym = y == 0 ? L.ny - 1 : y - 1, yp = y + 1 == L.ny ? 0 : y + 1;
+    const bool lo = L.walls && y == 0, hi = L.walls && y == L.ny - 1;
+    C e[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const bool bounce = (ey(i) > 0 && lo) || (ey(i) < 0 && hi);
+        const int sy = bounce ? y : (ey(i) > 0 ? ym : (ey(i) < 0 ? yp : y));
+        const S* row = src + (long long)(bounce ? opp(i) : i) * L.plane + (long long)sy * L.pitch;
+        ld_pair<S>(row + x, L, s0[i], s1[i]);
+        e[i] = C(0);
+        if (!bounce && ex(i) == 1) e[i] = St<S>::ldc(row + xm, L);
+        if (!bounce && ex(i) == -1) e[i] = St<S>::ldc(row + xp2, L);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const bool bounce = (ey(i) > 0 && lo) || (ey(i) < 0 && hi);
+        if (bounce) {
+            const int j = opp(i);
+            const C uw = ey(i) > 0 ? lat_c<C>(L.ub, L.ubf) : lat_c<C>(L.ut, L.utf);
+            const C corr = C(6) * wgt<C>(j) * C(ex(j)) * uw;
+            s0[i] -= corr;
+            s1[i] -= corr;
+        } else if (ex(i) == 1) {      // values at x - 1, x
+            s1[i] = s0[i];
+            s0[i] = e[i];
+        } else if (ex(i) == -1) {     // values at x + 1, x + 2
+            s0[i] = s1[i];
+            s1[i] = e[i];
+        }
+    }
+}
+
 // Force-tile value at lattice node (x, y), or zero when the node is outside the tile.
 // (x0w, y0w): tile origin wrapped into the lattice (y0w unwrapped between walls).
 template <typename C>
@@ -129,6 +198,32 @@ __device__ void run_case(const BatchDev& d, int c, int nsteps, const CapSmem& sm
         {
             const int x0w = t.use ? wrapi(t.x0, L.nx) : 0;
             const int y0w = t.use ? (L.walls ? t.y0 : wrapi(t.y0, L.ny)) : 0;
+            if ((L.nx & 1) == 0) {
+                // node pairs (x, x + 1), x even: walk pair tid, tid + B, ... by carries
+                const int np = L.nx >> 1;
+                const int dq = (int)blockDim.x / np, dr = (int)blockDim.x - dq * np;
+                int y = (int)threadIdx.x / np, xp = (int)threadIdx.x - y * np;
+                while (y < L.ny) {
+                    const int x = 2 * xp;
+                    C s0[9], s1[9];
+                    pull_pair<S>(src, L, x, y, s0, s1);
+                    C fx0, fy0, fx1, fy1;
+                    tile_force<C>(t, L, x0w, y0w, x, y, fx0, fy0);
+                    tile_force<C>(t, L, x0w, y0w, x + 1, y, fx1, fy1);
+                    const C u0 = collide<C>(s0, gx + fx0, gy + fy0, om);
+                    const C u1 = collide<C>(s1, gx + fx1, gy + fy1, om);
+                    stable &= u0 < C(0.09) && u1 < C(0.09);
+                    S* o = dst + (long long)y * L.pitch + x;
+#pragma unroll
+                    for (int i = 0; i < 9; i++) st_pair<S>(o + (long long)i * L.plane, L, s0[i], s1[i]);
+                    xp += dr;
+                    y += dq;
+                    if (xp >= np) {
+                        xp -= np;
+                        y++;
+                    }
+                }
+            } else {
             const int dq = (int)blockDim.x / L.nx, dr = (int)blockDim.x - dq * L.nx;
             int y = (int)threadIdx.x / L.nx, x = (int)threadIdx.x - y * L.nx;
             while (y < L.ny) {
@@ -147,6 +242,7 @@ __device__ void run_case(const BatchDev& d, int c, int nsteps, const CapSmem& sm
                     x -= L.nx;
                     y++;
                 }
+            }
             }
         }
         __syncthreads();  // the block's global stores are visible to the block after the barrier
