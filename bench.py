@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--adjoint-steps", type=int, default=800, help="horizon T of the adjoint measurement")
     p.add_argument("--batch-autotune", type=int, default=20,
                    help="steps per candidate launch shape of the batch autotuner (0: default shape)")
-    p.add_argument("--only", default="all", choices=["all", "batched", "adjoint"],
+    p.add_argument("--only", default="all", choices=["all", "batched", "adjoint", "precision"],
                    help="batched / adjoint: run only that measurement and print its JSON object")
     return p.parse_args()
 
@@ -276,6 +276,7 @@ def run_gpu(a):
         line["e2e"] = e2e_run(a, case, L, scheme, dev)
     if rank == 0 and not a.no_extras:
         ctx.close()
+        line["precision"] = precision_run(L, dev)
         line["batched"] = batched_run(L, a.batch_steps, a.batch_autotune)
         line["adjoint"] = {"dynamic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=1),
                            "kinematic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=0)}
@@ -284,6 +285,55 @@ def run_gpu(a):
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
+
+
+# FP64 instructions (DADD + DMUL + DFMA, thread level) per lattice update of the FP64
+# lattice kernel, from one ncu count (profiles/k_collide_stream_fp64_alu.md); GB300 issues
+# 2 such instructions per SM per cycle (ncu peak_sustained of the DFMA counter).
+FP64_INSTR_PER_UPDATE = 145.5
+FP64_INSTR_PER_SM_CYCLE = 2
+SM_COUNT = 152
+
+
+def precision_run(L, dev, steps=(12, 60)):
+    """Lattice update alone on the 16384 x 8192 lattice with FP64 and FP16 storage:
+    FP16 against the HBM roofline (36 B per update), FP64 against the FP64 ALU roofline
+    (measured instructions per update x updates/s against 2 per SM per cycle at the
+    sampled clock)."""
+    import torch
+
+    out = {}
+    for storage, n in (("fp64", steps[0]), ("fp16", steps[1])):
+        case = W.Case("lattice", 16384, 8192, 0.7, True, gx=W.poiseuille_force(0.7, 0.02, 8192), init="parabola")
+        ctx = L.from_case(case, storage=storage)
+        ctx.set_option(L.OPT_TIMING, 1)
+        ctx.step(2)
+        ctx.sync()
+        ctx.kernel_time(reset=True)
+        with Clocks(dev) as clk:
+            ctx.step(n)
+            ctx.sync()
+        ms, launches = ctx.kernel_time(reset=True)
+        per = ms / max(1, launches)
+        nodes = 16384 * 8192
+        gl = nodes / (per / 1e3) / 1e9
+        r = {"kernel_ms": per, "glups": gl, "bytes_per_update": ctx.bytes_per_update, "clocks": clk.summary()}
+        if storage == "fp16":
+            hbm, src = peaks()
+            achieved = ctx.bytes_per_update * nodes / (per / 1e3) / 1e9
+            r["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                             "frac": achieved / hbm, "peak_source": src}
+        else:
+            mhz = clk.summary().get("sm_mhz") or 2070.0
+            peak = FP64_INSTR_PER_SM_CYCLE * SM_COUNT * mhz * 1e6 / 1e9   # G instr/s
+            r["roofline"] = {"bound": "alu", "unit": "G FP64 instr/s", "peak": peak,
+                             "peak_source": "2 FP64 instructions per SM per cycle x 152 SMs x sampled SM clock",
+                             "achieved": (FP64_INSTR_PER_UPDATE * gl if FP64_INSTR_PER_UPDATE else None)}
+            if FP64_INSTR_PER_UPDATE:
+                r["roofline"]["frac"] = r["roofline"]["achieved"] / peak
+        out[storage] = r
+        ctx.close()
+    return out
 
 
 def batched_run(L, steps, autotune=20):
@@ -432,6 +482,7 @@ def main():
         from paper_1903_03356_gb300 import lbmib as L
 
         out = (batched_run(L, a.batch_steps, a.batch_autotune) if a.only == "batched"
+               else precision_run(L, int(os.environ.get("LOCAL_RANK", "0"))) if a.only == "precision"
                else {"dynamic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=1),
                      "kinematic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=0)})
         print(json.dumps(out), flush=True)

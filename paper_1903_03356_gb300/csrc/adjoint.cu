@@ -30,6 +30,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "ctx.cuh"
@@ -70,63 +71,81 @@ __device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ double dexp(double a) { return exp(a); }
 
 // A value with its derivatives along four directions at once (one pass instead of four
-// when the value parts, exponentials included, would be the same in each).
-struct Dual4 {
-    double v, d[4];
+// when the value parts, exponentials included, would be the same in each), in the real
+// type R (float for single-precision storage, double otherwise).
+template <typename R>
+struct D4 {
+    R v, d[4];
 };
-__device__ __forceinline__ Dual4 d4(double v) { return Dual4{v, {0.0, 0.0, 0.0, 0.0}}; }
-__device__ __forceinline__ Dual4 operator+(Dual4 a, Dual4 b) {
-    Dual4 r{a.v + b.v, {}};
+template <typename R>
+__device__ __forceinline__ D4<R> d4(R v) { return D4<R>{v, {R(0), R(0), R(0), R(0)}}; }
+template <typename R>
+__device__ __forceinline__ D4<R> operator+(D4<R> a, D4<R> b) {
+    D4<R> r{a.v + b.v, {}};
 #pragma unroll
     for (int k = 0; k < 4; k++) r.d[k] = a.d[k] + b.d[k];
     return r;
 }
-__device__ __forceinline__ Dual4 operator-(Dual4 a, Dual4 b) {
-    Dual4 r{a.v - b.v, {}};
+template <typename R>
+__device__ __forceinline__ D4<R> operator-(D4<R> a, D4<R> b) {
+    D4<R> r{a.v - b.v, {}};
 #pragma unroll
     for (int k = 0; k < 4; k++) r.d[k] = a.d[k] - b.d[k];
     return r;
 }
-__device__ __forceinline__ Dual4 operator-(Dual4 a) {
-    Dual4 r{-a.v, {}};
+template <typename R>
+__device__ __forceinline__ D4<R> operator-(D4<R> a) {
+    D4<R> r{-a.v, {}};
 #pragma unroll
     for (int k = 0; k < 4; k++) r.d[k] = -a.d[k];
     return r;
 }
-__device__ __forceinline__ Dual4 operator*(Dual4 a, Dual4 b) {
-    Dual4 r{a.v * b.v, {}};
+template <typename R>
+__device__ __forceinline__ D4<R> operator*(D4<R> a, D4<R> b) {
+    D4<R> r{a.v * b.v, {}};
 #pragma unroll
     for (int k = 0; k < 4; k++) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
     return r;
 }
-__device__ __forceinline__ Dual4 operator/(Dual4 a, Dual4 b) {
-    const double q = a.v / b.v, ib = 1.0 / b.v;
-    Dual4 r{q, {}};
+template <typename R>
+__device__ __forceinline__ D4<R> operator/(D4<R> a, D4<R> b) {
+    const R q = a.v / b.v, ib = R(1) / b.v;
+    D4<R> r{q, {}};
 #pragma unroll
     for (int k = 0; k < 4; k++) r.d[k] = (a.d[k] - q * b.d[k]) * ib;
     return r;
 }
-__device__ __forceinline__ Dual4 operator*(double s, Dual4 a) {
-    Dual4 r{s * a.v, {}};
+template <typename R>
+__device__ __forceinline__ D4<R> operator*(R s, D4<R> a) {
+    D4<R> r{s * a.v, {}};
 #pragma unroll
     for (int k = 0; k < 4; k++) r.d[k] = s * a.d[k];
     return r;
 }
-__device__ __forceinline__ Dual4 operator+(Dual4 a, double s) { a.v += s; return a; }
-__device__ __forceinline__ Dual4 dsqrt(Dual4 a) {
-    const double r = sqrt(a.v), h = 0.5 / r;
-    Dual4 o{r, {}};
+template <typename R>
+__device__ __forceinline__ D4<R> operator+(D4<R> a, R s) { a.v += s; return a; }
+template <typename R>
+__device__ __forceinline__ D4<R> dsqrt(D4<R> a) {
+    const R r = sqrt(a.v), h = R(0.5) / r;
+    D4<R> o{r, {}};
 #pragma unroll
     for (int k = 0; k < 4; k++) o.d[k] = a.d[k] * h;
     return o;
 }
-__device__ __forceinline__ Dual4 dexp(Dual4 a) {
-    const double e = exp(a.v);
-    Dual4 o{e, {}};
+template <typename R>
+__device__ __forceinline__ D4<R> dexp(D4<R> a) {
+    const R e = exp(a.v);
+    D4<R> o{e, {}};
 #pragma unroll
     for (int k = 0; k < 4; k++) o.d[k] = e * a.d[k];
     return o;
 }
+__device__ __forceinline__ float dexp(float a) { return expf(a); }
+
+// Real type underlying a scalar type (for constants in templated arithmetic).
+template <typename T> struct RealOf { using type = T; };
+template <typename R> struct RealOf<D4<R>> { using type = R; };
+template <> struct RealOf<Dual> { using type = double; };
 
 template <typename T>
 struct P2 {
@@ -154,17 +173,18 @@ struct Axis {
 
 template <typename T>
 __device__ Axis<T> mls_axis(T d0) {
+    using R = typename RealOf<T>::type;
     T w[3], d[3];
-    T s0 = T{0.0}, s1 = T{0.0};
+    T s0 = T{R(0)}, s1 = T{R(0)};
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        d[a] = d0 + double(a - 1);
-        w[a] = dexp(-kMlsInvLen2 * (d[a] * d[a]));
+        d[a] = d0 + R(a - 1);
+        w[a] = dexp(R(-kMlsInvLen2) * (d[a] * d[a]));
         s0 = s0 + w[a];
         s1 = s1 + w[a] * d[a];
     }
     const T m = s1 / s0;
-    T V = T{0.0};
+    T V = T{R(0)};
 #pragma unroll
     for (int a = 0; a < 3; a++) V = V + w[a] * ((d[a] - m) * (d[a] - m));
     Axis<T> r;
@@ -671,13 +691,13 @@ struct ProbeVal {
     T rho, G[2][2];   // G[a][b] = d u_a / d x_b
 };
 
-template <typename T>
-__device__ ProbeVal<T> probe_eval(T Px, T Py, int cx, int cy, const double* drho, const double* ux,
-                                  const double* uy) {
-    const Axis<T> ax = mls_axis<T>(T{(double)cx} - Px), ay = mls_axis<T>(T{(double)cy} - Py);
+template <typename T, typename F>
+__device__ ProbeVal<T> probe_eval(T d0x, T d0y, const F* drho, const F* ux, const F* uy) {
+    using R = typename RealOf<T>::type;
+    const Axis<T> ax = mls_axis<T>(d0x), ay = mls_axis<T>(d0y);
     ProbeVal<T> o;
-    o.rho = T{1.0};
-    o.G[0][0] = o.G[0][1] = o.G[1][0] = o.G[1][1] = T{0.0};
+    o.rho = T{R(1)};
+    o.G[0][0] = o.G[0][1] = o.G[1][0] = o.G[1][1] = T{R(0)};
 #pragma unroll
     for (int b = 0; b < 3; b++)
 #pragma unroll
@@ -685,11 +705,11 @@ __device__ ProbeVal<T> probe_eval(T Px, T Py, int cx, int cy, const double* drho
             const int k = 3 * b + a;
             const T phi = ax.h[a] * ay.q[b] + ax.q[a] * ay.h[b] - ax.q[a] * ay.q[b];
             const T gx = ax.g[a] * ay.q[b], gy = ax.q[a] * ay.g[b];
-            o.rho = o.rho + drho[k] * phi;
-            o.G[0][0] = o.G[0][0] + ux[k] * gx;
-            o.G[0][1] = o.G[0][1] + ux[k] * gy;
-            o.G[1][0] = o.G[1][0] + uy[k] * gx;
-            o.G[1][1] = o.G[1][1] + uy[k] * gy;
+            o.rho = o.rho + R(drho[k]) * phi;
+            o.G[0][0] = o.G[0][0] + R(ux[k]) * gx;
+            o.G[0][1] = o.G[0][1] + R(ux[k]) * gy;
+            o.G[1][0] = o.G[1][0] + R(uy[k]) * gx;
+            o.G[1][1] = o.G[1][1] + R(uy[k]) * gy;
         }
     return o;
 }
@@ -698,28 +718,31 @@ __device__ ProbeVal<T> probe_eval(T Px, T Py, int cx, int cy, const double* drho
 // at the centroid + 1.2 n; 1: inner, at - 1.2 n), with n = (dy, -dx)/l the outward normal
 // of a counter-clockwise ring, p = rho/3 and tau = rho nu (G + G^T):
 //   F = l (-(p+ - p-) n + (tau+ - tau-) n) = T_0 - T_1,  T_s = l (-p_s n + tau_s n).
-// Returns (+/-) T_s for fields sampled at the probe's support (centre fixed); any
+// Returns (+/-) T_s for fields sampled at the probe's support; the end points are given
+// relative to the support's centre node (so single precision keeps their digits). Any
 // scalar type.
-template <typename T>
-__device__ P2<T> probe_traction(P2<T> X1, P2<T> X2, int s, int cx, int cy, const double* drho, const double* ux,
-                                const double* uy, double nu) {
+template <typename T, typename F>
+__device__ P2<T> probe_traction(P2<T> X1, P2<T> X2, int s, const F* drho, const F* ux, const F* uy,
+                                typename RealOf<T>::type nu) {
+    using R = typename RealOf<T>::type;
     const P2<T> d = X2 - X1;
     const T len = dsqrt(d.x * d.x + d.y * d.y);
     const P2<T> nn{d.y / len, -(d.x / len)};
-    const double sg = s == 0 ? 1.2 : -1.2;
-    const ProbeVal<T> o = probe_eval<T>(0.5 * (X1.x + X2.x) + sg * nn.x, 0.5 * (X1.y + X2.y) + sg * nn.y, cx, cy,
-                                        drho, ux, uy);
-    const T p = (1.0 / 3.0) * o.rho;
+    const R sg = s == 0 ? R(1.2) : R(-1.2);
+    // support offsets from the probe: centre - P = -(C + sg n) in these coordinates
+    const ProbeVal<T> o = probe_eval<T, F>(-(R(0.5) * (X1.x + X2.x) + sg * nn.x),
+                                           -(R(0.5) * (X1.y + X2.y) + sg * nn.y), drho, ux, uy);
+    const T p = R(1.0 / 3.0) * o.rho;
     const T n_[2] = {nn.x, nn.y};
-    T F[2];
+    T Fo[2];
 #pragma unroll
     for (int a = 0; a < 2; a++) {
         T t = -(p * n_[a]);
 #pragma unroll
         for (int b = 0; b < 2; b++) t = t + nu * (o.rho * (o.G[a][b] + o.G[b][a])) * n_[b];
-        F[a] = (s == 0 ? 1.0 : -1.0) * (len * t);
+        Fo[a] = (s == 0 ? R(1) : R(-1)) * (len * t);
     }
-    return P2<T>{F[0], F[1]};
+    return P2<T>{Fo[0], Fo[1]};
 }
 
 // DR0: the spread force of step n-1 (and of step n at the first reverse step of a
@@ -844,6 +867,8 @@ __global__ void __launch_bounds__(32) k_adjd_tract(Lat L, Nodes nd, int count, c
                                                    const S* __restrict__ post1, const double* __restrict__ fib,
                                                    const double2* ftb, double2* xout, double* sbar, double* bbar,
                                                    double* grad_g, unsigned* status) {
+    // the traction adjoint computes in single precision for single-precision storage
+    using R = typename std::conditional<sizeof(S) == 8, double, float>::type;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int g1 = t >> 1, s = t & 1;
     double gsx = 0.0, gsy = 0.0;
@@ -854,14 +879,13 @@ __global__ void __launch_bounds__(32) k_adjd_tract(Lat L, Nodes nd, int count, c
         const int g2 = P.off + (v + 1 == P.n ? 0 : v + 1);
         const double2 X1 = Xn[g1], X2 = Xn[g2];
         const double2 f1 = ftb[g1], f2 = ftb[g2];
-        const double Fb[2] = {0.5 * (f1.x + f2.x), 0.5 * (f1.y + f2.y)};
+        const R Fb[2] = {R(0.5 * (f1.x + f2.x)), R(0.5 * (f1.y + f2.y))};
         const double dx = X2.x - X1.x, dy = X2.y - X1.y, len = sqrt(dx * dx + dy * dy);
-        const double nn[2] = {dy / len, -dx / len};
         const double sg = s == 0 ? 1.2 : -1.2, sgn = s == 0 ? 1.0 : -1.0;
-        double Px = 0.5 * (X1.x + X2.x) + sg * nn[0], Py = 0.5 * (X1.y + X2.y) + sg * nn[1];
+        double Px = 0.5 * (X1.x + X2.x) + sg * dy / len, Py = 0.5 * (X1.y + X2.y) - sg * dx / len;
         int cx, cy;
         ok = support_centre(L, Px, Py, cx, cy);
-        double drho[9], ux[9], uy[9];
+        R drho[9], ux[9], uy[9];
         long long cells[9];
 #pragma unroll
         for (int b = 0; b < 3; b++)
@@ -870,40 +894,50 @@ __global__ void __launch_bounds__(32) k_adjd_tract(Lat L, Nodes nd, int count, c
                 const int k = 3 * b + a;
                 const int xk = wrapi(cx + a - 1, L.nx), yk = support_row(L, cy + b - 1);
                 cells[k] = (long long)yk * L.nx + xk;
-                node_fields<S>(post1, L, fib, xk, yk, drho[k], ux[k], uy[k]);
+                double dr, u, w;
+                node_fields<S>(post1, L, fib, xk, yk, dr, u, w);
+                drho[k] = R(dr);
+                ux[k] = R(u);
+                uy[k] = R(w);
             }
+        // end points relative to the support's centre node
+        const R r1x = R(X1.x - cx), r1y = R(X1.y - cy), r2x = R(X2.x - cx), r2y = R(X2.y - cy);
         // positions: derivatives along the four end coordinates, in one pass
-        Dual4 c1x = d4(X1.x), c1y = d4(X1.y), c2x = d4(X2.x), c2y = d4(X2.y);
-        c1x.d[0] = c1y.d[1] = c2x.d[2] = c2y.d[3] = 1.0;
-        const P2<Dual4> F = probe_traction<Dual4>(P2<Dual4>{c1x, c1y}, P2<Dual4>{c2x, c2y}, s, cx, cy, drho, ux, uy,
-                                                  L.nu);
+        D4<R> c1x = d4<R>(r1x), c1y = d4<R>(r1y), c2x = d4<R>(r2x), c2y = d4<R>(r2y);
+        c1x.d[0] = c1y.d[1] = c2x.d[2] = c2y.d[3] = R(1);
+        const P2<D4<R>> F = probe_traction<D4<R>, R>(P2<D4<R>>{c1x, c1y}, P2<D4<R>>{c2x, c2y}, s, drho, ux, uy,
+                                                     R(L.nu));
         double e[4];
 #pragma unroll
-        for (int j = 0; j < 4; j++) e[j] = Fb[0] * F.x.d[j] + Fb[1] * F.y.d[j];
+        for (int j = 0; j < 4; j++) e[j] = (double)(Fb[0] * F.x.d[j] + Fb[1] * F.y.d[j]);
         atomicAdd(&xout[g1].x, e[0]);
         atomicAdd(&xout[g1].y, e[1]);
         atomicAdd(&xout[g2].x, e[2]);
         atomicAdd(&xout[g2].y, e[3]);
         // fields: dT/drho and dT/dG contracted with F_l-bar
-        const ProbeVal<double> o = probe_eval<double>(Px, Py, cx, cy, drho, ux, uy);
-        double rho_b = 0.0, Gb[2][2];
+        const R nn[2] = {R(dy / len), R(-dx / len)};
+        const R d0x = R(cx - Px), d0y = R(cy - Py);
+        const ProbeVal<R> o = probe_eval<R, R>(d0x, d0y, drho, ux, uy);
+        const R lsg = R(sgn * len), nu = R(L.nu);
+        R rho_b = R(0), Gb[2][2];
         for (int a = 0; a < 2; a++) {
-            double tt = -nn[a] / 3.0;
-            for (int b = 0; b < 2; b++) tt += L.nu * (o.G[a][b] + o.G[b][a]) * nn[b];
-            rho_b += Fb[a] * sgn * len * tt;
+            R tt = -nn[a] / R(3);
+            for (int b = 0; b < 2; b++) tt += nu * (o.G[a][b] + o.G[b][a]) * nn[b];
+            rho_b += Fb[a] * lsg * tt;
         }
         for (int a = 0; a < 2; a++)
-            for (int b = 0; b < 2; b++) Gb[a][b] = sgn * len * o.rho * L.nu * (Fb[a] * nn[b] + Fb[b] * nn[a]);
-        const Axis<double> ax = mls_axis<double>((double)cx - Px), ay = mls_axis<double>((double)cy - Py);
+            for (int b = 0; b < 2; b++) Gb[a][b] = lsg * o.rho * nu * (Fb[a] * nn[b] + Fb[b] * nn[a]);
+        const Axis<R> ax = mls_axis<R>(d0x), ay = mls_axis<R>(d0y);
 #pragma unroll
         for (int b = 0; b < 3; b++)
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 const int k = 3 * b + a;
-                const double phi = ax.h[a] * ay.q[b] + ax.q[a] * ay.h[b] - ax.q[a] * ay.q[b];
-                const double gx = ax.g[a] * ay.q[b], gy = ax.q[a] * ay.g[b];
-                inject_fields(L, cells[k], phi * rho_b, Gb[0][0] * gx + Gb[0][1] * gy, Gb[1][0] * gx + Gb[1][1] * gy,
-                              ux[k], uy[k], 1.0 + drho[k], sbar, bbar, gsx, gsy);
+                const R phi = ax.h[a] * ay.q[b] + ax.q[a] * ay.h[b] - ax.q[a] * ay.q[b];
+                const R gx = ax.g[a] * ay.q[b], gy = ax.q[a] * ay.g[b];
+                inject_fields(L, cells[k], (double)(phi * rho_b), (double)(Gb[0][0] * gx + Gb[0][1] * gy),
+                              (double)(Gb[1][0] * gx + Gb[1][1] * gy), (double)ux[k], (double)uy[k],
+                              1.0 + (double)drho[k], sbar, bbar, gsx, gsy);
             }
     }
     for (int o = 16; o > 0; o >>= 1) {
