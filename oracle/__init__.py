@@ -108,6 +108,11 @@ def _declare(L):
         "orc_sim_read_capsule": (C.c_int, [vp, C.c_int, vp, vp, vp, vp]),
         "orc_sim_observables": (C.c_int, [vp, C.c_int, _dp]),
         "orc_sim_step_count": (C.c_longlong, [vp]),
+        "orc_vertex_normal": (None, [_dp, C.c_int, C.c_int, _dp]),
+        "orc_repulsion": (None, [C.POINTER(C.POINTER(C.c_double)), _ip, C.c_int, C.c_double, C.c_double,
+                                 C.c_double, C.c_double, C.POINTER(C.POINTER(C.c_double))]),
+        "orc_sim_set_repulsion": (None, [vp, C.c_double, C.c_double]),
+        "orc_sim_read_repulsion": (C.c_int, [vp, C.c_int, _dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -254,6 +259,31 @@ KINEMATIC = 0
 DYNAMIC = 1
 
 
+# Eq. 27 coefficient: 1e-4 / (8 sqrt 2) with dx = 1
+REPULSION_COEFF = 1e-4 / (8.0 * np.sqrt(2.0))
+
+
+def vertex_normal(xy: np.ndarray, v: int) -> np.ndarray:
+    """Outward unit normal at vertex v of a counter-clockwise ring (reading R24)."""
+    xy = _f64(xy); out = np.zeros(2)
+    lib().orc_vertex_normal(xy, xy.size // 2, v, out)
+    return out
+
+
+def repulsion(rings, rc: float, coeff: float = REPULSION_COEFF, px: float = 0.0, py: float = 0.0):
+    """Eq. 27 forces on every vertex of every ring (list of (n, 2) arrays); periods px,
+    py (0: none) for minimum-image distances. Returns a list of (n, 2) arrays."""
+    rings = [_f64(r).reshape(-1) for r in rings]
+    k = len(rings)
+    out = [np.zeros_like(r) for r in rings]
+    dpp = C.POINTER(C.c_double)
+    Xp = (dpp * k)(*[r.ctypes.data_as(dpp) for r in rings])
+    Fp = (dpp * k)(*[f.ctypes.data_as(dpp) for f in out])
+    n = np.array([r.size // 2 for r in rings], dtype=np.int32)
+    lib().orc_repulsion(Xp, n, k, rc, coeff, px, py, Fp)
+    return [f.reshape(-1, 2) for f in out]
+
+
 class Sim:
     """Lattice plus capsules stepped with the Kinematic (Section 2.4) or Dynamic
     (Section 2.3) scheme."""
@@ -319,6 +349,15 @@ class Sim:
         xy = np.zeros(2 * n); vel = np.zeros(2 * n); fi = np.zeros(2 * n); fe = np.zeros(2 * n)
         lib().orc_sim_read_capsule(self._h, cid, _ptr(xy), _ptr(vel), _ptr(fi), _ptr(fe))
         return xy, vel, fi, fe
+
+    def set_repulsion(self, rc: float, coeff: float = REPULSION_COEFF):
+        """Capsule-capsule repulsion (Eq. 27) with cut-off rc (0: off)."""
+        lib().orc_sim_set_repulsion(self._h, rc, coeff)
+
+    def read_repulsion(self, cid: int) -> np.ndarray:
+        out = np.zeros(2 * self._n[cid])
+        lib().orc_sim_read_repulsion(self._h, cid, out)
+        return out
 
     def observables(self, cid: int) -> np.ndarray:
         """(area, perimeter, D, xc, yc, Sw, inclination, delta_p)."""

@@ -38,6 +38,12 @@
  *   R11 Eq. 23: xdot_0 is interpolated after the fluid update, at X^n.
  *   R12 viscous stress tau = rho nu (grad u + grad u^T), pressure p = rho / 3.
  *   R15 Taylor D from the eigenvalues of the polygon's area second-moment tensor.
+ *   R23 Capsule-capsule repulsion (Section 3.4, Eq. 27): a vertex feels every vertex of
+ *       every other ring closer than a cut-off r_c (the paper gives the force law and
+ *       that it holds the separation near dx, but no range); x (and y without walls)
+ *       distances are minimum images on the periodic lattice.
+ *   R24 The normal at a vertex is the normalised sum of the outward unit normals
+ *       (dy, -dx)/l of the two elements meeting there; Eq. 27 acts along its negative.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -475,13 +481,62 @@ void orc_dynamic_advance(int n2, const double* X, const double* Xm1, const doubl
 }
 
 /* ---------------------------------------------------------------------------------- */
+/* Capsule-capsule repulsion (Section 3.4, Eq. 27; readings R23, R24).                   */
+/* ---------------------------------------------------------------------------------- */
+/* Outward unit normal at vertex v of a counter-clockwise ring of n vertices: the
+ * normalised sum of the outward normals (dy, -dx)/l of elements v-1 and v. */
+void orc_vertex_normal(const double* X, int n, int v, double out[2]) {
+    int vl = (v + n - 1) % n, vr = (v + 1) % n;
+    double ax = X[2 * v] - X[2 * vl], ay = X[2 * v + 1] - X[2 * vl + 1];
+    double bx = X[2 * vr] - X[2 * v], by = X[2 * vr + 1] - X[2 * v + 1];
+    double la = hypot(ax, ay), lb = hypot(bx, by);
+    double nx = ay / la + by / lb, ny = -ax / la - bx / lb;
+    double ln = hypot(nx, ny);
+    out[0] = nx / ln;
+    out[1] = ny / ln;
+}
+
+/* Minimum-image difference a - b along an axis of period P (P = 0: not periodic). */
+static double min_image(double d, double P) {
+    if (P > 0.0) d -= P * floor(d / P + 0.5);
+    return d;
+}
+
+/* F[c] (2 n_c doubles each, overwritten): on every vertex 1 of ring c, from every vertex
+ * 2 of every other ring at distance d < rc, coeff * sqrt(dx / d^5) along the inward
+ * normal at vertex 1 (Eq. 27 with coeff = 1e-4 / (8 sqrt 2) and dx = 1 lattice unit).
+ * Periods px, py (0: none) for minimum-image distances. */
+void orc_repulsion(const double* const* X, const int* n, int ncaps, double rc, double coeff, double px,
+                   double py, double* const* F) {
+    for (int a = 0; a < ncaps; a++) {
+        for (int v = 0; v < n[a]; v++) {
+            double nrm[2];
+            orc_vertex_normal(X[a], n[a], v, nrm);
+            double f = 0.0;
+            for (int b = 0; b < ncaps; b++) {
+                if (b == a) continue;
+                for (int w = 0; w < n[b]; w++) {
+                    double dx = min_image(X[a][2 * v] - X[b][2 * w], px);
+                    double dy = min_image(X[a][2 * v + 1] - X[b][2 * w + 1], py);
+                    double d = sqrt(dx * dx + dy * dy);
+                    if (d < rc) f += coeff * sqrt(1.0 / (d * d * d * d * d));
+                }
+            }
+            F[a][2 * v] = -f * nrm[0];
+            F[a][2 * v + 1] = -f * nrm[1];
+        }
+    }
+}
+
+
+/* ---------------------------------------------------------------------------------- */
 /* Simulation: lattice + capsules, stepped with the Kinematic (Section 2.4, steps i-viii)*/
 /* or Dynamic (Section 2.3, steps 1-8) scheme.                                          */
 /* ---------------------------------------------------------------------------------- */
 typedef struct {
     int n;
     double ks, kb, ka, m;
-    double *X, *Xm1, *uv, *Fint, *Fext, *L0, *th0;
+    double *X, *Xm1, *uv, *Fint, *Fext, *Fpp, *L0, *th0;
     double A0, P0;
     int age;
 } orc_capsule;
@@ -493,7 +548,33 @@ typedef struct {
     orc_capsule* caps;
     long long step;
     int status;
+    double rep_rc, rep_c;   /* repulsion cut-off (0: off) and coefficient of Eq. 27 */
 } orc_sim;
+
+/* Repulsion forces of all capsules of a simulation at their current positions. */
+static void sim_repulsion(orc_sim* s) {
+    if (s->rep_rc <= 0.0 || s->ncaps < 2) {
+        for (int c = 0; c < s->ncaps; c++) memset(s->caps[c].Fpp, 0, 2 * s->caps[c].n * sizeof(double));
+        return;
+    }
+    const double** X = (const double**)malloc(s->ncaps * sizeof(double*));
+    int* n = (int*)malloc(s->ncaps * sizeof(int));
+    double** F = (double**)malloc(s->ncaps * sizeof(double*));
+    for (int c = 0; c < s->ncaps; c++) {
+        X[c] = s->caps[c].X;
+        n[c] = s->caps[c].n;
+        F[c] = s->caps[c].Fpp;
+    }
+    orc_repulsion(X, n, s->ncaps, s->rep_rc, s->rep_c, (double)s->L.nx, s->L.walls ? 0.0 : (double)s->L.ny, F);
+    free(X);
+    free(n);
+    free(F);
+}
+
+void orc_sim_set_repulsion(orc_sim* s, double rc, double coeff) {
+    s->rep_rc = rc;
+    s->rep_c = coeff;
+}
 
 orc_sim* orc_sim_create(const orc_lattice* L) {
     orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
@@ -511,7 +592,7 @@ void orc_sim_destroy(orc_sim* s) {
     if (!s) return;
     for (int c = 0; c < s->ncaps; c++) {
         orc_capsule* k = &s->caps[c];
-        free(k->X); free(k->Xm1); free(k->uv); free(k->Fint); free(k->Fext);
+        free(k->X); free(k->Xm1); free(k->uv); free(k->Fint); free(k->Fext); free(k->Fpp);
         free(k->L0); free(k->th0);
     }
     free(s->caps);
@@ -541,6 +622,7 @@ int orc_sim_add_capsule(orc_sim* s, const double* xy, int n, double ks, double k
     k->uv = (double*)calloc(2 * n, sizeof(double));
     k->Fint = (double*)calloc(2 * n, sizeof(double));
     k->Fext = (double*)calloc(2 * n, sizeof(double));
+    k->Fpp = (double*)calloc(2 * n, sizeof(double));
     k->L0 = (double*)malloc(n * sizeof(double));
     k->th0 = (double*)malloc(n * sizeof(double));
     memcpy(k->X, xy, 2 * n * sizeof(double));
@@ -567,14 +649,16 @@ static void kinematic_step(orc_sim* s) {
     orc_lattice* L = &s->L;
     size_t N = (size_t)L->nx * (size_t)L->ny;
     memset(s->fibnew, 0, 2 * N * sizeof(double));
-    /* i: internal forces at X^n; ii-iii: spread with c_v = 1 */
+    /* i: internal forces at X^n (and the capsule-capsule repulsion of Eq. 27);
+     * ii-iii: spread with c_v = 1 */
+    sim_repulsion(s);
     for (int c = 0; c < s->ncaps; c++) {
         orc_capsule* k = &s->caps[c];
         orc_membrane_force(k->X, k->n, k->L0, k->th0, k->A0, k->ks, k->kb, k->ka, k->Fint);
         for (int v = 0; v < k->n; v++) {
             k->Fext[2 * v] = k->Fext[2 * v + 1] = 0.0;
-            if (orc_spread(L, k->X[2 * v], k->X[2 * v + 1], k->Fint[2 * v], k->Fint[2 * v + 1],
-                           1.0, s->fibnew))
+            if (orc_spread(L, k->X[2 * v], k->X[2 * v + 1], k->Fint[2 * v] + k->Fpp[2 * v],
+                           k->Fint[2 * v + 1] + k->Fpp[2 * v + 1], 1.0, s->fibnew))
                 s->status = ORC_ERR_SUPPORT;
         }
     }
@@ -651,6 +735,7 @@ static void dynamic_step(orc_sim* s) {
     orc_lattice* L = &s->L;
     size_t N = (size_t)L->nx * (size_t)L->ny;
     memset(s->fibnew, 0, 2 * N * sizeof(double));
+    sim_repulsion(s);   /* Eq. 27 at X^n, part of the total force of step 7 */
     /* 1-3: U = I(u^n) with half of the last spread force, F_l = (U_b - U)/dt, spread */
     for (int c = 0; c < s->ncaps; c++) {
         orc_capsule* k = &s->caps[c];
@@ -700,7 +785,7 @@ static void dynamic_step(orc_sim* s) {
         }
         if (orc_tractions(L, s->f, s->fib, k->X, n, k->Fext)) s->status = ORC_ERR_SUPPORT;
         orc_membrane_force(k->X, n, k->L0, k->th0, k->A0, k->ks, k->kb, k->ka, k->Fint);
-        for (int m = 0; m < 2 * n; m++) Ftot[m] = k->Fint[m] + k->Fext[m];
+        for (int m = 0; m < 2 * n; m++) Ftot[m] = k->Fint[m] + k->Fext[m] + k->Fpp[m];
         orc_dynamic_advance(2 * n, k->X, k->Xm1, xdot0, Ftot, k->m, Xnew, k->uv);
         memcpy(k->Xm1, k->X, 2 * n * sizeof(double));
         memcpy(k->X, Xnew, 2 * n * sizeof(double));
@@ -735,6 +820,13 @@ int orc_sim_read_capsule(orc_sim* s, int id, double* xy, double* vel, double* fi
     if (vel) memcpy(vel, k->uv, 2 * k->n * sizeof(double));
     if (fint) memcpy(fint, k->Fint, 2 * k->n * sizeof(double));
     if (fext) memcpy(fext, k->Fext, 2 * k->n * sizeof(double));
+    return 0;
+}
+
+/* Last repulsion forces of capsule id (2n doubles). */
+int orc_sim_read_repulsion(orc_sim* s, int id, double* fpp) {
+    if (id < 0 || id >= s->ncaps) return 1;
+    memcpy(fpp, s->caps[id].Fpp, 2 * s->caps[id].n * sizeof(double));
     return 0;
 }
 
