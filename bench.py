@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--adjoint-steps", type=int, default=800, help="horizon T of the adjoint measurement")
     p.add_argument("--batch-autotune", type=int, default=20,
                    help="steps per candidate launch shape of the batch autotuner (0: default shape)")
-    p.add_argument("--only", default="all", choices=["all", "batched", "adjoint", "precision"],
+    p.add_argument("--only", default="all", choices=["all", "batched", "adjoint", "precision", "dense"],
                    help="batched / adjoint: run only that measurement and print its JSON object")
     return p.parse_args()
 
@@ -277,6 +277,7 @@ def run_gpu(a):
     if rank == 0 and not a.no_extras:
         ctx.close()
         line["precision"] = precision_run(L, dev)
+        line["dense"] = dense_run(L)
         line["batched"] = batched_run(L, a.batch_steps, a.batch_autotune)
         line["adjoint"] = {"dynamic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=1),
                            "kinematic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=0)}
@@ -332,6 +333,33 @@ def precision_run(L, dev, steps=(12, 60)):
             if FP64_INSTR_PER_UPDATE:
                 r["roofline"]["frac"] = r["roofline"]["achieved"] / peak
         out[storage] = r
+        ctx.close()
+    return out
+
+
+def dense_run(L, steps=200, warmup=20, rc=2.0):
+    """Section 3.4 suspension: 16 biconcave capsules of 1000 vertices at 30% hematocrit in a
+    1200 x 450 channel (540 000 lattice nodes, 16 000 markers), Dynamic IB, FP32, with the
+    capsule-capsule repulsion of Eq. 27 (cut-off rc) and without it."""
+    import torch
+
+    case = W.dense_biconcave()
+    out = {"workload": "1200x450 channel, 16 biconcave capsules x 1000 vertices, 30% hematocrit, Dynamic, FP32",
+           "steps": steps, "cutoff": rc}
+    for key, cut in (("with_repulsion", rc), ("without", 0.0)):
+        ctx = L.from_case(case, storage="fp32")
+        ctx.set_repulsion(cut)
+        ctx.step(warmup, L.DYNAMIC)
+        ctx.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        ctx.step(steps, L.DYNAMIC)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ctx.sync()
+        out[key] = {"ms_per_step": ms / steps, "mlups": case.nx * case.ny * steps / ms / 1e3}
         ctx.close()
     return out
 
@@ -483,6 +511,7 @@ def main():
 
         out = (batched_run(L, a.batch_steps, a.batch_autotune) if a.only == "batched"
                else precision_run(L, int(os.environ.get("LOCAL_RANK", "0"))) if a.only == "precision"
+               else dense_run(L) if a.only == "dense"
                else {"dynamic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=1),
                      "kinematic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=0)})
         print(json.dumps(out), flush=True)

@@ -115,6 +115,18 @@ lbmib_status lbmib_step(lbmib_ctx* ctx, long long nsteps, lbmib_scheme scheme);
 /* Wait for the stream and report any sticky device status. */
 lbmib_status lbmib_sync(lbmib_ctx* ctx);
 
+/* Capsule-capsule repulsion (Section 3.4, Eq. 27): from the next step on, every vertex
+ * of a capsule feels coeff * sqrt(dx / d^5) along its inward normal (the negated,
+ * normalised sum of the outward normals of its two elements) from every vertex of every
+ * other capsule at distance d < cutoff (minimum image along periodic axes); dx = 1.
+ * coeff = 0 selects the printed 1e-4 / (8 sqrt 2); cutoff = 0 turns the repulsion off
+ * (the default). The force joins the spread force (Kinematic) or the total vertex force
+ * of Eq. 23 (Dynamic). Neighbours are found through a grid of cells of at least 1.5 x
+ * the largest reference capsule extent + cutoff; a capsule that outgrows its cell, or
+ * more than 16 capsules hashed to one grid bucket, raise LBMIB_ERR_STATE at the next
+ * synchronising call. Errors: LBMIB_ERR_ARG (cutoff outside [0, 16], coeff < 0). */
+lbmib_status lbmib_set_repulsion(lbmib_ctx* ctx, double cutoff, double coeff);
+
 /* Fluid fields at the current time into host arrays (ny*nx doubles each, any may be
  * NULL): rho (Eq. 6) and u (Eq. 7) with half of the body force plus the last spread
  * immersed-boundary force. Synchronises. */

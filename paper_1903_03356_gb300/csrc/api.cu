@@ -61,6 +61,13 @@ Layout make_layout(const lbmib_config* c) {
     L.mls = take(M * sizeof(MlsW<double>));
     L.caps = take(K * sizeof(CapsuleParams));
     L.obs = take(8 * K * sizeof(double));
+    L.Fpp = take(M * sizeof(double2));
+    L.rep_buckets = 64;
+    while (L.rep_buckets < 4 * (int)K) L.rep_buckets *= 2;
+    L.rep_box = take(4 * K * sizeof(double));
+    L.rep_cellof = take(K * sizeof(int));
+    L.rep_count = take((size_t)L.rep_buckets * sizeof(int));
+    L.rep_slot = take((size_t)L.rep_buckets * kRepSlots * sizeof(int));
     L.pts = take(M * sizeof(double2));
     L.pts_out = take(8 * M * sizeof(double));
     L.total = o;
@@ -135,6 +142,10 @@ void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
     const int list_cap = 9 * (c->cfg.max_nodes > 0 ? c->cfg.max_nodes : 1);
     Spread sp{c->fib[fc], c->mark, c->list[fc], &c->ctr->count[fc], &c->ctr->step_stamp, list_cap, status};
     const lbmib_storage st = c->cfg.storage;
+    if (ncaps > 1 && c->rep_rc > 0.0) {
+        launch_repulsion(L, c->nd, ncaps, c->max_n, c->rep, status, s);
+        c->launches += 2;
+    }
     if (ncaps > 0) {
         if (scheme == LBMIB_DYNAMIC) {
             if (st == LBMIB_FP64)
@@ -203,6 +214,8 @@ lbmib_status device_status(lbmib_ctx* c) {
     if (st & kStatUnstable) return fail(c, LBMIB_ERR_UNSTABLE, "unstable lattice: |u| > 0.3 or NaN");
     if (st & kStatSupport) return fail(c, LBMIB_ERR_SUPPORT, "an MLS support or probe left the channel");
     if (st & kStatTimeout) return fail(c, LBMIB_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (st & kStatGrid)
+        return fail(c, LBMIB_ERR_STATE, "repulsion neighbour grid: a capsule outgrew its cell or a bucket overflowed");
     if (st & (kStatList | kStatCell | kStatRing))
         return fail(c, LBMIB_ERR_STATE, "device bookkeeping check failed (status bits " + std::to_string(st) + ")");
     return LBMIB_OK;
@@ -212,7 +225,24 @@ lbmib_status device_status(lbmib_ctx* c) {
 
 namespace {
 
-int kernels_per_step(const lbmib_ctx* c) { return c->caps.empty() ? 1 : 4; }
+int kernels_per_step(const lbmib_ctx* c) {
+    return c->caps.empty() ? 1 : (c->rep_rc > 0.0 && c->caps.size() > 1 ? 6 : 4);
+}
+
+// Neighbour grid of the repulsion for the current capsules: coarse cells at least
+// 1.5 x the largest reference extent plus the cut-off (room for deformation; the bin
+// kernel flags a capsule that outgrows it), a whole number of cells per axis.
+void update_rep_grid(lbmib_ctx* c) {
+    RepGrid& g = c->rep;
+    g.rc = c->rep_rc;
+    g.coeff = c->rep_coeff;
+    const double want = 1.5 * c->max_extent + c->rep_rc + 1.0;
+    g.ncx = std::max(1, (int)std::floor(c->cfg.nx / want));
+    g.ncy = std::max(1, (int)std::floor(c->cfg.ny / want));
+    g.cellx = (double)c->cfg.nx / g.ncx;
+    g.celly = (double)c->cfg.ny / g.ncy;
+    c->nd.Fpp = c->rep_rc > 0.0 ? (double2*)(c->arena + c->lay.Fpp) : nullptr;
+}
 
 lbmib_status capture(lbmib_ctx* c, lbmib_scheme scheme, int cur, int cur_fib, int len, cudaGraphExec_t* out) {
     LBMIB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -296,6 +326,12 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     c->nd.age = (int*)(a + lay.age);
     c->nd.capid = (int*)(a + lay.capid);
     c->nd.mls = a + lay.mls;
+    c->nd.Fpp = nullptr;   // set while repulsion is on
+    c->rep.count = (int*)(a + lay.rep_count);
+    c->rep.slot = (int*)(a + lay.rep_slot);
+    c->rep.cellof = (int*)(a + lay.rep_cellof);
+    c->rep.box = (double*)(a + lay.rep_box);
+    c->rep.nbuckets = lay.rep_buckets;
     c->d_caps = (CapsuleParams*)(a + lay.caps);
     c->nd.caps = c->d_caps;
     c->nd.count = 0;
@@ -468,8 +504,19 @@ lbmib_status lbmib_add_capsule(lbmib_ctx* c, const double* xy, int n, double ks,
         c->tile_cells = cells;
         set_capsule_smem_limits(c->max_n, c->tile_cells);
     }
+    update_rep_grid(c);
     drop_graphs(c);  // launch shapes changed
     if (id_out) *id_out = id;
+    return LBMIB_OK;
+}
+
+lbmib_status lbmib_set_repulsion(lbmib_ctx* c, double cutoff, double coeff) {
+    if (!c || !(cutoff >= 0.0 && cutoff <= 16.0) || !(coeff >= 0.0))
+        return fail(c, LBMIB_ERR_ARG, "repulsion: cut-off must be in [0, 16] and the coefficient >= 0");
+    c->rep_rc = cutoff;
+    c->rep_coeff = coeff > 0.0 ? coeff : 1e-4 / (8.0 * std::sqrt(2.0));   // Eq. 27 with dx = 1
+    update_rep_grid(c);
+    drop_graphs(c);
     return LBMIB_OK;
 }
 

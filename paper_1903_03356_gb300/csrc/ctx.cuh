@@ -22,6 +22,8 @@ inline size_t storage_bytes(lbmib_storage s) { return s == LBMIB_FP64 ? 8 : (s =
 struct Layout {
     size_t pops[2], fib[2], mark, list[2], ctr, scratch;
     size_t X, Xm1, uv, Fint, Fext, L0, c0, s0, age, capid, mls, caps, obs, pts, pts_out;
+    size_t Fpp, rep_box, rep_cellof, rep_count, rep_slot;
+    int rep_buckets;
     size_t total;
     int pitch;
     long long plane;
@@ -41,6 +43,9 @@ struct lbmib_ctx {
     cudaStream_t ib_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_spread = nullptr, ev_patch = nullptr, ev_join = nullptr;
     int overlap = -1;   // 1 on, 0 off, -1 automatic (on while the capsules cannot fill the GPU)
+    // capsule-capsule repulsion (Eq. 27); rep_rc = 0: off
+    double rep_rc = 0.0, rep_coeff = 0.0;
+    lbmib::RepGrid rep{};
     int sms = 0;        // multiprocessors of the device
     char* arena = nullptr;
     void* pops[2]{};

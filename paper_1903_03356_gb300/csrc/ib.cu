@@ -251,7 +251,8 @@ __global__ void __launch_bounds__(128) k_dyn_update(const S* __restrict__ dst, L
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
         const int vl = v == 0 ? n - 1 : v - 1;
         const double2 Fi = node_internal_force(sm, P, v, A);
-        const double2 Fe = 0.5 * (sm.ext[v] + sm.ext[vl]);
+        double2 Fe = 0.5 * (sm.ext[v] + sm.ext[vl]);
+        if (nd.Fpp) Fe = Fe + nd.Fpp[off + v];   // Eq. 27, part of the total force (step 7)
         const double2 Xv = sm.X[v];
         const double2 Xm = nd.Xm1[off + v];
         const double2 xd = sm.xd[v];
@@ -290,10 +291,11 @@ __global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int m
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
         const double2 F = node_internal_force(sm, P, v, A);
         nd.Fint[off + v] = F;
+        const double2 Fp = nd.Fpp ? nd.Fpp[off + v] : make_double2(0.0, 0.0);   // Eq. 27
         nd.Fext[off + v] = make_double2(0.0, 0.0);
         const MlsW<C> m = mls_setup<C>(L, sm.X[v].x, sm.X[v].y);
         reinterpret_cast<MlsW<C>*>(nd.mls)[off + v] = m;
-        ok &= spread_with<C>(m, t, L, sp, stamp, F.x, F.y, 1.0);
+        ok &= spread_with<C>(m, t, L, sp, stamp, F.x + Fp.x, F.y + Fp.y, 1.0);
     }
     __syncthreads();
     if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));

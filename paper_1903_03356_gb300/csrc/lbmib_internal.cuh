@@ -391,7 +391,8 @@ enum : unsigned {
     kStatTimeout = 4u,    // a bounded wait gave up
     kStatList = 8u,       // touched-cell list full (entry dropped)
     kStatCell = 16u,      // a list entry outside the lattice (skipped)
-    kStatRing = 32u       // capsule parameters outside the launch's bounds (skipped)
+    kStatRing = 32u,      // capsule parameters outside the launch's bounds (skipped)
+    kStatGrid = 64u       // repulsion: a capsule outgrew the neighbour grid, or a bucket overflowed
 };
 
 // Small device block of counters and flags inside the arena.

@@ -22,7 +22,22 @@ struct Nodes {
     double2* Flc;    // optional (null): c_l F_l of the last Dynamic spread, per vertex
     void* mls;       // MLS shape functions of each vertex at X^n (MlsW of the compute type),
                      // written by the spread kernels, read by the node update of the step
+    double2* Fpp;    // optional (null): capsule-capsule repulsion at X^n (Eq. 27)
 };
+
+// Neighbour grid of the capsule-capsule repulsion: capsules hashed by the coarse cell of
+// their bounding-box centre into fixed-capacity buckets.
+struct RepGrid {
+    double cellx, celly;   // coarse cell sides (>= largest capsule extent + cut-off)
+    int ncx, ncy;      // coarse cells along x and y
+    int nbuckets;      // power of two
+    int* count;        // per bucket (cleared every step)
+    int* slot;         // nbuckets x kRepSlots capsule ids
+    int* cellof;       // per capsule: its coarse cell (iy * ncx + ix)
+    double* box;       // per capsule: min x, min y, max x, max y
+    double rc, coeff;  // cut-off and coefficient of Eq. 27
+};
+constexpr int kRepSlots = 16;
 
 // Touched-cell bookkeeping for the spread of one step.
 struct Spread {
@@ -66,6 +81,8 @@ void launch_observables(Nodes nd, int ncaps, int max_n, double* out, cudaStream_
 template <typename S>
 void launch_interp_points(const void* src, const Lat& L, const double* fib, const double2* pts, int n,
                           double* out, unsigned* status, cudaStream_t s);
+// repulsion.cu
+void launch_repulsion(const Lat& L, Nodes nd, int ncaps, int max_n, RepGrid g, unsigned* status, cudaStream_t s);
 size_t capsule_smem_bytes(int max_n);
 int tile_budget(int max_n, double extent);
 void set_capsule_smem_limits(int max_n, int tile_cells);

@@ -87,6 +87,7 @@ _SIGS = {
     "lbmib_kernel_time": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
     "lbmib_launch_count": (C.c_longlong, [_vp]),
     "lbmib_bytes_per_update": (C.c_double, [_vp]),
+    "lbmib_set_repulsion": (C.c_int, [_vp, C.c_double, C.c_double]),
     "lbmib_adjoint_workspace_bytes": (C.c_size_t, [_vp, C.c_longlong, C.c_int]),
     "lbmib_adjoint": (C.c_int, [_vp, C.c_longlong, C.c_int, C.c_int, C.c_int, C.c_int, _vp, C.c_size_t, _vp, _vp]),
     "lbmib_batch_arena_bytes": (C.c_size_t, [_vp, C.c_int, C.c_int]),
@@ -228,6 +229,10 @@ def lbmib_bytes_per_update(h) -> float:
     return float(_lib.lbmib_bytes_per_update(h))
 
 
+def lbmib_set_repulsion(h, cutoff: float, coeff: float = 0.0):
+    _check(h, _lib.lbmib_set_repulsion(h, float(cutoff), float(coeff)))
+
+
 def lbmib_adjoint_workspace_bytes(h, nsteps: int, ckpt_every: int) -> int:
     return int(_lib.lbmib_adjoint_workspace_bytes(h, int(nsteps), int(ckpt_every)))
 
@@ -338,6 +343,10 @@ class Context:
 
     def set_capsule_positions(self, cid, xy):
         lbmib_set_capsule_positions(self.h, cid, xy)
+
+    def set_repulsion(self, cutoff: float, coeff: float = 0.0):
+        """Capsule-capsule repulsion of Eq. 27 (cutoff 0: off; coeff 0: the printed one)."""
+        lbmib_set_repulsion(self.h, cutoff, coeff)
 
     # stepping
     def step(self, nsteps: int, scheme: int = KINEMATIC):

@@ -299,6 +299,40 @@ def adjoint_capsule(nx=512, ny=128, tau=0.7, u_max=0.02, radius=16.0, n=128, ca=
     return c
 
 
+def dense_biconcave(nx=1200, ny=450, count=16, n=1000, hematocrit=0.30, tau=0.7, u_max=0.02, ca=1e-2,
+                    gap=1.2, seed=2, scheme=DYNAMIC, steps=1) -> Case:
+    """Dense suspension of biconcave capsules in a body-force channel (Section 3.4
+    shape): `count` capsules of n vertices whose total area is `hematocrit` of the
+    channel, on a jittered grid with at least `gap` lattice units between bounding boxes
+    and 3 from the walls. For the repulsion of Eq. 27."""
+    rng = np.random.default_rng(seed)
+    proto = biconcave(n, 1.0, 0.0, 0.0)
+    a = float(np.sqrt(hematocrit * nx * ny / count / signed_area(proto)))
+    proto = biconcave(n, a, 0.0, 0.0)
+    w = proto[:, 0].max() - proto[:, 0].min()
+    h = proto[:, 1].max() - proto[:, 1].min()
+    cols = int(np.floor((nx) / (w + gap)))
+    rows = int(np.floor((ny - 6.0) / (h + gap)))
+    if cols * rows < count:
+        raise ValueError("capsules do not fit at this hematocrit and gap")
+    cells = rng.permutation(cols * rows)[:count]
+    sx, sy = nx / cols, (ny - 6.0) / rows
+    g = poiseuille_force(tau, u_max, ny)
+    ks = ks_from_umax_ca(tau, u_max, ca)
+    caps = []
+    for k in sorted(cells):
+        i, j = k % cols, k // cols
+        cx = (i + 0.5) * sx + rng.uniform(-0.5, 0.5) * max(0.0, sx - w - gap) + 0.013
+        cy = 3.0 + (j + 0.5) * sy + rng.uniform(-0.5, 0.5) * max(0.0, sy - h - gap) + 0.017
+        xy = biconcave(n, a, cx, cy)
+        check_no_ties(xy)
+        m = node_mass(1.0, signed_area(xy), n)
+        kb = kb_from_eb(stable_eb(0.01, ks, 0.5 * w, xy, m), ks, 0.5 * w)
+        caps.append(Capsule(xy, ks, kb, 0.0, m))
+    return Case("dense_biconcave", nx, ny, tau, True, gx=g, init="parabola", capsules=caps, scheme=scheme,
+                steps=steps)
+
+
 BATCH_SIZES = (64, 96, 128, 192, 256)
 BATCH_NODES = (48, 64, 96, 128)
 
