@@ -203,14 +203,23 @@ lbmib_status lbmib_load_state(lbmib_ctx* ctx, const void* host_buf, size_t bytes
  *                           step (force and spread) and of the next step (node
  *                           update); 0: every kernel on the context stream; -1
  *                           (default): on while there are fewer than two capsules per
- *                           multiprocessor. Results do not depend on it.            */
+ *                           multiprocessor. Results do not depend on it.
+ *   LBMIB_OPT_ARCS          CTAs per capsule in the immersed-boundary kernels, 1..8:
+ *                           each takes an even share of the ring's vertices, and the
+ *                           kernels that need the enclosed area run a capsule's CTAs
+ *                           as one thread-block cluster. 0 (default): one CTA per
+ *                           capsule while the capsules number at least the
+ *                           multiprocessors, otherwise min(8, multiprocessors /
+ *                           capsules, vertices / 32). Results do not depend on it
+ *                           beyond the order of the area sum.                       */
 enum {
     LBMIB_OPT_GRAPHS = 1,
     LBMIB_OPT_TIMING = 2,
     LBMIB_OPT_GRAPH_STEPS = 3,
     LBMIB_OPT_FP16_SCALE = 4,
     LBMIB_OPT_LATTICE_VARIANT = 5,
-    LBMIB_OPT_OVERLAP = 6
+    LBMIB_OPT_OVERLAP = 6,
+    LBMIB_OPT_ARCS = 7
 };
 lbmib_status lbmib_set_option(lbmib_ctx* ctx, int option, long long value);
 

@@ -11,6 +11,7 @@
 // hot loop stays at 18 population transfers per lattice update. Two force buffers
 // alternate: a step spreads into one while interpolation reads the last spread force
 // from the other; the patch of a step clears the older buffer at its touched cells.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -143,19 +144,19 @@ void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
     Spread sp{c->fib[fc], c->mark, c->list[fc], &c->ctr->count[fc], &c->ctr->step_stamp, list_cap, status};
     const lbmib_storage st = c->cfg.storage;
     if (ncaps > 1 && c->rep_rc > 0.0) {
-        launch_repulsion(L, c->nd, ncaps, c->max_n, c->rep, status, s);
+        launch_repulsion(L, c->nd, ncaps, c->max_n, c->arcs, c->rep, status, s);
         c->launches += 2;
     }
     if (ncaps > 0) {
         if (scheme == LBMIB_DYNAMIC) {
             if (st == LBMIB_FP64)
-                launch_dyn_force_spread<double>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->tile_cells, sp, status, s);
+                launch_dyn_force_spread<double>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, sp, status, s);
             else if (st == LBMIB_FP32)
-                launch_dyn_force_spread<float>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->tile_cells, sp, status, s);
+                launch_dyn_force_spread<float>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, sp, status, s);
             else
-                launch_dyn_force_spread<__half>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->tile_cells, sp, status, s);
+                launch_dyn_force_spread<__half>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, sp, status, s);
         } else {
-            launch_kin_force_spread(L, c->nd, ncaps, c->max_n, c->tile_cells, sp, status, st == LBMIB_FP64, s);
+            launch_kin_force_spread(L, c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, sp, status, st == LBMIB_FP64, s);
         }
         c->launches++;
         if (ov) cudaEventRecord(c->ev_spread, s);
@@ -193,13 +194,13 @@ void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
         }
         int* reset = &c->ctr->count[fp];
         if (scheme == LBMIB_DYNAMIC) {
-            if (st == LBMIB_FP64) launch_dyn_update<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, reset, status, s);
-            else if (st == LBMIB_FP32) launch_dyn_update<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, reset, status, s);
-            else launch_dyn_update<__half>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, reset, status, s);
+            if (st == LBMIB_FP64) launch_dyn_update<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, reset, status, s);
+            else if (st == LBMIB_FP32) launch_dyn_update<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, reset, status, s);
+            else launch_dyn_update<__half>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, reset, status, s);
         } else {
-            if (st == LBMIB_FP64) launch_kin_advance<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, reset, status, s);
-            else if (st == LBMIB_FP32) launch_kin_advance<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, reset, status, s);
-            else launch_kin_advance<__half>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, reset, status, s);
+            if (st == LBMIB_FP64) launch_kin_advance<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, reset, status, s);
+            else if (st == LBMIB_FP32) launch_kin_advance<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, reset, status, s);
+            else launch_kin_advance<__half>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, reset, status, s);
         }
         c->launches += 2;
         cur_fib = fc;
@@ -224,6 +225,38 @@ lbmib_status device_status(lbmib_ctx* c) {
 }  // namespace lbmib
 
 namespace {
+
+// Arcs per capsule: one CTA per capsule while the capsules fill the multiprocessors;
+// with fewer capsules, up to kMaxArcs CTAs per capsule (at least 32 vertices each) so
+// that the capsule kernels still spread over the GPU. Then the tile budget for arcs of
+// the longest reference arc (1.5 x for stretching), capped by the capsule diameter; a
+// box that outgrows it takes the global path, with the same results.
+void update_arcs(lbmib_ctx* c) {
+    const int ncaps = (int)c->caps.size();
+    int a = c->arcs_opt;
+    if (a == 0) {
+        const int sms = c->sms > 0 ? c->sms : 1;
+        a = ncaps == 0 || ncaps >= sms ? 1 : std::min({kMaxArcs, sms / ncaps, (c->max_n + 31) / 32});
+        a = std::max(a, 1);
+    }
+    auto arc_of = [a](const CapsuleParams& P) {
+        return P.P0 * (double)((P.n + a - 1) / a + 2 * kHalo) / (double)P.n;
+    };
+    double arc = 0.0;
+    if (a == c->arcs && !c->caps.empty()) arc = std::max(c->max_arc_len, arc_of(c->caps.back()));
+    else
+        for (const CapsuleParams& P : c->caps) arc = std::max(arc, arc_of(P));
+    const int slots = arc_slots(std::max(c->max_n, 1), a);
+    // a curve of length l fits a box of w + h <= sqrt(2) l, so a split arc's box is at
+    // most l / sqrt(2) on a side on average: budget for that square (with 1.5 x l)
+    const double reach = std::min(c->max_extent, 1.5 * arc);
+    const int cells = tile_budget(slots, a > 1 ? reach / std::sqrt(2.0) : reach, a > 1);
+    c->arcs = a;
+    c->max_arc_len = arc;
+    c->tile_cells = cells;
+    set_capsule_smem_limits(slots, cells);
+    drop_graphs(c);   // launch shapes may have changed
+}
 
 int kernels_per_step(const lbmib_ctx* c) {
     return c->caps.empty() ? 1 : (c->rep_rc > 0.0 && c->caps.size() > 1 ? 6 : 4);
@@ -499,11 +532,7 @@ lbmib_status lbmib_add_capsule(lbmib_ctx* c, const double* xy, int n, double ks,
     }
     const double ext = std::hypot(x1 - x0, y1 - y0);
     if (ext > c->max_extent) c->max_extent = ext;
-    const int cells = tile_budget(c->max_n, c->max_extent);
-    if (cells != c->tile_cells || n == c->max_n) {
-        c->tile_cells = cells;
-        set_capsule_smem_limits(c->max_n, c->tile_cells);
-    }
+    update_arcs(c);
     update_rep_grid(c);
     drop_graphs(c);  // launch shapes changed
     if (id_out) *id_out = id;
@@ -817,6 +846,12 @@ lbmib_status lbmib_set_option(lbmib_ctx* c, int option, long long value) {
             break;
         case LBMIB_OPT_LATTICE_VARIANT:
             c->lattice_variant = (int)value;
+            drop_graphs(c);
+            break;
+        case LBMIB_OPT_ARCS:
+            if (value < 0 || value > kMaxArcs) return fail(c, LBMIB_ERR_ARG, "arcs must be in [0, 8]");
+            c->arcs_opt = (int)value;
+            update_arcs(c);
             drop_graphs(c);
             break;
         default: return fail(c, LBMIB_ERR_ARG, "unknown option");

@@ -162,7 +162,7 @@ __device__ void run_case(const BatchDev& d, int c, int nsteps, const CapSmem& sm
         t.use = false;
         if (caps) {
             // i-iii: internal forces at X^n and their spread (c_v = 1) into the force tile
-            t = make_tile<C>(sm, n, 1, tile_cells, true, true);
+            t = make_tile<C>(sm, 0, n, 1, tile_cells, true, true);
             // a tile wider than the periodic lattice would alias lattice nodes
             if (t.use && (t.w > L.nx || (!L.walls && t.h > L.ny))) t.use = false;
             ok &= t.use;

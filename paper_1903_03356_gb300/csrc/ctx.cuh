@@ -62,7 +62,10 @@ struct lbmib_ctx {
     std::vector<lbmib::CapsuleParams> caps;
     int max_n = 0;
     double max_extent = 0.0;  // largest reference diameter of a capsule
-    int tile_cells = 256;     // per-capsule shared tile budget
+    double max_arc_len = 0.0; // longest reference arc of the current split (slots included)
+    int tile_cells = 256;     // per-CTA shared tile budget of the capsule kernels
+    int arcs = 1;             // CTAs per capsule in the capsule kernels
+    int arcs_opt = 0;         // requested arcs (0: automatic)
     int cur = 0;      // population buffer holding the latest post-collision state
     int cur_fib = 0;  // force buffer holding the last spread force
     long long steps = 0;

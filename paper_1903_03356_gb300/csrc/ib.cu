@@ -3,17 +3,28 @@
 // (Eq. 15-16), and the node updates of the Dynamic (Eq. 21-24) and Kinematic (Eq. 25)
 // schemes. Coclite et al., arXiv:1903.03356.
 //
-// Every kernel here runs one CTA per capsule. The CTA stages its ring in shared memory,
-// takes the bounding box of the ring (plus the reach of the supports, and of the
-// probes when it needs them) and fills a shared tile with the lattice moments of every
-// node in the box once (nine pulls per node). Node and probe interpolations then read
+// Every kernel here runs `arcs` CTAs per capsule, each owning one arc of the ring (the
+// whole ring when arcs = 1; more arcs when the capsules are too few to fill the GPU).
+// The CTA stages its arc in shared memory, takes the bounding box of the arc (plus the
+// reach of the supports, and of the probes when it needs them) and fills a shared tile
+// with the lattice moments of every node in the box once (nine pulls per node). Node and probe interpolations then read
 // that tile instead of re-gathering 81 populations each, and the spread accumulates
 // into a shared force tile that is flushed once per touched node (one global atomic
 // per node instead of one per marker and support point). A capsule whose box does not
-// fit the tile budget takes the same path with global pulls and global atomics.
+// fit the tile budget takes the same path with global pulls and global atomics. The
+// kernels that need the enclosed area run each capsule's CTAs as a thread-block cluster
+// and add the arcs' partial sums through distributed shared memory.
 // Positions, velocities, forces, reference lengths and the MLS reciprocals are double
 // in every storage mode; in FP32/FP16 modes the weights and weighted sums are float.
+#include <cooperative_groups.h>
+
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "ring.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace lbmib {
 
@@ -135,17 +146,72 @@ __device__ __forceinline__ bool spread_with(const MlsW<C>& m, Tile<C>& t, const 
     return m.ok && (in_tile || !t.use);
 }
 
-// Load the CTA's capsule; false (after flagging) when its parameters are out of range.
-__device__ __forceinline__ bool load_ring(const Nodes& nd, const CapSmem& sm, int max_n, CapsuleParams& P,
-                                          unsigned* status) {
-    P = nd.caps[blockIdx.x];
+// ---------------------------------------------------------------------------------
+// Arcs. A launch gives each capsule `arcs` CTAs (a thread-block cluster when the kernel
+// needs the enclosed area): CTA `rank` owns the vertices [v0, v0 + m) of an even split
+// of the ring and stages them in slots kHalo .. kHalo + m - 1, with kHalo neighbours on
+// each side (wrapping around the ring). Its tile covers only its arc. With arcs = 1 the
+// one arc is the whole ring.
+// ---------------------------------------------------------------------------------
+struct Arc {
+    int n, v0, m;   // ring size, first own vertex, own vertices
+    double2 X0;     // X_0, the origin of the area sums
+    // node index (within the capsule) of staged slot li
+    __device__ __forceinline__ int node(int li) const { return (v0 - kHalo + li + n) % n; }
+};
+
+// Load this CTA's capsule and stage its arc (with the halo slots when `halo`); false
+// (after flagging) when the capsule's parameters are out of range, which every CTA of
+// the capsule sees alike.
+__device__ __forceinline__ bool load_arc(const Nodes& nd, const CapSmem& sm, int max_n, int arcs, bool halo,
+                                         CapsuleParams& P, Arc& a, unsigned* status) {
+    const int cap = blockIdx.x / arcs, rank = blockIdx.x - cap * arcs;
+    P = nd.caps[cap];
     if (P.n < 3 || P.n > max_n || P.off < 0 || P.off + P.n > nd.count) {
         if (threadIdx.x == 0) atomicOr(status, kStatRing);
         return false;
     }
-    for (int v = threadIdx.x; v < P.n; v += blockDim.x) sm.X[v] = nd.X[P.off + v];
+    const int chunk = (P.n + arcs - 1) / arcs;
+    a.n = P.n;
+    a.v0 = rank * chunk;
+    a.m = max(0, min(P.n - a.v0, chunk));
+    a.X0 = nd.X[P.off];
+    const int lo = halo ? 0 : kHalo, hi = a.m == 0 ? lo : a.m + kHalo + (halo ? kHalo : 0);
+    for (int li = lo + threadIdx.x; li < hi; li += blockDim.x) sm.X[li] = nd.X[P.off + a.node(li)];
     __syncthreads();
     return true;
+}
+
+// Sum of a CTA-uniform value over the CTAs of this capsule's cluster, added in rank
+// order so that every CTA gets the same bits. Collective over the cluster.
+__device__ __forceinline__ double cluster_total(double v, int arcs) {
+    if (arcs == 1) return v;
+    __shared__ double part;
+    cg::cluster_group cl = cg::this_cluster();
+    if (threadIdx.x == 0) part = v;
+    cl.sync();
+    double t = 0.0;
+    for (int r = 0; r < arcs; r++) t += *cl.map_shared_rank(&part, r);
+    cl.sync();   // no CTA leaves while another still reads its partial
+    return t;
+}
+
+// A whole ring's halo slots repeat its own last and first vertex: copy their terms
+// (and the element tractions when `ext`). Collective; ends with a barrier.
+__device__ __forceinline__ void copy_halo_terms(const CapSmem& sm, int m, bool ext) {
+    if (threadIdx.x == 0) {
+        const int lo = kHalo - 1, last = kHalo + m - 1, hi = kHalo + m, first = kHalo;
+        sm.sst[lo] = sm.sst[last];
+        sm.bs[lo] = sm.bs[last];
+        sm.bdl[lo] = sm.bdl[last];
+        sm.bdr[lo] = sm.bdr[last];
+        if (ext) sm.ext[lo] = sm.ext[last];
+        sm.sst[hi] = sm.sst[first];
+        sm.bs[hi] = sm.bs[first];
+        sm.bdl[hi] = sm.bdl[first];
+        sm.bdr[hi] = sm.bdr[first];
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------------
@@ -156,76 +222,93 @@ __device__ __forceinline__ bool load_ring(const Nodes& nd, const CapSmem& sm, in
 template <typename S>
 __global__ void __launch_bounds__(128) k_dyn_force_spread(const S* __restrict__ src, Lat L,
                                                           const double* __restrict__ fib_prev, Nodes nd, int max_n,
-                                                          int tile_cells, Spread sp, unsigned* status) {
+                                                          int arcs, int tile_cells, Spread sp, unsigned* status) {
     using C = typename St<S>::C;
     extern __shared__ __align__(16) unsigned char smem[];
-    const CapSmem sm = carve(smem, max_n);
+    const CapSmem sm = carve(smem, arc_slots(max_n, arcs));
     CapsuleParams P;
-    if (!load_ring(nd, sm, max_n, P, status)) return;
-    const int n = P.n, off = P.off;
-    Tile<C> t = make_tile<C>(sm, n, 1, tile_cells, true, true);
+    Arc a;
+    if (!load_arc(nd, sm, max_n, arcs, true, P, a, status)) return;
+    const int m = a.m;
+    Tile<C> t = make_tile<C>(sm, kHalo, kHalo + m, 1, tile_cells, true, true);
     if (t.use) {
         fill_moments<S>(t, src, L, fib_prev);
         zero_forces<C>(t);
     }
-    __syncthreads();
-    // element lengths, once per element (c_l of reading R4)
-    for (int v = threadIdx.x; v < n; v += blockDim.x) {
-        const double2 d = sm.X[v + 1 == n ? 0 : v + 1] - sm.X[v];
-        sm.sst[v] = sqrt(d.x * d.x + d.y * d.y);
+    // lengths of the elements on both sides of every own vertex (c_l of reading R4)
+    for (int e = threadIdx.x; e < (m > 0 ? m + 1 : 0); e += blockDim.x) {
+        const int li = kHalo - 1 + e;
+        const double2 d = sm.X[li + 1] - sm.X[li];
+        sm.sst[li] = sqrt(d.x * d.x + d.y * d.y);
     }
     __syncthreads();
     const int stamp = *sp.stamp + 1;
     bool ok = true;
-    for (int v = threadIdx.x; v < n; v += blockDim.x) {
-        const double2 Xv = sm.X[v];
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        const int li = kHalo + k, g = P.off + a.v0 + k;
+        const double2 Xv = sm.X[li];
         // shape functions at X^n: used for U, for the spread, and by this step's update
-        const MlsW<C> m = mls_setup<C>(L, Xv.x, Xv.y);
-        reinterpret_cast<MlsW<C>*>(nd.mls)[off + v] = m;
+        const MlsW<C> w = mls_setup<C>(L, Xv.x, Xv.y);
+        reinterpret_cast<MlsW<C>*>(nd.mls)[g] = w;
         InterpT<C> o;
-        ok &= interp_with<S, false>(m, t, src, L, fib_prev, o);
+        ok &= interp_with<S, false>(w, t, src, L, fib_prev, o);
         const double Ux = (double)o.ux, Uy = (double)o.uy;
-        double2 uv = nd.uv[off + v];
-        if (nd.age[off + v] == 0) {
+        double2 uv = nd.uv[g];
+        if (nd.age[g] == 0) {
             uv = make_double2(Ux, Uy);
-            nd.uv[off + v] = uv;
-            nd.Xm1[off + v] = Xv - uv;
+            nd.uv[g] = uv;
+            nd.Xm1[g] = Xv - uv;
         }
-        const double cl = 0.5 * (sm.sst[v == 0 ? n - 1 : v - 1] + sm.sst[v]);
-        if (nd.Flc) nd.Flc[off + v] = make_double2(cl * (uv.x - Ux), cl * (uv.y - Uy));
-        ok &= spread_with<C>(m, t, L, sp, stamp, uv.x - Ux, uv.y - Uy, cl);
+        const double cl = 0.5 * (sm.sst[li - 1] + sm.sst[li]);
+        if (nd.Flc) nd.Flc[g] = make_double2(cl * (uv.x - Ux), cl * (uv.y - Uy));
+        ok &= spread_with<C>(w, t, L, sp, stamp, uv.x - Ux, uv.y - Uy, cl);
     }
     __syncthreads();
     if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
     if (!ok) atomicOr(status, kStatSupport);
 }
 
-// Dynamic IB steps 5-8 for one capsule per CTA: xdot_0 = I(u^{n+1}) at X^n, probe
-// tractions (Eq. 15-16), internal forces (Eq. 11, 13, 14), Verlet position (Eq. 23) and
-// BDF2 velocity (Eq. 24).
+// Dynamic IB steps 5-8: xdot_0 = I(u^{n+1}) at X^n, probe tractions (Eq. 15-16),
+// internal forces (Eq. 11, 13, 14), Verlet position (Eq. 23) and BDF2 velocity (Eq. 24).
+// With arcs > 1 the capsule's CTAs form a cluster: the enclosed area is summed over it,
+// and its barrier also orders every CTA's reads of X^n (own and halo) before any CTA
+// writes X^{n+1}.
 template <typename S>
 __global__ void __launch_bounds__(128) k_dyn_update(const S* __restrict__ dst, Lat L,
-                                                    const double* __restrict__ fib, Nodes nd, int max_n,
+                                                    const double* __restrict__ fib, Nodes nd, int max_n, int arcs,
                                                     int tile_cells, int* reset_count, unsigned* status) {
     using C = typename St<S>::C;
     extern __shared__ __align__(16) unsigned char smem[];
-    const CapSmem sm = carve(smem, max_n);
+    const CapSmem sm = carve(smem, arc_slots(max_n, arcs));
     if (blockIdx.x == 0 && threadIdx.x == 0 && reset_count) *reset_count = 0;
     CapsuleParams P;
-    if (!load_ring(nd, sm, max_n, P, status)) return;
-    const int n = P.n, off = P.off;
-    Tile<C> t = make_tile<C>(sm, n, 3, tile_cells, true, false);
+    Arc a;
+    if (!load_arc(nd, sm, max_n, arcs, true, P, a, status)) return;
+    const int m = a.m;
+    // vertices v0-1 .. v0+m: the ends of every element whose probes this CTA evaluates
+    Tile<C> t = make_tile<C>(sm, kHalo - 1, m > 0 ? kHalo + m + 1 : kHalo - 1, 3, tile_cells, true, false);
     if (t.use) fill_moments<S>(t, dst, L, fib);
     __syncthreads();
     bool ok = true;
     double area2[1] = {0.0};
     const C nu = C(L.nu);
-    for (int v = threadIdx.x; v < n; v += blockDim.x) {
-        const double2 Xv = sm.X[v], Xr = sm.X[v + 1 == n ? 0 : v + 1];
-        InterpT<C> o;
-        ok &= interp_with<S, false>(reinterpret_cast<const MlsW<C>*>(nd.mls)[off + v], t, dst, L, fib, o);
-        sm.xd[v] = make_double2((double)o.ux, (double)o.uy);
-        // element v: probes at the centroid +/- 1.2 n+ (Section 2.2.2)
+    // task k < m: own vertex kHalo+k (velocity, ring terms, area) and its element
+    // (tractions). A split ring adds two tasks for the halo: element and ring terms of
+    // slot kHalo-1, ring terms of slot kHalo+m. A whole ring copies them instead.
+    const bool split = m > 0 && m < a.n;   // an arc without vertices has no tasks
+    for (int k = threadIdx.x; k < (split ? m + 2 : m); k += blockDim.x) {
+        const int li = k < m ? kHalo + k : (k == m ? kHalo - 1 : kHalo + m);
+        vertex_terms(sm, P, nd, li - 1, li, li + 1, P.off + a.node(li));
+        if (k == m + 1) continue;
+        const double2 Xv = sm.X[li], Xr = sm.X[li + 1];
+        if (k < m) {
+            InterpT<C> o;
+            ok &= interp_with<S, false>(reinterpret_cast<const MlsW<C>*>(nd.mls)[P.off + a.v0 + k], t, dst, L, fib,
+                                        o);
+            sm.xd[li] = make_double2((double)o.ux, (double)o.uy);
+            area2[0] += area_term(a.X0, Xv, Xr);
+        }
+        // element li: probes at the centroid +/- 1.2 n+ (Section 2.2.2)
         const double2 d = Xr - Xv;
         const double rl = rsqrt(d.x * d.x + d.y * d.y);
         const double npx = d.y * rl, npy = -d.x * rl;
@@ -242,60 +325,70 @@ __global__ void __launch_bounds__(128) k_dyn_update(const S* __restrict__ dst, L
         const C dp = op.p - om.p;
         const C nx = C(npx), ny = C(npy);
         const double len = (d.x * d.x + d.y * d.y) * rl;
-        sm.ext[v] = make_double2((double)(-dp * nx + txx * nx + txy * ny) * len,
-                                 (double)(-dp * ny + txy * nx + tyy * ny) * len);
-        area2[0] += ring_terms(sm, P, nd, v);
+        sm.ext[li] = make_double2((double)(-dp * nx + txx * nx + txy * ny) * len,
+                                  (double)(-dp * ny + txy * nx + tyy * ny) * len);
     }
     block_reduce<1, false>(area2, sm.red);
-    const double A = 0.5 * area2[0];
-    for (int v = threadIdx.x; v < n; v += blockDim.x) {
-        const int vl = v == 0 ? n - 1 : v - 1;
-        const double2 Fi = node_internal_force(sm, P, v, A);
-        double2 Fe = 0.5 * (sm.ext[v] + sm.ext[vl]);
-        if (nd.Fpp) Fe = Fe + nd.Fpp[off + v];   // Eq. 27, part of the total force (step 7)
-        const double2 Xv = sm.X[v];
-        const double2 Xm = nd.Xm1[off + v];
-        const double2 xd = sm.xd[v];
+    if (m == a.n) copy_halo_terms(sm, m, true);
+    const double A = 0.5 * cluster_total(area2[0], arcs);
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        const int li = kHalo + k, g = P.off + a.v0 + k;
+        const double2 Fi = internal_force(sm, P, li - 1, li, li + 1, A);
+        double2 Fe = 0.5 * (sm.ext[li] + sm.ext[li - 1]);
+        if (nd.Fpp) Fe = Fe + nd.Fpp[g];   // Eq. 27, part of the total force (step 7)
+        const double2 Xv = sm.X[li];
+        const double2 Xm = nd.Xm1[g];
+        const double2 xd = sm.xd[li];
         const double hm = 0.5 / P.m;
         const double2 Xn = make_double2(Xv.x + xd.x + hm * (Fi.x + Fe.x), Xv.y + xd.y + hm * (Fi.y + Fe.y));
-        nd.uv[off + v] = make_double2(1.5 * Xn.x - 2.0 * Xv.x + 0.5 * Xm.x, 1.5 * Xn.y - 2.0 * Xv.y + 0.5 * Xm.y);
-        nd.Xm1[off + v] = Xv;
-        nd.X[off + v] = Xn;
-        nd.Fint[off + v] = Fi;
-        nd.Fext[off + v] = Fe;
-        nd.age[off + v] += 1;
+        nd.uv[g] = make_double2(1.5 * Xn.x - 2.0 * Xv.x + 0.5 * Xm.x, 1.5 * Xn.y - 2.0 * Xv.y + 0.5 * Xm.y);
+        nd.Xm1[g] = Xv;
+        nd.X[g] = Xn;
+        nd.Fint[g] = Fi;
+        nd.Fext[g] = Fe;
+        nd.age[g] += 1;
     }
     if (!ok) atomicOr(status, kStatSupport);
 }
 
 // ---------------------------------------------------------------------------------
 // Kinematic IB (Section 2.4), steps i-iii: internal forces at X^n (Eq. 11, 13, 14) and
-// their spread with c_v = 1.
+// their spread with c_v = 1. With arcs > 1 the capsule's CTAs form a cluster that sums
+// the enclosed area.
 // ---------------------------------------------------------------------------------
 template <typename C>
-__global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int max_n, int tile_cells, Spread sp,
-                                                          unsigned* status) {
+__global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int max_n, int arcs, int tile_cells,
+                                                          Spread sp, unsigned* status) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const CapSmem sm = carve(smem, max_n);
+    const CapSmem sm = carve(smem, arc_slots(max_n, arcs));
     CapsuleParams P;
-    if (!load_ring(nd, sm, max_n, P, status)) return;
-    const int n = P.n, off = P.off;
-    Tile<C> t = make_tile<C>(sm, n, 1, tile_cells, false, true);
+    Arc a;
+    if (!load_arc(nd, sm, max_n, arcs, true, P, a, status)) return;
+    const int m = a.m;
+    Tile<C> t = make_tile<C>(sm, kHalo, kHalo + m, 1, tile_cells, false, true);
     if (t.use) zero_forces<C>(t);
     double area2[1] = {0.0};
-    for (int v = threadIdx.x; v < n; v += blockDim.x) area2[0] += ring_terms(sm, P, nd, v);
+    // own slots, then (split ring) the halo slots kHalo-1 and kHalo+m
+    const bool split = m > 0 && m < a.n;   // an arc without vertices has no tasks
+    for (int k = threadIdx.x; k < (split ? m + 2 : m); k += blockDim.x) {
+        const int li = k < m ? kHalo + k : (k == m ? kHalo - 1 : kHalo + m);
+        vertex_terms(sm, P, nd, li - 1, li, li + 1, P.off + a.node(li));
+        if (k < m) area2[0] += area_term(a.X0, sm.X[li], sm.X[li + 1]);
+    }
     block_reduce<1, false>(area2, sm.red);  // also orders the tile zeroing before the spread
-    const double A = 0.5 * area2[0];
+    if (m == a.n) copy_halo_terms(sm, m, false);
+    const double A = 0.5 * cluster_total(area2[0], arcs);
     const int stamp = *sp.stamp + 1;
     bool ok = true;
-    for (int v = threadIdx.x; v < n; v += blockDim.x) {
-        const double2 F = node_internal_force(sm, P, v, A);
-        nd.Fint[off + v] = F;
-        const double2 Fp = nd.Fpp ? nd.Fpp[off + v] : make_double2(0.0, 0.0);   // Eq. 27
-        nd.Fext[off + v] = make_double2(0.0, 0.0);
-        const MlsW<C> m = mls_setup<C>(L, sm.X[v].x, sm.X[v].y);
-        reinterpret_cast<MlsW<C>*>(nd.mls)[off + v] = m;
-        ok &= spread_with<C>(m, t, L, sp, stamp, F.x + Fp.x, F.y + Fp.y, 1.0);
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        const int li = kHalo + k, g = P.off + a.v0 + k;
+        const double2 F = internal_force(sm, P, li - 1, li, li + 1, A);
+        nd.Fint[g] = F;
+        const double2 Fp = nd.Fpp ? nd.Fpp[g] : make_double2(0.0, 0.0);   // Eq. 27
+        nd.Fext[g] = make_double2(0.0, 0.0);
+        const MlsW<C> w = mls_setup<C>(L, sm.X[li].x, sm.X[li].y);
+        reinterpret_cast<MlsW<C>*>(nd.mls)[g] = w;
+        ok &= spread_with<C>(w, t, L, sp, stamp, F.x + Fp.x, F.y + Fp.y, 1.0);
     }
     __syncthreads();
     if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
@@ -304,38 +397,41 @@ __global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int m
 
 // Kinematic IB steps vii-viii: xdot = I(u^{n+1}) at X^n with half the spread force,
 // X^{n+1} = 2/3 (2 X^n - X^{n-1}/2 + xdot) (Eq. 25); forward Euler on a first step.
+// Every CTA reads and writes only its own vertices.
 template <typename S>
 __global__ void __launch_bounds__(128) k_kin_advance(const S* __restrict__ dst, Lat L,
-                                                     const double* __restrict__ fib, Nodes nd, int max_n,
+                                                     const double* __restrict__ fib, Nodes nd, int max_n, int arcs,
                                                      int tile_cells, int* reset_count, unsigned* status) {
     using C = typename St<S>::C;
     extern __shared__ __align__(16) unsigned char smem[];
-    const CapSmem sm = carve(smem, max_n);
+    const CapSmem sm = carve(smem, arc_slots(max_n, arcs));
     if (blockIdx.x == 0 && threadIdx.x == 0 && reset_count) *reset_count = 0;
     CapsuleParams P;
-    if (!load_ring(nd, sm, max_n, P, status)) return;
-    const int n = P.n, off = P.off;
-    Tile<C> t = make_tile<C>(sm, n, 1, tile_cells, true, false);
+    Arc a;
+    if (!load_arc(nd, sm, max_n, arcs, false, P, a, status)) return;
+    const int m = a.m;
+    Tile<C> t = make_tile<C>(sm, kHalo, kHalo + m, 1, tile_cells, true, false);
     if (t.use) fill_moments<S>(t, dst, L, fib);
     __syncthreads();
     bool ok = true;
-    for (int v = threadIdx.x; v < n; v += blockDim.x) {
-        const double2 Xv = sm.X[v];
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        const int g = P.off + a.v0 + k;
+        const double2 Xv = sm.X[kHalo + k];
         InterpT<C> o;
-        ok &= interp_with<S, false>(reinterpret_cast<const MlsW<C>*>(nd.mls)[off + v], t, dst, L, fib, o);
+        ok &= interp_with<S, false>(reinterpret_cast<const MlsW<C>*>(nd.mls)[g], t, dst, L, fib, o);
         const double Ux = (double)o.ux, Uy = (double)o.uy;
         double2 Xn;
-        if (nd.age[off + v] == 0) {
+        if (nd.age[g] == 0) {
             Xn = make_double2(Xv.x + Ux, Xv.y + Uy);
         } else {
-            const double2 Xm = nd.Xm1[off + v];
+            const double2 Xm = nd.Xm1[g];
             Xn = make_double2((2.0 / 3.0) * (2.0 * Xv.x - 0.5 * Xm.x + Ux),
                               (2.0 / 3.0) * (2.0 * Xv.y - 0.5 * Xm.y + Uy));
         }
-        nd.Xm1[off + v] = Xv;
-        nd.X[off + v] = Xn;
-        nd.uv[off + v] = make_double2(Ux, Uy);
-        nd.age[off + v] += 1;
+        nd.Xm1[g] = Xv;
+        nd.X[g] = Xn;
+        nd.uv[g] = make_double2(Ux, Uy);
+        nd.age[g] += 1;
     }
     if (!ok) atomicOr(status, kStatSupport);
 }
@@ -419,25 +515,34 @@ static size_t tile_bytes(int cells, bool moments, bool forces) {
 }
 
 template <typename C>
-static size_t smem_bytes(int max_n, int cells, bool moments, bool forces) {
-    return ring_smem_bytes(max_n) + tile_bytes<C>(cells, moments, forces);
+static size_t smem_bytes(int slots, int cells, bool moments, bool forces) {
+    return ring_smem_bytes(slots) + tile_bytes<C>(cells, moments, forces);
 }
 
-int tile_budget(int max_n, double extent) {
-    // any rotation of the reference ring, probes and supports (3 nodes each side), and
-    // room for deformation
+int tile_budget(int slots, double extent, bool tight) {
+    // a square of side `extent` plus the probes and supports (3 nodes each side); for a
+    // whole ring 1.5 x that, room for any rotation and for deformation
     const double side = extent + 8.0;
-    long long cells = (long long)(1.5 * side * side);
+    long long cells = (long long)((tight ? 1.0 : 1.5) * side * side);
     if (cells < 256) cells = 256;
-    const size_t free_b = kSmemLimit - ring_smem_bytes(max_n);
+    const size_t free_b = kSmemLimit - ring_smem_bytes(slots);
     const long long cap = (long long)(free_b / (3 * sizeof(double) + 2 * sizeof(double)));
     if (cells > cap) cells = cap;
     return (int)cells;
 }
 
-void set_capsule_smem_limits(int max_n, int cells) {
-#define LBMIB_SMEM(K, C, M, F) \
-    cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<C>(max_n, cells, M, F))
+// The limits are per kernel and process-wide: raise them, never lower them, so that
+// contexts of different ring sizes can run side by side.
+void set_capsule_smem_limits(int slots, int cells) {
+    static std::mutex mu;
+    static std::map<const void*, size_t> set;
+    std::lock_guard<std::mutex> lock(mu);
+    auto raise = [&](const void* k, size_t bytes) {
+        size_t& cur = set[k];
+        if (bytes <= cur) return;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess) cur = bytes;
+    };
+#define LBMIB_SMEM(K, C, M, F) raise((const void*)K, smem_bytes<C>(slots, cells, M, F))
     LBMIB_SMEM(k_dyn_force_spread<double>, double, true, true);
     LBMIB_SMEM(k_dyn_force_spread<float>, float, true, true);
     LBMIB_SMEM(k_dyn_force_spread<__half>, float, true, true);
@@ -452,39 +557,62 @@ void set_capsule_smem_limits(int max_n, int cells) {
 #undef LBMIB_SMEM
 }
 
+// Launch a capsule kernel over ncaps x arcs CTAs of 128 threads; with `cluster`, each
+// capsule's arcs form one thread-block cluster.
+template <typename... P, typename... A>
+static void launch_arcs(void (*k)(P...), int ncaps, int arcs, bool cluster, size_t smem, cudaStream_t s,
+                        A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ncaps * (unsigned)arcs);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    if (cluster && arcs > 1) {
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)arcs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+    }
+    cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
+
 template <typename S>
 void launch_dyn_force_spread(const void* src, const Lat& L, const double* fib_prev, Nodes nd, int ncaps, int max_n,
-                             int cells, Spread sp, unsigned* status, cudaStream_t s) {
+                             int arcs, int cells, Spread sp, unsigned* status, cudaStream_t s) {
     using C = typename St<S>::C;
-    k_dyn_force_spread<S><<<ncaps, 128, smem_bytes<C>(max_n, cells, true, true), s>>>(
-        (const S*)src, L, fib_prev, nd, max_n, cells, sp, status);
+    launch_arcs(k_dyn_force_spread<S>, ncaps, arcs, false, smem_bytes<C>(arc_slots(max_n, arcs), cells, true, true),
+                s, (const S*)src, L, fib_prev, nd, max_n, arcs, cells, sp, status);
 }
 
 template <typename S>
 void launch_dyn_update(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
-                       int cells, int* reset_count, unsigned* status, cudaStream_t s) {
+                       int arcs, int cells, int* reset_count, unsigned* status, cudaStream_t s) {
     using C = typename St<S>::C;
-    k_dyn_update<S><<<ncaps, 128, smem_bytes<C>(max_n, cells, true, false), s>>>(
-        (const S*)dst, L, fib_cur, nd, max_n, cells, reset_count, status);
+    launch_arcs(k_dyn_update<S>, ncaps, arcs, true, smem_bytes<C>(arc_slots(max_n, arcs), cells, true, false), s,
+                (const S*)dst, L, fib_cur, nd, max_n, arcs, cells, reset_count, status);
 }
 
-void launch_kin_force_spread(const Lat& L, Nodes nd, int ncaps, int max_n, int cells, Spread sp, unsigned* status,
-                             bool fp64_weights, cudaStream_t s) {
+void launch_kin_force_spread(const Lat& L, Nodes nd, int ncaps, int max_n, int arcs, int cells, Spread sp,
+                             unsigned* status, bool fp64_weights, cudaStream_t s) {
     // double MLS weights when the populations are double, float otherwise
+    const int slots = arc_slots(max_n, arcs);
     if (fp64_weights)
-        k_kin_force_spread<double><<<ncaps, 128, smem_bytes<double>(max_n, cells, false, true), s>>>(
-            L, nd, max_n, cells, sp, status);
+        launch_arcs(k_kin_force_spread<double>, ncaps, arcs, true, smem_bytes<double>(slots, cells, false, true), s,
+                    L, nd, max_n, arcs, cells, sp, status);
     else
-        k_kin_force_spread<float><<<ncaps, 128, smem_bytes<float>(max_n, cells, false, true), s>>>(
-            L, nd, max_n, cells, sp, status);
+        launch_arcs(k_kin_force_spread<float>, ncaps, arcs, true, smem_bytes<float>(slots, cells, false, true), s,
+                    L, nd, max_n, arcs, cells, sp, status);
 }
 
 template <typename S>
 void launch_kin_advance(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
-                        int cells, int* reset_count, unsigned* status, cudaStream_t s) {
+                        int arcs, int cells, int* reset_count, unsigned* status, cudaStream_t s) {
     using C = typename St<S>::C;
-    k_kin_advance<S><<<ncaps, 128, smem_bytes<C>(max_n, cells, true, false), s>>>(
-        (const S*)dst, L, fib_cur, nd, max_n, cells, reset_count, status);
+    launch_arcs(k_kin_advance<S>, ncaps, arcs, false, smem_bytes<C>(arc_slots(max_n, arcs), cells, true, false), s,
+                (const S*)dst, L, fib_cur, nd, max_n, arcs, cells, reset_count, status);
 }
 
 void launch_observables(Nodes nd, int ncaps, int max_n, double* out, cudaStream_t s) {
@@ -502,11 +630,11 @@ void launch_interp_points(const void* src, const Lat& L, const double* fib, cons
 
 #define LBMIB_INSTANTIATE_IB(S)                                                                              \
     template void launch_dyn_force_spread<S>(const void*, const Lat&, const double*, Nodes, int, int, int,   \
-                                             Spread, unsigned*, cudaStream_t);                               \
-    template void launch_dyn_update<S>(const void*, const Lat&, const double*, Nodes, int, int, int, int*,   \
-                                       unsigned*, cudaStream_t);                                             \
-    template void launch_kin_advance<S>(const void*, const Lat&, const double*, Nodes, int, int, int, int*,  \
-                                        unsigned*, cudaStream_t);                                            \
+                                             int, Spread, unsigned*, cudaStream_t);                          \
+    template void launch_dyn_update<S>(const void*, const Lat&, const double*, Nodes, int, int, int, int,    \
+                                       int*, unsigned*, cudaStream_t);                                       \
+    template void launch_kin_advance<S>(const void*, const Lat&, const double*, Nodes, int, int, int, int,   \
+                                        int*, unsigned*, cudaStream_t);                                      \
     template void launch_interp_points<S>(const void*, const Lat&, const double*, const double2*, int,       \
                                           double*, unsigned*, cudaStream_t);
 

@@ -65,26 +65,34 @@ void launch_macros(const void* src, const Lat& L, const double* fib, double* rho
 template <typename S>
 void launch_populations(const void* src, const Lat& L, int i0, double* out, cudaStream_t s);
 
-// ib.cu
+// ib.cu. The capsule kernels run `arcs` CTAs per capsule (1..kMaxArcs), each on an even
+// share of the ring.
+constexpr int kHalo = 2;       // neighbour slots staged on each side of an arc
+constexpr int kMaxArcs = 8;    // portable thread-block cluster size
+// staged vertex slots per CTA for rings of at most max_n vertices in `arcs` arcs
+__host__ __device__ inline int arc_slots(int max_n, int arcs) { return (max_n + arcs - 1) / arcs + 2 * kHalo; }
 template <typename S>
 void launch_dyn_force_spread(const void* src, const Lat& L, const double* fib_prev, Nodes nd, int ncaps, int max_n,
-                             int cells, Spread sp, unsigned* status, cudaStream_t s);
+                             int arcs, int cells, Spread sp, unsigned* status, cudaStream_t s);
 template <typename S>
 void launch_dyn_update(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
-                       int cells, int* reset_count, unsigned* status, cudaStream_t s);
-void launch_kin_force_spread(const Lat& L, Nodes nd, int ncaps, int max_n, int cells, Spread sp, unsigned* status,
-                             bool fp64_weights, cudaStream_t s);
+                       int arcs, int cells, int* reset_count, unsigned* status, cudaStream_t s);
+void launch_kin_force_spread(const Lat& L, Nodes nd, int ncaps, int max_n, int arcs, int cells, Spread sp,
+                             unsigned* status, bool fp64_weights, cudaStream_t s);
 template <typename S>
 void launch_kin_advance(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
-                        int cells, int* reset_count, unsigned* status, cudaStream_t s);
+                        int arcs, int cells, int* reset_count, unsigned* status, cudaStream_t s);
 void launch_observables(Nodes nd, int ncaps, int max_n, double* out, cudaStream_t s);
 template <typename S>
 void launch_interp_points(const void* src, const Lat& L, const double* fib, const double2* pts, int n,
                           double* out, unsigned* status, cudaStream_t s);
 // repulsion.cu
-void launch_repulsion(const Lat& L, Nodes nd, int ncaps, int max_n, RepGrid g, unsigned* status, cudaStream_t s);
+void launch_repulsion(const Lat& L, Nodes nd, int ncaps, int max_n, int arcs, RepGrid g, unsigned* status,
+                      cudaStream_t s);
 size_t capsule_smem_bytes(int max_n);
-int tile_budget(int max_n, double extent);
-void set_capsule_smem_limits(int max_n, int tile_cells);
+// tile cells per CTA for `slots` staged vertices and boxes of about `extent` across
+// (`tight`: no allowance for rotation and deformation)
+int tile_budget(int slots, double extent, bool tight = false);
+void set_capsule_smem_limits(int slots, int tile_cells);
 
 }  // namespace lbmib

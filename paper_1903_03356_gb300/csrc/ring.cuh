@@ -89,11 +89,13 @@ struct Tile {
     }
 };
 
-// Bounding box of the staged ring and the tile layout. Collective (all threads).
+// Bounding box of the staged slots [lo, hi) and the tile layout (no tile for an empty
+// range). Collective (all threads).
 template <typename C>
-__device__ Tile<C> make_tile(const CapSmem& sm, int n, int margin, int tile_cells, bool moments, bool forces) {
+__device__ Tile<C> make_tile(const CapSmem& sm, int lo, int hi, int margin, int tile_cells, bool moments,
+                             bool forces) {
     double r[4] = {1e300, 1e300, 1e300, 1e300};  // min x, min y, -max x, -max y
-    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+    for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
         const double2 X = sm.X[v];
         r[0] = fmin(r[0], X.x);
         r[1] = fmin(r[1], X.y);
@@ -138,33 +140,46 @@ __device__ void zero_forces(Tile<C>& t) {
     }
 }
 
-// Per-element stretch factor and per-vertex bending terms of vertex/element v, and
-// this vertex's contribution to twice the enclosed area (Green's theorem, about X_0).
-__device__ __forceinline__ double ring_terms(const CapSmem& sm, const CapsuleParams& P, const Nodes& nd, int v) {
-    const int n = P.n;
-    const double2 Xv = sm.X[v], Xr = sm.X[v + 1 == n ? 0 : v + 1], Xl = sm.X[v == 0 ? n - 1 : v - 1];
+// Stretch factor of element v and bending terms of vertex v (Eq. 11, 13) into the
+// staged slots: vl, v, vr are the slots of X_{v-1}, X_v, X_{v+1}; g is v's index in
+// the node arrays.
+__device__ __forceinline__ void vertex_terms(const CapSmem& sm, const CapsuleParams& P, const Nodes& nd, int vl,
+                                             int v, int vr, int g) {
+    const double2 Xv = sm.X[v], Xr = sm.X[vr], Xl = sm.X[vl];
     const double2 a = Xv - Xl, b = Xr - Xv;   // incoming edge, outgoing edge (element v)
     const double a2 = a.x * a.x + a.y * a.y, b2 = b.x * b.x + b.y * b.y;
     const double ra = rsqrt(a2), rb = rsqrt(b2);   // 1/|a|, 1/|b|
     // Eq. 11: element v joins v and v+1, length |b|
-    sm.sst[v] = -P.ks * (b2 * rb - nd.L0[P.off + v]) * rb;
+    sm.sst[v] = -P.ks * (b2 * rb - nd.L0[g]) * rb;
     // Eq. 13 as F = -k_b sin(theta - theta_0) d(theta)/dX with theta the signed turning
     // angle at v; sin(theta - theta_0) from the cross and dot products and theta_0's
     // stored cosine and sine.
     const double cr = a.x * b.y - a.y * b.x, dt = a.x * b.x + a.y * b.y;
-    const double sdiff = (cr * nd.c0[P.off + v] - dt * nd.s0[P.off + v]) * (ra * rb);
+    const double sdiff = (cr * nd.c0[g] - dt * nd.s0[g]) * (ra * rb);
     sm.bs[v] = P.kb * sdiff;
     const double ia2 = ra * ra, ib2 = rb * rb;
     sm.bdl[v] = make_double2(-a.y * ia2, a.x * ia2);
     sm.bdr[v] = make_double2(-b.y * ib2, b.x * ib2);
-    const double2 X0 = sm.X[0];
+}
+
+// Element v's contribution to twice the enclosed area (Green's theorem about X_0).
+__device__ __forceinline__ double area_term(double2 X0, double2 Xv, double2 Xr) {
     return (Xv.x - X0.x) * (Xr.y - X0.y) - (Xr.x - X0.x) * (Xv.y - X0.y);
 }
 
-// Internal force on vertex v (Eq. 22: stretch + bending + area) from the staged terms.
-__device__ __forceinline__ double2 node_internal_force(const CapSmem& sm, const CapsuleParams& P, int v, double A) {
+// Per-element stretch factor and per-vertex bending terms of vertex/element v of a
+// whole staged ring, and this vertex's contribution to twice the enclosed area.
+__device__ __forceinline__ double ring_terms(const CapSmem& sm, const CapsuleParams& P, const Nodes& nd, int v) {
     const int n = P.n;
-    const int vl = v == 0 ? n - 1 : v - 1, vr = v + 1 == n ? 0 : v + 1;
+    const int vr = v + 1 == n ? 0 : v + 1;
+    vertex_terms(sm, P, nd, v == 0 ? n - 1 : v - 1, v, vr, P.off + v);
+    return area_term(sm.X[0], sm.X[v], sm.X[vr]);
+}
+
+// Internal force on the vertex in slot v (Eq. 22: stretch + bending + area) from the
+// staged terms of slots vl, v, vr (its neighbours) and the enclosed area A.
+__device__ __forceinline__ double2 internal_force(const CapSmem& sm, const CapsuleParams& P, int vl, int v, int vr,
+                                                  double A) {
     const double2 Xv = sm.X[v], Xl = sm.X[vl], Xr = sm.X[vr];
     double2 F = sm.sst[v] * (Xv - Xr);           // element v, this vertex first
     F = F + (-sm.sst[vl]) * (Xl - Xv);           // element v-1, this vertex second
@@ -177,6 +192,12 @@ __device__ __forceinline__ double2 node_internal_force(const CapSmem& sm, const 
     F.x += fa * (dr.y + dl.y);
     F.y -= fa * (dr.x + dl.x);
     return F;
+}
+
+// Internal force on vertex v of a whole staged ring.
+__device__ __forceinline__ double2 node_internal_force(const CapSmem& sm, const CapsuleParams& P, int v, double A) {
+    const int n = P.n;
+    return internal_force(sm, P, v == 0 ? n - 1 : v - 1, v, v + 1 == n ? 0 : v + 1, A);
 }
 
 }  // namespace lbmib

@@ -290,18 +290,3 @@ def test_unstable_velocity_is_reported(L):
     with pytest.raises(L.LbmibError) as e:
         ctx.sync()
     assert e.value.status == L.ERR_UNSTABLE
-
-
-@pytest.mark.parametrize("scheme", [o.KINEMATIC, o.DYNAMIC])
-def test_capsule_larger_than_the_tile_takes_the_global_path(L, scheme):
-    # radius 26: the bounding box (about 58 x 58 nodes) exceeds the per-capsule tile, so
-    # the kernels gather and spread through global memory; results are the same
-    case = W.shear_capsule(nx=96, ny=96, radius=26.0, n=160, ca=1e-2, scheme=scheme)
-    ctx = L.from_case(case, storage="fp64")
-    s = oracle_sim(case)
-    ctx.step(300, scheme)
-    assert s.step(300, scheme) == 0
-    _, u_g, v_g = ctx.read_fields()
-    _, u_o, v_o = s.read_fields()
-    assert rel(np.stack([u_g, v_g]), np.stack([u_o, v_o])) < 1e-10
-    assert np.abs(ctx.read_capsule(0)[0] - s.read_capsule(0)[0]).max() < 1e-9
