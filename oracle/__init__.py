@@ -55,6 +55,9 @@ class Lattice(C.Structure):
         ("tau", C.c_double),
         ("gx", C.c_double),
         ("gy", C.c_double),
+        ("inflow", C.c_int),
+        ("rho_out", C.c_double),
+        ("u_in", C.POINTER(C.c_double)),
     ]
 
     @property
@@ -62,9 +65,21 @@ class Lattice(C.Structure):
         return self.nx * self.ny
 
 
-def lattice(nx, ny, tau, walls=False, u_bottom=0.0, u_top=0.0, gx=0.0, gy=0.0) -> Lattice:
-    return Lattice(int(nx), int(ny), int(bool(walls)), float(u_bottom), float(u_top),
-                   float(tau), float(gx), float(gy))
+def lattice(nx, ny, tau, walls=False, u_bottom=0.0, u_top=0.0, gx=0.0, gy=0.0, u_in=None,
+            rho_out=1.0) -> Lattice:
+    """Lattice description. With u_in (ny inlet x-velocities) x is an open channel: a
+    known-velocity inlet at x = 0 and a known-density (rho_out) outlet at x = nx - 1
+    (reading R26); otherwise x is periodic."""
+    L = Lattice(int(nx), int(ny), int(bool(walls)), float(u_bottom), float(u_top),
+                float(tau), float(gx), float(gy), 0, float(rho_out), None)
+    if u_in is not None:
+        u = np.ascontiguousarray(np.asarray(u_in, dtype=np.float64).reshape(-1))
+        if u.size != int(ny):
+            raise ValueError("u_in needs one value per row")
+        L._u_in = u                      # keeps the profile alive while the lattice is used
+        L.inflow = 1
+        L.u_in = u.ctypes.data_as(C.POINTER(C.c_double))
+    return L
 
 
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -79,6 +94,7 @@ def _declare(L):
         "orc_macros": (None, [_LP, _dp, vp, _dp, _dp, _dp]),
         "orc_collide_stream": (None, [_LP, _dp, vp, _dp]),
         "orc_init_equilibrium": (None, [_LP, vp, vp, vp, _dp]),
+        "orc_open_boundaries": (None, [_LP, _dp]),
         "orc_mls": (C.c_int, [_LP, C.c_double, C.c_double, _ip, _ip, _dp, _dp, _dp]),
         "orc_interp": (C.c_int, [_LP, _dp, vp, C.c_double, C.c_double, _dp]),
         "orc_interp_scalar": (C.c_int, [_LP, _dp, C.c_double, C.c_double, _dp]),
@@ -159,6 +175,14 @@ def collide_stream(L: Lattice, f: np.ndarray, fib: Optional[np.ndarray] = None) 
     out = np.zeros((9, L.ny, L.nx))
     fib = None if fib is None else _f64(fib)
     lib().orc_collide_stream(C.byref(L), _f64(f), _ptr(fib), out)
+    return out
+
+
+def open_boundaries(L: Lattice, f: np.ndarray) -> np.ndarray:
+    """Zou-He closure of the inlet and outlet columns (reading R26) applied to a copy of
+    the pre-collision populations f (9, ny, nx); f itself is unchanged."""
+    out = _f64(f).copy()
+    lib().orc_open_boundaries(C.byref(L), out)
     return out
 
 

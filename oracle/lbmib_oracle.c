@@ -15,7 +15,8 @@
  *
  * Units: dx = dt = 1, rho_0 = 1, c_s^2 = 1/3, nu = (tau - 1/2)/3. Lattice node (i, j)
  * sits at (x, y) = (i, j). With walls, half-way bounce-back walls sit at y = -1/2 and
- * y = ny - 1/2 (channel height H = ny); x is always periodic.
+ * y = ny - 1/2 (channel height H = ny). x is periodic, or open: a known-velocity inlet
+ * at column x = 0 and a known-density outlet at x = nx - 1 (Zou and He, reading R26).
  *
  * Readings of the paper where it is silent, ambiguous or garbled (each also listed in
  * the design notes of the repository):
@@ -44,6 +45,20 @@
  *       distances are minimum images on the periodic lattice.
  *   R24 The normal at a vertex is the normalised sum of the outward unit normals
  *       (dy, -dx)/l of the two elements meeting there; Eq. 27 acts along its negative.
+ *   R26 Open channel (Section 2.1, boundaries of Zou and He; Section 3.2 inlet profile
+ *       and outlet pressure): on the pre-collision populations of the inlet column the
+ *       three populations entering from x < 0 are rebuilt so that the node has the
+ *       prescribed velocity (u_in(y), 0); on the outlet column those entering from
+ *       x > nx - 1 so that it has density rho_out and zero y-velocity. Closure: mass and
+ *       normal momentum fix rho (inlet) or u_x (outlet); the non-equilibrium part
+ *       bounces back along the normal, f_1 - f_1^eq = f_3 - f_3^eq; the diagonals carry
+ *       the tangential non-equilibrium momentum, f_5^neq - f_7^neq = -(f_2^neq -
+ *       f_4^neq)/2 and f_8^neq - f_6^neq = +(f_2^neq - f_4^neq)/2. With the Guo force F
+ *       the known momentum is rho u - F/2 and the equilibria are taken at the velocity
+ *       of that momentum. The whole column is closed, the wall rows included (their
+ *       wall-crossing populations are bounced back first). Supports of markers and
+ *       probes must stay inside columns 1 .. nx - 2, so the open columns carry only the
+ *       uniform force g; distances along x are not periodic.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -68,6 +83,9 @@ typedef struct {
     double u_top;       /* x-velocity of the wall at y = ny - 1/2                    */
     double tau;         /* BGK relaxation time                                       */
     double gx, gy;      /* uniform body-force density added to f_ib everywhere       */
+    int inflow;         /* 0: periodic in x; 1: open inlet and outlet columns (R26)  */
+    double rho_out;     /* outlet density                                            */
+    const double* u_in; /* inlet x-velocity of every row (ny values)                 */
 } orc_lattice;
 
 /* index of population i at node (x, y) */
@@ -131,12 +149,57 @@ void orc_macros(const orc_lattice* L, const double* f, const double* fib, double
 }
 
 /*
+ * Zou-He closure of the open columns (reading R26) on the pre-collision populations f:
+ * column x = 0 gets velocity (u_in[y], 0), column x = nx - 1 density rho_out and zero
+ * y-velocity. The open columns carry only the uniform force g.
+ */
+void orc_open_boundaries(const orc_lattice* L, double* f) {
+    if (!L->inflow) return;
+    const double Fx = L->gx, Fy = L->gy;
+    for (int side = 0; side < 2; side++) {
+        const int x = side == 0 ? 0 : L->nx - 1;
+        for (int y = 0; y < L->ny; y++) {
+            double fi[9], feq[9];
+            for (int i = 0; i < 9; i++) fi[i] = f[fidx(L, i, x, y)];
+            double rho, jx;
+            const double jy = -0.5 * Fy;   /* v = 0: rho v - F_y/2 */
+            if (side == 0) {
+                /* unknown: 1, 5, 8. Mass: rho = K + (f1 + f5 + f8); normal momentum:
+                 * (f1 + f5 + f8) - (f3 + f6 + f7) = rho u - F_x/2. */
+                const double u = L->u_in[y];
+                const double K = fi[0] + fi[2] + fi[4] + fi[3] + fi[6] + fi[7];
+                rho = (K + fi[3] + fi[6] + fi[7] - 0.5 * Fx) / (1.0 - u);
+                jx = rho * u - 0.5 * Fx;
+            } else {
+                /* unknown: 3, 6, 7. Mass fixes the unknown sum, normal momentum follows. */
+                rho = L->rho_out;
+                const double K = fi[0] + fi[2] + fi[4] + fi[1] + fi[5] + fi[8];
+                jx = (fi[1] + fi[5] + fi[8]) - (rho - K);
+            }
+            orc_feq(rho, jx / rho, jy / rho, feq);
+            const double nt = (fi[2] - feq[2]) - (fi[4] - feq[4]);   /* tangential non-equilibrium */
+            if (side == 0) {
+                fi[1] = fi[3] + (feq[1] - feq[3]);
+                fi[5] = fi[7] + (feq[5] - feq[7]) - 0.5 * nt;
+                fi[8] = fi[6] + (feq[8] - feq[6]) + 0.5 * nt;
+            } else {
+                fi[3] = fi[1] - (feq[1] - feq[3]);
+                fi[7] = fi[5] - (feq[5] - feq[7]) + 0.5 * nt;
+                fi[6] = fi[8] - (feq[8] - feq[6]) - 0.5 * nt;
+            }
+            for (int i = 0; i < 9; i++) f[fidx(L, i, x, y)] = fi[i];
+        }
+    }
+}
+
+/*
  * One lattice update, Eq. 4 with the forcing term of Eq. 5: every node collides
  * (BGK, Eq. 1-2) with the Guo term built from the total force g + f_ib, then every
  * post-collision population streams to x + e_i. A population that would cross a
  * wall returns to its own node in the opposite direction, corrected by
- * -2 w_i rho_0 (e_i . u_w) / c_s^2 (reading R2). f is pre-collision at time t,
- * fnew receives pre-collision populations at t + 1.
+ * -2 w_i rho_0 (e_i . u_w) / c_s^2 (reading R2). On an open channel the populations
+ * that would enter through the inlet or outlet column are then rebuilt (R26). f is
+ * pre-collision at time t, fnew receives pre-collision populations at t + 1.
  */
 void orc_collide_stream(const orc_lattice* L, const double* f, const double* fib, double* fnew) {
     const double tau = L->tau;
@@ -168,6 +231,7 @@ void orc_collide_stream(const orc_lattice* L, const double* f, const double* fib
             }
         }
     }
+    orc_open_boundaries(L, fnew);   /* replaces what the periodic wrap carried across */
 }
 
 /* Fill populations with the equilibrium of given fields (rest state where NULL). */
@@ -241,7 +305,12 @@ int orc_mls(const orc_lattice* L, double X, double Y, int ix[9], int iy[9], doub
                 for (int n = 0; n < 3; n++) A[m][n] += Wk * p[m] * p[n];
                 B[m][k] = Wk * p[m];
             }
-            ix[k] = wrap(xk, L->nx);
+            if (L->inflow) {   /* open channel: supports stay off the open columns (R26) */
+                if (xk < 1 || xk > L->nx - 2) status = ORC_ERR_SUPPORT;
+                ix[k] = xk < 0 ? 0 : (xk >= L->nx ? L->nx - 1 : xk);
+            } else {
+                ix[k] = wrap(xk, L->nx);
+            }
             if (L->walls) {
                 if (yk < 0 || yk >= L->ny) status = ORC_ERR_SUPPORT;
                 iy[k] = yk < 0 ? 0 : (yk >= L->ny ? L->ny - 1 : yk);
@@ -565,7 +634,8 @@ static void sim_repulsion(orc_sim* s) {
         n[c] = s->caps[c].n;
         F[c] = s->caps[c].Fpp;
     }
-    orc_repulsion(X, n, s->ncaps, s->rep_rc, s->rep_c, (double)s->L.nx, s->L.walls ? 0.0 : (double)s->L.ny, F);
+    orc_repulsion(X, n, s->ncaps, s->rep_rc, s->rep_c, s->L.inflow ? 0.0 : (double)s->L.nx,
+                  s->L.walls ? 0.0 : (double)s->L.ny, F);
     free(X);
     free(n);
     free(F);
@@ -602,6 +672,7 @@ void orc_sim_destroy(orc_sim* s) {
 
 void orc_sim_init_fields(orc_sim* s, const double* rho, const double* ux, const double* uy) {
     orc_init_equilibrium(&s->L, rho, ux, uy, s->f);
+    orc_open_boundaries(&s->L, s->f);   /* the open columns hold their prescribed state */
 }
 
 /* direct access for tests: populations (9*N, pre-collision) and last spread force */
