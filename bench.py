@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--adjoint-steps", type=int, default=800, help="horizon T of the adjoint measurement")
     p.add_argument("--batch-autotune", type=int, default=20,
                    help="steps per candidate launch shape of the batch autotuner (0: default shape)")
-    p.add_argument("--only", default="all", choices=["all", "batched", "adjoint", "precision", "dense"],
+    p.add_argument("--only", default="all", choices=["all", "batched", "adjoint", "precision", "dense", "open"],
                    help="batched / adjoint: run only that measurement and print its JSON object")
     return p.parse_args()
 
@@ -278,6 +278,7 @@ def run_gpu(a):
         ctx.close()
         line["precision"] = precision_run(L, dev)
         line["dense"] = dense_run(L)
+        line["open"] = open_run(L)
         line["batched"] = batched_run(L, a.batch_steps, a.batch_autotune)
         line["adjoint"] = {"dynamic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=1),
                            "kinematic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=0)}
@@ -361,6 +362,46 @@ def dense_run(L, steps=200, warmup=20, rc=2.0):
         ctx.sync()
         out[key] = {"ms_per_step": ms / steps, "mlups": case.nx * case.ny * steps / ms / 1e3}
         ctx.close()
+    return out
+
+
+def open_run(L, steps=500, warmup=50):
+    """Section 3.2 open channel (Zou-He parabolic inlet, constant-pressure outlet): the
+    capsule case at H = 120 (3H x H = 360 x 120, diameter 56 = 7/15 H, 586 vertices at 0.3
+    lattice units), both schemes, FP32; and the 16384 x 8192 lattice with open ends and no
+    capsules, against the same lattice periodic in x (the cost of the open columns)."""
+    import torch
+
+    def timed(ctx, n, scheme):
+        ctx.step(warmup, scheme)
+        ctx.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        ctx.step(n, scheme)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ctx.sync()
+        return e0.elapsed_time(e1) / n
+
+    out = {"workload": "Section 3.2 open channel: parabolic Zou-He inlet (u_max 0.02), outlet density 1, FP32"}
+    for name, scheme in (("dynamic", L.DYNAMIC), ("kinematic", L.KINEMATIC)):
+        case = W.open_channel_capsule(scheme=scheme)
+        ctx = L.from_case(case, storage="fp32")
+        ms = timed(ctx, steps, scheme)
+        out[f"capsule_{name}"] = {"lattice": f"{case.nx}x{case.ny}", "vertices": len(case.capsules[0].xy),
+                                  "ms_per_step": ms, "mlups": case.nx * case.ny / ms / 1e3}
+        ctx.close()
+    nx, ny = 16384, 8192
+    big = {}
+    for key, u_in in (("open", W.inlet_parabola(ny, 0.02)), ("periodic", None)):
+        case = W.Case("lattice", nx, ny, 0.7, True, init="rest", u_in=u_in)
+        ctx = L.from_case(case, storage="fp32")
+        ms = timed(ctx, 100, L.KINEMATIC)
+        big[key] = {"ms_per_step": ms, "glups": nx * ny / ms / 1e6}
+        ctx.close()
+    big["open_cost"] = big["open"]["ms_per_step"] / big["periodic"]["ms_per_step"] - 1.0
+    out["lattice_16384x8192"] = big
     return out
 
 
@@ -512,6 +553,7 @@ def main():
         out = (batched_run(L, a.batch_steps, a.batch_autotune) if a.only == "batched"
                else precision_run(L, int(os.environ.get("LOCAL_RANK", "0"))) if a.only == "precision"
                else dense_run(L) if a.only == "dense"
+               else open_run(L) if a.only == "open"
                else {"dynamic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=1),
                      "kinematic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=0)})
         print(json.dumps(out), flush=True)

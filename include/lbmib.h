@@ -115,6 +115,22 @@ lbmib_status lbmib_step(lbmib_ctx* ctx, long long nsteps, lbmib_scheme scheme);
 /* Wait for the stream and report any sticky device status. */
 lbmib_status lbmib_sync(lbmib_ctx* ctx);
 
+/* Open channel (Section 2.1: known-velocity boundaries of Zou and He; Section 3.2:
+ * parabolic inlet and constant outlet pressure). From the next step on, x is no longer
+ * periodic: column x = 0 is an inlet whose nodes get the velocity (u_in[y], 0) and column
+ * x = nx - 1 an outlet whose nodes get density rho_out (pressure rho_out / 3) and zero
+ * y-velocity. The three populations entering through each column are rebuilt from the
+ * others (mass and normal momentum fix the density or the normal velocity; the
+ * non-equilibrium part bounces back along the normal; the diagonals share the tangential
+ * one; with a body force g the known momentum is rho u - g/2). The whole column is
+ * closed, wall rows included. u_in: ny host doubles, |u| < 0.3, copied during the call;
+ * rho_out in (0.5, 2). u_in = NULL makes x periodic again. MLS supports of vertices and
+ * probes must then stay within columns 1 .. nx - 2 (LBMIB_ERR_SUPPORT otherwise); the
+ * repulsion takes x distances without the periodic image. Not covered by lbmib_adjoint
+ * (LBMIB_ERR_STATE); not part of the saved state (set it again after lbmib_load_state).
+ * Synchronises the context stream. */
+lbmib_status lbmib_set_inflow(lbmib_ctx* ctx, const double* u_in, double rho_out);
+
 /* Capsule-capsule repulsion (Section 3.4, Eq. 27): from the next step on, every vertex
  * of a capsule feels coeff * sqrt(dx / d^5) along its inward normal (the negated,
  * normalised sum of the outward normals of its two elements) from every vertex of every

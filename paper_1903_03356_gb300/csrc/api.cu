@@ -71,6 +71,7 @@ Layout make_layout(const lbmib_config* c) {
     L.rep_slot = take((size_t)L.rep_buckets * kRepSlots * sizeof(int));
     L.pts = take(M * sizeof(double2));
     L.pts_out = take(8 * M * sizeof(double));
+    L.u_in = take((size_t)c->ny * sizeof(double));
     L.total = o;
     return L;
 }
@@ -179,6 +180,12 @@ void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
     else launch_collide_stream<__half>(src, dst, L, status, c->lattice_variant, s_lat);
     c->launches++;
     if (timed) cudaEventRecord(e1, s_lat);
+    if (L.inflow) {   // open channel: the inlet and outlet columns, over the lattice kernel's output
+        if (st == LBMIB_FP64) launch_open_columns<double>(src, dst, L, status, s_lat);
+        else if (st == LBMIB_FP32) launch_open_columns<float>(src, dst, L, status, s_lat);
+        else launch_open_columns<__half>(src, dst, L, status, s_lat);
+        c->launches++;
+    }
     if (ncaps > 0) {
         const int cap = list_cap;
         if (ov) cudaStreamWaitEvent(s_lat, c->ev_spread, 0);
@@ -259,7 +266,7 @@ void update_arcs(lbmib_ctx* c) {
 }
 
 int kernels_per_step(const lbmib_ctx* c) {
-    return c->caps.empty() ? 1 : (c->rep_rc > 0.0 && c->caps.size() > 1 ? 6 : 4);
+    return (c->caps.empty() ? 1 : (c->rep_rc > 0.0 && c->caps.size() > 1 ? 6 : 4)) + (c->L.inflow ? 1 : 0);
 }
 
 // Neighbour grid of the repulsion for the current capsules: coarse cells at least
@@ -371,6 +378,7 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     c->obs = (double*)(a + lay.obs);
     c->pts = (double2*)(a + lay.pts);
     c->pts_out = (double*)(a + lay.pts_out);
+    c->d_u_in = (double*)(a + lay.u_in);
 
     Lat& L = c->L;
     L.nx = cfg->nx;
@@ -536,6 +544,29 @@ lbmib_status lbmib_add_capsule(lbmib_ctx* c, const double* xy, int n, double ks,
     update_rep_grid(c);
     drop_graphs(c);  // launch shapes changed
     if (id_out) *id_out = id;
+    return LBMIB_OK;
+}
+
+lbmib_status lbmib_set_inflow(lbmib_ctx* c, const double* u_in, double rho_out) {
+    if (!c) return LBMIB_ERR_ARG;
+    Lat& L = c->L;
+    if (!u_in) {
+        L.inflow = 0;
+        L.u_in = nullptr;
+        drop_graphs(c);
+        return LBMIB_OK;
+    }
+    if (L.nx < 5) return fail(c, LBMIB_ERR_ARG, "an open channel needs nx >= 5");
+    if (!(rho_out > 0.5 && rho_out < 2.0)) return fail(c, LBMIB_ERR_ARG, "outlet density must be in (0.5, 2)");
+    for (int y = 0; y < L.ny; y++)
+        if (!(std::fabs(u_in[y]) < 0.3)) return fail(c, LBMIB_ERR_ARG, "inlet velocities must satisfy |u| < 0.3");
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->d_u_in, u_in, (size_t)L.ny * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    LBMIB_CUDA(c, cudaStreamSynchronize(c->stream));
+    L.inflow = 1;
+    L.u_in = c->d_u_in;
+    L.drho_out = rho_out - 1.0;
+    L.drho_outf = (float)L.drho_out;
+    drop_graphs(c);
     return LBMIB_OK;
 }
 

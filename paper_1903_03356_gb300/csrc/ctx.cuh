@@ -22,7 +22,7 @@ inline size_t storage_bytes(lbmib_storage s) { return s == LBMIB_FP64 ? 8 : (s =
 struct Layout {
     size_t pops[2], fib[2], mark, list[2], ctr, scratch;
     size_t X, Xm1, uv, Fint, Fext, L0, c0, s0, age, capid, mls, caps, obs, pts, pts_out;
-    size_t Fpp, rep_box, rep_cellof, rep_count, rep_slot;
+    size_t Fpp, rep_box, rep_cellof, rep_count, rep_slot, u_in;
     int rep_buckets;
     size_t total;
     int pitch;
@@ -59,6 +59,7 @@ struct lbmib_ctx {
     double* obs = nullptr;
     double2* pts = nullptr;
     double* pts_out = nullptr;
+    double* d_u_in = nullptr;   // inlet profile of an open channel (ny doubles)
     std::vector<lbmib::CapsuleParams> caps;
     int max_n = 0;
     double max_extent = 0.0;  // largest reference diameter of a capsule

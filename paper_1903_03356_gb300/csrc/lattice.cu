@@ -457,11 +457,32 @@ __global__ void k_populations(const S* __restrict__ src, Lat L, int i0, double* 
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const int y = (int)(n / L.nx), x = (int)(n - (long long)y * L.nx);
+    typename St<S>::C s[9];
+    pull_all<S>(src, L, x, y, s);
     for (int k = 0; k < 3 && i0 + k < 9; k++) {
         const int i = i0 + k;
         double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
-        out[k * N + n] = (double)pull<S>(src, L, i, x, y) + w;
+        out[k * N + n] = (double)s[i] + w;
     }
+}
+
+// Open channel: redo the update of the inlet and outlet columns (2 ny nodes), whose
+// pulls across x = 0 and x = nx - 1 the lattice kernel took through the periodic wrap:
+// pull_all applies the Zou-He closure there, then the node collides with the uniform
+// force (Eq. 4-5) like every other node. Runs after the lattice kernel, on its output.
+template <typename S>
+__global__ void __launch_bounds__(128) k_open_columns(const S* __restrict__ src, S* __restrict__ dst, Lat L,
+                                                      unsigned* status) {
+    using C = typename St<S>::C;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 2 * L.ny) return;
+    const int y = k >> 1, x = (k & 1) ? L.nx - 1 : 0;
+    C s[9];
+    pull_all<S>(src, L, x, y, s);
+    const C usq = collide<C>(s, lat_c<C>(L.gx, L.gxf), lat_c<C>(L.gy, L.gyf), lat_c<C>(L.omega, L.omegaf));
+    if (!(usq < C(0.09))) atomicOr(status, kStatUnstable);
+#pragma unroll
+    for (int i = 0; i < 9; i++) St<S>::st(dst + (long long)i * L.plane + (long long)y * L.pitch + x, s[i], L);
 }
 
 // ---------------------------------------------------------------------------------
@@ -506,6 +527,11 @@ void launch_patch(const void* src, void* dst, const Lat& L, const double* fib_c,
 }
 
 template <typename S>
+void launch_open_columns(const void* src, void* dst, const Lat& L, unsigned* status, cudaStream_t s) {
+    k_open_columns<S><<<blocks_for(2LL * L.ny, 128), 128, 0, s>>>((const S*)src, (S*)dst, L, status);
+}
+
+template <typename S>
 void launch_init(void* dst, const Lat& L, const double* rho, const double* ux, const double* uy, cudaStream_t s) {
     k_init<S><<<blocks_for((long long)L.nx * L.ny, 256), 256, 0, s>>>((S*)dst, L, rho, ux, uy);
 }
@@ -525,6 +551,7 @@ void launch_populations(const void* src, const Lat& L, int i0, double* out, cuda
     template void launch_collide_stream<S>(const void*, void*, const Lat&, unsigned*, int, cudaStream_t); \
     template void launch_patch<S>(const void*, void*, const Lat&, const double*, const int*, double*, \
                                   const int*, DevCounters*, int, int, cudaStream_t);                  \
+    template void launch_open_columns<S>(const void*, void*, const Lat&, unsigned*, cudaStream_t);     \
     template void launch_init<S>(void*, const Lat&, const double*, const double*, const double*,      \
                                  cudaStream_t);                                                       \
     template void launch_macros<S>(const void*, const Lat&, const double*, double*, double*, double*, \

@@ -51,6 +51,12 @@ struct Lat {
     // float copies for single-precision kernels (a double-to-float conversion in every
     // thread would occupy GB300's narrow FP64 pipe)
     float gxf, gyf, omegaf, ubf, utf;
+    // open channel (0: periodic in x): Zou-He known-velocity inlet at column 0 with
+    // x-velocity u_in[y] (device, ny values), known-density outlet at column nx - 1
+    int inflow;
+    const double* u_in;
+    double drho_out;      // outlet density - 1
+    float drho_outf;
 };
 
 // Lattice constant in the compute type C.
@@ -101,7 +107,8 @@ __device__ __forceinline__ int wrapi(int a, int n) {
 }
 
 // Pre-collision population i at node (x, y) of the step that reads `src` (Eq. 1, left
-// side): the pull of the post-collision population from x - e_i, or the wall reflection.
+// side): the pull of the post-collision population from x - e_i, or the wall reflection
+// (periodic x only: the open columns of an open channel need pull_all).
 // NC selects the read-only load path (src not written during the launch).
 template <typename S, bool NC = true>
 __device__ __forceinline__ typename St<S>::C pull(const S* __restrict__ src, const Lat& L, int i,
@@ -119,9 +126,40 @@ __device__ __forceinline__ typename St<S>::C pull(const S* __restrict__ src, con
     return ld(src + (long long)i * L.plane + (long long)ys * L.pitch + xs);
 }
 
+// Zou-He closure of an open column (inlet x = 0, outlet x = nx - 1) on the shifted
+// pre-collision populations s of node (x, y): the three populations that enter from
+// outside the lattice are rebuilt so that the node has velocity (u_in(y), 0) (inlet) or
+// density rho_out and zero y-velocity (outlet), the non-equilibrium part bounced back
+// along the normal and the tangential one shared by the diagonals. The known momentum is
+// rho u - F/2 with F the uniform force (supports stay off the open columns). Explicit
+// form of the closure in shifted variables (the rest weights cancel pairwise).
+template <typename C>
+__device__ __forceinline__ void open_column(C (&s)[9], const Lat& L, int x, int y) {
+    const C Fx = lat_c<C>(L.gx, L.gxf), Fy = lat_c<C>(L.gy, L.gyf);
+    const C jy = C(-0.5) * Fy;
+    const C t = C(0.5) * (s[2] - s[4]);
+    if (x == 0) {
+        const C u = C(L.u_in[y]);
+        // rho (1 - u) = 1 + s0 + s2 + s4 + 2 (s3 + s6 + s7) - Fx/2
+        const C known = (s[0] + s[2] + s[4]) + C(2) * (s[3] + s[6] + s[7]);
+        const C drho = (known - C(0.5) * Fx + u) / (C(1) - u);
+        const C jx = (C(1) + drho) * u - C(0.5) * Fx;
+        s[1] = s[3] + C(2.0 / 3.0) * jx;
+        s[5] = s[7] - t + jx * C(1.0 / 6.0) + C(0.5) * jy;
+        s[8] = s[6] + t + jx * C(1.0 / 6.0) - C(0.5) * jy;
+    } else {
+        // mass fixes the entering populations' sum, x-momentum follows
+        const C jx = ((s[0] + s[2] + s[4]) + C(2) * (s[1] + s[5] + s[8])) - lat_c<C>(L.drho_out, L.drho_outf);
+        s[3] = s[1] - C(2.0 / 3.0) * jx;
+        s[7] = s[5] + t - jx * C(1.0 / 6.0) - C(0.5) * jy;
+        s[6] = s[8] - t - jx * C(1.0 / 6.0) + C(0.5) * jy;
+    }
+}
+
 // All nine pre-collision populations of node (x, y), as pull() but with the neighbour
 // coordinates formed by comparisons instead of the periodic wrap's integer division,
-// and every load issued before any is used. NC as for pull().
+// and every load issued before any is used, and the Zou-He closure on the open columns
+// of an open channel. NC as for pull().
 template <typename S, bool NC = true>
 __device__ __forceinline__ void pull_all(const S* __restrict__ src, const Lat& L, int x, int y,
                                          typename St<S>::C (&s)[9]) {
@@ -146,6 +184,8 @@ __device__ __forceinline__ void pull_all(const S* __restrict__ src, const Lat& L
             s[i] -= C(6) * wgt<C>(j) * C(ex(j)) * uw;
         }
     }
+    // open channel: what the periodic wrap brought across the inlet or outlet is replaced
+    if (L.inflow && (x == 0 || x == L.nx - 1)) open_column<C>(s, L, x, y);
 }
 
 // Density deviation, momentum (Eq. 6-7 without the force) of shifted populations.
@@ -225,7 +265,7 @@ struct MlsW {
 };
 
 // Support geometry of a point: centre node and whether the 3x3 block stays inside the
-// walls. A non-finite or runaway position (an unstable run) is moved to the origin so
+// walls (and, in an open channel, off the open columns). A non-finite or runaway position (an unstable run) is moved to the origin so
 // that every access stays inside the lattice, and reported as a support failure.
 __device__ __forceinline__ bool support_centre(const Lat& L, double& X, double& Y, int& cx, int& cy) {
     const bool sane = fabs(X) < 1e9 && fabs(Y) < 1e9;   // false for NaN too
@@ -235,7 +275,8 @@ __device__ __forceinline__ bool support_centre(const Lat& L, double& X, double& 
     }
     cx = (int)floor(X + 0.5);
     cy = (int)floor(Y + 0.5);
-    return sane && (!L.walls || (cy >= 1 && cy <= L.ny - 2));
+    // open channel: the support (cx - 1 .. cx + 1) stays off the inlet and outlet columns
+    return sane && (!L.walls || (cy >= 1 && cy <= L.ny - 2)) && (!L.inflow || (cx >= 2 && cx <= L.nx - 3));
 }
 
 // Double reciprocal of a value known to lie well inside float range (the MLS weight

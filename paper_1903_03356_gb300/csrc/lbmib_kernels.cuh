@@ -57,6 +57,9 @@ void launch_collide_stream(const void* src, void* dst, const Lat& L, unsigned* s
 template <typename S>
 void launch_patch(const void* src, void* dst, const Lat& L, const double* fib_c, const int* list_c,
                   double* fib_p, const int* list_p, DevCounters* ctr, int c, int capacity, cudaStream_t s);
+// open channel: Zou-He inlet and outlet columns, after launch_collide_stream on its output
+template <typename S>
+void launch_open_columns(const void* src, void* dst, const Lat& L, unsigned* status, cudaStream_t s);
 template <typename S>
 void launch_init(void* dst, const Lat& L, const double* rho, const double* ux, const double* uy, cudaStream_t s);
 template <typename S>

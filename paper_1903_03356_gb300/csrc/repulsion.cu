@@ -3,7 +3,7 @@
 //   F_1 += 1e-4 / (8 sqrt 2) sqrt(dx / d_12^5) n_1^-   (dx = 1),
 // with n_1^- the inward normal at vertex 1: the negated, normalised sum of the outward
 // normals (dy, -dx)/l of the two elements that meet there. Distances along periodic
-// axes are minimum images.
+// axes are minimum images (x is not periodic in an open channel).
 //
 // Broad phase: each capsule's bounding box, and its coarse cell (side >= largest capsule
 // extent + r_c, so interacting capsules sit in neighbouring cells), hashed into
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(128) k_repulsion(Lat L, Nodes nd, int max_n, i
     if (P.n < 3 || P.n > max_n) return;
     const int n = P.n, chunk = (n + arcs - 1) / arcs, v0 = rank * chunk, m = min(n - v0, chunk);
     if (m <= 0) return;
-    const double px = (double)L.nx, py = L.walls ? 0.0 : (double)L.ny;
+    const double px = L.inflow ? 0.0 : (double)L.nx, py = L.walls ? 0.0 : (double)L.ny;
     for (int li = threadIdx.x; li < m + 2; li += blockDim.x) own[li] = nd.X[P.off + (v0 - 1 + li + n) % n];
     __syncthreads();
     double r[4] = {1e300, 1e300, 1e300, 1e300};   // the arc's box: min x, min y, -max x, -max y

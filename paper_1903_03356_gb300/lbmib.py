@@ -88,6 +88,7 @@ _SIGS = {
     "lbmib_launch_count": (C.c_longlong, [_vp]),
     "lbmib_bytes_per_update": (C.c_double, [_vp]),
     "lbmib_set_repulsion": (C.c_int, [_vp, C.c_double, C.c_double]),
+    "lbmib_set_inflow": (C.c_int, [_vp, _vp, C.c_double]),
     "lbmib_adjoint_workspace_bytes": (C.c_size_t, [_vp, C.c_longlong, C.c_int]),
     "lbmib_adjoint": (C.c_int, [_vp, C.c_longlong, C.c_int, C.c_int, C.c_int, C.c_int, _vp, C.c_size_t, _vp, _vp]),
     "lbmib_batch_arena_bytes": (C.c_size_t, [_vp, C.c_int, C.c_int]),
@@ -233,6 +234,14 @@ def lbmib_set_repulsion(h, cutoff: float, coeff: float = 0.0):
     _check(h, _lib.lbmib_set_repulsion(h, float(cutoff), float(coeff)))
 
 
+def lbmib_set_inflow(h, u_in, rho_out: float = 1.0):
+    if u_in is None:
+        _check(h, _lib.lbmib_set_inflow(h, None, float(rho_out)))
+        return
+    u = _f64(u_in)
+    _check(h, _lib.lbmib_set_inflow(h, u.ctypes.data_as(_vp), float(rho_out)))
+
+
 def lbmib_adjoint_workspace_bytes(h, nsteps: int, ckpt_every: int) -> int:
     return int(_lib.lbmib_adjoint_workspace_bytes(h, int(nsteps), int(ckpt_every)))
 
@@ -348,6 +357,13 @@ class Context:
         """Capsule-capsule repulsion of Eq. 27 (cutoff 0: off; coeff 0: the printed one)."""
         lbmib_set_repulsion(self.h, cutoff, coeff)
 
+    def set_inflow(self, u_in, rho_out: float = 1.0):
+        """Open channel: Zou-He inlet with x-velocity u_in (ny values) at x = 0 and outlet
+        density rho_out at x = nx - 1 (u_in None: periodic x again)."""
+        if u_in is not None and np.asarray(u_in).size != self.ny:
+            raise ValueError("u_in needs one value per row")
+        lbmib_set_inflow(self.h, u_in, rho_out)
+
     # stepping
     def step(self, nsteps: int, scheme: int = KINEMATIC):
         lbmib_step(self.h, nsteps, scheme)
@@ -444,6 +460,8 @@ def from_case(case, storage="fp64", extra_nodes=0, extra_capsules=0, **kw) -> Co
                   storage=storage, max_capsules=len(case.capsules) + extra_capsules,
                   max_nodes=case.n_nodes + extra_nodes, **kw)
     ctx.init_fields(*case.fields())
+    if getattr(case, "u_in", None) is not None:
+        ctx.set_inflow(case.u_in, case.rho_out)
     for c in case.capsules:
         ctx.add_capsule(c.xy, c.ks, c.kb, c.ka, c.mass)
     return ctx

@@ -15,6 +15,9 @@ Workloads (all synthetic; the paper's own data are not used):
   poiseuille_biconcave - many biconcave capsules (Eq. 26 shape), seeded placement
   batch_cases        - many independent shear-flow cases of uneven sizes
   adjoint_capsule    - circular capsule in Poiseuille flow for gradients
+  open_channel_capsule - circular capsule in the open channel of Section 3.2 (parabolic
+                       Zou-He inlet, constant-pressure outlet, fluid at rest at the start)
+  dense_biconcave    - dense suspension of biconcave capsules (Section 3.4 shape)
 """
 from __future__ import annotations
 
@@ -158,6 +161,8 @@ class Case:
     capsules: List[Capsule] = field(default_factory=list)
     scheme: int = KINEMATIC
     steps: int = 1
+    u_in: Optional[np.ndarray] = None   # open channel: inlet x-velocity per row (x not periodic)
+    rho_out: float = 1.0                # open channel: outlet density
 
     def fields(self):
         if self.init == "shear":
@@ -297,6 +302,35 @@ def adjoint_capsule(nx=512, ny=128, tau=0.7, u_max=0.02, radius=16.0, n=128, ca=
                            eb=eb, density_ratio=density_ratio, scheme=scheme, steps=steps)
     c.name = "adjoint_capsule"
     return c
+
+
+def inlet_parabola(ny: int, u_max: float) -> np.ndarray:
+    """Section 3.2 inlet profile u_x = -u_max (|1 - y / (H/2)|^2 - 1), y measured from the
+    bottom wall (at -1/2) to the row, H = ny."""
+    y = np.arange(ny) + 0.5
+    return -u_max * (np.abs(1.0 - y / (0.5 * ny)) ** 2 - 1.0)
+
+
+def open_channel_capsule(ny=120, length=3.0, tau=0.7, u_max=0.02, diameter=56.0, spacing=0.3, ca=1e-2,
+                         eb=0.01, y_frac=0.5, density_ratio=1.0, scheme=DYNAMIC, steps=1) -> Case:
+    """Section 3.2 set-up: a circular capsule (diameter 7/15 of the channel height, element
+    length `spacing` lattice units) in a channel of length `length` x H, driven by the
+    parabolic inlet (Zou-He, u_max on the centre line) against a constant-pressure outlet,
+    fluid at rest at the start; centre at `y_frac` H (6.5, 7.5, 8.5 um of 15 um: 0.433,
+    0.5, 0.567) and 1.5 diameters from the inlet."""
+    nx = int(round(length * ny))
+    r = 0.5 * diameter
+    n = int(round(2.0 * np.pi * r / spacing))
+    xy = circle(n, r, 1.5 * diameter + 0.13, y_frac * ny - 0.5 + 0.07)
+    k = 0
+    while min_half_integer_distance(xy) <= 1e-9:
+        k += 1
+        xy = circle(n, r, 1.5 * diameter + 0.13 + 1e-4 * k, y_frac * ny - 0.5 + 0.07)
+    ks = ks_from_umax_ca(tau, u_max, ca)
+    m = node_mass(density_ratio, signed_area(xy), n)
+    kb = kb_from_eb(stable_eb(eb, ks, r, xy, m), ks, r)
+    return Case("open_channel_capsule", nx, ny, tau, True, init="rest", capsules=[Capsule(xy, ks, kb, 0.0, m)],
+                scheme=scheme, steps=steps, u_in=inlet_parabola(ny, u_max), rho_out=1.0)
 
 
 def dense_biconcave(nx=1200, ny=450, count=16, n=1000, hematocrit=0.30, tau=0.7, u_max=0.02, ca=1e-2,
