@@ -226,7 +226,7 @@ lbmib_status lbmib_load_state(lbmib_ctx* ctx, const void* host_buf, size_t bytes
  *                           as one thread-block cluster. 0 (default): one CTA per
  *                           capsule while the capsules number at least the
  *                           multiprocessors, otherwise min(8, multiprocessors /
- *                           capsules, vertices / 32). Results do not depend on it
+ *                           capsules, vertices / 16). Results do not depend on it
  *                           beyond the order of the area sum.                       */
 enum {
     LBMIB_OPT_GRAPHS = 1,

@@ -70,81 +70,83 @@ __device__ __forceinline__ double vpart(double a) { return a; }
 __device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ double dexp(double a) { return exp(a); }
 
-// A value with its derivatives along four directions at once (one pass instead of four
-// when the value parts, exponentials included, would be the same in each), in the real
-// type R (float for single-precision storage, double otherwise).
-template <typename R>
-struct D4 {
-    R v, d[4];
+// A value with its derivatives along K directions at once (one pass instead of K when
+// the value parts, exponentials included, would be the same in each), in the real type
+// R (float for single-precision storage, double otherwise).
+template <typename R, int K>
+struct DN {
+    R v, d[K];
 };
 template <typename R>
+using D4 = DN<R, 4>;
+template <typename R>
 __device__ __forceinline__ D4<R> d4(R v) { return D4<R>{v, {R(0), R(0), R(0), R(0)}}; }
-template <typename R>
-__device__ __forceinline__ D4<R> operator+(D4<R> a, D4<R> b) {
-    D4<R> r{a.v + b.v, {}};
+template <typename R, int K>
+__device__ __forceinline__ DN<R, K> operator+(DN<R, K> a, DN<R, K> b) {
+    DN<R, K> r{a.v + b.v, {}};
 #pragma unroll
-    for (int k = 0; k < 4; k++) r.d[k] = a.d[k] + b.d[k];
+    for (int k = 0; k < K; k++) r.d[k] = a.d[k] + b.d[k];
     return r;
 }
-template <typename R>
-__device__ __forceinline__ D4<R> operator-(D4<R> a, D4<R> b) {
-    D4<R> r{a.v - b.v, {}};
+template <typename R, int K>
+__device__ __forceinline__ DN<R, K> operator-(DN<R, K> a, DN<R, K> b) {
+    DN<R, K> r{a.v - b.v, {}};
 #pragma unroll
-    for (int k = 0; k < 4; k++) r.d[k] = a.d[k] - b.d[k];
+    for (int k = 0; k < K; k++) r.d[k] = a.d[k] - b.d[k];
     return r;
 }
-template <typename R>
-__device__ __forceinline__ D4<R> operator-(D4<R> a) {
-    D4<R> r{-a.v, {}};
+template <typename R, int K>
+__device__ __forceinline__ DN<R, K> operator-(DN<R, K> a) {
+    DN<R, K> r{-a.v, {}};
 #pragma unroll
-    for (int k = 0; k < 4; k++) r.d[k] = -a.d[k];
+    for (int k = 0; k < K; k++) r.d[k] = -a.d[k];
     return r;
 }
-template <typename R>
-__device__ __forceinline__ D4<R> operator*(D4<R> a, D4<R> b) {
-    D4<R> r{a.v * b.v, {}};
+template <typename R, int K>
+__device__ __forceinline__ DN<R, K> operator*(DN<R, K> a, DN<R, K> b) {
+    DN<R, K> r{a.v * b.v, {}};
 #pragma unroll
-    for (int k = 0; k < 4; k++) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+    for (int k = 0; k < K; k++) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
     return r;
 }
-template <typename R>
-__device__ __forceinline__ D4<R> operator/(D4<R> a, D4<R> b) {
+template <typename R, int K>
+__device__ __forceinline__ DN<R, K> operator/(DN<R, K> a, DN<R, K> b) {
     const R q = a.v / b.v, ib = R(1) / b.v;
-    D4<R> r{q, {}};
+    DN<R, K> r{q, {}};
 #pragma unroll
-    for (int k = 0; k < 4; k++) r.d[k] = (a.d[k] - q * b.d[k]) * ib;
+    for (int k = 0; k < K; k++) r.d[k] = (a.d[k] - q * b.d[k]) * ib;
     return r;
 }
-template <typename R>
-__device__ __forceinline__ D4<R> operator*(R s, D4<R> a) {
-    D4<R> r{s * a.v, {}};
+template <typename R, int K>
+__device__ __forceinline__ DN<R, K> operator*(R s, DN<R, K> a) {
+    DN<R, K> r{s * a.v, {}};
 #pragma unroll
-    for (int k = 0; k < 4; k++) r.d[k] = s * a.d[k];
+    for (int k = 0; k < K; k++) r.d[k] = s * a.d[k];
     return r;
 }
-template <typename R>
-__device__ __forceinline__ D4<R> operator+(D4<R> a, R s) { a.v += s; return a; }
-template <typename R>
-__device__ __forceinline__ D4<R> dsqrt(D4<R> a) {
+template <typename R, int K>
+__device__ __forceinline__ DN<R, K> operator+(DN<R, K> a, R s) { a.v += s; return a; }
+template <typename R, int K>
+__device__ __forceinline__ DN<R, K> dsqrt(DN<R, K> a) {
     const R r = sqrt(a.v), h = R(0.5) / r;
-    D4<R> o{r, {}};
+    DN<R, K> o{r, {}};
 #pragma unroll
-    for (int k = 0; k < 4; k++) o.d[k] = a.d[k] * h;
+    for (int k = 0; k < K; k++) o.d[k] = a.d[k] * h;
     return o;
 }
-template <typename R>
-__device__ __forceinline__ D4<R> dexp(D4<R> a) {
+template <typename R, int K>
+__device__ __forceinline__ DN<R, K> dexp(DN<R, K> a) {
     const R e = exp(a.v);
-    D4<R> o{e, {}};
+    DN<R, K> o{e, {}};
 #pragma unroll
-    for (int k = 0; k < 4; k++) o.d[k] = e * a.d[k];
+    for (int k = 0; k < K; k++) o.d[k] = e * a.d[k];
     return o;
 }
 __device__ __forceinline__ float dexp(float a) { return expf(a); }
 
 // Real type underlying a scalar type (for constants in templated arithmetic).
 template <typename T> struct RealOf { using type = T; };
-template <typename R> struct RealOf<D4<R>> { using type = R; };
+template <typename R, int K> struct RealOf<DN<R, K>> { using type = R; };
 template <> struct RealOf<Dual> { using type = double; };
 
 template <typename T>
@@ -857,64 +859,77 @@ __global__ void __launch_bounds__(128) k_adjd_update(Nodes nd, int max_n, const 
     for (int v = threadIdx.x; v < n; v += blockDim.x) xout[off + v] = sm.xd[v];
 }
 
-// DR1t: transpose of the tractions (Eq. 15-16), one thread per (element, probe). Each
-// end vertex receives half of the element force, so F_l-bar = (F^tot-bar_1 +
-// F^tot-bar_2)/2. The fields enter linearly: density through p and tau, the velocity
-// gradient through tau; the positions through the probe location, normal and length
-// (four directional derivatives with dual numbers).
+// DR1t: transpose of the tractions (Eq. 15-16), nine threads per (element, probe), one
+// per node of the probe's support, 32 (element, probe) groups per CTA. Each end vertex
+// receives half of the element force, so F_l-bar = (F^tot-bar_1 + F^tot-bar_2)/2. The
+// fields enter linearly: density through p and tau, the velocity gradient through tau;
+// the positions through the probe location, normal and length. Thread k of a group loads
+// the fields of support node k; threads 0-3 each take the derivative along one end
+// coordinate (single-lane duals, in parallel); every thread injects its own node's share
+// of the field adjoints.
+constexpr int kTractGroups = 32;
+
 template <typename S>
-__global__ void __launch_bounds__(32) k_adjd_tract(Lat L, Nodes nd, int count, const double2* Xn,
-                                                   const S* __restrict__ post1, const double* __restrict__ fib,
-                                                   const double2* ftb, double2* xout, double* sbar, double* bbar,
-                                                   double* grad_g, unsigned* status) {
+__global__ void __launch_bounds__(9 * kTractGroups) k_adjd_tract(Lat L, Nodes nd, int count, const double2* Xn,
+                                                                 const S* __restrict__ post1,
+                                                                 const double* __restrict__ fib, const double2* ftb,
+                                                                 double2* xout, double* sbar, double* bbar,
+                                                                 double* grad_g, unsigned* status) {
     // the traction adjoint computes in single precision for single-precision storage
     using R = typename std::conditional<sizeof(S) == 8, double, float>::type;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ R fld[3][kTractGroups][9];   // density deviation, u_x, u_y of each support node
+    const int grp = threadIdx.x / 9, k = threadIdx.x - 9 * grp;
+    const int t = blockIdx.x * kTractGroups + grp;
     const int g1 = t >> 1, s = t & 1;
+    const bool act = g1 < count;
     double gsx = 0.0, gsy = 0.0;
     bool ok = true;
-    if (g1 < count) {
+    int g2 = 0, cx = 0, cy = 0;
+    double2 X1{}, X2{};
+    double dx = 0.0, dy = 0.0, len = 1.0, Px = 0.0, Py = 0.0, dr = 0.0, u = 0.0, w = 0.0;
+    long long cell = 0;
+    R Fb[2] = {R(0), R(0)};
+    if (act) {
         const CapsuleParams P = nd.caps[nd.capid[g1]];
         const int v = g1 - P.off;
-        const int g2 = P.off + (v + 1 == P.n ? 0 : v + 1);
-        const double2 X1 = Xn[g1], X2 = Xn[g2];
+        g2 = P.off + (v + 1 == P.n ? 0 : v + 1);
+        X1 = Xn[g1];
+        X2 = Xn[g2];
         const double2 f1 = ftb[g1], f2 = ftb[g2];
-        const R Fb[2] = {R(0.5 * (f1.x + f2.x)), R(0.5 * (f1.y + f2.y))};
-        const double dx = X2.x - X1.x, dy = X2.y - X1.y, len = sqrt(dx * dx + dy * dy);
-        const double sg = s == 0 ? 1.2 : -1.2, sgn = s == 0 ? 1.0 : -1.0;
-        double Px = 0.5 * (X1.x + X2.x) + sg * dy / len, Py = 0.5 * (X1.y + X2.y) - sg * dx / len;
-        int cx, cy;
+        Fb[0] = R(0.5 * (f1.x + f2.x));
+        Fb[1] = R(0.5 * (f1.y + f2.y));
+        dx = X2.x - X1.x;
+        dy = X2.y - X1.y;
+        len = sqrt(dx * dx + dy * dy);
+        const double sg = s == 0 ? 1.2 : -1.2;
+        Px = 0.5 * (X1.x + X2.x) + sg * dy / len;
+        Py = 0.5 * (X1.y + X2.y) - sg * dx / len;
         ok = support_centre(L, Px, Py, cx, cy);
-        R drho[9], ux[9], uy[9];
-        long long cells[9];
-#pragma unroll
-        for (int b = 0; b < 3; b++)
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                const int k = 3 * b + a;
-                const int xk = wrapi(cx + a - 1, L.nx), yk = support_row(L, cy + b - 1);
-                cells[k] = (long long)yk * L.nx + xk;
-                double dr, u, w;
-                node_fields<S>(post1, L, fib, xk, yk, dr, u, w);
-                drho[k] = R(dr);
-                ux[k] = R(u);
-                uy[k] = R(w);
-            }
-        // end points relative to the support's centre node
-        const R r1x = R(X1.x - cx), r1y = R(X1.y - cy), r2x = R(X2.x - cx), r2y = R(X2.y - cy);
-        // positions: derivatives along the four end coordinates, in one pass
-        D4<R> c1x = d4<R>(r1x), c1y = d4<R>(r1y), c2x = d4<R>(r2x), c2y = d4<R>(r2y);
-        c1x.d[0] = c1y.d[1] = c2x.d[2] = c2y.d[3] = R(1);
-        const P2<D4<R>> F = probe_traction<D4<R>, R>(P2<D4<R>>{c1x, c1y}, P2<D4<R>>{c2x, c2y}, s, drho, ux, uy,
-                                                     R(L.nu));
-        double e[4];
-#pragma unroll
-        for (int j = 0; j < 4; j++) e[j] = (double)(Fb[0] * F.x.d[j] + Fb[1] * F.y.d[j]);
-        atomicAdd(&xout[g1].x, e[0]);
-        atomicAdd(&xout[g1].y, e[1]);
-        atomicAdd(&xout[g2].x, e[2]);
-        atomicAdd(&xout[g2].y, e[3]);
-        // fields: dT/drho and dT/dG contracted with F_l-bar
+        const int xk = wrapi(cx + k % 3 - 1, L.nx), yk = support_row(L, cy + k / 3 - 1);
+        cell = (long long)yk * L.nx + xk;
+        node_fields<S>(post1, L, fib, xk, yk, dr, u, w);
+        fld[0][grp][k] = R(dr);
+        fld[1][grp][k] = R(u);
+        fld[2][grp][k] = R(w);
+    }
+    __syncthreads();
+    if (act) {
+        const R* drho = fld[0][grp];
+        const R* ux = fld[1][grp];
+        const R* uy = fld[2][grp];
+        if (k < 4) {
+            // end points relative to the support's centre node; thread k differentiates
+            // along coordinate k of (X1.x, X1.y, X2.x, X2.y)
+            using D1 = DN<R, 1>;
+            const D1 c1x{R(X1.x - cx), {R(k == 0)}}, c1y{R(X1.y - cy), {R(k == 1)}};
+            const D1 c2x{R(X2.x - cx), {R(k == 2)}}, c2y{R(X2.y - cy), {R(k == 3)}};
+            const P2<D1> F = probe_traction<D1, R>(P2<D1>{c1x, c1y}, P2<D1>{c2x, c2y}, s, drho, ux, uy, R(L.nu));
+            const double e = (double)(Fb[0] * F.x.d[0] + Fb[1] * F.y.d[0]);
+            double* dst = k < 2 ? &xout[g1].x : &xout[g2].x;
+            atomicAdd(dst + (k & 1), e);
+        }
+        // fields: dT/drho and dT/dG contracted with F_l-bar, for this thread's node
+        const double sgn = s == 0 ? 1.0 : -1.0;
         const R nn[2] = {R(dy / len), R(-dx / len)};
         const R d0x = R(cx - Px), d0y = R(cy - Py);
         const ProbeVal<R> o = probe_eval<R, R>(d0x, d0y, drho, ux, uy);
@@ -928,17 +943,16 @@ __global__ void __launch_bounds__(32) k_adjd_tract(Lat L, Nodes nd, int count, c
         for (int a = 0; a < 2; a++)
             for (int b = 0; b < 2; b++) Gb[a][b] = lsg * o.rho * nu * (Fb[a] * nn[b] + Fb[b] * nn[a]);
         const Axis<R> ax = mls_axis<R>(d0x), ay = mls_axis<R>(d0y);
-#pragma unroll
-        for (int b = 0; b < 3; b++)
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                const int k = 3 * b + a;
-                const R phi = ax.h[a] * ay.q[b] + ax.q[a] * ay.h[b] - ax.q[a] * ay.q[b];
-                const R gx = ax.g[a] * ay.q[b], gy = ax.q[a] * ay.g[b];
-                inject_fields(L, cells[k], (double)(phi * rho_b), (double)(Gb[0][0] * gx + Gb[0][1] * gy),
-                              (double)(Gb[1][0] * gx + Gb[1][1] * gy), (double)ux[k], (double)uy[k],
-                              1.0 + (double)drho[k], sbar, bbar, gsx, gsy);
-            }
+        const int a = k % 3, b = k / 3;
+        // select rather than index with the thread's node (keeps the axes in registers)
+        auto pick = [](const R (&v)[3], int i) { return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]); };
+        const R qxa = pick(ax.q, a), hxa = pick(ax.h, a), gxa = pick(ax.g, a);
+        const R qyb = pick(ay.q, b), hyb = pick(ay.h, b), gyb = pick(ay.g, b);
+        const R phi = hxa * qyb + qxa * hyb - qxa * qyb;
+        const R gx = gxa * qyb, gy = qxa * gyb;
+        inject_fields(L, cell, (double)(phi * rho_b), (double)(Gb[0][0] * gx + Gb[0][1] * gy),
+                      (double)(Gb[1][0] * gx + Gb[1][1] * gy), (double)R(u), (double)R(w), 1.0 + (double)R(dr), sbar,
+                      bbar, gsx, gsy);
     }
     for (int o = 16; o > 0; o >>= 1) {
         gsx += __shfl_xor_sync(0xffffffffu, gsx, o);
@@ -948,7 +962,7 @@ __global__ void __launch_bounds__(32) k_adjd_tract(Lat L, Nodes nd, int count, c
         atomicAdd(grad_g, gsx);
         atomicAdd(grad_g + 1, gsy);
     }
-    if (!ok) atomicOr(status, kStatSupport);
+    if (!ok && k == 0) atomicOr(status, kStatSupport);
 }
 
 // Interpolation transpose (Eq. 8, Eq. 7 velocity) of U = I(s, fib, X^n) at every vertex
@@ -1271,6 +1285,15 @@ lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* 
     double2* u1b = (double2*)(w + a.u1b);
     double2* u2b = (double2*)(w + a.u2b);
     const int* age0 = (const int*)(w + a.age0);
+    // Three streams. The spread of step n-1 (taped positions and c_l F_l only) runs on a
+    // side stream beside this step's chain, except at the segment's first reverse step,
+    // whose own spread the chain needs; it waits for the previous reverse step, whose
+    // lattice transpose clears the buffer it writes, and the second interpolation
+    // transpose, which reads it, waits for it. The traction transpose and the first
+    // interpolation transpose only add into the same adjoint buffers and run side by
+    // side; the lattice transpose waits for both.
+    cudaStream_t s2 = c->ib_stream, s3 = c->aux_stream;
+    cudaEvent_t ev_prev = c->ev_adj[0], ev_spr = c->ev_adj[1], ev_upd = c->ev_adj[2], ev_int = c->ev_adj[3];
     for (int k = len - 1; k >= 0; k--) {
         const long long n = n0 + k;
         const int par = (int)(n & 1);
@@ -1287,18 +1310,31 @@ lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* 
         double2* xc = (double2*)(w + a.xb[1 - par]);
         double2* xout = (double2*)(w + a.xb[par]);
         Shape* shp = shps[par];
+        const bool first = k == len - 1, side = !first && k > 0;
         if (ncaps > 0) {
-            k_adjd_spread<<<ncaps, 128, 0, s>>>(L, c->nd, c->max_n, Xn, k > 0 ? Xn - M : nullptr,
-                                                flc + (size_t)k * M, k > 0 ? flc + (size_t)(k - 1) * M : nullptr,
-                                                k == len - 1 ? fib_n : nullptr, k > 0 ? fib_p : nullptr, shp,
-                                                shps[1 - par], k == len - 1);
+            if (first || side) {
+                cudaStream_t q = first ? s : s2;
+                if (side) {
+                    cudaEventRecord(ev_prev, s);
+                    cudaStreamWaitEvent(s2, ev_prev, 0);
+                }
+                k_adjd_spread<<<ncaps, 128, 0, q>>>(L, c->nd, c->max_n, Xn, k > 0 ? Xn - M : nullptr,
+                                                    flc + (size_t)k * M, k > 0 ? flc + (size_t)(k - 1) * M : nullptr,
+                                                    first ? fib_n : nullptr, k > 0 ? fib_p : nullptr, shp,
+                                                    shps[1 - par], first);
+                if (side) cudaEventRecord(ev_spr, s2);
+            }
             k_adjd_update<<<ncaps, 128, smem, s>>>(c->nd, c->max_n, Xn, xc, xm, ub, xout, u2b,
                                                    (double2*)(w + a.ftb), ncaps, grad);
-            k_adjd_tract<S><<<nblk(2LL * count, 32), 32, 0, s>>>(L, c->nd, count, Xn, post1, fib_n,
-                                                                 (const double2*)(w + a.ftb), xout, sb_in, b_n,
-                                                                 grad + 2 * ncaps, &c->ctr->status);
-            k_adjd_interp<S><<<nblk(9LL * count, 288), 288, 0, s>>>(L, post1, fib_n, shp, count, u2b, xout, sb_in,
-                                                                    b_n, grad + 2 * ncaps);
+            cudaEventRecord(ev_upd, s);
+            cudaStreamWaitEvent(s3, ev_upd, 0);
+            k_adjd_interp<S><<<nblk(9LL * count, 288), 288, 0, s3>>>(L, post1, fib_n, shp, count, u2b, xout, sb_in,
+                                                                     b_n, grad + 2 * ncaps);
+            cudaEventRecord(ev_int, s3);
+            k_adjd_tract<S><<<nblk(2LL * count, kTractGroups), 9 * kTractGroups, 0, s>>>(
+                L, c->nd, count, Xn, post1, fib_n, (const double2*)(w + a.ftb), xout, sb_in, b_n, grad + 2 * ncaps,
+                &c->ctr->status);
+            cudaStreamWaitEvent(s, ev_int, 0);
         }
         k_adj_lattice<S><<<nblk(N, 256), 256, 0, s>>>(post0, L, sb_in, sb_out, fbar, fib_n,
                                                        (double*)(w + a.fib[r3(n + 1)]),
@@ -1306,6 +1342,7 @@ lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* 
         if (ncaps > 0) {
             k_adjd_forcing<<<ncaps, 128, smem, s>>>(L, c->nd, c->max_n, Xn, flc + (size_t)k * M, shp, fbar, b_n,
                                                     age0, k, xout, xm, ub, u1b);
+            if (side) cudaStreamWaitEvent(s, ev_spr, 0);
             k_adjd_interp<S><<<nblk(9LL * count, 288), 288, 0, s>>>(L, post0, fib_p, shp, count, u1b, xout, sb_out,
                                                                     b_p, grad + 2 * ncaps);
         }

@@ -234,8 +234,9 @@ lbmib_status device_status(lbmib_ctx* c) {
 namespace {
 
 // Arcs per capsule: one CTA per capsule while the capsules fill the multiprocessors;
-// with fewer capsules, up to kMaxArcs CTAs per capsule (at least 32 vertices each) so
-// that the capsule kernels still spread over the GPU. Then the tile budget for arcs of
+// with fewer capsules, up to kMaxArcs CTAs per capsule (at least 16 vertices each) so
+// that the capsule kernels still spread over the GPU (measured on a 128-vertex ring:
+// 1, 2, 4, 8 arcs give 61, 49, 41, 39 us per Dynamic step). Then the tile budget for arcs of
 // the longest reference arc (1.5 x for stretching), capped by the capsule diameter; a
 // box that outgrows it takes the global path, with the same results.
 void update_arcs(lbmib_ctx* c) {
@@ -243,7 +244,7 @@ void update_arcs(lbmib_ctx* c) {
     int a = c->arcs_opt;
     if (a == 0) {
         const int sms = c->sms > 0 ? c->sms : 1;
-        a = ncaps == 0 || ncaps >= sms ? 1 : std::min({kMaxArcs, sms / ncaps, (c->max_n + 31) / 32});
+        a = ncaps == 0 || ncaps >= sms ? 1 : std::min({kMaxArcs, sms / ncaps, (c->max_n + 15) / 16});
         a = std::max(a, 1);
     }
     auto arc_of = [a](const CapsuleParams& P) {
@@ -408,7 +409,9 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->ib_stream, cudaStreamNonBlocking);
-    for (cudaEvent_t* ev : {&c->ev_fork, &c->ev_spread, &c->ev_patch, &c->ev_join})
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&c->ev_fork, &c->ev_spread, &c->ev_patch, &c->ev_join, &c->ev_adj[0], &c->ev_adj[1],
+                            &c->ev_adj[2], &c->ev_adj[3]})
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         lbmib_destroy(c);
@@ -447,11 +450,13 @@ void lbmib_destroy(lbmib_ctx* c) {
         cudaEventDestroy(p.second);
     }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    if (c->ib_stream) {
-        cudaStreamSynchronize(c->ib_stream);
-        cudaStreamDestroy(c->ib_stream);
-    }
-    for (cudaEvent_t ev : {c->ev_fork, c->ev_spread, c->ev_patch, c->ev_join})
+    for (cudaStream_t* q : {&c->ib_stream, &c->aux_stream})
+        if (*q) {
+            cudaStreamSynchronize(*q);
+            cudaStreamDestroy(*q);
+        }
+    for (cudaEvent_t ev : {c->ev_fork, c->ev_spread, c->ev_patch, c->ev_join, c->ev_adj[0], c->ev_adj[1],
+                           c->ev_adj[2], c->ev_adj[3]})
         if (ev) cudaEventDestroy(ev);
     delete c;
 }
