@@ -1084,8 +1084,8 @@ struct AdjLayout {
     int K = 0, nseg = 0;
     size_t pb = 0, ckpt = 0;
     size_t tape_pops = 0, tape_X = 0, tape_flc = 0, tape_fib0 = 0, age0 = 0, ckpts = 0, sbar[2]{}, fbar = 0,
-           fib[3]{}, bbar[3]{}, xc = 0, xp = 0, xnew = 0, xb[2]{}, ub = 0, u1b = 0, u2b = 0, ftb = 0, fv = 0, shp = 0,
-           shp1 = 0, grad = 0, J = 0, total = 0;
+           fib[3]{}, bbar[3]{}, xc = 0, xp = 0, xnew = 0, xb[2]{}, ub = 0, u1b = 0, u2b = 0, ftb = 0, fv = 0, fv1 = 0,
+           shp = 0, shp1 = 0, grad = 0, J = 0, total = 0;
 };
 
 // The adjoint fields (population and force adjoints) are double in every storage mode:
@@ -1127,8 +1127,9 @@ AdjLayout adj_layout(const lbmib_ctx* c, long long T, int K) {
     a.xp = take(M * sizeof(double2));
     a.xnew = take(M * sizeof(double2));
     a.fv = take(M * sizeof(double2));
+    a.fv1 = take(M * sizeof(double2));   // Kinematic: forces of the other step parity
     a.shp = take(M * sizeof(Shape));
-    a.shp1 = take(M * sizeof(Shape));   // Dynamic: shapes of the other step parity
+    a.shp1 = take(M * sizeof(Shape));    // shapes of the other step parity
     a.grad = take((2 * c->caps.size() + 2) * sizeof(double));
     a.J = take(sizeof(double));
     a.total = o;
@@ -1223,9 +1224,15 @@ lbmib_status tape_forward(lbmib_ctx* c, lbmib_scheme scheme, int len, char* w, c
 }
 
 // Reverse sweep of one taped segment: global steps n0 + len - 1 down to n0.
+// The spread of step n (membrane forces, shapes and spread at the taped X^n) depends on
+// the tape alone, so while step n's interpolation, lattice and membrane transposes run,
+// a side stream already spreads step n-1 into the other parity's forces and shapes and
+// the third force buffer (cleared by step n+1's lattice transpose, whose completion it
+// waits for); step n-1 waits for it before its interpolation transpose.
 template <typename S>
 lbmib_status reverse_segment(lbmib_ctx* c, long long n0, int len, char* w, const AdjLayout& a) {
-    cudaStream_t s = c->stream;
+    cudaStream_t s = c->stream, s2 = c->ib_stream;
+    cudaEvent_t ev_prev = c->ev_adj[0], ev_spr = c->ev_adj[1];
     const Lat& L = c->L;
     const int ncaps = (int)c->caps.size();
     const int count = c->nd.count;
@@ -1233,33 +1240,47 @@ lbmib_status reverse_segment(lbmib_ctx* c, long long n0, int len, char* w, const
     const long long N = (long long)L.nx * L.ny;
     const size_t smem = ring_smem_bytes(c->max_n);
     double* grad = (double*)(w + a.grad);
+    auto r3 = [](long long n) { return (int)(((n % 3) + 3) % 3); };
+    double2* Fvs[2] = {(double2*)(w + a.fv), (double2*)(w + a.fv1)};     // forces at X^m in Fvs[m & 1]
+    Shape* shps[2] = {(Shape*)(w + a.shp), (Shape*)(w + a.shp1)};       // shapes at X^m in shps[m & 1]
+    auto spread = [&](long long m, int km, cudaStream_t q) {
+        const double2* Xm = (const double2*)(w + a.tape_X) + (size_t)km * M;
+        k_adj_spread<<<ncaps, 128, smem, q>>>(L, c->nd, Xm, c->max_n, Fvs[m & 1], shps[m & 1],
+                                              (double*)(w + a.fib[r3(m)]));
+    };
     for (int k = len - 1; k >= 0; k--) {
-        const int par = (int)((n0 + k) & 1);
+        const long long n = n0 + k;
+        const int par = (int)(n & 1);
         const S* post0 = (const S*)(w + a.tape_pops + (size_t)k * a.pb);
         const S* post1 = (const S*)(w + a.tape_pops + (size_t)(k + 1) * a.pb);
         const double2* Xn = (const double2*)(w + a.tape_X) + (size_t)k * M;
-        double* fib = (double*)(w + a.fib[par]);
+        double* fib = (double*)(w + a.fib[r3(n)]);
         double* bbar = (double*)(w + a.bbar[par]);
         double* sb_in = (double*)(w + a.sbar[1 - par]);
         double* sb_out = (double*)(w + a.sbar[par]);
         double* fbar = (double*)(w + a.fbar);
-        double2* Fv = (double2*)(w + a.fv);
         double2* xc = (double2*)(w + a.xc);
         double2* xp = (double2*)(w + a.xp);
-        Shape* shp = (Shape*)(w + a.shp);
         double2* xnew = (double2*)(w + a.xnew);
         if (ncaps > 0) {
-            k_adj_spread<<<ncaps, 128, smem, s>>>(L, c->nd, Xn, c->max_n, Fv, shp, fib);
-            k_adj_interp<S><<<nblk(9LL * count, 288), 288, 0, s>>>(L, post1, fib, shp, (const int*)(w + a.age0), k,
-                                                                   count, xc, xp, xnew, sb_in, bbar,
-                                                                   grad + 2 * ncaps, &c->ctr->status);
+            if (k == len - 1) spread(n, k, s);            // the segment's first reverse step
+            else cudaStreamWaitEvent(s, ev_spr, 0);       // spread on the side stream last step
+            if (k > 0) {
+                cudaEventRecord(ev_prev, s);
+                cudaStreamWaitEvent(s2, ev_prev, 0);
+                spread(n - 1, k - 1, s2);
+                cudaEventRecord(ev_spr, s2);
+            }
+            k_adj_interp<S><<<nblk(9LL * count, 288), 288, 0, s>>>(L, post1, fib, shps[par],
+                                                                   (const int*)(w + a.age0), k, count, xc, xp, xnew,
+                                                                   sb_in, bbar, grad + 2 * ncaps, &c->ctr->status);
         }
         k_adj_lattice<S><<<nblk(N, 256), 256, 0, s>>>(post0, L, sb_in, sb_out, fbar, fib,
-                                                       (double*)(w + a.fib[1 - par]),
+                                                       (double*)(w + a.fib[r3(n + 1)]),
                                                        (double*)(w + a.bbar[1 - par]), grad + 2 * ncaps);
         if (ncaps > 0)
-            k_adj_membrane<<<ncaps, 128, smem, s>>>(L, c->nd, Xn, c->max_n, Fv, shp, fbar, bbar, xnew, xc,
-                                                       ncaps, grad);
+            k_adj_membrane<<<ncaps, 128, smem, s>>>(L, c->nd, Xn, c->max_n, Fvs[par], shps[par], fbar, bbar, xnew,
+                                                       xc, ncaps, grad);
         c->launches += ncaps > 0 ? 4 : 1;
         LBMIB_CUDA(c, cudaGetLastError());
     }
