@@ -129,6 +129,10 @@ def _declare(L):
                                  C.c_double, C.c_double, C.POINTER(C.POINTER(C.c_double))]),
         "orc_sim_set_repulsion": (None, [vp, C.c_double, C.c_double]),
         "orc_sim_read_repulsion": (C.c_int, [vp, C.c_int, _dp]),
+        "orc_sim_add_rigid": (C.c_int, [vp, _dp, C.c_int, C.c_double, C.c_double]),
+        "orc_sim_read_rigid": (C.c_int, [vp, C.c_int, _dp]),
+        "orc_rigid_load": (C.c_int, [_LP, _dp, vp, _dp, C.c_int, C.c_double, C.c_double, _dp, vp]),
+        "orc_rigid_advance": (None, [_dp, _dp, _dp, C.c_double, C.c_double]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -276,6 +280,23 @@ def dynamic_advance(X, Xm1, xdot0, Ftot, m):
     return Xn, uv
 
 
+def rigid_load(L: Lattice, f: np.ndarray, fib: Optional[np.ndarray], xy, cx: float, cy: float):
+    """Eq. 17-18 load on a rigid ring about (cx, cy): ((F_x, F_y, M), status)."""
+    xy = _f64(xy).reshape(-1)
+    out = np.zeros(3)
+    fib = None if fib is None else _f64(fib)
+    st = lib().orc_rigid_load(C.byref(L), _f64(f), _ptr(fib), xy, xy.size // 2, float(cx), float(cy), out, None)
+    return out, st
+
+
+def rigid_advance(body, prev, load, mass: float, inertia: float):
+    """Eq. 19-20 (reading R29) on body = (c_x, c_y, theta, u_x, u_y, omega) at n and prev at
+    n - 1: returns (body at n + 1, body at n)."""
+    b = _f64(body).copy(); p = _f64(prev).copy()
+    lib().orc_rigid_advance(b, p, _f64(load), float(mass), float(inertia))
+    return b, p
+
+
 # ----------------------------------------------------------------------------------
 # Whole simulation
 # ----------------------------------------------------------------------------------
@@ -377,6 +398,22 @@ class Sim:
     def set_repulsion(self, rc: float, coeff: float = REPULSION_COEFF):
         """Capsule-capsule repulsion (Eq. 27) with cut-off rc (0: off)."""
         lib().orc_sim_set_repulsion(self._h, rc, coeff)
+
+    def add_rigid(self, xy, mass, inertia) -> int:
+        """Rigid particle (readings R27-R30) with its ring, mass and moment of inertia about
+        the area centroid; at rest. Dynamic scheme only."""
+        xy = _f64(xy).reshape(-1)
+        n = xy.size // 2
+        cid = lib().orc_sim_add_rigid(self._h, xy, n, float(mass), float(inertia))
+        self._n.append(n)
+        return cid
+
+    def read_rigid(self, cid: int) -> np.ndarray:
+        """(c_x, c_y, theta, u_x, u_y, omega, F_x, F_y, M) of rigid particle cid."""
+        out = np.zeros(9)
+        if lib().orc_sim_read_rigid(self._h, cid, out):
+            raise ValueError("not a rigid particle")
+        return out
 
     def read_repulsion(self, cid: int) -> np.ndarray:
         out = np.zeros(2 * self._n[cid])

@@ -59,6 +59,21 @@
  *       wall-crossing populations are bounced back first). Supports of markers and
  *       probes must stay inside columns 1 .. nx - 2, so the open columns carry only the
  *       uniform force g; distances along x are not periodic.
+ *   R27 Rigid particle (Section 2.3.1): a ring of markers fixed in the body frame, X_v =
+ *       c + R(theta) r_v with c the area centroid of the initial ring and r_v = X_v^0 -
+ *       c^0. In the Dynamic coupling (Section 2.3.2 steps 1-3) its markers' desired
+ *       velocity is the rigid-body velocity u + omega x (X_v - c).
+ *   R28 Eq. 17-18: the fluid load is the outer probes' traction (tau+ . n+ - p+ n+) l_l of
+ *       every element (no inner fluid), evaluated at X^n after the fluid update (as R11),
+ *       with the lever arm r_l from c to the element centroid; the Eq. 27 repulsion on the
+ *       markers (when on) adds its sum and moment.
+ *   R29 Eq. 19-20 with u(t) -> u^{n+1}, u(t - dt) -> u^n, u(t - 2 dt) -> u^{n-1} and the
+ *       acceleration of the current load; the paper prints no position update, so c and
+ *       theta take the same second-order backward form as Eq. 24-25:
+ *       c^{n+1} = 2/3 (2 c^n - c^{n-1}/2 + u^{n+1} dt), likewise theta. At rest history
+ *       (u^{-1} = u^0, c^{-1} = c^0 - u^0 dt, theta^{-1} = theta^0 - omega^0 dt).
+ *   R30 Rigid particles exist only in the Dynamic scheme (the Kinematic scheme moves
+ *       markers with the fluid); a Kinematic step with one present is refused.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -66,6 +81,7 @@
 
 #define ORC_OK 0
 #define ORC_ERR_SUPPORT 5
+#define ORC_ERR_STATE 7
 
 /* ---------------------------------------------------------------------------------- */
 /* D2Q9 velocity set (Eq. 3) and weights (Section 2.1).                                  */
@@ -608,6 +624,11 @@ typedef struct {
     double *X, *Xm1, *uv, *Fint, *Fext, *Fpp, *L0, *th0;
     double A0, P0;
     int age;
+    /* rigid particle (R27-R30): body state {c_x, c_y, theta, u_x, u_y, omega} at n and
+     * at n - 1, mass, moment of inertia, reference offsets r_v, last load {F_x, F_y, M} */
+    int rigid;
+    double body[6], prev[6], mass, inertia, load[3];
+    double* R0;
 } orc_capsule;
 
 typedef struct {
@@ -663,7 +684,7 @@ void orc_sim_destroy(orc_sim* s) {
     for (int c = 0; c < s->ncaps; c++) {
         orc_capsule* k = &s->caps[c];
         free(k->X); free(k->Xm1); free(k->uv); free(k->Fint); free(k->Fext); free(k->Fpp);
-        free(k->L0); free(k->th0);
+        free(k->L0); free(k->th0); free(k->R0);
     }
     free(s->caps);
     free(s->f); free(s->fnew); free(s->fib); free(s->fibnew);
@@ -703,9 +724,55 @@ int orc_sim_add_capsule(orc_sim* s, const double* xy, int n, double ks, double k
     return s->ncaps++;
 }
 
+/* Markers of a rigid ring from its body state: X_v = c + R(theta) r_v; velocities
+ * u + omega x (X_v - c). */
+static void rigid_markers(orc_capsule* k) {
+    const double c = cos(k->body[2]), sn = sin(k->body[2]);
+    for (int v = 0; v < k->n; v++) {
+        double rx = c * k->R0[2 * v] - sn * k->R0[2 * v + 1];
+        double ry = sn * k->R0[2 * v] + c * k->R0[2 * v + 1];
+        k->X[2 * v] = k->body[0] + rx;
+        k->X[2 * v + 1] = k->body[1] + ry;
+        k->uv[2 * v] = k->body[3] - k->body[5] * ry;
+        k->uv[2 * v + 1] = k->body[4] + k->body[5] * rx;
+    }
+}
+
+/* Add a rigid particle (R27): ring xy (counter-clockwise), mass and moment of inertia
+ * about its area centroid; at rest. Returns its id. */
+int orc_sim_add_rigid(orc_sim* s, const double* xy, int n, double mass, double inertia) {
+    const int id = orc_sim_add_capsule(s, xy, n, 0.0, 0.0, 0.0, mass / n);
+    orc_capsule* k = &s->caps[id];
+    double o[8];
+    orc_observables(xy, n, o);   /* area centroid in o[3], o[4] */
+    k->rigid = 1;
+    k->mass = mass;
+    k->inertia = inertia;
+    k->R0 = (double*)malloc(2 * n * sizeof(double));
+    for (int v = 0; v < n; v++) {
+        k->R0[2 * v] = xy[2 * v] - o[3];
+        k->R0[2 * v + 1] = xy[2 * v + 1] - o[4];
+    }
+    for (int a = 0; a < 6; a++) k->body[a] = k->prev[a] = 0.0;
+    k->body[0] = k->prev[0] = o[3];
+    k->body[1] = k->prev[1] = o[4];
+    rigid_markers(k);
+    return id;
+}
+
+/* Body state of rigid particle id: {c_x, c_y, theta, u_x, u_y, omega, F_x, F_y, M} (the
+ * last load). Returns 1 if id is not a rigid particle. */
+int orc_sim_read_rigid(orc_sim* s, int id, double out[9]) {
+    if (id < 0 || id >= s->ncaps || !s->caps[id].rigid) return 1;
+    orc_capsule* k = &s->caps[id];
+    for (int a = 0; a < 6; a++) out[a] = k->body[a];
+    for (int a = 0; a < 3; a++) out[6 + a] = k->load[a];
+    return 0;
+}
+
 /* Start a capsule from positions other than its stress-free shape (X^n = X^{n-1} = xy). */
 int orc_sim_set_capsule_positions(orc_sim* s, int id, const double* xy) {
-    if (id < 0 || id >= s->ncaps) return 1;
+    if (id < 0 || id >= s->ncaps || s->caps[id].rigid) return 1;
     orc_capsule* k = &s->caps[id];
     memcpy(k->X, xy, 2 * k->n * sizeof(double));
     memcpy(k->Xm1, xy, 2 * k->n * sizeof(double));
@@ -801,6 +868,60 @@ int orc_tractions(const orc_lattice* L, const double* f, const double* fib, cons
     return st;
 }
 
+/* Fluid load on a rigid ring of n vertices about c (Eq. 17-18, reading R28): for every
+ * element the outer probe's traction (tau+ . n+ - p+ n+) l_l, summed (F_x, F_y) and its
+ * moment (r_l x f_l) about c, into load[3]. fext (may be NULL) gets half of each
+ * element's force at each end vertex. */
+int orc_rigid_load(const orc_lattice* L, const double* f, const double* fib, const double* X, int n,
+                   double cx, double cy, double load[3], double* fext) {
+    int st = ORC_OK;
+    double nu = (L->tau - 0.5) / 3.0;
+    load[0] = load[1] = load[2] = 0.0;
+    if (fext) for (int m = 0; m < 2 * n; m++) fext[m] = 0.0;
+    for (int l = 0; l < n; l++) {
+        int v1 = l, v2 = (l + 1) % n;
+        double dx = X[2 * v2] - X[2 * v1], dy = X[2 * v2 + 1] - X[2 * v1 + 1];
+        double len = hypot(dx, dy);
+        double npx = dy / len, npy = -dx / len;   /* outward normal (R7) */
+        double mx = 0.5 * (X[2 * v1] + X[2 * v2]), my = 0.5 * (X[2 * v1 + 1] + X[2 * v2 + 1]);
+        double op[8];
+        if (orc_interp(L, f, fib, mx + 1.2 * npx, my + 1.2 * npy, op)) st = ORC_ERR_SUPPORT;
+        double g[2][2] = {{op[4], op[5]}, {op[6], op[7]}}, t[2][2];
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2; b++) t[a][b] = op[2] * nu * (g[a][b] + g[b][a]);
+        /* Eq. 17 term of element l */
+        double fx = (t[0][0] * npx + t[0][1] * npy - op[3] * npx) * len;
+        double fy = (t[1][0] * npx + t[1][1] * npy - op[3] * npy) * len;
+        load[0] += fx;
+        load[1] += fy;
+        /* Eq. 18 term: r_l x f_l, r_l from c to the element centroid */
+        load[2] += (mx - cx) * fy - (my - cy) * fx;
+        if (fext) {
+            fext[2 * v1] += 0.5 * fx; fext[2 * v1 + 1] += 0.5 * fy;
+            fext[2 * v2] += 0.5 * fx; fext[2 * v2 + 1] += 0.5 * fy;
+        }
+    }
+    return st;
+}
+
+/* One rigid-body update (Eq. 19-20, reading R29). body = {c_x, c_y, theta, u_x, u_y,
+ * omega} at n, prev the same at n - 1; acceleration from load = {F_x, F_y, M} over mass
+ * and inertia. On return body holds n + 1 and prev n. */
+void orc_rigid_advance(double body[6], double prev[6], const double load[3], double mass, double inertia) {
+    const double acc[3] = {load[0] / mass, load[1] / mass, load[2] / inertia};
+    double next[6];
+    for (int a = 0; a < 3; a++) {
+        /* Eq. 19 (a = 0, 1) and Eq. 20 (a = 2) */
+        next[3 + a] = (2.0 / 3.0) * (2.0 * body[3 + a] - 0.5 * prev[3 + a] + acc[a]);
+        /* position and angle: the same backward form (R29) */
+        next[a] = (2.0 / 3.0) * (2.0 * body[a] - 0.5 * prev[a] + next[3 + a]);
+    }
+    for (int a = 0; a < 6; a++) {
+        prev[a] = body[a];
+        body[a] = next[a];
+    }
+}
+
 /* Dynamic IB, steps 1-8 (Section 2.3.2). */
 static void dynamic_step(orc_sim* s) {
     orc_lattice* L = &s->L;
@@ -816,7 +937,11 @@ static void dynamic_step(orc_sim* s) {
             double o[8];
             if (orc_interp(L, s->f, s->fib, k->X[2 * v], k->X[2 * v + 1], o))
                 s->status = ORC_ERR_SUPPORT;
-            if (k->age == 0) {
+            if (k->rigid) {
+                /* desired velocity: the rigid-body motion (R27) */
+                k->uv[2 * v] = k->body[3] - k->body[5] * (k->X[2 * v + 1] - k->body[1]);
+                k->uv[2 * v + 1] = k->body[4] + k->body[5] * (k->X[2 * v] - k->body[0]);
+            } else if (k->age == 0) {
                 /* start-up: node velocity = fluid velocity, X^{-1} = X^0 - u_v^0 */
                 k->uv[2 * v] = o[0];
                 k->uv[2 * v + 1] = o[1];
@@ -840,10 +965,25 @@ static void dynamic_step(orc_sim* s) {
     orc_collide_stream(L, s->f, s->fibnew, s->fnew);
     swap_ptr(&s->f, &s->fnew);
     swap_ptr(&s->fib, &s->fibnew);
-    /* 7-8: total force and Verlet update */
+    /* 7-8: total force and Verlet update (rigid particles: Eq. 17-20) */
     for (int c = 0; c < s->ncaps; c++) {
         orc_capsule* k = &s->caps[c];
         int n = k->n;
+        if (k->rigid) {
+            if (orc_rigid_load(L, s->f, s->fib, k->X, n, k->body[0], k->body[1], k->load, k->Fext))
+                s->status = ORC_ERR_SUPPORT;
+            for (int v = 0; v < n; v++) {   /* Eq. 27 on the markers (R28) */
+                k->load[0] += k->Fpp[2 * v];
+                k->load[1] += k->Fpp[2 * v + 1];
+                k->load[2] += (k->X[2 * v] - k->body[0]) * k->Fpp[2 * v + 1] -
+                              (k->X[2 * v + 1] - k->body[1]) * k->Fpp[2 * v];
+            }
+            orc_rigid_advance(k->body, k->prev, k->load, k->mass, k->inertia);
+            memcpy(k->Xm1, k->X, 2 * n * sizeof(double));
+            rigid_markers(k);
+            k->age++;
+            continue;
+        }
         double* xdot0 = (double*)malloc(2 * n * sizeof(double));
         double* Ftot = (double*)malloc(2 * n * sizeof(double));
         double* Xnew = (double*)malloc(2 * n * sizeof(double));
@@ -869,6 +1009,9 @@ static void dynamic_step(orc_sim* s) {
 
 /* scheme: 0 = Kinematic, 1 = Dynamic. Returns the sticky status. */
 int orc_sim_step(orc_sim* s, long long nsteps, int scheme) {
+    if (scheme == 0)
+        for (int c = 0; c < s->ncaps; c++)
+            if (s->caps[c].rigid) return ORC_ERR_STATE;   /* R30 */
     for (long long t = 0; t < nsteps; t++) {
         if (scheme == 0) kinematic_step(s);
         else dynamic_step(s);
