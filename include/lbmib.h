@@ -103,6 +103,27 @@ lbmib_status lbmib_init_fields(lbmib_ctx* ctx, const double* rho, const double* 
 lbmib_status lbmib_add_capsule(lbmib_ctx* ctx, const double* xy, int n, double k_s,
                                double k_b, double k_a, double node_mass, int* id_out);
 
+/* Add a rigid particle (Section 2.3.1): xy (2n doubles, host, counter-clockwise) is its
+ * ring of markers, fixed in the body frame about the ring's area centroid c; mass and
+ * inertia (moment of inertia about c) are > 0; it starts at rest. It moves only with
+ * the Dynamic scheme: its markers' desired velocity is the rigid-body velocity
+ * u + omega x (X - c) (steps 1-3); after the fluid update the load of the outer probes,
+ * F = sum_l (tau+ . n+ - p+ n+) l_l (Eq. 17) and M = sum_l r_l x that (Eq. 18, r_l from c
+ * to the element centroid), plus the Eq. 27 repulsion on its markers when on, drives
+ * u and omega by Eq. 19-20, and c and the angle by the same second-order backward
+ * formula. lbmib_step with the Kinematic scheme then fails with LBMIB_ERR_STATE, and
+ * lbmib_adjoint does not cover it. Shares the capsule capacity and ids with
+ * lbmib_add_capsule; its vertex data read through lbmib_read_capsule (velocities: the
+ * rigid-body motion; internal forces zero; external forces half of each element's
+ * outer traction at each end). *id_out gets its id. */
+lbmib_status lbmib_add_rigid(lbmib_ctx* ctx, const double* xy, int n, double mass, double inertia,
+                             int* id_out);
+
+/* Body state of rigid particle id (9 doubles, host): c_x, c_y, rotation angle, u_x, u_y,
+ * omega, and the last load F_x, F_y, M. Synchronises. LBMIB_ERR_ARG if id is not a rigid
+ * particle. */
+lbmib_status lbmib_read_rigid(lbmib_ctx* ctx, int id, double* out);
+
 /* Move capsule id to positions xy (2n doubles, host) without changing its stress-free
  * shape; its time history restarts (the next step is a start-up step). */
 lbmib_status lbmib_set_capsule_positions(lbmib_ctx* ctx, int id, const double* xy);

@@ -1394,6 +1394,8 @@ lbmib_status lbmib_adjoint(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme, 
         return fail(c, LBMIB_ERR_STATE, "lbmib_adjoint: the reverse sweep does not cover the capsule repulsion");
     if (c->L.inflow)
         return fail(c, LBMIB_ERR_STATE, "lbmib_adjoint: the reverse sweep does not cover the open-channel boundaries");
+    if (c->nrigid > 0)
+        return fail(c, LBMIB_ERR_STATE, "lbmib_adjoint: the reverse sweep does not cover rigid particles");
     const AdjLayout a = adj_layout(c, nsteps, ckpt_every);
     if (work_bytes < a.total) return fail(c, LBMIB_ERR_OOM, "lbmib_adjoint: workspace too small");
     lbmib_status st = device_status(c);

@@ -72,6 +72,8 @@ Layout make_layout(const lbmib_config* c) {
     L.pts = take(M * sizeof(double2));
     L.pts_out = take(8 * M * sizeof(double));
     L.u_in = take((size_t)c->ny * sizeof(double));
+    L.rb = take(K * sizeof(RigidBody));
+    L.R0 = take(M * sizeof(double2));
     L.total = o;
     return L;
 }
@@ -151,11 +153,11 @@ void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
     if (ncaps > 0) {
         if (scheme == LBMIB_DYNAMIC) {
             if (st == LBMIB_FP64)
-                launch_dyn_force_spread<double>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, sp, status, s);
+                launch_dyn_force_spread<double>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, c->nrigid > 0, sp, status, s);
             else if (st == LBMIB_FP32)
-                launch_dyn_force_spread<float>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, sp, status, s);
+                launch_dyn_force_spread<float>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, c->nrigid > 0, sp, status, s);
             else
-                launch_dyn_force_spread<__half>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, sp, status, s);
+                launch_dyn_force_spread<__half>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, c->nrigid > 0, sp, status, s);
         } else {
             launch_kin_force_spread(L, c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, sp, status, st == LBMIB_FP64, s);
         }
@@ -181,9 +183,9 @@ void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
     c->launches++;
     if (timed) cudaEventRecord(e1, s_lat);
     if (L.inflow) {   // open channel: the inlet and outlet columns, over the lattice kernel's output
-        if (st == LBMIB_FP64) launch_open_columns<double>(src, dst, L, status, s_lat);
-        else if (st == LBMIB_FP32) launch_open_columns<float>(src, dst, L, status, s_lat);
-        else launch_open_columns<__half>(src, dst, L, status, s_lat);
+        if (st == LBMIB_FP64) launch_open_columns<double>(src, dst, L, c->open, status, s_lat);
+        else if (st == LBMIB_FP32) launch_open_columns<float>(src, dst, L, c->open, status, s_lat);
+        else launch_open_columns<__half>(src, dst, L, c->open, status, s_lat);
         c->launches++;
     }
     if (ncaps > 0) {
@@ -201,9 +203,9 @@ void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
         }
         int* reset = &c->ctr->count[fp];
         if (scheme == LBMIB_DYNAMIC) {
-            if (st == LBMIB_FP64) launch_dyn_update<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, reset, status, s);
-            else if (st == LBMIB_FP32) launch_dyn_update<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, reset, status, s);
-            else launch_dyn_update<__half>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, reset, status, s);
+            if (st == LBMIB_FP64) launch_dyn_update<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, c->nrigid > 0, reset, status, s);
+            else if (st == LBMIB_FP32) launch_dyn_update<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, c->nrigid > 0, reset, status, s);
+            else launch_dyn_update<__half>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, c->nrigid > 0, reset, status, s);
         } else {
             if (st == LBMIB_FP64) launch_kin_advance<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, reset, status, s);
             else if (st == LBMIB_FP32) launch_kin_advance<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, reset, status, s);
@@ -368,6 +370,8 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     c->nd.capid = (int*)(a + lay.capid);
     c->nd.mls = a + lay.mls;
     c->nd.Fpp = nullptr;   // set while repulsion is on
+    c->nd.rb = (RigidBody*)(a + lay.rb);
+    c->nd.R0 = (double2*)(a + lay.R0);
     c->rep.count = (int*)(a + lay.rep_count);
     c->rep.slot = (int*)(a + lay.rep_slot);
     c->rep.cellof = (int*)(a + lay.rep_cellof);
@@ -552,12 +556,62 @@ lbmib_status lbmib_add_capsule(lbmib_ctx* c, const double* xy, int n, double ks,
     return LBMIB_OK;
 }
 
+lbmib_status lbmib_add_rigid(lbmib_ctx* c, const double* xy, int n, double mass, double inertia, int* id_out) {
+    if (!c) return LBMIB_ERR_ARG;
+    if (!xy || n < 3 || n > kMaxRing || !(mass > 0.0) || !(inertia > 0.0))
+        return fail(c, LBMIB_ERR_ARG, "bad rigid particle arguments");
+    // area centroid (shoelace, about the first vertex)
+    double A2 = 0.0, sx = 0.0, sy = 0.0;
+    for (int v = 0; v < n; v++) {
+        const int r = v + 1 == n ? 0 : v + 1;
+        const double ax = xy[2 * v] - xy[0], ay = xy[2 * v + 1] - xy[1];
+        const double bx = xy[2 * r] - xy[0], by = xy[2 * r + 1] - xy[1];
+        const double cr = ax * by - bx * ay;
+        A2 += cr;
+        sx += (ax + bx) * cr;
+        sy += (ay + by) * cr;
+    }
+    if (!(A2 > 0.0)) return fail(c, LBMIB_ERR_ARG, "rigid particle ring must be counter-clockwise");
+    const double cx = xy[0] + sx / (3.0 * A2), cy = xy[1] + sy / (3.0 * A2);
+    int id = -1;
+    lbmib_status st = lbmib_add_capsule(c, xy, n, 0.0, 0.0, 0.0, mass / n, &id);
+    if (st != LBMIB_OK) return st;
+    CapsuleParams& P = c->caps[id];
+    P.rigid = 1;
+    std::vector<double2> r0(n);
+    for (int v = 0; v < n; v++) r0[v] = make_double2(xy[2 * v] - cx, xy[2 * v + 1] - cy);
+    RigidBody B{};
+    B.body[0] = B.prev[0] = cx;
+    B.body[1] = B.prev[1] = cy;
+    B.mass = mass;
+    B.inertia = inertia;
+    cudaStream_t s = c->stream;
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->d_caps + id, &P, sizeof(P), cudaMemcpyHostToDevice, s));
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.R0 + P.off, r0.data(), n * sizeof(double2), cudaMemcpyHostToDevice, s));
+    LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.rb + id, &B, sizeof(B), cudaMemcpyHostToDevice, s));
+    LBMIB_CUDA(c, cudaStreamSynchronize(s));
+    c->nrigid++;
+    if (id_out) *id_out = id;
+    return LBMIB_OK;
+}
+
+lbmib_status lbmib_read_rigid(lbmib_ctx* c, int id, double* out) {
+    if (!c || !out || id < 0 || id >= (int)c->caps.size() || !c->caps[id].rigid)
+        return c ? fail(c, LBMIB_ERR_ARG, "not a rigid particle") : LBMIB_ERR_ARG;
+    RigidBody B;
+    LBMIB_CUDA(c, cudaStreamSynchronize(c->stream));
+    LBMIB_CUDA(c, cudaMemcpy(&B, c->nd.rb + id, sizeof(B), cudaMemcpyDeviceToHost));
+    for (int j = 0; j < 6; j++) out[j] = B.body[j];
+    for (int j = 0; j < 3; j++) out[6 + j] = B.load[j];
+    return device_status(c);
+}
+
 lbmib_status lbmib_set_inflow(lbmib_ctx* c, const double* u_in, double rho_out) {
     if (!c) return LBMIB_ERR_ARG;
     Lat& L = c->L;
     if (!u_in) {
         L.inflow = 0;
-        L.u_in = nullptr;
+        c->open = OpenBC{};
         drop_graphs(c);
         return LBMIB_OK;
     }
@@ -568,9 +622,9 @@ lbmib_status lbmib_set_inflow(lbmib_ctx* c, const double* u_in, double rho_out) 
     LBMIB_CUDA(c, cudaMemcpyAsync(c->d_u_in, u_in, (size_t)L.ny * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     LBMIB_CUDA(c, cudaStreamSynchronize(c->stream));
     L.inflow = 1;
-    L.u_in = c->d_u_in;
-    L.drho_out = rho_out - 1.0;
-    L.drho_outf = (float)L.drho_out;
+    c->open.u_in = c->d_u_in;
+    c->open.drho_out = rho_out - 1.0;
+    c->open.drho_outf = (float)c->open.drho_out;
     drop_graphs(c);
     return LBMIB_OK;
 }
@@ -587,6 +641,7 @@ lbmib_status lbmib_set_repulsion(lbmib_ctx* c, double cutoff, double coeff) {
 
 lbmib_status lbmib_set_capsule_positions(lbmib_ctx* c, int id, const double* xy) {
     if (!c || !xy || id < 0 || id >= (int)c->caps.size()) return LBMIB_ERR_ARG;
+    if (c->caps[id].rigid) return fail(c, LBMIB_ERR_ARG, "a rigid particle moves only with its body state");
     const CapsuleParams& P = c->caps[id];
     std::vector<int> zi(P.n, 0);
     LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.X + P.off, xy, P.n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
@@ -598,6 +653,8 @@ lbmib_status lbmib_set_capsule_positions(lbmib_ctx* c, int id, const double* xy)
 
 lbmib_status lbmib_step(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme) {
     if (!c || nsteps < 0 || (scheme != LBMIB_KINEMATIC && scheme != LBMIB_DYNAMIC)) return LBMIB_ERR_ARG;
+    if (scheme == LBMIB_KINEMATIC && c->nrigid > 0)
+        return fail(c, LBMIB_ERR_STATE, "rigid particles move only with the Dynamic scheme");
     const int sc = scheme == LBMIB_DYNAMIC ? 1 : 0;
     if (c->timing || !c->use_graphs) {
         fork_ib(c, c->stream);
@@ -645,7 +702,7 @@ lbmib_status lbmib_read_fields(lbmib_ctx* c, double* rho, double* ux, double* uy
     const size_t N = (size_t)c->cfg.nx * c->cfg.ny;
     by_storage(c->cfg.storage, [&](auto tag) {
         using S = decltype(tag);
-        launch_macros<S>(c->pops[c->cur], c->L, c->fib[c->cur_fib], c->scratch, c->scratch + N,
+        launch_macros<S>(c->pops[c->cur], c->L, c->open, c->fib[c->cur_fib], c->scratch, c->scratch + N,
                          c->scratch + 2 * N, c->stream);
     });
     c->launches++;
@@ -664,7 +721,7 @@ lbmib_status lbmib_read_populations(lbmib_ctx* c, double* f) {
     for (int i0 = 0; i0 < 9; i0 += 3) {
         by_storage(c->cfg.storage, [&](auto tag) {
             using S = decltype(tag);
-            launch_populations<S>(c->pops[c->cur], c->L, i0, c->scratch, c->stream);
+            launch_populations<S>(c->pops[c->cur], c->L, c->open, i0, c->scratch, c->stream);
         });
         c->launches++;
         LBMIB_CUDA(c, cudaGetLastError());
@@ -781,7 +838,8 @@ size_t lbmib_state_bytes(const lbmib_ctx* c) {
     const size_t N = (size_t)c->cfg.nx * c->cfg.ny;
     const size_t M = (size_t)c->nd.count;
     return sizeof(SnapHeader) + 9 * (size_t)c->L.plane * storage_bytes(c->cfg.storage) + 2 * N * sizeof(double) +
-           9 * (M > 0 ? M : 1) * sizeof(int) + M * (5 * sizeof(double2) + sizeof(int));
+           9 * (M > 0 ? M : 1) * sizeof(int) + M * (5 * sizeof(double2) + sizeof(int)) +
+           c->caps.size() * sizeof(RigidBody);
 }
 
 lbmib_status lbmib_save_state(lbmib_ctx* c, void* buf, size_t bytes) {
@@ -790,7 +848,7 @@ lbmib_status lbmib_save_state(lbmib_ctx* c, void* buf, size_t bytes) {
     const size_t N = (size_t)c->cfg.nx * c->cfg.ny;
     const size_t M = (size_t)c->nd.count;
     SnapHeader h{};
-    memcpy(h.magic, "LBMIBv1", 8);
+    memcpy(h.magic, "LBMIBv2", 8);
     h.nx = c->cfg.nx;
     h.ny = c->cfg.ny;
     h.storage = c->cfg.storage;
@@ -815,6 +873,8 @@ lbmib_status lbmib_save_state(lbmib_ctx* c, void* buf, size_t bytes) {
         p += M * sizeof(double2);
     }
     LBMIB_CUDA(c, cudaMemcpy(p, c->nd.age, M * sizeof(int), cudaMemcpyDeviceToHost));
+    p += M * sizeof(int);
+    LBMIB_CUDA(c, cudaMemcpy(p, c->nd.rb, c->caps.size() * sizeof(RigidBody), cudaMemcpyDeviceToHost));
     return device_status(c);
 }
 
@@ -824,7 +884,7 @@ lbmib_status lbmib_load_state(lbmib_ctx* c, const void* buf, size_t bytes) {
     memcpy(&h, buf, sizeof(h));
     const size_t N = (size_t)c->cfg.nx * c->cfg.ny;
     const size_t M = (size_t)c->nd.count;
-    if (memcmp(h.magic, "LBMIBv1", 8) != 0 || h.nx != c->cfg.nx || h.ny != c->cfg.ny ||
+    if (memcmp(h.magic, "LBMIBv2", 8) != 0 || h.nx != c->cfg.nx || h.ny != c->cfg.ny ||
         h.storage != (int)c->cfg.storage || h.ncaps != (int)c->caps.size() || h.nnodes != (int)M ||
         bytes < lbmib_state_bytes(c))
         return fail(c, LBMIB_ERR_STATE, "snapshot does not match this context");
@@ -847,6 +907,8 @@ lbmib_status lbmib_load_state(lbmib_ctx* c, const void* buf, size_t bytes) {
         p += M * sizeof(double2);
     }
     LBMIB_CUDA(c, cudaMemcpy(c->nd.age, p, M * sizeof(int), cudaMemcpyHostToDevice));
+    p += M * sizeof(int);
+    LBMIB_CUDA(c, cudaMemcpy(c->nd.rb, p, c->caps.size() * sizeof(RigidBody), cudaMemcpyHostToDevice));
     // fresh stamps: no cell carries a stamp that a coming step will use
     LBMIB_CUDA(c, cudaMemset(c->mark, 0, N * sizeof(int)));
     DevCounters ctr{};

@@ -790,7 +790,7 @@ lbmib_status lbmib_batch_read_populations(lbmib_batch* b, int c, double* f) {
         by_st(b->storage, [&](auto tag) {
             using S = decltype(tag);
             const S* base = reinterpret_cast<const S*>(b->arena) + bc.pops + (bc.cur ? 9 * bc.L.plane : 0);
-            launch_populations<S>(base, bc.L, i0, scratch, b->stream);
+            launch_populations<S>(base, bc.L, OpenBC{}, i0, scratch, b->stream);
         });
         LBMIB_BCUDA(b, cudaGetLastError());
         LBMIB_BCUDA(b, cudaMemcpyAsync(f + i0 * N, scratch, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));

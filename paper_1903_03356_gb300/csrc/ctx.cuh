@@ -22,7 +22,7 @@ inline size_t storage_bytes(lbmib_storage s) { return s == LBMIB_FP64 ? 8 : (s =
 struct Layout {
     size_t pops[2], fib[2], mark, list[2], ctr, scratch;
     size_t X, Xm1, uv, Fint, Fext, L0, c0, s0, age, capid, mls, caps, obs, pts, pts_out;
-    size_t Fpp, rep_box, rep_cellof, rep_count, rep_slot, u_in;
+    size_t Fpp, rep_box, rep_cellof, rep_count, rep_slot, u_in, rb, R0;
     int rep_buckets;
     size_t total;
     int pitch;
@@ -63,8 +63,10 @@ struct lbmib_ctx {
     double2* pts = nullptr;
     double* pts_out = nullptr;
     double* d_u_in = nullptr;   // inlet profile of an open channel (ny doubles)
+    lbmib::OpenBC open{};       // open-channel data for the kernels that close the open columns
     std::vector<lbmib::CapsuleParams> caps;
     int max_n = 0;
+    int nrigid = 0;           // rigid particles among the capsules
     double max_extent = 0.0;  // largest reference diameter of a capsule
     double max_arc_len = 0.0; // longest reference arc of the current split (slots included)
     int tile_cells = 256;     // per-CTA shared tile budget of the capsule kernels

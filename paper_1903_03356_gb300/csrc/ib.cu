@@ -154,6 +154,7 @@ __device__ __forceinline__ bool spread_with(const MlsW<C>& m, Tile<C>& t, const 
 // one arc is the whole ring.
 // ---------------------------------------------------------------------------------
 struct Arc {
+    int cap, rank;  // capsule, position among its CTAs
     int n, v0, m;   // ring size, first own vertex, own vertices
     double2 X0;     // X_0, the origin of the area sums
     // node index (within the capsule) of staged slot li
@@ -172,6 +173,8 @@ __device__ __forceinline__ bool load_arc(const Nodes& nd, const CapSmem& sm, int
         return false;
     }
     const int chunk = (P.n + arcs - 1) / arcs;
+    a.cap = cap;
+    a.rank = rank;
     a.n = P.n;
     a.v0 = rank * chunk;
     a.m = max(0, min(P.n - a.v0, chunk));
@@ -184,16 +187,32 @@ __device__ __forceinline__ bool load_arc(const Nodes& nd, const CapSmem& sm, int
 
 // Sum of a CTA-uniform value over the CTAs of this capsule's cluster, added in rank
 // order so that every CTA gets the same bits. Collective over the cluster.
-__device__ __forceinline__ double cluster_total(double v, int arcs) {
-    if (arcs == 1) return v;
-    __shared__ double part;
+template <int K>
+__device__ __forceinline__ void cluster_total(double (&v)[K], int arcs) {
+    if (arcs == 1) return;
+    __shared__ double part[K];
     cg::cluster_group cl = cg::this_cluster();
-    if (threadIdx.x == 0) part = v;
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int j = 0; j < K; j++) part[j] = v[j];
     cl.sync();
-    double t = 0.0;
-    for (int r = 0; r < arcs; r++) t += *cl.map_shared_rank(&part, r);
-    cl.sync();   // no CTA leaves while another still reads its partial
-    return t;
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        double t = 0.0;
+        for (int r = 0; r < arcs; r++) t += cl.map_shared_rank(part, r)[j];
+        v[j] = t;
+    }
+    cl.sync();   // no CTA leaves while another still reads its partials
+}
+__device__ __forceinline__ double cluster_total(double v, int arcs) {
+    double t[1] = {v};
+    cluster_total<1>(t, arcs);
+    return t[0];
+}
+
+// Velocity of the rigid-body motion of body state b at point X.
+__device__ __forceinline__ double2 rigid_velocity(const double* b, double2 X) {
+    return make_double2(b[3] - b[5] * (X.y - b[1]), b[4] + b[5] * (X.x - b[0]));
 }
 
 // A whole ring's halo slots repeat its own last and first vertex: copy their terms
@@ -219,7 +238,7 @@ __device__ __forceinline__ void copy_halo_terms(const CapSmem& sm, int m, bool e
 // force, F_l = u_v - U, spread with c_l = (l_left + l_right)/2. First step of a vertex:
 // u_v = U and X^{-1} = X^0 - U.
 // ---------------------------------------------------------------------------------
-template <typename S>
+template <typename S, bool RIGID>
 __global__ void __launch_bounds__(128) k_dyn_force_spread(const S* __restrict__ src, Lat L,
                                                           const double* __restrict__ fib_prev, Nodes nd, int max_n,
                                                           int arcs, int tile_cells, Spread sp, unsigned* status) {
@@ -253,11 +272,16 @@ __global__ void __launch_bounds__(128) k_dyn_force_spread(const S* __restrict__ 
         InterpT<C> o;
         ok &= interp_with<S, false>(w, t, src, L, fib_prev, o);
         const double Ux = (double)o.ux, Uy = (double)o.uy;
-        double2 uv = nd.uv[g];
-        if (nd.age[g] == 0) {
-            uv = make_double2(Ux, Uy);
-            nd.uv[g] = uv;
-            nd.Xm1[g] = Xv - uv;
+        double2 uv;
+        if (RIGID && P.rigid) {
+            uv = rigid_velocity(nd.rb[a.cap].body, Xv);   // the body's motion (Section 2.3.1)
+        } else {
+            uv = nd.uv[g];
+            if (nd.age[g] == 0) {
+                uv = make_double2(Ux, Uy);
+                nd.uv[g] = uv;
+                nd.Xm1[g] = Xv - uv;
+            }
         }
         const double cl = 0.5 * (sm.sst[li - 1] + sm.sst[li]);
         if (nd.Flc) nd.Flc[g] = make_double2(cl * (uv.x - Ux), cl * (uv.y - Uy));
@@ -266,6 +290,44 @@ __global__ void __launch_bounds__(128) k_dyn_force_spread(const S* __restrict__ 
     __syncthreads();
     if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
     if (!ok) atomicOr(status, kStatSupport);
+}
+
+// Rigid particle, after its load is summed (Section 2.3.1): accelerations F/m and M/I,
+// Eq. 19-20 for the velocities, the same backward form for the centre and the angle,
+// and the markers X_v = c + R(theta) r_v moving with u + omega x (X_v - c). Every CTA of
+// the particle computes the same update from the same totals; the first stores it.
+__device__ void rigid_update(const Nodes& nd, const CapsuleParams& P, const Arc& a, const CapSmem& sm,
+                             const double* body, const double* prev, const double (&sums)[3]) {
+    const RigidBody& B = nd.rb[a.cap];
+    const double acc[3] = {sums[0] / B.mass, sums[1] / B.mass, sums[2] / B.inertia};
+    double next[6];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        next[3 + j] = (2.0 / 3.0) * (2.0 * body[3 + j] - 0.5 * prev[3 + j] + acc[j]);
+        next[j] = (2.0 / 3.0) * (2.0 * body[j] - 0.5 * prev[j] + next[3 + j]);
+    }
+    double sn, cs;
+    sincos(next[2], &sn, &cs);
+    for (int k = threadIdx.x; k < a.m; k += blockDim.x) {
+        const int li = kHalo + k, g = P.off + a.v0 + k;
+        const double2 r0 = nd.R0[g];
+        const double rx = cs * r0.x - sn * r0.y, ry = sn * r0.x + cs * r0.y;
+        nd.Xm1[g] = sm.X[li];
+        nd.X[g] = make_double2(next[0] + rx, next[1] + ry);
+        nd.uv[g] = make_double2(next[3] - next[5] * ry, next[4] + next[5] * rx);
+        nd.Fint[g] = make_double2(0.0, 0.0);
+        nd.Fext[g] = 0.5 * (sm.ext[li] + sm.ext[li - 1]);
+        nd.age[g] += 1;
+    }
+    if (a.rank == 0 && threadIdx.x == 0) {
+        RigidBody& W = nd.rb[a.cap];
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            W.prev[j] = body[j];
+            W.body[j] = next[j];
+        }
+        for (int j = 0; j < 3; j++) W.load[j] = sums[j];
+    }
 }
 
 // Dynamic IB steps 5-8: xdot_0 = I(u^{n+1}) at X^n, probe tractions (Eq. 15-16),
@@ -284,7 +346,9 @@ __global__ void __launch_bounds__(128) k_dyn_update(const S* __restrict__ dst, L
     CapsuleParams P;
     Arc a;
     if (!load_arc(nd, sm, max_n, arcs, true, P, a, status)) return;
-    const int m = a.m;
+    // a rigid particle's CTAs do no work here (k_rigid_update moves it); they take part in
+    // the cluster's sums with nothing (a branch out would cost this kernel registers)
+    const int m = P.rigid ? 0 : a.m;
     // vertices v0-1 .. v0+m: the ends of every element whose probes this CTA evaluates
     Tile<C> t = make_tile<C>(sm, kHalo - 1, m > 0 ? kHalo + m + 1 : kHalo - 1, 3, tile_cells, true, false);
     if (t.use) fill_moments<S>(t, dst, L, fib);
@@ -348,6 +412,79 @@ __global__ void __launch_bounds__(128) k_dyn_update(const S* __restrict__ dst, L
         nd.Fext[g] = Fe;
         nd.age[g] += 1;
     }
+    if (!ok) atomicOr(status, kStatSupport);
+}
+
+// Rigid particles after the fluid update (Section 2.3.1, Eq. 17-20): the outer probe of
+// every element, the load summed over the particle (its CTAs form a cluster when its ring
+// is split), then rigid_update. Capsules' CTAs return at once; launched only when the
+// context holds rigid particles.
+template <typename S>
+__global__ void __launch_bounds__(128) k_rigid_update(const S* __restrict__ dst, Lat L,
+                                                      const double* __restrict__ fib, Nodes nd, int max_n, int arcs,
+                                                      int tile_cells, unsigned* status) {
+    using C = typename St<S>::C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CapSmem sm = carve(smem, arc_slots(max_n, arcs));
+    CapsuleParams P;
+    Arc a;
+    if (!load_arc(nd, sm, max_n, arcs, true, P, a, status)) return;
+    if (!P.rigid) return;   // uniform over the capsule's cluster
+    const int m = a.m;
+    Tile<C> t = make_tile<C>(sm, kHalo - 1, m > 0 ? kHalo + m + 1 : kHalo - 1, 3, tile_cells, true, false);
+    if (t.use) fill_moments<S>(t, dst, L, fib);
+    // the particle's state at n and n - 1, staged before the cluster barrier after which
+    // the first CTA overwrites it
+    __shared__ double body[12];
+    if (threadIdx.x < 12)
+        body[threadIdx.x] = threadIdx.x < 6 ? nd.rb[a.cap].body[threadIdx.x] : nd.rb[a.cap].prev[threadIdx.x - 6];
+    __syncthreads();
+    bool ok = true;
+    double sums[3] = {0.0, 0.0, 0.0};   // F_x, F_y, M (Eq. 17-18)
+    const C nu = C(L.nu);
+    // own elements; a split ring also evaluates the element before its arc (for the
+    // vertex shares of the first own vertex)
+    const bool split = m > 0 && m < a.n;
+    for (int k = threadIdx.x; k < (split ? m + 1 : m); k += blockDim.x) {
+        const int li = k < m ? kHalo + k : kHalo - 1;
+        const double2 Xv = sm.X[li], Xr = sm.X[li + 1];
+        const double2 d = Xr - Xv;
+        const double rl = rsqrt(d.x * d.x + d.y * d.y);
+        const double npx = d.y * rl, npy = -d.x * rl;
+        const double cx = 0.5 * (Xv.x + Xr.x), cy = 0.5 * (Xv.y + Xr.y);
+        const double len = (d.x * d.x + d.y * d.y) * rl;
+        InterpT<C> op;
+        ok &= interp_at<S, true>(t, dst, L, fib, cx + 1.2 * npx, cy + 1.2 * npy, op);
+        // Eq. 17: (tau+ . n+ - p+ n+) l_l of the outer fluid alone; Eq. 18: its moment
+        // about c, lever arm to the element centroid. The reference pressure 1/3 adds
+        // nothing over a closed ring (sum n_l l_l = 0, sum r_l x n_l l_l = 0) and is left
+        // out, so that the load of a nearly balanced particle is not a small difference of
+        // large single-precision terms.
+        const C mp = op.rho * nu, nx = C(npx), ny = C(npy), pd = op.drho * C(1.0 / 3.0);
+        const C txx = C(2) * mp * op.dudx, tyy = C(2) * mp * op.dvdy, txy = mp * (op.dudy + op.dvdx);
+        const double fx = (double)(txx * nx + txy * ny - pd * nx) * len;
+        const double fy = (double)(txy * nx + tyy * ny - pd * ny) * len;
+        sm.ext[li] = make_double2(fx, fy);
+        if (k < m) {
+            sums[0] += fx;
+            sums[1] += fy;
+            sums[2] += (cx - body[0]) * fy - (cy - body[1]) * fx;
+        }
+    }
+    if (nd.Fpp)   // Eq. 27 on the markers: part of the load and its moment
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            const double2 f = nd.Fpp[P.off + a.v0 + k], X = sm.X[kHalo + k];
+            sums[0] += f.x;
+            sums[1] += f.y;
+            sums[2] += (X.x - body[0]) * f.y - (X.y - body[1]) * f.x;
+        }
+    block_reduce<3, false>(sums, sm.red);   // also publishes the element forces
+    if (m == a.n) {   // a whole ring: the element before the first vertex is the last one
+        if (threadIdx.x == 0) sm.ext[kHalo - 1] = sm.ext[kHalo + m - 1];
+        __syncthreads();
+    }
+    cluster_total<3>(sums, arcs);
+    rigid_update(nd, P, a, sm, body, body + 6, sums);
     if (!ok) atomicOr(status, kStatSupport);
 }
 
@@ -543,9 +680,15 @@ void set_capsule_smem_limits(int slots, int cells) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess) cur = bytes;
     };
 #define LBMIB_SMEM(K, C, M, F) raise((const void*)K, smem_bytes<C>(slots, cells, M, F))
-    LBMIB_SMEM(k_dyn_force_spread<double>, double, true, true);
-    LBMIB_SMEM(k_dyn_force_spread<float>, float, true, true);
-    LBMIB_SMEM(k_dyn_force_spread<__half>, float, true, true);
+    LBMIB_SMEM((k_dyn_force_spread<double, false>), double, true, true);
+    LBMIB_SMEM((k_dyn_force_spread<float, false>), float, true, true);
+    LBMIB_SMEM((k_dyn_force_spread<__half, false>), float, true, true);
+    LBMIB_SMEM((k_dyn_force_spread<double, true>), double, true, true);
+    LBMIB_SMEM((k_dyn_force_spread<float, true>), float, true, true);
+    LBMIB_SMEM((k_dyn_force_spread<__half, true>), float, true, true);
+    LBMIB_SMEM(k_rigid_update<double>, double, true, false);
+    LBMIB_SMEM(k_rigid_update<float>, float, true, false);
+    LBMIB_SMEM(k_rigid_update<__half>, float, true, false);
     LBMIB_SMEM(k_dyn_update<double>, double, true, false);
     LBMIB_SMEM(k_dyn_update<float>, float, true, false);
     LBMIB_SMEM(k_dyn_update<__half>, float, true, false);
@@ -581,18 +724,27 @@ static void launch_arcs(void (*k)(P...), int ncaps, int arcs, bool cluster, size
 
 template <typename S>
 void launch_dyn_force_spread(const void* src, const Lat& L, const double* fib_prev, Nodes nd, int ncaps, int max_n,
-                             int arcs, int cells, Spread sp, unsigned* status, cudaStream_t s) {
+                             int arcs, int cells, bool rigid, Spread sp, unsigned* status, cudaStream_t s) {
     using C = typename St<S>::C;
-    launch_arcs(k_dyn_force_spread<S>, ncaps, arcs, false, smem_bytes<C>(arc_slots(max_n, arcs), cells, true, true),
-                s, (const S*)src, L, fib_prev, nd, max_n, arcs, cells, sp, status);
+    const size_t sh = smem_bytes<C>(arc_slots(max_n, arcs), cells, true, true);
+    if (rigid)
+        launch_arcs(k_dyn_force_spread<S, true>, ncaps, arcs, false, sh, s, (const S*)src, L, fib_prev, nd, max_n,
+                    arcs, cells, sp, status);
+    else
+        launch_arcs(k_dyn_force_spread<S, false>, ncaps, arcs, false, sh, s, (const S*)src, L, fib_prev, nd, max_n,
+                    arcs, cells, sp, status);
 }
 
 template <typename S>
 void launch_dyn_update(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
-                       int arcs, int cells, int* reset_count, unsigned* status, cudaStream_t s) {
+                       int arcs, int cells, bool rigid, int* reset_count, unsigned* status, cudaStream_t s) {
     using C = typename St<S>::C;
-    launch_arcs(k_dyn_update<S>, ncaps, arcs, true, smem_bytes<C>(arc_slots(max_n, arcs), cells, true, false), s,
-                (const S*)dst, L, fib_cur, nd, max_n, arcs, cells, reset_count, status);
+    const size_t sh = smem_bytes<C>(arc_slots(max_n, arcs), cells, true, false);
+    launch_arcs(k_dyn_update<S>, ncaps, arcs, true, sh, s, (const S*)dst, L, fib_cur, nd, max_n, arcs, cells,
+                reset_count, status);
+    if (rigid)
+        launch_arcs(k_rigid_update<S>, ncaps, arcs, true, sh, s, (const S*)dst, L, fib_cur, nd, max_n, arcs, cells,
+                    status);
 }
 
 void launch_kin_force_spread(const Lat& L, Nodes nd, int ncaps, int max_n, int arcs, int cells, Spread sp,
@@ -630,9 +782,9 @@ void launch_interp_points(const void* src, const Lat& L, const double* fib, cons
 
 #define LBMIB_INSTANTIATE_IB(S)                                                                              \
     template void launch_dyn_force_spread<S>(const void*, const Lat&, const double*, Nodes, int, int, int,   \
-                                             int, Spread, unsigned*, cudaStream_t);                          \
+                                             int, bool, Spread, unsigned*, cudaStream_t);                    \
     template void launch_dyn_update<S>(const void*, const Lat&, const double*, Nodes, int, int, int, int,    \
-                                       int*, unsigned*, cudaStream_t);                                       \
+                                       bool, int*, unsigned*, cudaStream_t);                                 \
     template void launch_kin_advance<S>(const void*, const Lat&, const double*, Nodes, int, int, int, int,   \
                                         int*, unsigned*, cudaStream_t);                                      \
     template void launch_interp_points<S>(const void*, const Lat&, const double*, const double2*, int,       \

@@ -433,7 +433,7 @@ __global__ void k_init(S* __restrict__ dst, Lat L, const double* __restrict__ rh
 
 // Read-back: rho (Eq. 6) and u (Eq. 7, half of g + f_ib) at every node, in double.
 template <typename S>
-__global__ void k_macros(const S* __restrict__ src, Lat L, const double* __restrict__ fib,
+__global__ void k_macros(const S* __restrict__ src, Lat L, OpenBC ob, const double* __restrict__ fib,
                          double* __restrict__ rho, double* __restrict__ ux, double* __restrict__ uy) {
     using C = typename St<S>::C;
     const long long N = (long long)L.nx * L.ny;
@@ -441,7 +441,7 @@ __global__ void k_macros(const S* __restrict__ src, Lat L, const double* __restr
     if (n >= N) return;
     const int y = (int)(n / L.nx), x = (int)(n - (long long)y * L.nx);
     C s[9];
-    pull_all<S>(src, L, x, y, s);
+    pull_all<S>(src, L, x, y, s, &ob);
     C drho, mx, my;
     moments<C>(s, drho, mx, my);
     const double r = 1.0 + (double)drho;
@@ -452,13 +452,13 @@ __global__ void k_macros(const S* __restrict__ src, Lat L, const double* __restr
 
 // Read-back: unshifted pre-collision populations i0 .. i0+2 in double.
 template <typename S>
-__global__ void k_populations(const S* __restrict__ src, Lat L, int i0, double* __restrict__ out) {
+__global__ void k_populations(const S* __restrict__ src, Lat L, OpenBC ob, int i0, double* __restrict__ out) {
     const long long N = (long long)L.nx * L.ny;
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const int y = (int)(n / L.nx), x = (int)(n - (long long)y * L.nx);
     typename St<S>::C s[9];
-    pull_all<S>(src, L, x, y, s);
+    pull_all<S>(src, L, x, y, s, &ob);
     for (int k = 0; k < 3 && i0 + k < 9; k++) {
         const int i = i0 + k;
         double w = i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
@@ -472,13 +472,13 @@ __global__ void k_populations(const S* __restrict__ src, Lat L, int i0, double* 
 // force (Eq. 4-5) like every other node. Runs after the lattice kernel, on its output.
 template <typename S>
 __global__ void __launch_bounds__(128) k_open_columns(const S* __restrict__ src, S* __restrict__ dst, Lat L,
-                                                      unsigned* status) {
+                                                      OpenBC ob, unsigned* status) {
     using C = typename St<S>::C;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= 2 * L.ny) return;
     const int y = k >> 1, x = (k & 1) ? L.nx - 1 : 0;
     C s[9];
-    pull_all<S>(src, L, x, y, s);
+    pull_all<S>(src, L, x, y, s, &ob);
     const C usq = collide<C>(s, lat_c<C>(L.gx, L.gxf), lat_c<C>(L.gy, L.gyf), lat_c<C>(L.omega, L.omegaf));
     if (!(usq < C(0.09))) atomicOr(status, kStatUnstable);
 #pragma unroll
@@ -527,8 +527,9 @@ void launch_patch(const void* src, void* dst, const Lat& L, const double* fib_c,
 }
 
 template <typename S>
-void launch_open_columns(const void* src, void* dst, const Lat& L, unsigned* status, cudaStream_t s) {
-    k_open_columns<S><<<blocks_for(2LL * L.ny, 128), 128, 0, s>>>((const S*)src, (S*)dst, L, status);
+void launch_open_columns(const void* src, void* dst, const Lat& L, const OpenBC& ob, unsigned* status,
+                         cudaStream_t s) {
+    k_open_columns<S><<<blocks_for(2LL * L.ny, 128), 128, 0, s>>>((const S*)src, (S*)dst, L, ob, status);
 }
 
 template <typename S>
@@ -537,26 +538,27 @@ void launch_init(void* dst, const Lat& L, const double* rho, const double* ux, c
 }
 
 template <typename S>
-void launch_macros(const void* src, const Lat& L, const double* fib, double* rho, double* ux, double* uy,
-                   cudaStream_t s) {
-    k_macros<S><<<blocks_for((long long)L.nx * L.ny, 256), 256, 0, s>>>((const S*)src, L, fib, rho, ux, uy);
+void launch_macros(const void* src, const Lat& L, const OpenBC& ob, const double* fib, double* rho, double* ux,
+                   double* uy, cudaStream_t s) {
+    k_macros<S><<<blocks_for((long long)L.nx * L.ny, 256), 256, 0, s>>>((const S*)src, L, ob, fib, rho, ux, uy);
 }
 
 template <typename S>
-void launch_populations(const void* src, const Lat& L, int i0, double* out, cudaStream_t s) {
-    k_populations<S><<<blocks_for((long long)L.nx * L.ny, 256), 256, 0, s>>>((const S*)src, L, i0, out);
+void launch_populations(const void* src, const Lat& L, const OpenBC& ob, int i0, double* out, cudaStream_t s) {
+    k_populations<S><<<blocks_for((long long)L.nx * L.ny, 256), 256, 0, s>>>((const S*)src, L, ob, i0, out);
 }
 
 #define LBMIB_INSTANTIATE_LATTICE(S)                                                                  \
     template void launch_collide_stream<S>(const void*, void*, const Lat&, unsigned*, int, cudaStream_t); \
     template void launch_patch<S>(const void*, void*, const Lat&, const double*, const int*, double*, \
                                   const int*, DevCounters*, int, int, cudaStream_t);                  \
-    template void launch_open_columns<S>(const void*, void*, const Lat&, unsigned*, cudaStream_t);     \
+    template void launch_open_columns<S>(const void*, void*, const Lat&, const OpenBC&, unsigned*,     \
+                                         cudaStream_t);                                               \
     template void launch_init<S>(void*, const Lat&, const double*, const double*, const double*,      \
                                  cudaStream_t);                                                       \
-    template void launch_macros<S>(const void*, const Lat&, const double*, double*, double*, double*, \
-                                   cudaStream_t);                                                     \
-    template void launch_populations<S>(const void*, const Lat&, int, double*, cudaStream_t);
+    template void launch_macros<S>(const void*, const Lat&, const OpenBC&, const double*, double*,     \
+                                   double*, double*, cudaStream_t);                                   \
+    template void launch_populations<S>(const void*, const Lat&, const OpenBC&, int, double*, cudaStream_t);
 
 LBMIB_INSTANTIATE_LATTICE(double)
 LBMIB_INSTANTIATE_LATTICE(float)

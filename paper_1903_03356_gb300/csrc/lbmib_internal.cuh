@@ -51,9 +51,16 @@ struct Lat {
     // float copies for single-precision kernels (a double-to-float conversion in every
     // thread would occupy GB300's narrow FP64 pipe)
     float gxf, gyf, omegaf, ubf, utf;
-    // open channel (0: periodic in x): Zou-He known-velocity inlet at column 0 with
-    // x-velocity u_in[y] (device, ny values), known-density outlet at column nx - 1
+    // open channel (0: periodic in x; the boundary data travel in OpenBC). Placed in the
+    // tail padding: the size of this struct, and with it the register allocation of the
+    // lattice kernel, stays as it was.
     int inflow;
+};
+
+// Open channel: Zou-He known-velocity inlet at column 0 with x-velocity u_in[y] (device,
+// ny values), known-density outlet at column nx - 1. Passed only to the kernels whose
+// results at the open columns are used (supports of markers and probes stay off them).
+struct OpenBC {
     const double* u_in;
     double drho_out;      // outlet density - 1
     float drho_outf;
@@ -134,12 +141,12 @@ __device__ __forceinline__ typename St<S>::C pull(const S* __restrict__ src, con
 // rho u - F/2 with F the uniform force (supports stay off the open columns). Explicit
 // form of the closure in shifted variables (the rest weights cancel pairwise).
 template <typename C>
-__device__ __forceinline__ void open_column(C (&s)[9], const Lat& L, int x, int y) {
+__device__ __forceinline__ void open_column(C (&s)[9], const Lat& L, const OpenBC& ob, int x, int y) {
     const C Fx = lat_c<C>(L.gx, L.gxf), Fy = lat_c<C>(L.gy, L.gyf);
     const C jy = C(-0.5) * Fy;
     const C t = C(0.5) * (s[2] - s[4]);
     if (x == 0) {
-        const C u = C(L.u_in[y]);
+        const C u = C(ob.u_in[y]);
         // rho (1 - u) = 1 + s0 + s2 + s4 + 2 (s3 + s6 + s7) - Fx/2
         const C known = (s[0] + s[2] + s[4]) + C(2) * (s[3] + s[6] + s[7]);
         const C drho = (known - C(0.5) * Fx + u) / (C(1) - u);
@@ -149,7 +156,7 @@ __device__ __forceinline__ void open_column(C (&s)[9], const Lat& L, int x, int 
         s[8] = s[6] + t + jx * C(1.0 / 6.0) - C(0.5) * jy;
     } else {
         // mass fixes the entering populations' sum, x-momentum follows
-        const C jx = ((s[0] + s[2] + s[4]) + C(2) * (s[1] + s[5] + s[8])) - lat_c<C>(L.drho_out, L.drho_outf);
+        const C jx = ((s[0] + s[2] + s[4]) + C(2) * (s[1] + s[5] + s[8])) - lat_c<C>(ob.drho_out, ob.drho_outf);
         s[3] = s[1] - C(2.0 / 3.0) * jx;
         s[7] = s[5] + t - jx * C(1.0 / 6.0) - C(0.5) * jy;
         s[6] = s[8] - t - jx * C(1.0 / 6.0) + C(0.5) * jy;
@@ -158,11 +165,11 @@ __device__ __forceinline__ void open_column(C (&s)[9], const Lat& L, int x, int 
 
 // All nine pre-collision populations of node (x, y), as pull() but with the neighbour
 // coordinates formed by comparisons instead of the periodic wrap's integer division,
-// and every load issued before any is used, and the Zou-He closure on the open columns
-// of an open channel. NC as for pull().
+// and every load issued before any is used, and, given the open-channel data ob, the
+// Zou-He closure on the open columns. NC as for pull().
 template <typename S, bool NC = true>
 __device__ __forceinline__ void pull_all(const S* __restrict__ src, const Lat& L, int x, int y,
-                                         typename St<S>::C (&s)[9]) {
+                                         typename St<S>::C (&s)[9], const OpenBC* ob = nullptr) {
     using C = typename St<S>::C;
     const int xm = x == 0 ? L.nx - 1 : x - 1, xp = x + 1 == L.nx ? 0 : x + 1;
     const int ym = y == 0 ? L.ny - 1 : y - 1, yp = y + 1 == L.ny ? 0 : y + 1;
@@ -185,7 +192,7 @@ __device__ __forceinline__ void pull_all(const S* __restrict__ src, const Lat& L
         }
     }
     // open channel: what the periodic wrap brought across the inlet or outlet is replaced
-    if (L.inflow && (x == 0 || x == L.nx - 1)) open_column<C>(s, L, x, y);
+    if (ob && L.inflow && (x == 0 || x == L.nx - 1)) open_column<C>(s, L, *ob, x, y);
 }
 
 // Density deviation, momentum (Eq. 6-7 without the force) of shifted populations.
@@ -344,6 +351,7 @@ __device__ __forceinline__ MlsW<C> mls_setup(const Lat& L, double X, double Y) {
 template <typename C>
 struct InterpT {
     C ux, uy, rho, p;
+    C drho;   // rho - 1, kept apart so that single precision keeps its digits
     C dudx, dudy, dvdx, dvdy;
 };
 using Interp = InterpT<double>;
@@ -399,7 +407,8 @@ __device__ __forceinline__ void mls_apply(const MlsW<C>& m, Get&& get, InterpT<C
     }
     o.ux = m.k0 * u0 + m.kx * u1 + m.ky * u2;
     o.uy = m.k0 * v0 + m.kx * v1 + m.ky * v2;
-    o.rho = C(1) + (m.k0 * r0 + m.kx * r1 + m.ky * r2);
+    o.drho = m.k0 * r0 + m.kx * r1 + m.ky * r2;
+    o.rho = C(1) + o.drho;
     o.p = o.rho * C(1.0 / 3.0);
     if (GRAD) {
         o.dudx = m.gx * u1; o.dudy = m.gy * u2;
@@ -449,6 +458,7 @@ struct CapsuleParams {
     int off, n;            // first vertex, vertex count
     double ks, kb, ka, m;  // Eq. 10, 12, 14 constants and per-vertex mass
     double A0, P0;         // stress-free area and perimeter
+    int rigid;             // 1: a rigid particle (Section 2.3.1), state in Nodes::rb
 };
 
 }  // namespace lbmib

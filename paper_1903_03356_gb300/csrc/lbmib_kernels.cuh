@@ -5,6 +5,15 @@
 
 namespace lbmib {
 
+// State of a rigid particle (Section 2.3.1, Eq. 17-20): {c_x, c_y, theta, u_x, u_y,
+// omega} at step n and at n - 1 (c the area centroid), mass, moment of inertia about c,
+// and the last fluid load {F_x, F_y, M}.
+struct RigidBody {
+    double body[6], prev[6];
+    double mass, inertia;
+    double load[3];
+};
+
 // Membrane vertex state, structure of arrays over all vertices of all capsules.
 struct Nodes {
     double2* X;      // X^n
@@ -23,6 +32,8 @@ struct Nodes {
     void* mls;       // MLS shape functions of each vertex at X^n (MlsW of the compute type),
                      // written by the spread kernels, read by the node update of the step
     double2* Fpp;    // optional (null): capsule-capsule repulsion at X^n (Eq. 27)
+    RigidBody* rb;   // per capsule; read for capsules with CapsuleParams::rigid
+    double2* R0;     // per vertex of a rigid particle: offset from c in the body frame
 };
 
 // Neighbour grid of the capsule-capsule repulsion: capsules hashed by the coarse cell of
@@ -59,14 +70,15 @@ void launch_patch(const void* src, void* dst, const Lat& L, const double* fib_c,
                   double* fib_p, const int* list_p, DevCounters* ctr, int c, int capacity, cudaStream_t s);
 // open channel: Zou-He inlet and outlet columns, after launch_collide_stream on its output
 template <typename S>
-void launch_open_columns(const void* src, void* dst, const Lat& L, unsigned* status, cudaStream_t s);
+void launch_open_columns(const void* src, void* dst, const Lat& L, const OpenBC& ob, unsigned* status,
+                         cudaStream_t s);
 template <typename S>
 void launch_init(void* dst, const Lat& L, const double* rho, const double* ux, const double* uy, cudaStream_t s);
 template <typename S>
-void launch_macros(const void* src, const Lat& L, const double* fib, double* rho, double* ux, double* uy,
+void launch_macros(const void* src, const Lat& L, const OpenBC& ob, const double* fib, double* rho, double* ux, double* uy,
                    cudaStream_t s);
 template <typename S>
-void launch_populations(const void* src, const Lat& L, int i0, double* out, cudaStream_t s);
+void launch_populations(const void* src, const Lat& L, const OpenBC& ob, int i0, double* out, cudaStream_t s);
 
 // ib.cu. The capsule kernels run `arcs` CTAs per capsule (1..kMaxArcs), each on an even
 // share of the ring.
@@ -76,10 +88,12 @@ constexpr int kMaxArcs = 8;    // portable thread-block cluster size
 __host__ __device__ inline int arc_slots(int max_n, int arcs) { return (max_n + arcs - 1) / arcs + 2 * kHalo; }
 template <typename S>
 void launch_dyn_force_spread(const void* src, const Lat& L, const double* fib_prev, Nodes nd, int ncaps, int max_n,
-                             int arcs, int cells, Spread sp, unsigned* status, cudaStream_t s);
+                             int arcs, int cells, bool rigid, Spread sp, unsigned* status, cudaStream_t s);
+// the node update of the capsules, then (rigid: the context holds rigid particles) that
+// of the rigid particles
 template <typename S>
 void launch_dyn_update(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
-                       int arcs, int cells, int* reset_count, unsigned* status, cudaStream_t s);
+                       int arcs, int cells, bool rigid, int* reset_count, unsigned* status, cudaStream_t s);
 void launch_kin_force_spread(const Lat& L, Nodes nd, int ncaps, int max_n, int arcs, int cells, Spread sp,
                              unsigned* status, bool fp64_weights, cudaStream_t s);
 template <typename S>

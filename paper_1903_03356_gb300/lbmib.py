@@ -89,6 +89,8 @@ _SIGS = {
     "lbmib_bytes_per_update": (C.c_double, [_vp]),
     "lbmib_set_repulsion": (C.c_int, [_vp, C.c_double, C.c_double]),
     "lbmib_set_inflow": (C.c_int, [_vp, _vp, C.c_double]),
+    "lbmib_add_rigid": (C.c_int, [_vp, _vp, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_int)]),
+    "lbmib_read_rigid": (C.c_int, [_vp, C.c_int, _vp]),
     "lbmib_adjoint_workspace_bytes": (C.c_size_t, [_vp, C.c_longlong, C.c_int]),
     "lbmib_adjoint": (C.c_int, [_vp, C.c_longlong, C.c_int, C.c_int, C.c_int, C.c_int, _vp, C.c_size_t, _vp, _vp]),
     "lbmib_batch_arena_bytes": (C.c_size_t, [_vp, C.c_int, C.c_int]),
@@ -356,6 +358,23 @@ class Context:
     def set_repulsion(self, cutoff: float, coeff: float = 0.0):
         """Capsule-capsule repulsion of Eq. 27 (cutoff 0: off; coeff 0: the printed one)."""
         lbmib_set_repulsion(self.h, cutoff, coeff)
+
+    def add_rigid(self, xy, mass: float, inertia: float) -> int:
+        """Rigid particle (Section 2.3.1): ring xy (n, 2), mass and moment of inertia about
+        its area centroid; at rest; Dynamic scheme only."""
+        xy = _f64(xy)
+        n = xy.size // 2
+        out = C.c_int(-1)
+        _check(self.h, _lib.lbmib_add_rigid(self.h, xy.ctypes.data_as(_vp), n, float(mass), float(inertia),
+                                            C.byref(out)))
+        self._n.append(n)
+        return out.value
+
+    def read_rigid(self, cid: int) -> np.ndarray:
+        """(c_x, c_y, theta, u_x, u_y, omega, F_x, F_y, M) of rigid particle cid."""
+        out = np.zeros(9)
+        _check(self.h, _lib.lbmib_read_rigid(self.h, int(cid), out.ctypes.data_as(_vp)))
+        return out
 
     def set_inflow(self, u_in, rho_out: float = 1.0):
         """Open channel: Zou-He inlet with x-velocity u_in (ny values) at x = 0 and outlet

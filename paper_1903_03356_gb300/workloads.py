@@ -103,6 +103,27 @@ def biconcave(n: int, a: float, cx: float, cy: float) -> np.ndarray:
     return xy
 
 
+def polygon_inertia(xy: np.ndarray):
+    """Area, area centroid and polar second moment about the centroid of a polygon (a
+    uniform rigid particle of density rho_s has mass rho_s A and inertia rho_s J)."""
+    x, y = xy[:, 0] - xy[0, 0], xy[:, 1] - xy[0, 1]
+    xn, yn = np.roll(x, -1), np.roll(y, -1)
+    cr = x * yn - xn * y
+    A = 0.5 * cr.sum()
+    cx = ((x + xn) * cr).sum() / (6 * A)
+    cy = ((y + yn) * cr).sum() / (6 * A)
+    J = (((x * x + x * xn + xn * xn) + (y * y + y * yn + yn * yn)) * cr).sum() / 12.0 - A * (cx * cx + cy * cy)
+    return A, cx + xy[0, 0], cy + xy[0, 1], J
+
+
+def ellipse(n: int, a: float, b: float, cx: float, cy: float, angle: float = 0.0, phase: float = 0.137) -> np.ndarray:
+    """Counter-clockwise ellipse of semi-axes a, b turned by `angle`."""
+    t = 2 * np.pi * (np.arange(n) + phase) / n
+    x, y = a * np.cos(t), b * np.sin(t)
+    c, s = np.cos(angle), np.sin(angle)
+    return np.stack([cx + c * x - s * y, cy + s * x + c * y], axis=1)
+
+
 def min_half_integer_distance(xy: np.ndarray) -> float:
     """Distance of the nearest coordinate to a half-integer line (support switch)."""
     d = np.abs((xy + 0.5) - np.round(xy + 0.5))
