@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--adjoint-steps", type=int, default=800, help="horizon T of the adjoint measurement")
     p.add_argument("--batch-autotune", type=int, default=20,
                    help="steps per candidate launch shape of the batch autotuner (0: default shape)")
-    p.add_argument("--only", default="all", choices=["all", "batched", "adjoint", "precision", "dense", "open"],
+    p.add_argument("--only", default="all", choices=["all", "batched", "adjoint", "precision", "dense", "open", "rigid"],
                    help="batched / adjoint: run only that measurement and print its JSON object")
     return p.parse_args()
 
@@ -279,6 +279,7 @@ def run_gpu(a):
         line["precision"] = precision_run(L, dev)
         line["dense"] = dense_run(L)
         line["open"] = open_run(L)
+        line["rigid"] = rigid_run(L)
         line["batched"] = batched_run(L, a.batch_steps, a.batch_autotune)
         line["adjoint"] = {"dynamic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=1),
                            "kinematic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=0)}
@@ -402,6 +403,46 @@ def open_run(L, steps=500, warmup=50):
         ctx.close()
     big["open_cost"] = big["open"]["ms_per_step"] / big["periodic"]["ms_per_step"] - 1.0
     out["lattice_16384x8192"] = big
+    return out
+
+
+def rigid_run(L, steps=200, warmup=20):
+    """Rigid particles (Section 2.3.1, Eq. 17-20): the 256 biconcave shapes of the 4096 x 512
+    precision workload (seed 0, jittered grid, 128 vertices) as rigid particles of the
+    fluid's density, Dynamic, FP32, against the same shapes as deformable capsules."""
+    import dataclasses
+    import torch
+
+    case = W.poiseuille_biconcave(nx=4096, ny=512, count=256, n=128, seed=0, placement="grid", steps=steps)
+
+    def timed(ctx):
+        ctx.step(warmup, L.DYNAMIC)
+        ctx.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        ctx.step(steps, L.DYNAMIC)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ctx.sync()
+        return e0.elapsed_time(e1) / steps
+
+    out = {"workload": "4096x512 channel, 256 biconcave shapes x 128 vertices (seed 0), Dynamic, FP32",
+           "steps": steps}
+    ctx = L.from_case(case, storage="fp32")
+    ms = timed(ctx)
+    out["deformable"] = {"ms_per_step": ms, "mlups": case.nx * case.ny / ms / 1e3}
+    ctx.close()
+    ctx = L.from_case(dataclasses.replace(case, capsules=[]), storage="fp32", extra_nodes=case.n_nodes,
+                      extra_capsules=len(case.capsules))
+    for c in case.capsules:
+        A, _, _, J = W.polygon_inertia(c.xy)
+        ctx.add_rigid(c.xy, A, J)
+    ms = timed(ctx)
+    b = ctx.read_rigid(0)
+    out["rigid"] = {"ms_per_step": ms, "mlups": case.nx * case.ny / ms / 1e3,
+                    "particle0_after": {"c": [b[0], b[1]], "theta": b[2], "u": [b[3], b[4]], "omega": b[5]}}
+    ctx.close()
     return out
 
 
@@ -554,6 +595,7 @@ def main():
                else precision_run(L, int(os.environ.get("LOCAL_RANK", "0"))) if a.only == "precision"
                else dense_run(L) if a.only == "dense"
                else open_run(L) if a.only == "open"
+               else rigid_run(L) if a.only == "rigid"
                else {"dynamic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=1),
                      "kinematic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=0)})
         print(json.dumps(out), flush=True)

@@ -860,14 +860,14 @@ __global__ void __launch_bounds__(128) k_adjd_update(Nodes nd, int max_n, const 
 }
 
 // DR1t: transpose of the tractions (Eq. 15-16), nine threads per (element, probe), one
-// per node of the probe's support, 32 (element, probe) groups per CTA. Each end vertex
+// per node of the probe's support, kTractGroups (element, probe) groups per CTA. Each end vertex
 // receives half of the element force, so F_l-bar = (F^tot-bar_1 + F^tot-bar_2)/2. The
 // fields enter linearly: density through p and tau, the velocity gradient through tau;
 // the positions through the probe location, normal and length. Thread k of a group loads
 // the fields of support node k; threads 0-3 each take the derivative along one end
 // coordinate (single-lane duals, in parallel); every thread injects its own node's share
 // of the field adjoints.
-constexpr int kTractGroups = 32;
+constexpr int kTractGroups = 8;   // (element, probe) groups per CTA: 72 threads, work spread over many SMs
 
 template <typename S>
 __global__ void __launch_bounds__(9 * kTractGroups) k_adjd_tract(Lat L, Nodes nd, int count, const double2* Xn,
