@@ -867,10 +867,14 @@ __global__ void __launch_bounds__(128) k_adjd_update(Nodes nd, int max_n, const 
 // the fields of support node k; threads 0-3 each take the derivative along one end
 // coordinate (single-lane duals, in parallel); every thread injects its own node's share
 // of the field adjoints.
-constexpr int kTractGroups = 8;   // (element, probe) groups per CTA: 72 threads, work spread over many SMs
+// (element, probe) groups per CTA, and the CTA rounded up to whole warps (the spare
+// threads only join the final warp reduction): few groups per CTA spread the work over
+// many SMs
+constexpr int kTractGroups = 10;
+constexpr int kTractThreads = (9 * kTractGroups + 31) / 32 * 32;
 
 template <typename S>
-__global__ void __launch_bounds__(9 * kTractGroups) k_adjd_tract(Lat L, Nodes nd, int count, const double2* Xn,
+__global__ void __launch_bounds__(kTractThreads) k_adjd_tract(Lat L, Nodes nd, int count, const double2* Xn,
                                                                  const S* __restrict__ post1,
                                                                  const double* __restrict__ fib, const double2* ftb,
                                                                  double2* xout, double* sbar, double* bbar,
@@ -881,7 +885,7 @@ __global__ void __launch_bounds__(9 * kTractGroups) k_adjd_tract(Lat L, Nodes nd
     const int grp = threadIdx.x / 9, k = threadIdx.x - 9 * grp;
     const int t = blockIdx.x * kTractGroups + grp;
     const int g1 = t >> 1, s = t & 1;
-    const bool act = g1 < count;
+    const bool act = grp < kTractGroups && g1 < count;
     double gsx = 0.0, gsy = 0.0;
     bool ok = true;
     int g2 = 0, cx = 0, cy = 0;
@@ -1352,7 +1356,7 @@ lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* 
             k_adjd_interp<S><<<nblk(9LL * count, 288), 288, 0, s3>>>(L, post1, fib_n, shp, count, u2b, xout, sb_in,
                                                                      b_n, grad + 2 * ncaps);
             cudaEventRecord(ev_int, s3);
-            k_adjd_tract<S><<<nblk(2LL * count, kTractGroups), 9 * kTractGroups, 0, s>>>(
+            k_adjd_tract<S><<<nblk(2LL * count, kTractGroups), kTractThreads, 0, s>>>(
                 L, c->nd, count, Xn, post1, fib_n, (const double2*)(w + a.ftb), xout, sb_in, b_n, grad + 2 * ncaps,
                 &c->ctr->status);
             cudaStreamWaitEvent(s, ev_int, 0);
