@@ -199,6 +199,10 @@ __device__ Axis<T> mls_axis(T d0) {
     return r;
 }
 
+// Threads per CTA of the interpolation transposes (one thread per vertex and support
+// node, mapped over the whole grid): small CTAs spread a few capsules over many SMs.
+constexpr int kInterpThreads = 64;
+
 struct Shape {
     int cx, cy;
     bool ok;
@@ -385,7 +389,7 @@ __global__ void __launch_bounds__(128) k_adj_spread(Lat L, Nodes nd, const doubl
 // by R3.
 // ---------------------------------------------------------------------------------
 template <typename S>
-__global__ void __launch_bounds__(288) k_adj_interp(Lat L, const S* __restrict__ post1,
+__global__ void __launch_bounds__(kInterpThreads) k_adj_interp(Lat L, const S* __restrict__ post1,
                                                     const double* __restrict__ fib, const Shape* __restrict__ shp,
                                                     const int* age0, int nloc, int count, const double2* xc,
                                                     double2* xp, double2* xnew, double* sbar,
@@ -973,7 +977,7 @@ __global__ void __launch_bounds__(kTractThreads) k_adjd_tract(Lat L, Nodes nd, i
 // for a given U-bar: one thread per (vertex, support node). Adds to the population
 // adjoint, the half-force adjoint and dJ/dX^n (xout).
 template <typename S>
-__global__ void __launch_bounds__(288) k_adjd_interp(Lat L, const S* __restrict__ post, const double* __restrict__ fib,
+__global__ void __launch_bounds__(kInterpThreads) k_adjd_interp(Lat L, const S* __restrict__ post, const double* __restrict__ fib,
                                                      const Shape* __restrict__ shp, int count, const double2* ubar,
                                                      double2* xout, double* sbar, double* bbar, double* grad_g) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1275,7 +1279,7 @@ lbmib_status reverse_segment(lbmib_ctx* c, long long n0, int len, char* w, const
                 spread(n - 1, k - 1, s2);
                 cudaEventRecord(ev_spr, s2);
             }
-            k_adj_interp<S><<<nblk(9LL * count, 288), 288, 0, s>>>(L, post1, fib, shps[par],
+            k_adj_interp<S><<<nblk(9LL * count, kInterpThreads), kInterpThreads, 0, s>>>(L, post1, fib, shps[par],
                                                                    (const int*)(w + a.age0), k, count, xc, xp, xnew,
                                                                    sb_in, bbar, grad + 2 * ncaps, &c->ctr->status);
         }
@@ -1353,7 +1357,7 @@ lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* 
                                                    (double2*)(w + a.ftb), ncaps, grad);
             cudaEventRecord(ev_upd, s);
             cudaStreamWaitEvent(s3, ev_upd, 0);
-            k_adjd_interp<S><<<nblk(9LL * count, 288), 288, 0, s3>>>(L, post1, fib_n, shp, count, u2b, xout, sb_in,
+            k_adjd_interp<S><<<nblk(9LL * count, kInterpThreads), kInterpThreads, 0, s3>>>(L, post1, fib_n, shp, count, u2b, xout, sb_in,
                                                                      b_n, grad + 2 * ncaps);
             cudaEventRecord(ev_int, s3);
             k_adjd_tract<S><<<nblk(2LL * count, kTractGroups), kTractThreads, 0, s>>>(
@@ -1368,7 +1372,7 @@ lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* 
             k_adjd_forcing<<<ncaps, 128, smem, s>>>(L, c->nd, c->max_n, Xn, flc + (size_t)k * M, shp, fbar, b_n,
                                                     age0, k, xout, xm, ub, u1b);
             if (side) cudaStreamWaitEvent(s, ev_spr, 0);
-            k_adjd_interp<S><<<nblk(9LL * count, 288), 288, 0, s>>>(L, post0, fib_p, shp, count, u1b, xout, sb_out,
+            k_adjd_interp<S><<<nblk(9LL * count, kInterpThreads), kInterpThreads, 0, s>>>(L, post0, fib_p, shp, count, u1b, xout, sb_out,
                                                                     b_p, grad + 2 * ncaps);
         }
         c->launches += ncaps > 0 ? 7 : 1;
