@@ -293,7 +293,7 @@ def run_gpu(a):
 # FP64 instructions (DADD + DMUL + DFMA, thread level) per lattice update of the FP64
 # lattice kernel, from one ncu count (profiles/k_collide_stream_fp64_alu.md); GB300 issues
 # 2 such instructions per SM per cycle (ncu peak_sustained of the DFMA counter).
-FP64_INSTR_PER_UPDATE = 145.5
+FP64_INSTR_PER_UPDATE = 105.5
 FP64_INSTR_PER_SM_CYCLE = 2
 SM_COUNT = 152
 

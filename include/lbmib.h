@@ -221,6 +221,20 @@ size_t lbmib_state_bytes(const lbmib_ctx* ctx);
 lbmib_status lbmib_save_state(lbmib_ctx* ctx, void* host_buf, size_t bytes);
 lbmib_status lbmib_load_state(lbmib_ctx* ctx, const void* host_buf, size_t bytes);
 
+/* Device addresses of the context's fields, for zero-copy views (the one call that gives
+ * out device pointers; they point into the caller's arena). field:
+ *   LBMIB_FIELD_POPULATIONS  the latest post-collision populations in the storage type,
+ *                            stored shifted (f_i - w_i; FP16 times the storage scale),
+ *                            laid out [9][ny][pitch] with pitch >= nx elements per row;
+ *                            the pre-collision populations of the next step are their
+ *                            pull f_i(x) = f*_i(x - e_i) (reflected at walls).
+ *   LBMIB_FIELD_FORCE        the immersed-boundary force density of the last spread,
+ *                            double [2][ny][nx] (x plane, then y); pitch = nx.
+ * The two population and force buffers alternate from step to step: an address is valid
+ * until the next lbmib_step. Synchronises the context stream. */
+enum { LBMIB_FIELD_POPULATIONS = 0, LBMIB_FIELD_FORCE = 1 };
+lbmib_status lbmib_field_ptr(lbmib_ctx* ctx, int field, void** ptr, int* pitch);
+
 /* Options (lbmib_set_option):
  *   LBMIB_OPT_GRAPHS        1 (default): replay steps from captured CUDA graphs;
  *                           0: launch kernels directly.

@@ -556,6 +556,15 @@ lbmib_status lbmib_add_capsule(lbmib_ctx* c, const double* xy, int n, double ks,
     return LBMIB_OK;
 }
 
+lbmib_status lbmib_field_ptr(lbmib_ctx* c, int field, void** ptr, int* pitch) {
+    if (!c || !ptr || (field != LBMIB_FIELD_POPULATIONS && field != LBMIB_FIELD_FORCE))
+        return c ? fail(c, LBMIB_ERR_ARG, "unknown field") : LBMIB_ERR_ARG;
+    LBMIB_CUDA(c, cudaStreamSynchronize(c->stream));
+    *ptr = field == LBMIB_FIELD_POPULATIONS ? c->pops[c->cur] : (void*)c->fib[c->cur_fib];
+    if (pitch) *pitch = field == LBMIB_FIELD_POPULATIONS ? c->L.pitch : c->L.nx;
+    return LBMIB_OK;
+}
+
 lbmib_status lbmib_add_rigid(lbmib_ctx* c, const double* xy, int n, double mass, double inertia, int* id_out) {
     if (!c) return LBMIB_ERR_ARG;
     if (!xy || n < 3 || n > kMaxRing || !(mass > 0.0) || !(inertia > 0.0))

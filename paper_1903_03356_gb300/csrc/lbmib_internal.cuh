@@ -205,6 +205,11 @@ __device__ __forceinline__ void moments(const C s[9], C& drho, C& mx, C& my) {
 
 // BGK collision with the Guo forcing term (Eq. 4-5) on shifted populations, in place.
 // F is the total force density at the node. Returns u^2 for the stability check.
+// Opposite directions i and opp(i) see e.u and e.F change sign and their squares and
+// products not, so the shifted equilibrium and the Guo term split into a part even and
+// a part odd in e, computed once per pair:
+//   f_eq - w = w (drho + rho (4.5 (e.u)^2 - 1.5 u^2))  +/-  3 w rho (e.u)
+//   Guo term = (1 - 1/2tau) w (9 (e.u)(e.F) - 3 u.F)    +/-  3 (1 - 1/2tau) w (e.F)
 template <typename C>
 __device__ __forceinline__ C collide(C s[9], C Fx, C Fy, C omega) {
     C drho, mx, my;
@@ -216,17 +221,21 @@ __device__ __forceinline__ C collide(C s[9], C Fx, C Fy, C omega) {
     const C usq = ux * ux + uy * uy;
     const C u15 = C(1.5) * usq;
     const C fpre = C(1) - C(0.5) * omega;   // 1 - 1/(2 tau)
-    const C uF = ux * Fx + uy * Fy;
+    const C uF3 = C(3) * (ux * Fx + uy * Fy);
+    const C keep = C(1) - omega;
+    // rest population: even parts only
+    s[0] = keep * s[0] + wgt<C>(0) * (omega * (drho - rho * u15) - fpre * uF3);
+    // the pairs (1, 3), (2, 4), (5, 7), (6, 8): i has e = (ex, ey), opp(i) has -e
 #pragma unroll
-    for (int i = 0; i < 9; i++) {
+    for (int i : {1, 2, 5, 6}) {
+        const int j = opp(i);
         const C eu = C(ex(i)) * ux + C(ey(i)) * uy;
         const C eF = C(ex(i)) * Fx + C(ey(i)) * Fy;
-        // shifted equilibrium f_eq - w = w (drho + rho (3eu + 4.5eu^2 - 1.5u^2)): every
-        // term is small, so nothing cancels against the rest weight in float
-        const C seq = wgt<C>(i) * (drho + rho * (eu * (C(3) + C(4.5) * eu) - u15));
-        // Eq. 5: (1 - 1/2tau) w [3 (e - u) + 9 (e . u) e] . F
-        const C Fi = fpre * wgt<C>(i) * (C(3) * (eF - uF) + C(9) * eu * eF);
-        s[i] = s[i] - omega * (s[i] - seq) + Fi;
+        const C w = wgt<C>(i);
+        const C even = w * (omega * (drho + rho * (C(4.5) * eu * eu - u15)) + fpre * (C(9) * eu * eF - uF3));
+        const C odd = C(3) * w * (omega * rho * eu + fpre * eF);
+        s[i] = keep * s[i] + (even + odd);
+        s[j] = keep * s[j] + (even - odd);
     }
     if constexpr (sizeof(C) < 8) {
         // Single precision: rounding inside the collision would break the exact

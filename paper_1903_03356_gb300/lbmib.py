@@ -23,6 +23,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_UNSTABLE, ERR_SUPPORT, ERR_TIMEOUT, ERR_STAT
 FP64, FP32, FP16 = 0, 1, 2
 KINEMATIC, DYNAMIC = 0, 1
 OPT_GRAPHS, OPT_TIMING, OPT_GRAPH_STEPS, OPT_FP16_SCALE, OPT_LATTICE_VARIANT, OPT_OVERLAP, OPT_ARCS = 1, 2, 3, 4, 5, 6, 7
+FIELD_POPULATIONS, FIELD_FORCE = 0, 1
 OBJ_TAYLOR_D, OBJ_CENTROID_Y, OBJ_CENTROID_X = 0, 1, 2
 STORAGE = {"fp64": FP64, "fp32": FP32, "fp16": FP16}
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_UNSTABLE",
@@ -91,6 +92,7 @@ _SIGS = {
     "lbmib_set_inflow": (C.c_int, [_vp, _vp, C.c_double]),
     "lbmib_add_rigid": (C.c_int, [_vp, _vp, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_int)]),
     "lbmib_read_rigid": (C.c_int, [_vp, C.c_int, _vp]),
+    "lbmib_field_ptr": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(C.c_int)]),
     "lbmib_adjoint_workspace_bytes": (C.c_size_t, [_vp, C.c_longlong, C.c_int]),
     "lbmib_adjoint": (C.c_int, [_vp, C.c_longlong, C.c_int, C.c_int, C.c_int, C.c_int, _vp, C.c_size_t, _vp, _vp]),
     "lbmib_batch_arena_bytes": (C.c_size_t, [_vp, C.c_int, C.c_int]),
@@ -375,6 +377,27 @@ class Context:
         out = np.zeros(9)
         _check(self.h, _lib.lbmib_read_rigid(self.h, int(cid), out.ctypes.data_as(_vp)))
         return out
+
+    def field_view(self, field: int):
+        """Zero-copy torch view of a device field (no synchronisation afterwards; valid until
+        the next step): FIELD_POPULATIONS -> (9, ny, pitch) post-collision populations in the
+        storage dtype, stored as f_i - w_i (FP16: times the storage scale); FIELD_FORCE ->
+        (2, ny, nx) float64 immersed-boundary force of the last spread."""
+        import torch
+
+        ptr = _vp()
+        pitch = C.c_int(0)
+        _check(self.h, _lib.lbmib_field_ptr(self.h, int(field), C.byref(ptr), C.byref(pitch)))
+        off = ptr.value - self.arena.data_ptr()
+        if field == FIELD_POPULATIONS:
+            dtype = {STORAGE["fp64"]: torch.float64, STORAGE["fp32"]: torch.float32,
+                     STORAGE["fp16"]: torch.float16}[self.cfg.storage]
+            shape = (9, self.ny, pitch.value)
+        else:
+            dtype, shape = torch.float64, (2, self.ny, self.nx)
+        n = int(np.prod(shape))
+        size = torch.empty((), dtype=dtype).element_size()
+        return self.arena[off:off + n * size].view(dtype).view(shape)
 
     def set_inflow(self, u_in, rho_out: float = 1.0):
         """Open channel: Zou-He inlet with x-velocity u_in (ny values) at x = 0 and outlet
