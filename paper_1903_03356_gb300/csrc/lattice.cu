@@ -188,15 +188,33 @@ __global__ void __launch_bounds__(BS, MINB) k_collide_stream(const S* __restrict
 
     const C gx = lat_c<C>(L.gx, L.gxf), gy = lat_c<C>(L.gy, L.gyf), om = lat_c<C>(L.omega, L.omegaf);
     bool bad = false;
+    if constexpr (std::is_same<S, __half>::value) {
+        // FP16 storage (issue-bound): nodes in pairs, two lanes per instruction, as in the
+        // packed FP16 kernel, whose results this kernel reproduces bit for bit
 #pragma unroll
-    for (int j = 0; j < V; j++) {
-        C s[9];
+        for (int j = 0; j < V; j += 2) {
+            F2 s[9];
 #pragma unroll
-        for (int i = 0; i < 9; i++) s[i] = f[i][j];
-        const C usq = collide<C>(s, gx, gy, om);
-        bad |= !(usq < C(0.09));  // |u| > 0.3 or NaN
+            for (int i = 0; i < 9; i++) s[i] = F2{f[i][j], f[i][j + 1]};
+            const F2 usq = collide2(s, gx, gy, om);
+            bad |= !(usq.x < 0.09f) || !(usq.y < 0.09f);  // |u| > 0.3 or NaN
 #pragma unroll
-        for (int i = 0; i < 9; i++) f[i][j] = s[i];
+            for (int i = 0; i < 9; i++) {
+                f[i][j] = s[i].x;
+                f[i][j + 1] = s[i].y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            C s[9];
+#pragma unroll
+            for (int i = 0; i < 9; i++) s[i] = f[i][j];
+            const C usq = collide<C>(s, gx, gy, om);
+            bad |= !(usq < C(0.09));  // |u| > 0.3 or NaN
+#pragma unroll
+            for (int i = 0; i < 9; i++) f[i][j] = s[i];
+        }
     }
     if (full) {
 #pragma unroll
@@ -269,7 +287,34 @@ __device__ __forceinline__ float pop_value(const PopH<I>& p, __half across, int 
     if (wall || EX == 0) v = p.elem(j);
     else if (EX == 1) v = j == 0 ? across : p.elem(j - 1);
     else v = j == 7 ? across : p.elem(j + 1);
-    return __half2float(v) * inv_scale - (wall ? corr : 0.0f);
+    // unscaling never fused with the wall correction (as St<__half>::ld)
+    return __fmul_rn(__half2float(v), inv_scale) - (wall ? corr : 0.0f);
+}
+
+// The ragged chunk at the end of a row of the packed FP16 kernel (nx not a multiple of
+// 8): element-wise loads with the pull's own wrap, nodes in pairs with the lane arithmetic
+// of the full chunks (a missing partner repeats the node and is not stored). Run
+// by k_ragged_h. Returns whether a node is unstable.
+__device__ __forceinline__ bool ragged_chunk_h(const __half* __restrict__ src, __half* __restrict__ dst, const Lat& L,
+                                            int x0, int y, float gx, float gy, float om) {
+    bool bad = false;
+    for (int j = 0; j < 8 && x0 + j < L.nx; j += 2) {
+        const bool two = x0 + j + 1 < L.nx;
+        float a[9], b[9];
+        pull_all<__half>(src, L, x0 + j, y, a);
+        pull_all<__half>(src, L, two ? x0 + j + 1 : x0 + j, y, b);
+        F2 s[9];
+#pragma unroll
+        for (int i = 0; i < 9; i++) s[i] = F2{a[i], b[i]};
+        const F2 usq = collide2(s, gx, gy, om);
+        bad |= !(usq.x < 0.09f) || (two && !(usq.y < 0.09f));
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            St<__half>::st(dst + (long long)i * L.plane + (long long)y * L.pitch + x0 + j, s[i].x, L);
+            if (two) St<__half>::st(dst + (long long)i * L.plane + (long long)y * L.pitch + x0 + j + 1, s[i].y, L);
+        }
+    }
+    return bad;
 }
 
 template <int BS, int MINB>
@@ -307,28 +352,28 @@ __global__ void __launch_bounds__(BS, MINB) k_collide_stream_h(const __half* __r
     bool bad = false;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-        float r[2][9];
+        // nodes 2q and 2q + 1, two lanes per instruction
+        F2 s[9];
 #pragma unroll
         for (int t = 0; t < 2; t++) {
             const int j = 2 * q + t;
-            float s[9];
-            s[0] = pop_value(p0, a1, j, false, 0.0f, is);
-            s[1] = pop_value(p1, a1, j, false, 0.0f, is);
-            s[2] = pop_value(p2, a1, j, lo, c2, is);
-            s[3] = pop_value(p3, a3, j, false, 0.0f, is);
-            s[4] = pop_value(p4, a1, j, hi, c2, is);
-            s[5] = pop_value(p5, a5, j, lo, c5, is);
-            s[6] = pop_value(p6, a6, j, lo, c6, is);
-            s[7] = pop_value(p7, a7, j, hi, c7, is);
-            s[8] = pop_value(p8, a8, j, hi, c8, is);
-            const float usq = collide<float>(s, gx, gy, om);
-            bad |= !(usq < 0.09f);
-#pragma unroll
-            for (int i = 0; i < 9; i++) r[t][i] = s[i];
+            float* lane = t == 0 ? &s[0].x : &s[0].y;   // lane t of every population pair
+            lane[0 * 2] = pop_value(p0, a1, j, false, 0.0f, is);
+            lane[1 * 2] = pop_value(p1, a1, j, false, 0.0f, is);
+            lane[2 * 2] = pop_value(p2, a1, j, lo, c2, is);
+            lane[3 * 2] = pop_value(p3, a3, j, false, 0.0f, is);
+            lane[4 * 2] = pop_value(p4, a1, j, hi, c2, is);
+            lane[5 * 2] = pop_value(p5, a5, j, lo, c5, is);
+            lane[6 * 2] = pop_value(p6, a6, j, lo, c6, is);
+            lane[7 * 2] = pop_value(p7, a7, j, hi, c7, is);
+            lane[8 * 2] = pop_value(p8, a8, j, hi, c8, is);
         }
+        const F2 usq = collide2(s, gx, gy, om);
+        bad |= !(usq.x < 0.09f) || !(usq.y < 0.09f);
 #pragma unroll
         for (int i = 0; i < 9; i++) {
-            const __half2 hv = __floats2half2_rn(r[0][i] * sc, r[1][i] * sc);
+            const F2 v = s[i] * f2(sc);
+            const __half2 hv = __floats2half2_rn(v.x, v.y);
             (&out[i].x)[q] = *reinterpret_cast<const unsigned*>(&hv);
         }
     }
@@ -336,20 +381,18 @@ __global__ void __launch_bounds__(BS, MINB) k_collide_stream_h(const __half* __r
 #pragma unroll
         for (int i = 0; i < 9; i++)
             *reinterpret_cast<uint4*>(dst + (long long)i * L.plane + (long long)y * L.pitch + x0) = out[i];
-    } else if (active) {
-        // ragged chunk at the end of a row: element-wise, with the pull's own wrap
-        bad = false;
-        for (int j = 0; j < V && x0 + j < L.nx; j++) {
-            float s[9];
-            pull_all<__half>(src, L, x0 + j, y, s);
-            const float usq = collide<float>(s, gx, gy, om);
-            bad |= !(usq < 0.09f);
-#pragma unroll
-            for (int i = 0; i < 9; i++)
-                St<__half>::st(dst + (long long)i * L.plane + (long long)y * L.pitch + x0 + j, s[i], L);
-        }
-    }
-    if (__any_sync(0xffffffffu, bad && active) && lane == 0) atomicOr(status, kStatUnstable);
+    }   // a ragged chunk at the end of a row is k_ragged_h's
+    if (__any_sync(0xffffffffu, bad && full) && lane == 0) atomicOr(status, kStatUnstable);
+}
+
+// The ragged chunk at the end of every row of the packed FP16 kernel (nx not a multiple
+// of 8), one thread per row, launched after it: a separate kernel keeps the element-wise
+// path out of the hot kernel's registers.
+__global__ void __launch_bounds__(128) k_ragged_h(const __half* __restrict__ src, __half* __restrict__ dst, Lat L,
+                                                  unsigned* __restrict__ status) {
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= L.ny) return;
+    if (ragged_chunk_h(src, dst, L, L.nx / 8 * 8, y, L.gxf, L.gyf, L.omegaf)) atomicOr(status, kStatUnstable);
 }
 
 // Forced-node patch: redo the collision of every node in the current touched-cell list
@@ -509,6 +552,7 @@ void launch_collide_stream(const void* src, void* dst, const Lat& L, unsigned* s
             const unsigned g8 = blocks_for(segs8 * L.ny * 32, bs);
             if (bs == 128) k_collide_stream_h<128, 4><<<g8, 128, 0, s>>>(a, b, L, status);
             else k_collide_stream_h<256, 2><<<g8, 256, 0, s>>>(a, b, L, status);
+            if (L.nx % 8) k_ragged_h<<<blocks_for(L.ny, 128), 128, 0, s>>>(a, b, L, status);
             return;
         }
     }

@@ -97,11 +97,13 @@ struct St<float> {
 template <>
 struct St<__half> {
     using C = float;
+    // the unscaling is never fused with a following wall correction, so that every
+    // kernel rounds a loaded FP16 population the same way
     static __device__ __forceinline__ float ld(const __half* p, const Lat& L) {
-        return __half2float(__ldg(p)) * L.inv_scale;
+        return __fmul_rn(__half2float(__ldg(p)), L.inv_scale);
     }
     static __device__ __forceinline__ float ldc(const __half* p, const Lat& L) {
-        return __half2float(*p) * L.inv_scale;
+        return __fmul_rn(__half2float(*p), L.inv_scale);
     }
     static __device__ __forceinline__ void st(__half* p, float v, const Lat& L) {
         *p = __float2half_rn(v * L.scale);
@@ -247,6 +249,74 @@ __device__ __forceinline__ C collide(C s[9], C Fx, C Fy, C omega) {
         s[2] = s[4] + ((my + Fy) - ((s[5] + s[6]) - (s[7] + s[8])));
         s[0] = drho - (((s[1] + s[2]) + (s[3] + s[4])) + ((s[5] + s[6]) + (s[7] + s[8])));
     }
+    return usq;
+}
+
+// Two single-precision lanes in one instruction (packed FP32 add, sub, mul and fma of
+// sm_100 and later): the single-precision lattice kernels update lattice nodes in pairs.
+// Each lane rounds as the scalar instruction would.
+struct F2 {
+    float x, y;
+};
+__device__ __forceinline__ F2 f2(float a) { return F2{a, a}; }
+#define LBMIB_F2_BINARY(NAME, INSTR)                                                               \
+    __device__ __forceinline__ F2 NAME(F2 a, F2 b) {                                               \
+        F2 r;                                                                                      \
+        asm("{.reg .b64 ra, rb, rd;\n\t"                                                           \
+            "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t" INSTR " rd, ra, rb;\n\t"           \
+            "mov.b64 {%0, %1}, rd;}"                                                               \
+            : "=f"(r.x), "=f"(r.y)                                                                 \
+            : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                             \
+        return r;                                                                                  \
+    }
+LBMIB_F2_BINARY(operator+, "add.rn.f32x2")
+LBMIB_F2_BINARY(operator-, "sub.rn.f32x2")
+LBMIB_F2_BINARY(operator*, "mul.rn.f32x2")
+#undef LBMIB_F2_BINARY
+// a * b + c, one rounding per lane
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {
+    F2 r;
+    asm("{.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
+}
+
+// collide<float> (Eq. 4-5, the direction-pair form and the single-precision
+// conservation reset) on two nodes at once, lane by lane; the same uniform force at both.
+// Returns u^2 of each node.
+__device__ __forceinline__ F2 collide2(F2 s[9], float Fx, float Fy, float omega) {
+    const F2 drho = (((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]))) + s[8];
+    const F2 mx = ((s[1] - s[3]) + (s[5] - s[6])) + (s[8] - s[7]);
+    const F2 my = ((s[2] - s[4]) + (s[5] + s[6])) - (s[7] + s[8]);
+    const F2 rho = f2(1.0f) + drho;
+    const F2 inv = F2{1.0f / rho.x, 1.0f / rho.y};
+    const F2 ux = (mx + f2(0.5f * Fx)) * inv;
+    const F2 uy = (my + f2(0.5f * Fy)) * inv;
+    const F2 usq = fma2(ux, ux, uy * uy);
+    const F2 u15 = f2(1.5f) * usq;
+    const float fpre = 1.0f - 0.5f * omega;
+    const F2 uF3 = f2(3.0f) * fma2(ux, f2(Fx), uy * f2(Fy));
+    const F2 keep = f2(1.0f - omega), om = f2(omega);
+    s[0] = fma2(keep, s[0], f2(4.0f / 9.0f) * (om * (drho - rho * u15) - f2(fpre) * uF3));
+#pragma unroll
+    for (int i : {1, 2, 5, 6}) {
+        const int j = opp(i);
+        const F2 eu = i == 1 ? ux : (i == 2 ? uy : (i == 5 ? ux + uy : uy - ux));
+        const float eF = float(ex(i)) * Fx + float(ey(i)) * Fy;
+        const float w = wgt<float>(i);
+        const F2 even = f2(w) * fma2(om, fma2(rho, fma2(f2(4.5f) * eu, eu, f2(0.0f) - u15), drho),
+                                     f2(fpre) * (f2(9.0f * eF) * eu - uF3));
+        const F2 odd = f2(3.0f * w) * fma2(om * rho, eu, f2(fpre * eF));
+        s[i] = fma2(keep, s[i], even + odd);
+        s[j] = fma2(keep, s[j], even - odd);
+    }
+    // conservation reset (see collide<float>)
+    s[1] = s[3] + ((mx + f2(Fx)) - ((s[5] - s[6]) + (s[8] - s[7])));
+    s[2] = s[4] + ((my + f2(Fy)) - ((s[5] + s[6]) - (s[7] + s[8])));
+    s[0] = drho - (((s[1] + s[2]) + (s[3] + s[4])) + ((s[5] + s[6]) + (s[7] + s[8])));
     return usq;
 }
 
