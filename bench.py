@@ -35,7 +35,7 @@ METRIC = "LBM-IB MLUPS (coupled step) and % of HBM roofline"
 # the current kernel (see profiles/k_collide_stream_*.md); scaled to a full launch by the
 # number of updates. None where no capture of the current kernel exists.
 MEASURED_TRAFFIC_PER_UPDATE = {"fp32": (302.065152e6 + 251.889152e6) / (4096 * 2048), "fp64": None,
-                               "fp16": (151.071488e6 + 103.876608e6) / (4096 * 2048)}
+                               "fp16": (151.071232e6 + 107.023104e6) / (4096 * 2048)}
 
 
 def parse():

@@ -234,7 +234,11 @@ __global__ void __launch_bounds__(BS, MINB) k_collide_stream(const S* __restrict
 // population fetched with one aligned 16-byte load and kept packed (four half2
 // registers) until its node pair is collided; the results are packed back and stored
 // as 16-byte vectors. This keeps the bytes in flight per thread at the FP32 kernel's
-// (9 x 16 B) without holding 72 floats in registers.
+// (9 x 16 B) without holding 72 floats in registers. The kernel is bound to 6 blocks of
+// 128 per SM (80 registers, a few spilled values): the chains of packed instructions
+// need the warps more than the spilled registers cost (4, 5, 6, 7, 8 blocks: 119, 130,
+// 136, 132, 127 GLUPS on a 16384 x 8192 lattice; 8-byte half stores instead of the
+// 16-byte ones, to spill less, 129).
 template <int I>
 struct PopH {
     __half2 h[4];   // halves of the source row at x0 .. x0+7 (own opposite row at a wall)
@@ -550,8 +554,8 @@ void launch_collide_stream(const void* src, void* dst, const Lat& L, unsigned* s
         if (variant & (1 << 19)) {   // packed 16-byte FP16 kernel, 8 nodes per thread
             const long long segs8 = (L.nx + 255) / 256;
             const unsigned g8 = blocks_for(segs8 * L.ny * 32, bs);
-            if (bs == 128) k_collide_stream_h<128, 4><<<g8, 128, 0, s>>>(a, b, L, status);
-            else k_collide_stream_h<256, 2><<<g8, 256, 0, s>>>(a, b, L, status);
+            if (bs == 128) k_collide_stream_h<128, 6><<<g8, 128, 0, s>>>(a, b, L, status);
+            else k_collide_stream_h<256, 3><<<g8, 256, 0, s>>>(a, b, L, status);
             if (L.nx % 8) k_ragged_h<<<blocks_for(L.ny, 128), 128, 0, s>>>(a, b, L, status);
             return;
         }
