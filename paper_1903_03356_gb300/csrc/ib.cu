@@ -14,8 +14,10 @@
 // fit the tile budget takes the same path with global pulls and global atomics. The
 // kernels that need the enclosed area run each capsule's CTAs as a thread-block cluster
 // and add the arcs' partial sums through distributed shared memory.
-// Positions, velocities, forces, reference lengths and the MLS reciprocals are double
-// in every storage mode; in FP32/FP16 modes the weights and weighted sums are float.
+// Positions, velocities, forces and reference lengths are double in every storage mode;
+// in FP32/FP16 modes the MLS weights, their solve and the weighted sums are float. The
+// two Dynamic IB kernels are bound to 6 CTAs per SM: their FP64 work issues at 2 per SM
+// per cycle on GB300, and more resident CTAs keep that pipe fed.
 #include <cooperative_groups.h>
 
 #include <map>
@@ -239,7 +241,7 @@ __device__ __forceinline__ void copy_halo_terms(const CapSmem& sm, int m, bool e
 // u_v = U and X^{-1} = X^0 - U.
 // ---------------------------------------------------------------------------------
 template <typename S, bool RIGID>
-__global__ void __launch_bounds__(128) k_dyn_force_spread(const S* __restrict__ src, Lat L,
+__global__ void __launch_bounds__(128, 6) k_dyn_force_spread(const S* __restrict__ src, Lat L,
                                                           const double* __restrict__ fib_prev, Nodes nd, int max_n,
                                                           int arcs, int tile_cells, Spread sp, unsigned* status) {
     using C = typename St<S>::C;
@@ -336,7 +338,7 @@ __device__ void rigid_update(const Nodes& nd, const CapsuleParams& P, const Arc&
 // and its barrier also orders every CTA's reads of X^n (own and halo) before any CTA
 // writes X^{n+1}.
 template <typename S>
-__global__ void __launch_bounds__(128) k_dyn_update(const S* __restrict__ dst, Lat L,
+__global__ void __launch_bounds__(128, 6) k_dyn_update(const S* __restrict__ dst, Lat L,
                                                     const double* __restrict__ fib, Nodes nd, int max_n, int arcs,
                                                     int tile_cells, int* reset_count, unsigned* status) {
     using C = typename St<S>::C;

@@ -378,8 +378,8 @@ __device__ __forceinline__ double rcp_bounded(double x) {
 
 // Shape functions of the point (X, Y). The offsets of the support from the point are
 // formed in double (positions are double) and then held in the compute type; weights,
-// sums and the application are in the compute type; the solve (three reciprocals and
-// the weighted means) is in double.
+// sums, the solve (three reciprocals and the weighted means) and the application are in
+// the compute type, the double solve's reciprocals refined from a float seed.
 template <typename C>
 __device__ __forceinline__ MlsW<C> mls_setup(const Lat& L, double X, double Y) {
     MlsW<C> m;
@@ -397,22 +397,34 @@ __device__ __forceinline__ MlsW<C> mls_setup(const Lat& L, double X, double Y) {
         sy0 += m.wy[a];
         sy1 += m.wy[a] * dy[a];
     }
+    if constexpr (sizeof(C) == 4) {
+        // single precision: the solve in float as well (its error is of the order of the
+        // float weighted sums it is applied to), off GB300's narrow FP64 pipe
+        const C isx = C(1) / sx0, isy = C(1) / sy0;
+        const C mx = sx1 * isx, my = sy1 * isy;
+        C vx = 0, vy = 0;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            m.dxp[a] = dx[a] - mx;
+            m.dyp[a] = dy[a] - my;
+            vx += m.wx[a] * m.dxp[a] * m.dxp[a];
+            vy += m.wy[a] * m.dyp[a] * m.dyp[a];
+        }
+        const C rVx = (C(1) / vx) * isy, rVy = (C(1) / vy) * isx;
+        m.k0 = isx * isy;
+        m.kx = -mx * rVx;
+        m.ky = -my * rVy;
+        m.gx = rVx;
+        m.gy = rVy;
+        return m;
+    }
     const double isx = rcp_bounded((double)sx0), isy = rcp_bounded((double)sy0);
     const double mx = (double)sx1 * isx, my = (double)sy1 * isy;
     C vx = 0, vy = 0;
-    // centred offsets, held in the compute type: for a single-precision C the subtraction
-    // is done in C (its result differs from the rounded double difference by at most
-    // one unit in the last place), which keeps GB300's narrow FP64 pipe for the solve
-    const C mxc = C(mx), myc = C(my);
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        if constexpr (sizeof(C) == 8) {
-            m.dxp[a] = dx[a] - mx;
-            m.dyp[a] = dy[a] - my;
-        } else {
-            m.dxp[a] = dx[a] - mxc;
-            m.dyp[a] = dy[a] - myc;
-        }
+        m.dxp[a] = dx[a] - mx;
+        m.dyp[a] = dy[a] - my;
         vx += m.wx[a] * m.dxp[a] * m.dxp[a];
         vy += m.wy[a] * m.dyp[a] * m.dyp[a];
     }
