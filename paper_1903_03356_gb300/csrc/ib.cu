@@ -123,10 +123,10 @@ __device__ __forceinline__ bool interp_at(const Tile<typename St<S>::C>& t, cons
 // straight into the lattice field when the capsule has no tile.
 template <typename C>
 __device__ __forceinline__ bool spread_with(const MlsW<C>& m, Tile<C>& t, const Lat& L, const Spread& sp, int stamp,
-                                            double Fx, double Fy, double c) {
+                                            C Fx, C Fy, C c) {
     const long long N = (long long)L.nx * L.ny;
     const bool in_tile = t.holds(m.cx, m.cy);
-    const C cFx = C(c * Fx), cFy = C(c * Fy);
+    const C cFx = c * Fx, cFy = c * Fy;
 #pragma unroll
     for (int b = 0; b < 3; b++) {
 #pragma unroll
@@ -137,10 +137,10 @@ __device__ __forceinline__ bool spread_with(const MlsW<C>& m, Tile<C>& t, const 
                 atomicAdd(t.fx + k, phi * cFx);
                 atomicAdd(t.fy + k, phi * cFy);
             } else {
-                const double w = c * (double)phi;
+                const double w = (double)c * (double)phi;
                 const int cell = support_row(L, m.cy + b - 1) * L.nx + wrapi(m.cx + a - 1, L.nx);
-                atomicAdd(sp.fib + cell, w * Fx);
-                atomicAdd(sp.fib + N + cell, w * Fy);
+                atomicAdd(sp.fib + cell, w * (double)Fx);
+                atomicAdd(sp.fib + N + cell, w * (double)Fy);
                 touch(sp, cell, stamp);
             }
         }
@@ -218,9 +218,17 @@ __device__ __forceinline__ double2 rigid_velocity(const double* b, double2 X) {
 }
 
 // A whole ring's halo slots repeat its own last and first vertex: copy their terms
-// (and the element tractions when `ext`). Collective; ends with a barrier.
+// (and the element tractions when `ext`), double or single-precision (F32) ones.
+// Collective; ends with a barrier.
+template <bool F32 = false>
 __device__ __forceinline__ void copy_halo_terms(const CapSmem& sm, int m, bool ext) {
-    if (threadIdx.x == 0) {
+    if (F32 && threadIdx.x == 0) {
+        const int lo = kHalo - 1, last = kHalo + m - 1, hi = kHalo + m, first = kHalo;
+        RingF* R = ring_f(sm);
+        R[lo] = R[last];
+        R[hi] = R[first];
+        if (ext) ext_f(sm)[lo] = ext_f(sm)[last];
+    } else if (threadIdx.x == 0) {
         const int lo = kHalo - 1, last = kHalo + m - 1, hi = kHalo + m, first = kHalo;
         sm.sst[lo] = sm.sst[last];
         sm.bs[lo] = sm.bs[last];
@@ -235,13 +243,21 @@ __device__ __forceinline__ void copy_halo_terms(const CapSmem& sm, int m, bool e
     __syncthreads();
 }
 
+// Resident CTAs per SM the Dynamic IB kernels are compiled for: 6 in single precision
+// (80 registers; their FP64 work issues at 2 per SM per cycle on GB300 and more CTAs keep
+// that pipe fed), the register file's own limit in double, which would spill at 6.
+template <typename S>
+constexpr int dyn_min_blocks() {
+    return sizeof(typename St<S>::C) == 4 ? 6 : 1;
+}
+
 // ---------------------------------------------------------------------------------
 // Dynamic IB (Section 2.3.2), steps 1-3: U = I(u^n) with half of the last spread
 // force, F_l = u_v - U, spread with c_l = (l_left + l_right)/2. First step of a vertex:
 // u_v = U and X^{-1} = X^0 - U.
 // ---------------------------------------------------------------------------------
 template <typename S, bool RIGID>
-__global__ void __launch_bounds__(128, 6) k_dyn_force_spread(const S* __restrict__ src, Lat L,
+__global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_force_spread(const S* __restrict__ src, Lat L,
                                                           const double* __restrict__ fib_prev, Nodes nd, int max_n,
                                                           int arcs, int tile_cells, Spread sp, unsigned* status) {
     using C = typename St<S>::C;
@@ -256,11 +272,17 @@ __global__ void __launch_bounds__(128, 6) k_dyn_force_spread(const S* __restrict
         fill_moments<S>(t, src, L, fib_prev);
         zero_forces<C>(t);
     }
+    constexpr bool F32 = sizeof(C) == 4;   // single precision: lengths and forces in float
     // lengths of the elements on both sides of every own vertex (c_l of reading R4)
     for (int e = threadIdx.x; e < (m > 0 ? m + 1 : 0); e += blockDim.x) {
         const int li = kHalo - 1 + e;
         const double2 d = sm.X[li + 1] - sm.X[li];
-        sm.sst[li] = sqrt(d.x * d.x + d.y * d.y);
+        if constexpr (F32) {
+            const float dx = (float)d.x, dy = (float)d.y;
+            len_f(sm)[li] = sqrtf(dx * dx + dy * dy);
+        } else {
+            sm.sst[li] = sqrt(d.x * d.x + d.y * d.y);
+        }
     }
     __syncthreads();
     const int stamp = *sp.stamp + 1;
@@ -285,9 +307,16 @@ __global__ void __launch_bounds__(128, 6) k_dyn_force_spread(const S* __restrict
                 nd.Xm1[g] = Xv - uv;
             }
         }
-        const double cl = 0.5 * (sm.sst[li - 1] + sm.sst[li]);
-        if (nd.Flc) nd.Flc[g] = make_double2(cl * (uv.x - Ux), cl * (uv.y - Uy));
-        ok &= spread_with<C>(w, t, L, sp, stamp, uv.x - Ux, uv.y - Uy, cl);
+        if constexpr (F32) {
+            const float cl = 0.5f * (len_f(sm)[li - 1] + len_f(sm)[li]);
+            const float Fx = (float)uv.x - o.ux, Fy = (float)uv.y - o.uy;
+            if (nd.Flc) nd.Flc[g] = make_double2((double)(cl * Fx), (double)(cl * Fy));
+            ok &= spread_with<C>(w, t, L, sp, stamp, Fx, Fy, cl);
+        } else {
+            const double cl = 0.5 * (sm.sst[li - 1] + sm.sst[li]);
+            if (nd.Flc) nd.Flc[g] = make_double2(cl * (uv.x - Ux), cl * (uv.y - Uy));
+            ok &= spread_with<C>(w, t, L, sp, stamp, uv.x - Ux, uv.y - Uy, cl);
+        }
     }
     __syncthreads();
     if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
@@ -338,7 +367,7 @@ __device__ void rigid_update(const Nodes& nd, const CapsuleParams& P, const Arc&
 // and its barrier also orders every CTA's reads of X^n (own and halo) before any CTA
 // writes X^{n+1}.
 template <typename S>
-__global__ void __launch_bounds__(128, 6) k_dyn_update(const S* __restrict__ dst, Lat L,
+__global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_update(const S* __restrict__ dst, Lat L,
                                                     const double* __restrict__ fib, Nodes nd, int max_n, int arcs,
                                                     int tile_cells, int* reset_count, unsigned* status) {
     using C = typename St<S>::C;
@@ -362,8 +391,39 @@ __global__ void __launch_bounds__(128, 6) k_dyn_update(const S* __restrict__ dst
     // (tractions). A split ring adds two tasks for the halo: element and ring terms of
     // slot kHalo-1, ring terms of slot kHalo+m. A whole ring copies them instead.
     const bool split = m > 0 && m < a.n;   // an arc without vertices has no tasks
+    constexpr bool F32 = sizeof(C) == 4;   // single precision: membrane terms and tractions in float
     for (int k = threadIdx.x; k < (split ? m + 2 : m); k += blockDim.x) {
         const int li = k < m ? kHalo + k : (k == m ? kHalo - 1 : kHalo + m);
+        if constexpr (F32) {
+            vertex_terms_f(sm, P, nd, li - 1, li, li + 1, P.off + a.node(li));
+            if (k == m + 1) continue;
+            // the vertex's shape functions at X^n (stored by this step's spread kernel) place
+            // the probes of its element in float
+            const MlsW<C> w = reinterpret_cast<const MlsW<C>*>(nd.mls)[P.off + a.node(li)];
+            if (k < m) {
+                InterpT<C> o;
+                ok &= interp_with<S, false>(w, t, dst, L, fib, o);
+                xd_f(sm)[li] = make_float2(o.ux, o.uy);
+                area2[0] += area_term(a.X0, sm.X[li], sm.X[li + 1]);
+            }
+            // element li: probes at the centroid +/- 1.2 n+ (Section 2.2.2)
+            const float2 e = ring_f(sm)[li].e;
+            const float e2 = e.x * e.x + e.y * e.y, rl = rsqrtf(e2);
+            const float nx = e.y * rl, ny = -e.x * rl;
+            InterpT<C> op, om;
+            ok &= interp_with<S, true>(mls_near<C>(L, w, 0.5f * e.x + 1.2f * nx, 0.5f * e.y + 1.2f * ny), t, dst,
+                                       L, fib, op);
+            ok &= interp_with<S, true>(mls_near<C>(L, w, 0.5f * e.x - 1.2f * nx, 0.5f * e.y - 1.2f * ny), t, dst,
+                                       L, fib, om);
+            const C mp = op.rho * nu, mm = om.rho * nu;
+            const C txx = C(2) * (mp * op.dudx - mm * om.dudx);
+            const C tyy = C(2) * (mp * op.dvdy - mm * om.dvdy);
+            const C txy = mp * (op.dudy + op.dvdx) - mm * (om.dudy + om.dvdx);
+            const C dp = op.p - om.p;
+            const float len = e2 * rl;
+            ext_f(sm)[li] = make_float2((-dp * nx + txx * nx + txy * ny) * len, (-dp * ny + txy * nx + tyy * ny) * len);
+            continue;
+        }
         vertex_terms(sm, P, nd, li - 1, li, li + 1, P.off + a.node(li));
         if (k == m + 1) continue;
         const double2 Xv = sm.X[li], Xr = sm.X[li + 1];
@@ -395,24 +455,51 @@ __global__ void __launch_bounds__(128, 6) k_dyn_update(const S* __restrict__ dst
                                   (double)(-dp * ny + txy * nx + tyy * ny) * len);
     }
     block_reduce<1, false>(area2, sm.red);
-    if (m == a.n) copy_halo_terms(sm, m, true);
+    if (m == a.n) copy_halo_terms<F32>(sm, m, true);
     const double A = 0.5 * cluster_total(area2[0], arcs);
-    for (int k = threadIdx.x; k < m; k += blockDim.x) {
-        const int li = kHalo + k, g = P.off + a.v0 + k;
-        const double2 Fi = internal_force(sm, P, li - 1, li, li + 1, A);
-        double2 Fe = 0.5 * (sm.ext[li] + sm.ext[li - 1]);
-        if (nd.Fpp) Fe = Fe + nd.Fpp[g];   // Eq. 27, part of the total force (step 7)
-        const double2 Xv = sm.X[li];
-        const double2 Xm = nd.Xm1[g];
-        const double2 xd = sm.xd[li];
-        const double hm = 0.5 / P.m;
-        const double2 Xn = make_double2(Xv.x + xd.x + hm * (Fi.x + Fe.x), Xv.y + xd.y + hm * (Fi.y + Fe.y));
-        nd.uv[g] = make_double2(1.5 * Xn.x - 2.0 * Xv.x + 0.5 * Xm.x, 1.5 * Xn.y - 2.0 * Xv.y + 0.5 * Xm.y);
-        nd.Xm1[g] = Xv;
-        nd.X[g] = Xn;
-        nd.Fint[g] = Fi;
-        nd.Fext[g] = Fe;
-        nd.age[g] += 1;
+    if constexpr (F32) {
+        const float fa = (float)(P.ka * (1.0 - A / P.A0) * (1.0 / 6.0));   // Eq. 14, p_ref / 2
+        const float hm = (float)(0.5 / P.m);
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            const int li = kHalo + k, g = P.off + a.v0 + k;
+            const float2 Fi = internal_force_f(sm, li - 1, li, li + 1, fa);
+            const float2 e0 = ext_f(sm)[li], e1 = ext_f(sm)[li - 1];
+            float2 Fe = make_float2(0.5f * (e0.x + e1.x), 0.5f * (e0.y + e1.y));
+            if (nd.Fpp) {   // Eq. 27, part of the total force (step 7)
+                const double2 f = nd.Fpp[g];
+                Fe.x += (float)f.x;
+                Fe.y += (float)f.y;
+            }
+            const double2 Xv = sm.X[li], Xm = nd.Xm1[g];
+            const float2 xd = xd_f(sm)[li];
+            // Eq. 23 as the increment X^{n+1} - X^n, and Eq. 24 as
+            // 1.5 (X^{n+1} - X^n) - 0.5 (X^n - X^{n-1})
+            const double dx = (double)(xd.x + hm * (Fi.x + Fe.x)), dy = (double)(xd.y + hm * (Fi.y + Fe.y));
+            nd.uv[g] = make_double2(1.5 * dx - 0.5 * (Xv.x - Xm.x), 1.5 * dy - 0.5 * (Xv.y - Xm.y));
+            nd.Xm1[g] = Xv;
+            nd.X[g] = make_double2(Xv.x + dx, Xv.y + dy);
+            nd.Fint[g] = make_double2(Fi.x, Fi.y);
+            nd.Fext[g] = make_double2(Fe.x, Fe.y);
+            nd.age[g] += 1;
+        }
+    } else {
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            const int li = kHalo + k, g = P.off + a.v0 + k;
+            const double2 Fi = internal_force(sm, P, li - 1, li, li + 1, A);
+            double2 Fe = 0.5 * (sm.ext[li] + sm.ext[li - 1]);
+            if (nd.Fpp) Fe = Fe + nd.Fpp[g];   // Eq. 27, part of the total force (step 7)
+            const double2 Xv = sm.X[li];
+            const double2 Xm = nd.Xm1[g];
+            const double2 xd = sm.xd[li];
+            const double hm = 0.5 / P.m;
+            const double2 Xn = make_double2(Xv.x + xd.x + hm * (Fi.x + Fe.x), Xv.y + xd.y + hm * (Fi.y + Fe.y));
+            nd.uv[g] = make_double2(1.5 * Xn.x - 2.0 * Xv.x + 0.5 * Xm.x, 1.5 * Xn.y - 2.0 * Xv.y + 0.5 * Xm.y);
+            nd.Xm1[g] = Xv;
+            nd.X[g] = Xn;
+            nd.Fint[g] = Fi;
+            nd.Fext[g] = Fe;
+            nd.age[g] += 1;
+        }
     }
     if (!ok) atomicOr(status, kStatSupport);
 }

@@ -343,12 +343,19 @@ struct MlsW {
     C dxp[3], dyp[3];     // centred offsets dx_a - mx, dy_b - my
     C k0, kx, ky;         // value weights: phi_ab = wx_a wy_b (k0 + kx dxp_a + ky dyp_b)
     C gx, gy;             // gradient weights: wx_a wy_b dxp_a gx, wx_a wy_b dyp_b gy
+    C d0x, d0y;           // offset of the centre node from the point, (cx - X, cy - Y)
     bool ok;              // support inside the channel and the point sane
     // phi_k (Eq. 8) of support node (cx + a - 1, cy + b - 1)
     __device__ __forceinline__ C phi(int a, int b) const {
         return wx[a] * wy[b] * (k0 + kx * dxp[a] + ky * dyp[b]);
     }
 };
+
+// Whether the 3x3 support centred on node (cx, cy) stays inside the walls and, in an open
+// channel, off the inlet and outlet columns.
+__device__ __forceinline__ bool support_inside(const Lat& L, int cx, int cy) {
+    return (!L.walls || (cy >= 1 && cy <= L.ny - 2)) && (!L.inflow || (cx >= 2 && cx <= L.nx - 3));
+}
 
 // Support geometry of a point: centre node and whether the 3x3 block stays inside the
 // walls (and, in an open channel, off the open columns). A non-finite or runaway position (an unstable run) is moved to the origin so
@@ -361,8 +368,7 @@ __device__ __forceinline__ bool support_centre(const Lat& L, double& X, double& 
     }
     cx = (int)floor(X + 0.5);
     cy = (int)floor(Y + 0.5);
-    // open channel: the support (cx - 1 .. cx + 1) stays off the inlet and outlet columns
-    return sane && (!L.walls || (cy >= 1 && cy <= L.ny - 2)) && (!L.inflow || (cx >= 2 && cx <= L.nx - 3));
+    return sane && support_inside(L, cx, cy);
 }
 
 // Double reciprocal of a value known to lie well inside float range (the MLS weight
@@ -381,10 +387,42 @@ __device__ __forceinline__ double rcp_bounded(double x) {
 // sums, the solve (three reciprocals and the weighted means) and the application are in
 // the compute type, the double solve's reciprocals refined from a float seed.
 template <typename C>
+__device__ __forceinline__ MlsW<C> mls_weights(int cx, int cy, C d0x, C d0y, bool ok);
+
+template <typename C>
 __device__ __forceinline__ MlsW<C> mls_setup(const Lat& L, double X, double Y) {
+    int cx, cy;
+    const bool ok = support_centre(L, X, Y, cx, cy);
+    return mls_weights<C>(cx, cy, C((double)cx - X), C((double)cy - Y), ok);   // offsets in [-1/2, 1/2]
+}
+
+// Single precision: shape functions of the point at the float offset (ox, oy) from a point
+// whose own shape functions w are known (a probe beside a vertex). Its centre node and
+// offset are found in float from w's centre node and offset, off the FP64 pipe; a
+// non-finite or runaway offset (an unstable run) is taken as zero and reported.
+template <typename C>
+__device__ __forceinline__ MlsW<C> mls_near(const Lat& L, const MlsW<C>& w, float ox, float oy) {
+    float px = ox - (float)w.d0x, py = oy - (float)w.d0y;   // from the centre node of w
+    const bool sane = fabsf(px) < 1024.0f && fabsf(py) < 1024.0f;   // false for NaN too
+    if (!sane) {
+        px = 0.0f;
+        py = 0.0f;
+    }
+    const float kx = floorf(px + 0.5f), ky = floorf(py + 0.5f);
+    const int cx = w.cx + (int)kx, cy = w.cy + (int)ky;
+    return mls_weights<C>(cx, cy, C(kx - px), C(ky - py), w.ok && sane && support_inside(L, cx, cy));
+}
+
+// Shape functions of the point whose centre node (cx, cy) lies at the offset (d0x, d0y)
+// from it; `ok` from the support search.
+template <typename C>
+__device__ __forceinline__ MlsW<C> mls_weights(int cx, int cy, C d0x, C d0y, bool ok) {
     MlsW<C> m;
-    m.ok = support_centre(L, X, Y, m.cx, m.cy);
-    const C d0x = C((double)m.cx - X), d0y = C((double)m.cy - Y);   // in [-1/2, 1/2]
+    m.cx = cx;
+    m.cy = cy;
+    m.d0x = d0x;
+    m.d0y = d0y;
+    m.ok = ok;
     C dx[3], dy[3], sx0 = 0, sx1 = 0, sy0 = 0, sy1 = 0;
 #pragma unroll
     for (int a = 0; a < 3; a++) {

@@ -38,15 +38,17 @@ __device__ __forceinline__ CapSmem carve(unsigned char* base, int max_n) {
     return s;
 }
 
-// Reduction of K doubles over the block (blockDim.x a multiple of 32, <= 1024); MIN
-// selects minimum instead of sum. Every thread receives the results.
-template <int K, bool MIN>
-__device__ void block_reduce(double (&v)[K], double* red) {
+// Reduction of K doubles or floats over the block (blockDim.x a multiple of 32, <= 1024);
+// MIN selects minimum instead of sum. Every thread receives the results. `red_` is the
+// block's double scratch (32 * 8 doubles).
+template <int K, bool MIN, typename T>
+__device__ void block_reduce(T (&v)[K], double* red_) {
+    T* red = reinterpret_cast<T*>(red_);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; k++)
         for (int o = 16; o > 0; o >>= 1) {
-            const double t = __shfl_xor_sync(0xffffffffu, v[k], o);
+            const T t = __shfl_xor_sync(0xffffffffu, v[k], o);
             v[k] = MIN ? fmin(v[k], t) : v[k] + t;
         }
     __syncthreads();
@@ -56,7 +58,7 @@ __device__ void block_reduce(double (&v)[K], double* red) {
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; k++) {
-        double t = red[k];
+        T t = red[k];
         for (int w = 1; w < nw; w++) t = MIN ? fmin(t, red[w * K + k]) : t + red[w * K + k];
         v[k] = t;
     }
@@ -90,25 +92,31 @@ struct Tile {
 };
 
 // Bounding box of the staged slots [lo, hi) and the tile layout (no tile for an empty
-// range). Collective (all threads).
+// range). Collective (all threads). Only the floors of the extreme coordinates matter,
+// so the box is reduced in float (off the narrow FP64 pipe): every coordinate is rounded
+// down to float, which keeps its floor while |X| < 2^24 (every integer up to there is a
+// float), and floor is monotone, so the floors of the float minima and maxima are those of
+// the double ones. A box reaching beyond 2^24 (a runaway capsule) takes no tile.
 template <typename C>
 __device__ Tile<C> make_tile(const CapSmem& sm, int lo, int hi, int margin, int tile_cells, bool moments,
                              bool forces) {
-    double r[4] = {1e300, 1e300, 1e300, 1e300};  // min x, min y, -max x, -max y
+    constexpr float kBig = 3.0e38f, kLimit = 16777216.0f;
+    float r[4] = {kBig, kBig, kBig, kBig};  // min x, min y, -max x, -max y
     for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
         const double2 X = sm.X[v];
-        r[0] = fmin(r[0], X.x);
-        r[1] = fmin(r[1], X.y);
-        r[2] = fmin(r[2], -X.x);
-        r[3] = fmin(r[3], -X.y);
+        const float x = __double2float_rd(X.x), y = __double2float_rd(X.y);   // NaN: ignored by fminf
+        r[0] = fminf(r[0], x);
+        r[1] = fminf(r[1], y);
+        r[2] = fminf(r[2], -x);
+        r[3] = fminf(r[3], -y);
     }
     block_reduce<4, true>(r, sm.red);
     Tile<C> t;
-    const bool sane = fabs(r[0]) < 1e9 && fabs(r[1]) < 1e9 && fabs(r[2]) < 1e9 && fabs(r[3]) < 1e9;
-    t.x0 = sane ? (int)floor(r[0]) - margin : 0;
-    t.y0 = sane ? (int)floor(r[1]) - margin : 0;
-    const long long w = sane ? (long long)floor(-r[2]) + 1 + margin - t.x0 + 1 : 1LL << 30;
-    const long long h = sane ? (long long)floor(-r[3]) + 1 + margin - t.y0 + 1 : 1LL << 30;
+    const bool sane = fabsf(r[0]) < kLimit && fabsf(r[1]) < kLimit && fabsf(r[2]) < kLimit && fabsf(r[3]) < kLimit;
+    t.x0 = sane ? (int)floorf(r[0]) - margin : 0;
+    t.y0 = sane ? (int)floorf(r[1]) - margin : 0;
+    const long long w = sane ? (long long)floorf(-r[2]) + 1 + margin - t.x0 + 1 : 1LL << 30;
+    const long long h = sane ? (long long)floorf(-r[3]) + 1 + margin - t.y0 + 1 : 1LL << 30;
     t.use = sane && w * h <= tile_cells;
     t.w = t.use ? (int)w : 0;
     t.h = t.use ? (int)h : 0;
@@ -160,6 +168,68 @@ __device__ __forceinline__ void vertex_terms(const CapSmem& sm, const CapsulePar
     const double ia2 = ra * ra, ib2 = rb * rb;
     sm.bdl[v] = make_double2(-a.y * ia2, a.x * ia2);
     sm.bdr[v] = make_double2(-b.y * ib2, b.x * ib2);
+}
+
+// ---------------------------------------------------------------------------------
+// Single-precision membrane terms (FP32 and FP16 storage). Positions stay double; the
+// edge vectors are formed as double differences and then held in float, and the
+// stretch strain uses the difference of squares |b|^2 - L0^2 in double, so that the
+// strain keeps its relative precision however close |b| is to L0. The terms of a staged
+// slot live in the storage of the double bending derivatives (32 bytes per slot, bdl
+// and bdr being adjacent arrays), the element tractions and vertex velocities in the
+// first half of their double slots.
+// ---------------------------------------------------------------------------------
+struct RingF {
+    float sst, bs;    // stretch factor of element v, k_b sin(theta_v - theta_v0)
+    float2 bdl, bdr;  // d(theta_v)/dX_{v-1}, d(theta_v)/dX_{v+1}
+    float2 e;         // element vector X_{v+1} - X_v
+};
+static_assert(sizeof(RingF) == 2 * sizeof(double2), "a RingF slot spans one bdl and one bdr slot");
+
+__device__ __forceinline__ RingF* ring_f(const CapSmem& sm) { return reinterpret_cast<RingF*>(sm.bdl); }
+__device__ __forceinline__ float2* ext_f(const CapSmem& sm) { return reinterpret_cast<float2*>(sm.ext); }
+__device__ __forceinline__ float2* xd_f(const CapSmem& sm) { return reinterpret_cast<float2*>(sm.xd); }
+__device__ __forceinline__ float* len_f(const CapSmem& sm) { return reinterpret_cast<float*>(sm.sst); }
+
+// vertex_terms in single precision (the same Eq. 11 and Eq. 13 terms).
+__device__ __forceinline__ void vertex_terms_f(const CapSmem& sm, const CapsuleParams& P, const Nodes& nd, int vl,
+                                               int v, int vr, int g) {
+    const double2 Xv = sm.X[v], Xr = sm.X[vr], Xl = sm.X[vl];
+    const double2 ad = Xv - Xl, bd = Xr - Xv;   // incoming edge, outgoing edge (element v)
+    const double L0 = nd.L0[g];
+    const double b2d = bd.x * bd.x + bd.y * bd.y;
+    const float dsq = (float)fma(-L0, L0, b2d);   // |b|^2 - L0^2
+    const float2 a = make_float2((float)ad.x, (float)ad.y), b = make_float2((float)bd.x, (float)bd.y);
+    const float a2 = a.x * a.x + a.y * a.y, b2 = (float)b2d;
+    const float ra = rsqrtf(a2), rb = rsqrtf(b2);
+    const float lb = b2 * rb;
+    RingF& o = ring_f(sm)[v];
+    // Eq. 11: -k_s (|b| - L0) / |b| with |b| - L0 = (|b|^2 - L0^2) / (|b| + L0)
+    o.sst = -(float)P.ks * dsq / ((lb + (float)L0) * lb);
+    // Eq. 13: k_b sin(theta - theta_0) from the cross and dot products
+    const float cr = a.x * b.y - a.y * b.x, dt = a.x * b.x + a.y * b.y;
+    o.bs = (float)P.kb * ((cr * (float)nd.c0[g] - dt * (float)nd.s0[g]) * (ra * rb));
+    const float ia2 = ra * ra, ib2 = rb * rb;
+    o.bdl = make_float2(-a.y * ia2, a.x * ia2);
+    o.bdr = make_float2(-b.y * ib2, b.x * ib2);
+    o.e = b;
+}
+
+// internal_force in single precision from the float terms of slots vl, v, vr; fa is the
+// Eq. 14 factor k_a (1 - A/A0) p_ref / 2.
+__device__ __forceinline__ float2 internal_force_f(const CapSmem& sm, int vl, int v, int vr, float fa) {
+    const RingF* R = ring_f(sm);
+    const RingF c = R[v], l = R[vl];
+    const float bsr = R[vr].bs;
+    const float2 bdlr = R[vr].bdl;
+    // stretch: element v (this vertex first, X_v - X_{v+1} = -e_v) and element v-1 (this
+    // vertex second, X_{v-1} - X_v = -e_{v-1}); bending: own angle, as left neighbour of
+    // v+1, as right neighbour of v-1; area: (dy, -dx) of both elements, half each
+    float fx = -c.sst * c.e.x + l.sst * l.e.x + c.bs * (c.bdl.x + c.bdr.x) - bsr * bdlr.x - l.bs * l.bdr.x;
+    float fy = -c.sst * c.e.y + l.sst * l.e.y + c.bs * (c.bdl.y + c.bdr.y) - bsr * bdlr.y - l.bs * l.bdr.y;
+    fx += fa * (c.e.y + l.e.y);
+    fy -= fa * (c.e.x + l.e.x);
+    return make_float2(fx, fy);
 }
 
 // Element v's contribution to twice the enclosed area (Green's theorem about X_0).
