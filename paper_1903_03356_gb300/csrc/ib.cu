@@ -458,8 +458,10 @@ __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_update(const S
     if (m == a.n) copy_halo_terms<F32>(sm, m, true);
     const double A = 0.5 * cluster_total(area2[0], arcs);
     if constexpr (F32) {
-        const float fa = (float)(P.ka * (1.0 - A / P.A0) * (1.0 / 6.0));   // Eq. 14, p_ref / 2
-        const float hm = (float)(0.5 / P.m);
+        // Eq. 14 factor k_a (1 - A/A0) p_ref / 2 from the exact difference A0 - A (no
+        // double division on the narrow FP64 pipe)
+        const float fa = (float)P.ka * ((float)(P.A0 - A) / (6.0f * (float)P.A0));
+        const float hm = 0.5f / (float)P.m;
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
             const int li = kHalo + k, g = P.off + a.v0 + k;
             const float2 Fi = internal_force_f(sm, li - 1, li, li + 1, fa);

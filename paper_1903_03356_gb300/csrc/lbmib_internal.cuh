@@ -505,8 +505,8 @@ __device__ __forceinline__ Mom<typename St<S>::C> node_moments(const S* __restri
     const C inv = C(1) / (C(1) + drho);
     Mom<C> m;
     m.drho = drho;
-    m.ux = (mx + C(0.5) * C(L.gx + fib[n])) * inv;
-    m.uy = (my + C(0.5) * C(L.gy + fib[N + n])) * inv;
+    m.ux = (mx + C(0.5) * (C(L.gx) + C(fib[n]))) * inv;
+    m.uy = (my + C(0.5) * (C(L.gy) + C(fib[N + n]))) * inv;
     return m;
 }
 
