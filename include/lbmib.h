@@ -262,7 +262,14 @@ lbmib_status lbmib_field_ptr(lbmib_ctx* ctx, int field, void** ptr, int* pitch);
  *                           capsule while the capsules number at least the
  *                           multiprocessors, otherwise min(8, multiprocessors /
  *                           capsules, vertices / 16). Results do not depend on it
- *                           beyond the order of the area sum.                       */
+ *                           beyond the order of the area sum.
+ *   LBMIB_OPT_FUSE_IB       1 (default): within one lbmib_step call of the Dynamic
+ *                           scheme, the node update of a step and the force and
+ *                           spread of the next run as one kernel (both read the
+ *                           same lattice state; Section 2.3.2 steps 5-8 and 1-3)
+ *                           when every capsule has one CTA and the context holds no
+ *                           rigid particles; 0: separate kernels. The state between
+ *                           calls and the results do not depend on it.             */
 enum {
     LBMIB_OPT_GRAPHS = 1,
     LBMIB_OPT_TIMING = 2,
@@ -270,7 +277,8 @@ enum {
     LBMIB_OPT_FP16_SCALE = 4,
     LBMIB_OPT_LATTICE_VARIANT = 5,
     LBMIB_OPT_OVERLAP = 6,
-    LBMIB_OPT_ARCS = 7
+    LBMIB_OPT_ARCS = 7,
+    LBMIB_OPT_FUSE_IB = 8
 };
 lbmib_status lbmib_set_option(lbmib_ctx* ctx, int option, long long value);
 

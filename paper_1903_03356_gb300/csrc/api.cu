@@ -132,8 +132,16 @@ void join_ib(lbmib_ctx* c, cudaStream_t s) {
     cudaStreamWaitEvent(s, c->ev_join, 0);
 }
 
-// Enqueue one coupled step on stream s, advancing (cur, cur_fib).
-void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cudaStream_t s_lat, bool timed) {
+// Whether the Dynamic node update of a step may also do the force and spread of the next
+// (k_dyn_update_spread): one CTA per capsule and no rigid particles.
+bool fusable(const lbmib_ctx* c) { return c->fuse_ib && c->arcs == 1 && c->nrigid == 0 && !c->caps.empty(); }
+
+// Enqueue one coupled step on stream s, advancing (cur, cur_fib). `spread_done`: the
+// previous step's update already did this step's force and spread; `fuse_next`: another
+// step of the same scheme follows in this run, so the update may do its force and
+// spread. Returns whether it did.
+bool enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cudaStream_t s_lat, bool timed,
+                  bool spread_done, bool fuse_next) {
     const Lat& L = c->L;
     const int ncaps = (int)c->caps.size();
     const bool ov = overlapped(c);
@@ -150,7 +158,7 @@ void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
         launch_repulsion(L, c->nd, ncaps, c->max_n, c->arcs, c->rep, status, s);
         c->launches += 2;
     }
-    if (ncaps > 0) {
+    if (ncaps > 0 && !spread_done) {
         if (scheme == LBMIB_DYNAMIC) {
             if (st == LBMIB_FP64)
                 launch_dyn_force_spread<double>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, c->nrigid > 0, sp, status, s);
@@ -202,6 +210,20 @@ void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
             cudaStreamWaitEvent(s, c->ev_patch, 0);
         }
         int* reset = &c->ctr->count[fp];
+        if (scheme == LBMIB_DYNAMIC && fuse_next && fusable(c)) {
+            // the next step spreads into the buffer and list this step's patch has just
+            // cleared and read: reset their counter first (the fused kernel appends to it)
+            cudaMemsetAsync(reset, 0, sizeof(int), s);
+            const Spread next{c->fib[fp], c->mark, c->list[fp], reset, &c->ctr->step_stamp, list_cap, status};
+            if (st == LBMIB_FP64) launch_dyn_update_spread<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, next, status, s);
+            else if (st == LBMIB_FP32) launch_dyn_update_spread<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, next, status, s);
+            else launch_dyn_update_spread<__half>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, next, status, s);
+            if (ov) cudaEventRecord(c->ev_spread, s);
+            c->launches += 2;
+            cur_fib = fc;
+            cur = 1 - cur;
+            return true;
+        }
         if (scheme == LBMIB_DYNAMIC) {
             if (st == LBMIB_FP64) launch_dyn_update<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, c->nrigid > 0, reset, status, s);
             else if (st == LBMIB_FP32) launch_dyn_update<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, c->nrigid > 0, reset, status, s);
@@ -215,6 +237,14 @@ void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
         cur_fib = fc;
     }
     cur = 1 - cur;
+    return false;
+}
+
+// Enqueue n steps of one scheme on stream s, fusing each Dynamic update with the next
+// step's force and spread where fusable.
+void enqueue_steps(lbmib_ctx* c, lbmib_scheme scheme, long long n, int& cur, int& cur_fib, cudaStream_t s, bool timed) {
+    bool ahead = false;
+    for (long long k = 0; k < n; k++) ahead = enqueue_step(c, scheme, cur, cur_fib, s, timed, ahead, k + 1 < n);
 }
 
 lbmib_status device_status(lbmib_ctx* c) {
@@ -268,9 +298,6 @@ void update_arcs(lbmib_ctx* c) {
     drop_graphs(c);   // launch shapes may have changed
 }
 
-int kernels_per_step(const lbmib_ctx* c) {
-    return (c->caps.empty() ? 1 : (c->rep_rc > 0.0 && c->caps.size() > 1 ? 6 : 4)) + (c->L.inflow ? 1 : 0);
-}
 
 // Neighbour grid of the repulsion for the current capsules: coarse cells at least
 // 1.5 x the largest reference extent plus the cut-off (room for deformation; the bin
@@ -287,12 +314,14 @@ void update_rep_grid(lbmib_ctx* c) {
     c->nd.Fpp = c->rep_rc > 0.0 ? (double2*)(c->arena + c->lay.Fpp) : nullptr;
 }
 
-lbmib_status capture(lbmib_ctx* c, lbmib_scheme scheme, int cur, int cur_fib, int len, cudaGraphExec_t* out) {
+lbmib_status capture(lbmib_ctx* c, lbmib_scheme scheme, int cur, int cur_fib, int len, cudaGraphExec_t* out,
+                     long long* kernels) {
     LBMIB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     const long long launches = c->launches;
     fork_ib(c, c->cap_stream);
-    for (int k = 0; k < len; k++) enqueue_step(c, scheme, cur, cur_fib, c->cap_stream, false);
+    enqueue_steps(c, scheme, len, cur, cur_fib, c->cap_stream, false);
     join_ib(c, c->cap_stream);
+    *kernels = c->launches - launches;
     c->launches = launches;  // capture does not launch
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
@@ -667,7 +696,7 @@ lbmib_status lbmib_step(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme) {
     const int sc = scheme == LBMIB_DYNAMIC ? 1 : 0;
     if (c->timing || !c->use_graphs) {
         fork_ib(c, c->stream);
-        for (long long k = 0; k < nsteps; k++) enqueue_step(c, scheme, c->cur, c->cur_fib, c->stream, c->timing);
+        enqueue_steps(c, scheme, nsteps, c->cur, c->cur_fib, c->stream, c->timing);
         join_ib(c, c->stream);
     } else {
         const int G = c->graph_steps > 0 ? c->graph_steps : 1;
@@ -679,12 +708,12 @@ lbmib_status lbmib_step(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme) {
                 g = nullptr;
             }
             if (!g) {
-                lbmib_status st = capture(c, scheme, c->cur, c->cur_fib, G, &g);
+                lbmib_status st = capture(c, scheme, c->cur, c->cur_fib, G, &g, &c->graph_kernels[sc][c->cur][c->cur_fib]);
                 if (st != LBMIB_OK) return st;
                 c->graph_len[sc][c->cur][c->cur_fib] = G;
             }
             LBMIB_CUDA(c, cudaGraphLaunch(g, c->stream));
-            c->launches += (long long)G * kernels_per_step(c);
+            c->launches += c->graph_kernels[sc][c->cur][c->cur_fib];
             // advance the host copy of the buffer parities by G steps
             for (int k = 0; k < G; k++) {
                 if (!c->caps.empty()) c->cur_fib = 1 - c->cur_fib;
@@ -693,7 +722,7 @@ lbmib_status lbmib_step(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme) {
             left -= G;
         }
         fork_ib(c, c->stream);
-        for (long long k = 0; k < left; k++) enqueue_step(c, scheme, c->cur, c->cur_fib, c->stream, false);
+        enqueue_steps(c, scheme, left, c->cur, c->cur_fib, c->stream, false);
         join_ib(c, c->stream);
     }
     c->steps += nsteps;
@@ -953,6 +982,11 @@ lbmib_status lbmib_set_option(lbmib_ctx* c, int option, long long value) {
             break;
         case LBMIB_OPT_LATTICE_VARIANT:
             c->lattice_variant = (int)value;
+            drop_graphs(c);
+            break;
+        case LBMIB_OPT_FUSE_IB:
+            if (value < 0 || value > 1) return fail(c, LBMIB_ERR_ARG, "fuse must be 0 or 1");
+            c->fuse_ib = value != 0;
             drop_graphs(c);
             break;
         case LBMIB_OPT_ARCS:

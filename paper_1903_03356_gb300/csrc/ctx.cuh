@@ -81,9 +81,11 @@ struct lbmib_ctx {
     bool timing = false;
     int graph_steps = 16;
     int lattice_variant = 256;
-    // graphs keyed by (scheme, cur, cur_fib)
+    bool fuse_ib = true;
+    // graphs keyed by (scheme, cur, cur_fib), with their steps and kernel launches
     cudaGraphExec_t graphs[2][2][2]{};
     int graph_len[2][2][2]{};
+    long long graph_kernels[2][2][2]{};
     // timing
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
     size_t ev_used = 0;
@@ -110,7 +112,8 @@ void drop_graphs(lbmib_ctx* c);
 // last spread force c->fib[cur_fib]; advances (cur, cur_fib). With overlap on, the
 // immersed-boundary kernels go to c->ib_stream: a sequence of steps must be bracketed
 // by fork_ib() and join_ib() on s.
-void enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cudaStream_t s, bool timed);
+bool enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cudaStream_t s, bool timed,
+                  bool spread_done = false, bool fuse_next = false);
 void fork_ib(lbmib_ctx* c, cudaStream_t s);
 void join_ib(lbmib_ctx* c, cudaStream_t s);
 // Whether the immersed-boundary kernels run on their own stream, and the stream they

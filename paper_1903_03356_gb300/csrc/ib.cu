@@ -256,25 +256,17 @@ constexpr int dyn_min_blocks() {
 // force, F_l = u_v - U, spread with c_l = (l_left + l_right)/2. First step of a vertex:
 // u_v = U and X^{-1} = X^0 - U.
 // ---------------------------------------------------------------------------------
+// Steps 1-3 on a staged arc whose tile holds the moments of the lattice state and zeroed
+// force accumulators (collective; starts with a barrier-ordered pass over the element
+// lengths). Returns false when a support left the channel or the tile.
 template <typename S, bool RIGID>
-__global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_force_spread(const S* __restrict__ src, Lat L,
-                                                          const double* __restrict__ fib_prev, Nodes nd, int max_n,
-                                                          int arcs, int tile_cells, Spread sp, unsigned* status) {
+__device__ __forceinline__ bool dyn_spread(const S* __restrict__ src, const Lat& L, const double* __restrict__ fib_prev,
+                                           const Nodes& nd, const CapsuleParams& P, const Arc& a, const CapSmem& sm,
+                                           Tile<typename St<S>::C>& t, const Spread& sp, int stamp) {
     using C = typename St<S>::C;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const CapSmem sm = carve(smem, arc_slots(max_n, arcs));
-    CapsuleParams P;
-    Arc a;
-    if (!load_arc(nd, sm, max_n, arcs, true, P, a, status)) return;
-    const int m = a.m;
-    Tile<C> t = make_tile<C>(sm, kHalo, kHalo + m, 1, tile_cells, true, true);
-    if (t.use) {
-        fill_moments<S>(t, src, L, fib_prev);
-        zero_forces<C>(t);
-    }
     constexpr bool F32 = sizeof(C) == 4;   // single precision: lengths and forces in float
     // lengths of the elements on both sides of every own vertex (c_l of reading R4)
-    for (int e = threadIdx.x; e < (m > 0 ? m + 1 : 0); e += blockDim.x) {
+    for (int e = threadIdx.x; e < (a.m > 0 ? a.m + 1 : 0); e += blockDim.x) {
         const int li = kHalo - 1 + e;
         const double2 d = sm.X[li + 1] - sm.X[li];
         if constexpr (F32) {
@@ -285,9 +277,8 @@ __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_force_spread(c
         }
     }
     __syncthreads();
-    const int stamp = *sp.stamp + 1;
     bool ok = true;
-    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    for (int k = threadIdx.x; k < a.m; k += blockDim.x) {
         const int li = kHalo + k, g = P.off + a.v0 + k;
         const double2 Xv = sm.X[li];
         // shape functions at X^n: used for U, for the spread, and by this step's update
@@ -318,6 +309,26 @@ __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_force_spread(c
             ok &= spread_with<C>(w, t, L, sp, stamp, uv.x - Ux, uv.y - Uy, cl);
         }
     }
+    return ok;
+}
+
+template <typename S, bool RIGID>
+__global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_force_spread(const S* __restrict__ src, Lat L,
+                                                          const double* __restrict__ fib_prev, Nodes nd, int max_n,
+                                                          int arcs, int tile_cells, Spread sp, unsigned* status) {
+    using C = typename St<S>::C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CapSmem sm = carve(smem, arc_slots(max_n, arcs));
+    CapsuleParams P;
+    Arc a;
+    if (!load_arc(nd, sm, max_n, arcs, true, P, a, status)) return;
+    Tile<C> t = make_tile<C>(sm, kHalo, kHalo + a.m, 1, tile_cells, true, true);
+    if (t.use) {
+        fill_moments<S>(t, src, L, fib_prev);
+        zero_forces<C>(t);
+    }
+    const int stamp = *sp.stamp + 1;
+    const bool ok = dyn_spread<S, RIGID>(src, L, fib_prev, nd, P, a, sm, t, sp, stamp);
     __syncthreads();
     if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
     if (!ok) atomicOr(status, kStatSupport);
@@ -366,24 +377,15 @@ __device__ void rigid_update(const Nodes& nd, const CapsuleParams& P, const Arc&
 // With arcs > 1 the capsule's CTAs form a cluster: the enclosed area is summed over it,
 // and its barrier also orders every CTA's reads of X^n (own and halo) before any CTA
 // writes X^{n+1}.
+// Steps 5-8 on a staged arc (m own vertices; 0 for a rigid particle's CTAs) whose tile
+// holds the moments of the lattice state after the fluid update. Collective over the
+// capsule's cluster when arcs > 1. Returns false when a support left the channel or the
+// tile.
 template <typename S>
-__global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_update(const S* __restrict__ dst, Lat L,
-                                                    const double* __restrict__ fib, Nodes nd, int max_n, int arcs,
-                                                    int tile_cells, int* reset_count, unsigned* status) {
+__device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat& L, const double* __restrict__ fib,
+                                           const Nodes& nd, const CapsuleParams& P, const Arc& a, const CapSmem& sm,
+                                           const Tile<typename St<S>::C>& t, int arcs, int m) {
     using C = typename St<S>::C;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const CapSmem sm = carve(smem, arc_slots(max_n, arcs));
-    if (blockIdx.x == 0 && threadIdx.x == 0 && reset_count) *reset_count = 0;
-    CapsuleParams P;
-    Arc a;
-    if (!load_arc(nd, sm, max_n, arcs, true, P, a, status)) return;
-    // a rigid particle's CTAs do no work here (k_rigid_update moves it); they take part in
-    // the cluster's sums with nothing (a branch out would cost this kernel registers)
-    const int m = P.rigid ? 0 : a.m;
-    // vertices v0-1 .. v0+m: the ends of every element whose probes this CTA evaluates
-    Tile<C> t = make_tile<C>(sm, kHalo - 1, m > 0 ? kHalo + m + 1 : kHalo - 1, 3, tile_cells, true, false);
-    if (t.use) fill_moments<S>(t, dst, L, fib);
-    __syncthreads();
     bool ok = true;
     double area2[1] = {0.0};
     const C nu = C(L.nu);
@@ -503,6 +505,63 @@ __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_update(const S
             nd.age[g] += 1;
         }
     }
+    return ok;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_update(const S* __restrict__ dst, Lat L,
+                                                    const double* __restrict__ fib, Nodes nd, int max_n, int arcs,
+                                                    int tile_cells, int* reset_count, unsigned* status) {
+    using C = typename St<S>::C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CapSmem sm = carve(smem, arc_slots(max_n, arcs));
+    if (blockIdx.x == 0 && threadIdx.x == 0 && reset_count) *reset_count = 0;
+    CapsuleParams P;
+    Arc a;
+    if (!load_arc(nd, sm, max_n, arcs, true, P, a, status)) return;
+    // a rigid particle's CTAs do no work here (k_rigid_update moves it); they take part in
+    // the cluster's sums with nothing (a branch out would cost this kernel registers)
+    const int m = P.rigid ? 0 : a.m;
+    // vertices v0-1 .. v0+m: the ends of every element whose probes this CTA evaluates
+    Tile<C> t = make_tile<C>(sm, kHalo - 1, m > 0 ? kHalo + m + 1 : kHalo - 1, 3, tile_cells, true, false);
+    if (t.use) fill_moments<S>(t, dst, L, fib);
+    __syncthreads();
+    const bool ok = dyn_update<S>(dst, L, fib, nd, P, a, sm, t, arcs, m);
+    if (!ok) atomicOr(status, kStatSupport);
+}
+
+// Steps 5-8 of step n and steps 1-3 of step n+1 in one pass, for one CTA per capsule
+// and no rigid particles (the host launches it only then). Both read the lattice state
+// after step n's patch: the moments with half of the force spread in step n. So the tile
+// filled for the update at X^n also serves the interpolation and the spread at X^{n+1},
+// whose supports lie inside the update's margin unless a vertex moved more than two
+// lattice units in a step (flagged, as for any point that leaves its tile). The spread
+// goes to the other force buffer and list (sp), whose counter the host has reset.
+template <typename S>
+__global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_update_spread(const S* __restrict__ dst, Lat L,
+                                                                const double* __restrict__ fib, Nodes nd,
+                                                                int max_n, int tile_cells, Spread sp,
+                                                                unsigned* status) {
+    using C = typename St<S>::C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CapSmem sm = carve(smem, arc_slots(max_n, 1));
+    CapsuleParams P;
+    Arc a;
+    if (!load_arc(nd, sm, max_n, 1, true, P, a, status)) return;
+    Tile<C> t = make_tile<C>(sm, kHalo - 1, kHalo + a.m + 1, 3, tile_cells, true, true);
+    if (t.use) {
+        fill_moments<S>(t, dst, L, fib);
+        zero_forces<C>(t);
+    }
+    __syncthreads();
+    bool ok = dyn_update<S>(dst, L, fib, nd, P, a, sm, t, 1, a.m);
+    __syncthreads();   // every X^{n+1} is written; the staged X^n is dead
+    for (int li = threadIdx.x; li < a.m + 2 * kHalo; li += blockDim.x) sm.X[li] = nd.X[P.off + a.node(li)];
+    __syncthreads();
+    const int stamp = *sp.stamp + 1;
+    ok &= dyn_spread<S, false>(dst, L, fib, nd, P, a, sm, t, sp, stamp);
+    __syncthreads();
+    if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
     if (!ok) atomicOr(status, kStatSupport);
 }
 
@@ -783,6 +842,9 @@ void set_capsule_smem_limits(int slots, int cells) {
     LBMIB_SMEM(k_dyn_update<double>, double, true, false);
     LBMIB_SMEM(k_dyn_update<float>, float, true, false);
     LBMIB_SMEM(k_dyn_update<__half>, float, true, false);
+    LBMIB_SMEM(k_dyn_update_spread<double>, double, true, true);
+    LBMIB_SMEM(k_dyn_update_spread<float>, float, true, true);
+    LBMIB_SMEM(k_dyn_update_spread<__half>, float, true, true);
     LBMIB_SMEM(k_kin_advance<double>, double, true, false);
     LBMIB_SMEM(k_kin_advance<float>, float, true, false);
     LBMIB_SMEM(k_kin_advance<__half>, float, true, false);
@@ -838,6 +900,15 @@ void launch_dyn_update(const void* dst, const Lat& L, const double* fib_cur, Nod
                     status);
 }
 
+template <typename S>
+void launch_dyn_update_spread(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
+                              int cells, Spread sp_next, unsigned* status, cudaStream_t s) {
+    using C = typename St<S>::C;
+    const size_t sh = smem_bytes<C>(arc_slots(max_n, 1), cells, true, true);
+    launch_arcs(k_dyn_update_spread<S>, ncaps, 1, false, sh, s, (const S*)dst, L, fib_cur, nd, max_n, cells, sp_next,
+                status);
+}
+
 void launch_kin_force_spread(const Lat& L, Nodes nd, int ncaps, int max_n, int arcs, int cells, Spread sp,
                              unsigned* status, bool fp64_weights, cudaStream_t s) {
     // double MLS weights when the populations are double, float otherwise
@@ -876,6 +947,8 @@ void launch_interp_points(const void* src, const Lat& L, const double* fib, cons
                                              int, bool, Spread, unsigned*, cudaStream_t);                    \
     template void launch_dyn_update<S>(const void*, const Lat&, const double*, Nodes, int, int, int, int,    \
                                        bool, int*, unsigned*, cudaStream_t);                                 \
+    template void launch_dyn_update_spread<S>(const void*, const Lat&, const double*, Nodes, int, int, int,  \
+                                              Spread, unsigned*, cudaStream_t);                              \
     template void launch_kin_advance<S>(const void*, const Lat&, const double*, Nodes, int, int, int, int,   \
                                         int*, unsigned*, cudaStream_t);                                      \
     template void launch_interp_points<S>(const void*, const Lat&, const double*, const double2*, int,       \

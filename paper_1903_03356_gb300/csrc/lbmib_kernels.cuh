@@ -94,6 +94,11 @@ void launch_dyn_force_spread(const void* src, const Lat& L, const double* fib_pr
 template <typename S>
 void launch_dyn_update(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
                        int arcs, int cells, bool rigid, int* reset_count, unsigned* status, cudaStream_t s);
+// the node update of step n and the force and spread of step n+1 in one kernel (one CTA
+// per capsule, no rigid particles), spreading through sp_next
+template <typename S>
+void launch_dyn_update_spread(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
+                              int cells, Spread sp_next, unsigned* status, cudaStream_t s);
 void launch_kin_force_spread(const Lat& L, Nodes nd, int ncaps, int max_n, int arcs, int cells, Spread sp,
                              unsigned* status, bool fp64_weights, cudaStream_t s);
 template <typename S>
