@@ -283,7 +283,7 @@ __device__ __forceinline__ bool dyn_spread(const S* __restrict__ src, const Lat&
         const double2 Xv = sm.X[li];
         // shape functions at X^n: used for U, for the spread, and by this step's update
         const MlsW<C> w = mls_setup<C>(L, Xv.x, Xv.y);
-        reinterpret_cast<MlsW<C>*>(nd.mls)[g] = w;
+        store_mls<C>(nd.mls, g, w);
         InterpT<C> o;
         ok &= interp_with<S, false>(w, t, src, L, fib_prev, o);
         const double Ux = (double)o.ux, Uy = (double)o.uy;
@@ -401,7 +401,7 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
             if (k == m + 1) continue;
             // the vertex's shape functions at X^n (stored by this step's spread kernel) place
             // the probes of its element in float
-            const MlsW<C> w = reinterpret_cast<const MlsW<C>*>(nd.mls)[P.off + a.node(li)];
+            const MlsW<C> w = load_mls<C>(L, nd.mls, P.off + a.node(li));
             if (k < m) {
                 InterpT<C> o;
                 ok &= interp_with<S, false>(w, t, dst, L, fib, o);
@@ -431,8 +431,7 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
         const double2 Xv = sm.X[li], Xr = sm.X[li + 1];
         if (k < m) {
             InterpT<C> o;
-            ok &= interp_with<S, false>(reinterpret_cast<const MlsW<C>*>(nd.mls)[P.off + a.v0 + k], t, dst, L, fib,
-                                        o);
+            ok &= interp_with<S, false>(load_mls<C>(L, nd.mls, P.off + a.v0 + k), t, dst, L, fib, o);
             sm.xd[li] = make_double2((double)o.ux, (double)o.uy);
             area2[0] += area_term(a.X0, Xv, Xr);
         }
@@ -674,7 +673,7 @@ __global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int m
         const double2 Fp = nd.Fpp ? nd.Fpp[g] : make_double2(0.0, 0.0);   // Eq. 27
         nd.Fext[g] = make_double2(0.0, 0.0);
         const MlsW<C> w = mls_setup<C>(L, sm.X[li].x, sm.X[li].y);
-        reinterpret_cast<MlsW<C>*>(nd.mls)[g] = w;
+        store_mls<C>(nd.mls, g, w);
         ok &= spread_with<C>(w, t, L, sp, stamp, F.x + Fp.x, F.y + Fp.y, 1.0);
     }
     __syncthreads();
@@ -705,7 +704,7 @@ __global__ void __launch_bounds__(128) k_kin_advance(const S* __restrict__ dst, 
         const int g = P.off + a.v0 + k;
         const double2 Xv = sm.X[kHalo + k];
         InterpT<C> o;
-        ok &= interp_with<S, false>(reinterpret_cast<const MlsW<C>*>(nd.mls)[g], t, dst, L, fib, o);
+        ok &= interp_with<S, false>(load_mls<C>(L, nd.mls, g), t, dst, L, fib, o);
         const double Ux = (double)o.ux, Uy = (double)o.uy;
         double2 Xn;
         if (nd.age[g] == 0) {

@@ -345,6 +345,7 @@ struct MlsW {
     C gx, gy;             // gradient weights: wx_a wy_b dxp_a gx, wx_a wy_b dyp_b gy
     C d0x, d0y;           // offset of the centre node from the point, (cx - X, cy - Y)
     bool ok;              // support inside the channel and the point sane
+    bool sane;            // the point sane (else taken at the origin)
     // phi_k (Eq. 8) of support node (cx + a - 1, cy + b - 1)
     __device__ __forceinline__ C phi(int a, int b) const {
         return wx[a] * wy[b] * (k0 + kx * dxp[a] + ky * dyp[b]);
@@ -360,8 +361,10 @@ __device__ __forceinline__ bool support_inside(const Lat& L, int cx, int cy) {
 // Support geometry of a point: centre node and whether the 3x3 block stays inside the
 // walls (and, in an open channel, off the open columns). A non-finite or runaway position (an unstable run) is moved to the origin so
 // that every access stays inside the lattice, and reported as a support failure.
-__device__ __forceinline__ bool support_centre(const Lat& L, double& X, double& Y, int& cx, int& cy) {
+__device__ __forceinline__ bool support_centre(const Lat& L, double& X, double& Y, int& cx, int& cy,
+                                               bool* sane_out = nullptr) {
     const bool sane = fabs(X) < 1e9 && fabs(Y) < 1e9;   // false for NaN too
+    if (sane_out) *sane_out = sane;
     if (!sane) {
         X = 0.0;
         Y = 0.0;
@@ -392,8 +395,47 @@ __device__ __forceinline__ MlsW<C> mls_weights(int cx, int cy, C d0x, C d0y, boo
 template <typename C>
 __device__ __forceinline__ MlsW<C> mls_setup(const Lat& L, double X, double Y) {
     int cx, cy;
-    const bool ok = support_centre(L, X, Y, cx, cy);
-    return mls_weights<C>(cx, cy, C((double)cx - X), C((double)cy - Y), ok);   // offsets in [-1/2, 1/2]
+    bool sane;
+    const bool ok = support_centre(L, X, Y, cx, cy, &sane);
+    MlsW<C> m = mls_weights<C>(cx, cy, C((double)cx - X), C((double)cy - Y), ok);   // offsets in [-1/2, 1/2]
+    m.sane = sane;
+    return m;
+}
+
+// A vertex's shape functions at X^n, kept from the kernel that computes them to the node
+// update of the same step. Double: the whole MlsW (its solve is costly on the FP64 pipe).
+// Single precision: only where the support lies, one aligned 16-byte record (centre node
+// and offset; a NaN offset marks a position that was not sane), from which the update
+// rebuilds the same weights in float: an array of 88-byte records would cost a
+// scattered 32-byte sector per thread and word on every store and load.
+struct __align__(16) MlsFrame {
+    int cx, cy;
+    float d0x, d0y;
+};
+
+template <typename C>
+__device__ __forceinline__ void store_mls(void* base, long long g, const MlsW<C>& w) {
+    if constexpr (sizeof(C) == 8) {
+        reinterpret_cast<MlsW<C>*>(base)[g] = w;
+    } else {
+        reinterpret_cast<MlsFrame*>(base)[g] = MlsFrame{w.cx, w.cy, w.sane ? (float)w.d0x : __int_as_float(0x7fc00000),
+                                                        (float)w.d0y};
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ MlsW<C> load_mls(const Lat& L, const void* base, long long g) {
+    if constexpr (sizeof(C) == 8) {
+        return reinterpret_cast<const MlsW<C>*>(base)[g];
+    } else {
+        const MlsFrame f = reinterpret_cast<const MlsFrame*>(base)[g];
+        const bool sane = !isnan(f.d0x);
+        const int cx = sane ? f.cx : 0, cy = sane ? f.cy : 0;
+        MlsW<C> m = mls_weights<C>(cx, cy, sane ? C(f.d0x) : C(0), sane ? C(f.d0y) : C(0),
+                                   sane && support_inside(L, cx, cy));
+        m.sane = sane;
+        return m;
+    }
 }
 
 // Single precision: shape functions of the point at the float offset (ox, oy) from a point
@@ -410,7 +452,9 @@ __device__ __forceinline__ MlsW<C> mls_near(const Lat& L, const MlsW<C>& w, floa
     }
     const float kx = floorf(px + 0.5f), ky = floorf(py + 0.5f);
     const int cx = w.cx + (int)kx, cy = w.cy + (int)ky;
-    return mls_weights<C>(cx, cy, C(kx - px), C(ky - py), w.ok && sane && support_inside(L, cx, cy));
+    MlsW<C> m = mls_weights<C>(cx, cy, C(kx - px), C(ky - py), w.ok && sane && support_inside(L, cx, cy));
+    m.sane = w.sane && sane;
+    return m;
 }
 
 // Shape functions of the point whose centre node (cx, cy) lies at the offset (d0x, d0y)
@@ -423,6 +467,7 @@ __device__ __forceinline__ MlsW<C> mls_weights(int cx, int cy, C d0x, C d0y, boo
     m.d0x = d0x;
     m.d0y = d0y;
     m.ok = ok;
+    m.sane = true;
     C dx[3], dy[3], sx0 = 0, sx1 = 0, sy0 = 0, sy1 = 0;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
