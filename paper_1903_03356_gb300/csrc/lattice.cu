@@ -450,31 +450,60 @@ __global__ void __launch_bounds__(256) k_patch(const S* __restrict__ src, S* __r
 template <typename S>
 __global__ void k_init(S* __restrict__ dst, Lat L, const double* __restrict__ rho,
                        const double* __restrict__ ux, const double* __restrict__ uy) {
+    using C = typename St<S>::C;
     const long long N = (long long)L.nx * L.ny;
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const int y = (int)(n / L.nx), x = (int)(n - (long long)y * L.nx);
+    if constexpr (sizeof(C) == 4) {
+        // single precision: each node converts its own fields once (rho - 1 formed in
+        // double) and pushes its nine shifted equilibria to the nodes that pull them,
+        // which keeps the start-up off the narrow FP64 pipe; a population that would be
+        // pulled from beyond a wall is this node's own reflected one
+        const double r = rho ? rho[n] : 1.0;
+        const C dr = C(r - 1.0), rr = C(r), u = ux ? C(ux[n]) : C(0), v = uy ? C(uy[n]) : C(0);
+        const C u15 = C(1.5) * (u * u + v * v);
 #pragma unroll
-    for (int i = 0; i < 9; i++) {
-        int xt = x + ex(i), yt = y + ey(i);
-        int k = i;
-        double corr = 0.0;
-        if (L.walls && (yt < 0 || yt >= L.ny)) {
-            // consumed by this node as the reflected population opp(i)
-            k = opp(i);
-            corr = 6.0 * wgt<double>(i) * ex(i) * (yt < 0 ? L.ub : L.ut);
-            xt = x;
-            yt = y;
-        } else {
-            xt = wrapi(xt, L.nx);
-            yt = wrapi(yt, L.ny);
+        for (int i = 0; i < 9; i++) {
+            const C eu = C(ex(i)) * u + C(ey(i)) * v;
+            const C w = wgt<C>(i);
+            const int ys = y - ey(i);
+            if (!L.walls || (ys >= 0 && ys < L.ny)) {
+                const int xs = wrapi(x - ex(i), L.nx), yw = L.walls ? ys : wrapi(ys, L.ny);
+                St<S>::st(dst + (long long)i * L.plane + (long long)yw * L.pitch + xs,
+                          w * (dr + rr * (C(3) * eu + C(4.5) * eu * eu - u15)), L);
+            }
+            const int yt = y + ey(i);
+            if (L.walls && (yt < 0 || yt >= L.ny)) {
+                // f_opp(i) of this node's own fields (e_opp(i) . u = -e_i . u), with the
+                // moving-wall correction
+                const C corr = C(6.0 * wgt<double>(i) * ex(i) * (yt < 0 ? L.ub : L.ut));
+                St<S>::st(dst + (long long)i * L.plane + (long long)y * L.pitch + x,
+                          w * (dr + rr * (C(-3) * eu + C(4.5) * eu * eu - u15)) + corr, L);
+            }
         }
-        const long long m = (long long)yt * L.nx + xt;
-        const double r = rho ? rho[m] : 1.0, u = ux ? ux[m] : 0.0, v = uy ? uy[m] : 0.0;
-        const double eu = ex(k) * u + ey(k) * v;
-        const double feq = wgt<double>(k) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * (u * u + v * v));
-        St<S>::st(dst + (long long)i * L.plane + (long long)y * L.pitch + x,
-                  typename St<S>::C(feq - wgt<double>(i) + corr), L);
+    } else {
+    #pragma unroll
+        for (int i = 0; i < 9; i++) {
+            int xt = x + ex(i), yt = y + ey(i);
+            int k = i;
+            double corr = 0.0;
+            if (L.walls && (yt < 0 || yt >= L.ny)) {
+                // consumed by this node as the reflected population opp(i)
+                k = opp(i);
+                corr = 6.0 * wgt<double>(i) * ex(i) * (yt < 0 ? L.ub : L.ut);
+                xt = x;
+                yt = y;
+            } else {
+                xt = wrapi(xt, L.nx);
+                yt = wrapi(yt, L.ny);
+            }
+            const long long m = (long long)yt * L.nx + xt;
+            const double r = rho ? rho[m] : 1.0, u = ux ? ux[m] : 0.0, v = uy ? uy[m] : 0.0;
+            const double eu = ex(k) * u + ey(k) * v;
+            const double feq = wgt<double>(k) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * (u * u + v * v));
+            St<S>::st(dst + (long long)i * L.plane + (long long)y * L.pitch + x, C(feq - wgt<double>(i) + corr), L);
+        }
     }
 }
 
@@ -491,10 +520,16 @@ __global__ void k_macros(const S* __restrict__ src, Lat L, OpenBC ob, const doub
     pull_all<S>(src, L, x, y, s, &ob);
     C drho, mx, my;
     moments<C>(s, drho, mx, my);
-    const double r = 1.0 + (double)drho;
-    rho[n] = r;
-    ux[n] = ((double)mx + 0.5 * (L.gx + fib[n])) / r;
-    uy[n] = ((double)my + 0.5 * (L.gy + fib[N + n])) / r;
+    rho[n] = 1.0 + (double)drho;
+    if constexpr (sizeof(C) == 4) {   // single precision: the velocity in float, off the FP64 pipe
+        const C inv = C(1) / (C(1) + drho);
+        ux[n] = (double)((mx + C(0.5) * (C(L.gx) + C(fib[n]))) * inv);
+        uy[n] = (double)((my + C(0.5) * (C(L.gy) + C(fib[N + n]))) * inv);
+    } else {
+        const double r = 1.0 + (double)drho;
+        ux[n] = ((double)mx + 0.5 * (L.gx + fib[n])) / r;
+        uy[n] = ((double)my + 0.5 * (L.gy + fib[N + n])) / r;
+    }
 }
 
 // Read-back: unshifted pre-collision populations i0 .. i0+2 in double.
