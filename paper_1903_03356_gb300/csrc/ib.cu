@@ -258,8 +258,9 @@ constexpr int dyn_min_blocks() {
 // ---------------------------------------------------------------------------------
 // Steps 1-3 on a staged arc whose tile holds the moments of the lattice state and zeroed
 // force accumulators (collective; starts with a barrier-ordered pass over the element
-// lengths). Returns false when a support left the channel or the tile.
-template <typename S, bool RIGID>
+// lengths). Returns false when a support left the channel or the tile. FRAMED (single
+// precision): the support frames at X^n are already stored (by the previous update).
+template <typename S, bool RIGID, bool FRAMED = false>
 __device__ __forceinline__ bool dyn_spread(const S* __restrict__ src, const Lat& L, const double* __restrict__ fib_prev,
                                            const Nodes& nd, const CapsuleParams& P, const Arc& a, const CapSmem& sm,
                                            Tile<typename St<S>::C>& t, const Spread& sp, int stamp) {
@@ -282,8 +283,13 @@ __device__ __forceinline__ bool dyn_spread(const S* __restrict__ src, const Lat&
         const int li = kHalo + k, g = P.off + a.v0 + k;
         const double2 Xv = sm.X[li];
         // shape functions at X^n: used for U, for the spread, and by this step's update
-        const MlsW<C> w = mls_setup<C>(L, Xv.x, Xv.y);
-        store_mls<C>(nd.mls, g, w);
+        MlsW<C> w;
+        if constexpr (FRAMED && sizeof(C) == 4) {
+            w = load_mls<C>(L, nd.mls, g);
+        } else {
+            w = mls_setup<C>(L, Xv.x, Xv.y);
+            store_mls<C>(nd.mls, g, w);
+        }
         InterpT<C> o;
         ok &= interp_with<S, false>(w, t, src, L, fib_prev, o);
         const double Ux = (double)o.ux, Uy = (double)o.uy;
@@ -380,14 +386,16 @@ __device__ void rigid_update(const Nodes& nd, const CapsuleParams& P, const Arc&
 // Steps 5-8 on a staged arc (m own vertices; 0 for a rigid particle's CTAs) whose tile
 // holds the moments of the lattice state after the fluid update. Collective over the
 // capsule's cluster when arcs > 1. Returns false when a support left the channel or the
-// tile.
-template <typename S>
+// tile. NEXT (single precision, one CTA per ring): also store each vertex's support frame
+// at X^{n+1}, found from its frame at X^n and the increment, for the next step's spread.
+template <typename S, bool NEXT = false>
 __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat& L, const double* __restrict__ fib,
                                            const Nodes& nd, const CapsuleParams& P, const Arc& a, const CapSmem& sm,
                                            const Tile<typename St<S>::C>& t, int arcs, int m) {
     using C = typename St<S>::C;
     bool ok = true;
     double area2[1] = {0.0};
+    float area2f[1] = {0.0f};   // single precision
     const C nu = C(L.nu);
     // task k < m: own vertex kHalo+k (velocity, ring terms, area) and its element
     // (tractions). A split ring adds two tasks for the halo: element and ring terms of
@@ -406,7 +414,11 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
                 InterpT<C> o;
                 ok &= interp_with<S, false>(w, t, dst, L, fib, o);
                 xd_f(sm)[li] = make_float2(o.ux, o.uy);
-                area2[0] += area_term(a.X0, sm.X[li], sm.X[li + 1]);
+                // the area term (X_v - X_0) x (X_{v+1} - X_0) = (X_v - X_0) x e_v, in float:
+                // its rounding is of the order of the float membrane terms'
+                const double2 Xv = sm.X[li];
+                const float2 e = ring_f(sm)[li].e;
+                area2f[0] += (float)(Xv.x - a.X0.x) * e.y - (float)(Xv.y - a.X0.y) * e.x;
             }
             // element li: probes at the centroid +/- 1.2 n+ (Section 2.2.2)
             const float2 e = ring_f(sm)[li].e;
@@ -455,7 +467,12 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
         sm.ext[li] = make_double2((double)(-dp * nx + txx * nx + txy * ny) * len,
                                   (double)(-dp * ny + txy * nx + tyy * ny) * len);
     }
-    block_reduce<1, false>(area2, sm.red);
+    if constexpr (F32) {
+        block_reduce<1, false>(area2f, sm.red);
+        area2[0] = area2f[0];
+    } else {
+        block_reduce<1, false>(area2, sm.red);
+    }
     if (m == a.n) copy_halo_terms<F32>(sm, m, true);
     const double A = 0.5 * cluster_total(area2[0], arcs);
     if constexpr (F32) {
@@ -477,10 +494,29 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
             const float2 xd = xd_f(sm)[li];
             // Eq. 23 as the increment X^{n+1} - X^n, and Eq. 24 as
             // 1.5 (X^{n+1} - X^n) - 0.5 (X^n - X^{n-1})
-            const double dx = (double)(xd.x + hm * (Fi.x + Fe.x)), dy = (double)(xd.y + hm * (Fi.y + Fe.y));
+            const float ix = xd.x + hm * (Fi.x + Fe.x), iy = xd.y + hm * (Fi.y + Fe.y);
+            const double dx = (double)ix, dy = (double)iy;
             nd.uv[g] = make_double2(1.5 * dx - 0.5 * (Xv.x - Xm.x), 1.5 * dy - 0.5 * (Xv.y - Xm.y));
             nd.Xm1[g] = Xv;
-            nd.X[g] = make_double2(Xv.x + dx, Xv.y + dy);
+            const double2 Xn = make_double2(Xv.x + dx, Xv.y + dy);
+            nd.X[g] = Xn;
+            if constexpr (NEXT) {
+                // centre node of X^{n+1}: from the frame at X^n (offset d0 = c - X^n) and the
+                // increment, in float; the offset itself as the exact double difference. A
+                // non-finite or runaway position keeps the NaN mark of a position that is not
+                // sane.
+                MlsFrame f = reinterpret_cast<const MlsFrame*>(nd.mls)[g];
+                const float px = ix - f.d0x, py = iy - f.d0y;   // X^{n+1} - c
+                if (fabsf(px) < 1024.0f && fabsf(py) < 1024.0f) {   // false for NaN too
+                    f.cx += (int)floorf(px + 0.5f);
+                    f.cy += (int)floorf(py + 0.5f);
+                    f.d0x = (float)((double)f.cx - Xn.x);
+                    f.d0y = (float)((double)f.cy - Xn.y);
+                } else {
+                    f.d0x = __int_as_float(0x7fc00000);
+                }
+                reinterpret_cast<MlsFrame*>(nd.mls)[g] = f;
+            }
             nd.Fint[g] = make_double2(Fi.x, Fi.y);
             nd.Fext[g] = make_double2(Fe.x, Fe.y);
             nd.age[g] += 1;
@@ -553,12 +589,12 @@ __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_update_spread(
         zero_forces<C>(t);
     }
     __syncthreads();
-    bool ok = dyn_update<S>(dst, L, fib, nd, P, a, sm, t, 1, a.m);
+    bool ok = dyn_update<S, true>(dst, L, fib, nd, P, a, sm, t, 1, a.m);
     __syncthreads();   // every X^{n+1} is written; the staged X^n is dead
     for (int li = threadIdx.x; li < a.m + 2 * kHalo; li += blockDim.x) sm.X[li] = nd.X[P.off + a.node(li)];
     __syncthreads();
     const int stamp = *sp.stamp + 1;
-    ok &= dyn_spread<S, false>(dst, L, fib, nd, P, a, sm, t, sp, stamp);
+    ok &= dyn_spread<S, false, true>(dst, L, fib, nd, P, a, sm, t, sp, stamp);
     __syncthreads();
     if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
     if (!ok) atomicOr(status, kStatSupport);
