@@ -277,6 +277,7 @@ def run_gpu(a):
         line["e2e"] = e2e_run(a, case, L, scheme, dev)
     if rank == 0 and not a.no_extras:
         ctx.close()
+        line["ib_fp64"] = ib_fp64_run(L, a, case, scheme)
         line["precision"] = precision_run(L, dev)
         line["dense"] = dense_run(L)
         line["open"] = open_run(L)
@@ -338,6 +339,28 @@ def precision_run(L, dev, steps=(12, 60)):
         out[storage] = r
         ctx.close()
     return out
+
+
+def ib_fp64_run(L, a, case, scheme, steps=100, warmup=10):
+    """The main workload with the immersed-boundary arithmetic in FP64 over the same
+    storage (LBMIB_OPT_IB_FP64: gathers in storage precision; MLS solve, membrane and
+    traction forces and node update in double)."""
+    import torch
+
+    ctx = L.from_case(case, storage=a.storage)
+    ctx.set_option(L.OPT_IB_FP64, 1)
+    ctx.step(warmup, scheme)
+    ctx.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    ctx.step(steps, scheme)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ctx.close()
+    return {"workload": workload_name(a, case) + "-ib-fp64", "steps": steps, "ms_per_step": ms,
+            "mlups": a.nx * a.ny / ms / 1e3}
 
 
 def dense_run(L, steps=200, warmup=20, rc=2.0):

@@ -269,7 +269,13 @@ lbmib_status lbmib_field_ptr(lbmib_ctx* ctx, int field, void** ptr, int* pitch);
  *                           same lattice state; Section 2.3.2 steps 5-8 and 1-3)
  *                           when every capsule has one CTA and the context holds no
  *                           rigid particles; 0: separate kernels. The state between
- *                           calls and the results do not depend on it.             */
+ *                           calls and the results do not depend on it.
+ *   LBMIB_OPT_IB_FP64       1: with FP32 or FP16 storage the immersed-boundary kernels
+ *                           gather in storage precision and do the MLS solve, the
+ *                           membrane and traction forces and the node update in FP64
+ *                           (slower: GB300's FP64 rate); 0 (default): they compute in
+ *                           FP32 around FP64 positions, velocities and enclosed areas.
+ *                           No effect with FP64 storage.                             */
 enum {
     LBMIB_OPT_GRAPHS = 1,
     LBMIB_OPT_TIMING = 2,
@@ -278,7 +284,8 @@ enum {
     LBMIB_OPT_LATTICE_VARIANT = 5,
     LBMIB_OPT_OVERLAP = 6,
     LBMIB_OPT_ARCS = 7,
-    LBMIB_OPT_FUSE_IB = 8
+    LBMIB_OPT_FUSE_IB = 8,
+    LBMIB_OPT_IB_FP64 = 9
 };
 lbmib_status lbmib_set_option(lbmib_ctx* ctx, int option, long long value);
 

@@ -132,6 +132,23 @@ void join_ib(lbmib_ctx* c, cudaStream_t s) {
     cudaStreamWaitEvent(s, c->ev_join, 0);
 }
 
+// Calls f with a value of the storage type the immersed-boundary kernels are instantiated
+// on: the storage itself, or with LBMIB_OPT_IB_FP64 over single-precision storage its
+// widening view (gathers in storage precision, the IB arithmetic in FP64).
+template <typename F>
+void with_ib_storage(const lbmib_ctx* c, F&& f) {
+    switch (c->cfg.storage) {
+        case LBMIB_FP64: f(double{}); break;
+        case LBMIB_FP32:
+            if (c->ib_fp64) f(f32w{});
+            else f(float{});
+            break;
+        default:
+            if (c->ib_fp64) f(f16w{});
+            else f(__half{});
+    }
+}
+
 // Whether the Dynamic node update of a step may also do the force and spread of the next
 // (k_dyn_update_spread): one CTA per capsule and no rigid particles.
 bool fusable(const lbmib_ctx* c) { return c->fuse_ib && c->arcs == 1 && c->nrigid == 0 && !c->caps.empty(); }
@@ -160,14 +177,13 @@ bool enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
     }
     if (ncaps > 0 && !spread_done) {
         if (scheme == LBMIB_DYNAMIC) {
-            if (st == LBMIB_FP64)
-                launch_dyn_force_spread<double>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, c->nrigid > 0, sp, status, s);
-            else if (st == LBMIB_FP32)
-                launch_dyn_force_spread<float>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, c->nrigid > 0, sp, status, s);
-            else
-                launch_dyn_force_spread<__half>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, c->nrigid > 0, sp, status, s);
+            with_ib_storage(c, [&](auto v) {
+                launch_dyn_force_spread<decltype(v)>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells,
+                                                     c->nrigid > 0, sp, status, s);
+            });
         } else {
-            launch_kin_force_spread(L, c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, sp, status, st == LBMIB_FP64, s);
+            launch_kin_force_spread(L, c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, sp, status,
+                                    st == LBMIB_FP64 || c->ib_fp64, s);
         }
         c->launches++;
         if (ov) cudaEventRecord(c->ev_spread, s);
@@ -215,9 +231,10 @@ bool enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
             // cleared and read: reset their counter first (the fused kernel appends to it)
             cudaMemsetAsync(reset, 0, sizeof(int), s);
             const Spread next{c->fib[fp], c->mark, c->list[fp], reset, &c->ctr->step_stamp, list_cap, status};
-            if (st == LBMIB_FP64) launch_dyn_update_spread<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, next, status, s);
-            else if (st == LBMIB_FP32) launch_dyn_update_spread<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, next, status, s);
-            else launch_dyn_update_spread<__half>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, next, status, s);
+            with_ib_storage(c, [&](auto v) {
+                launch_dyn_update_spread<decltype(v)>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, next,
+                                                      status, s);
+            });
             if (ov) cudaEventRecord(c->ev_spread, s);
             c->launches += 2;
             cur_fib = fc;
@@ -225,13 +242,15 @@ bool enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
             return true;
         }
         if (scheme == LBMIB_DYNAMIC) {
-            if (st == LBMIB_FP64) launch_dyn_update<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, c->nrigid > 0, reset, status, s);
-            else if (st == LBMIB_FP32) launch_dyn_update<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, c->nrigid > 0, reset, status, s);
-            else launch_dyn_update<__half>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, c->nrigid > 0, reset, status, s);
+            with_ib_storage(c, [&](auto v) {
+                launch_dyn_update<decltype(v)>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells,
+                                               c->nrigid > 0, reset, status, s);
+            });
         } else {
-            if (st == LBMIB_FP64) launch_kin_advance<double>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, reset, status, s);
-            else if (st == LBMIB_FP32) launch_kin_advance<float>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, reset, status, s);
-            else launch_kin_advance<__half>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells, reset, status, s);
+            with_ib_storage(c, [&](auto v) {
+                launch_kin_advance<decltype(v)>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells,
+                                                reset, status, s);
+            });
         }
         c->launches += 2;
         cur_fib = fc;
@@ -982,6 +1001,11 @@ lbmib_status lbmib_set_option(lbmib_ctx* c, int option, long long value) {
             break;
         case LBMIB_OPT_LATTICE_VARIANT:
             c->lattice_variant = (int)value;
+            drop_graphs(c);
+            break;
+        case LBMIB_OPT_IB_FP64:
+            if (value < 0 || value > 1) return fail(c, LBMIB_ERR_ARG, "IB FP64 must be 0 or 1");
+            c->ib_fp64 = value != 0 && c->cfg.storage != LBMIB_FP64;
             drop_graphs(c);
             break;
         case LBMIB_OPT_FUSE_IB:

@@ -82,6 +82,7 @@ struct lbmib_ctx {
     int graph_steps = 16;
     int lattice_variant = 256;
     bool fuse_ib = true;
+    bool ib_fp64 = false;     // IB arithmetic in FP64 over single-precision storage
     // graphs keyed by (scheme, cur, cur_fib), with their steps and kernel launches
     cudaGraphExec_t graphs[2][2][2]{};
     int graph_len[2][2][2]{};

@@ -877,6 +877,18 @@ void set_capsule_smem_limits(int slots, int cells) {
     LBMIB_SMEM(k_dyn_update<double>, double, true, false);
     LBMIB_SMEM(k_dyn_update<float>, float, true, false);
     LBMIB_SMEM(k_dyn_update<__half>, float, true, false);
+    LBMIB_SMEM((k_dyn_force_spread<f32w, false>), double, true, true);
+    LBMIB_SMEM((k_dyn_force_spread<f16w, false>), double, true, true);
+    LBMIB_SMEM((k_dyn_force_spread<f32w, true>), double, true, true);
+    LBMIB_SMEM((k_dyn_force_spread<f16w, true>), double, true, true);
+    LBMIB_SMEM(k_rigid_update<f32w>, double, true, false);
+    LBMIB_SMEM(k_rigid_update<f16w>, double, true, false);
+    LBMIB_SMEM(k_dyn_update<f32w>, double, true, false);
+    LBMIB_SMEM(k_dyn_update<f16w>, double, true, false);
+    LBMIB_SMEM(k_dyn_update_spread<f32w>, double, true, true);
+    LBMIB_SMEM(k_dyn_update_spread<f16w>, double, true, true);
+    LBMIB_SMEM(k_kin_advance<f32w>, double, true, false);
+    LBMIB_SMEM(k_kin_advance<f16w>, double, true, false);
     LBMIB_SMEM(k_dyn_update_spread<double>, double, true, true);
     LBMIB_SMEM(k_dyn_update_spread<float>, float, true, true);
     LBMIB_SMEM(k_dyn_update_spread<__half>, float, true, true);
@@ -992,5 +1004,7 @@ void launch_interp_points(const void* src, const Lat& L, const double* fib, cons
 LBMIB_INSTANTIATE_IB(double)
 LBMIB_INSTANTIATE_IB(float)
 LBMIB_INSTANTIATE_IB(__half)
+LBMIB_INSTANTIATE_IB(f32w)
+LBMIB_INSTANTIATE_IB(f16w)
 
 }  // namespace lbmib

@@ -110,6 +110,38 @@ struct St<__half> {
     }
 };
 
+// Single-precision storage seen by the immersed-boundary kernels that compute in double
+// (LBMIB_OPT_IB_FP64): the same 4- and 2-byte words, loaded as the storage type and then
+// widened, so that those kernels keep their gathers in storage precision and do the MLS
+// solve, the membrane and traction forces and the node update in FP64.
+struct f32w {
+    float v;
+};
+struct f16w {
+    __half v;
+};
+static_assert(sizeof(f32w) == sizeof(float) && sizeof(f16w) == sizeof(__half), "storage views keep the word size");
+template <>
+struct St<f32w> {
+    using C = double;
+    static __device__ __forceinline__ double ld(const f32w* p, const Lat&) { return (double)__ldg(&p->v); }
+    static __device__ __forceinline__ double ldc(const f32w* p, const Lat&) { return (double)p->v; }
+    static __device__ __forceinline__ void st(f32w* p, double v, const Lat&) { p->v = (float)v; }
+};
+template <>
+struct St<f16w> {
+    using C = double;
+    static __device__ __forceinline__ double ld(const f16w* p, const Lat& L) {
+        return (double)__fmul_rn(__half2float(__ldg(&p->v)), L.inv_scale);
+    }
+    static __device__ __forceinline__ double ldc(const f16w* p, const Lat& L) {
+        return (double)__fmul_rn(__half2float(p->v), L.inv_scale);
+    }
+    static __device__ __forceinline__ void st(f16w* p, double v, const Lat& L) {
+        p->v = __float2half_rn((float)v * L.scale);
+    }
+};
+
 __device__ __forceinline__ int wrapi(int a, int n) {
     int r = a % n;
     return r < 0 ? r + n : r;

@@ -22,8 +22,8 @@ LIB_PATH = os.path.join(HERE, "liblbmib.so")
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_UNSTABLE, ERR_SUPPORT, ERR_TIMEOUT, ERR_STATE = range(8)
 FP64, FP32, FP16 = 0, 1, 2
 KINEMATIC, DYNAMIC = 0, 1
-OPT_GRAPHS, OPT_TIMING, OPT_GRAPH_STEPS, OPT_FP16_SCALE, OPT_LATTICE_VARIANT, OPT_OVERLAP, OPT_ARCS, OPT_FUSE_IB = \
-    1, 2, 3, 4, 5, 6, 7, 8
+OPT_GRAPHS, OPT_TIMING, OPT_GRAPH_STEPS, OPT_FP16_SCALE, OPT_LATTICE_VARIANT, OPT_OVERLAP, OPT_ARCS, OPT_FUSE_IB, \
+    OPT_IB_FP64 = 1, 2, 3, 4, 5, 6, 7, 8, 9
 FIELD_POPULATIONS, FIELD_FORCE = 0, 1
 OBJ_TAYLOR_D, OBJ_CENTROID_Y, OBJ_CENTROID_X = 0, 1, 2
 STORAGE = {"fp64": FP64, "fp32": FP32, "fp16": FP16}
