@@ -46,6 +46,29 @@ def test_library_exports_every_declared_symbol(lib):
     assert not missing, missing
 
 
+def header_constants():
+    """Every enumerator `LBMIB_NAME = value` that include/*.h declares."""
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for name, value in re.findall(r"\bLBMIB_(\w+)\s*=\s*(\d+)", text):
+            out[name] = int(value)
+    return out
+
+
+def test_binding_constants_match_the_header():
+    from paper_1903_03356_gb300 import lbmib
+    hc = header_constants()
+    checked = 0
+    for name, value in hc.items():
+        if isinstance(getattr(lbmib, name, None), int):
+            assert getattr(lbmib, name) == value, name
+            checked += 1
+    opts = [n for n in hc if n.startswith("OPT_")]
+    assert len(opts) >= 9 and all(hasattr(lbmib, n) for n in opts), opts
+    assert checked >= len(opts) + 5
+
+
 def _cfg(lib_mod, **kw):
     base = dict(nx=100, ny=64, walls=1, tau=0.8, u_bottom=0.0, u_top=0.0, gx=0.0, gy=0.0,
                 storage=1, max_capsules=4, max_nodes=512)
