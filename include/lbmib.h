@@ -243,8 +243,8 @@ lbmib_status lbmib_field_ptr(lbmib_ctx* ctx, int field, void** ptr, int* pitch);
  *   LBMIB_OPT_GRAPH_STEPS   steps per captured graph (default 16).
  *   LBMIB_OPT_FP16_SCALE    log2 of the FP16 storage scale (default 10).
  *   LBMIB_OPT_LATTICE_VARIANT launch shape of the lattice-update kernel: bits 0-11 the
- *                           block size (128 or 256), bit 18 a register cap that keeps
- *                           four blocks resident per SM instead of three, bit 19 (FP16
+ *                           block size (128 or 256), bit 18 a 64-register cap (eight
+ *                           128-thread or four 256-thread blocks resident per SM), bit 19 (FP16
  *                           storage) the kernel that moves 8 nodes per thread as packed
  *                           16-byte vectors. Default: 128 threads, with the cap for
  *                           FP32/FP16 storage and bit 19 for FP16. Results do not

@@ -449,7 +449,7 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     L.inv_scale = 1.0f / L.scale;
     L.nu = (cfg->tau - 0.5) / 3.0;
     // lattice launch shape measured fastest on GB300: 128-thread blocks, and for the
-    // single-precision storages a 64-register cap (four resident blocks per SM)
+    // single-precision storages a 64-register cap (eight resident blocks per SM)
     c->lattice_variant = cfg->storage == LBMIB_FP64 ? 0x80 : (0x80 | (1 << 18));
     if (cfg->storage == LBMIB_FP16) c->lattice_variant |= 1 << 19;   // packed 16-byte FP16 kernel
     L.gxf = (float)L.gx;
