@@ -468,6 +468,9 @@ class Context:
         lbmib_load_state(self.h, np.ascontiguousarray(buf))
 
     def set_option(self, option: int, value: int):
+        """lbmib_set_option: OPT_GRAPHS, OPT_TIMING, OPT_GRAPH_STEPS, OPT_FP16_SCALE,
+        OPT_LATTICE_VARIANT, OPT_OVERLAP, OPT_ARCS, OPT_FUSE_IB, OPT_IB_FP64 (meanings and
+        ranges in include/lbmib.h)."""
         lbmib_set_option(self.h, option, value)
 
     def kernel_time(self, reset=False):
