@@ -21,7 +21,13 @@
  * Readings of the paper where it is silent, ambiguous or garbled (each also listed in
  * the design notes of the repository):
  *   R1  Eq. 7 prints the forcing term F_i where the body force f_ib is meant:
- *       rho u = sum_i f_i e_i + f_ib / 2 (standard Guo form).
+ *       rho u = sum_i f_i e_i + f_ib / 2 (standard Guo form). The collision uses the
+ *       force of its own step; the fields read back and the Kinematic interpolation use
+ *       the last spread force.
+ *   R1d In the Dynamic scheme the IB force of a step is what is being determined (the
+ *       direct forcing of Favier et al., which Section 2.3 names): every interpolation of
+ *       that scheme (U of step 1, the probes of Eq. 15-16 and Eq. 17-18) takes the velocity
+ *       of the populations before any IB force, rho u = sum_i f_i e_i + g / 2.
  *   R2  Boundaries: half-way bounce-back with wall velocity; the correction uses the
  *       reference density rho_0 = 1 (keeps mass exactly conserved and is linear).
  *   R3  Markers are the membrane vertices; element quantities go half to each vertex.
@@ -36,7 +42,11 @@
  *   R7  Green's theorem area A = 1/2 sum (x_i y_{i+1} - x_{i+1} y_i); each end node of
  *       an element receives half of F^a_l; counter-clockwise rings, n+ = (dy, -dx)/l.
  *   R10 Eq. 25: the interpolated velocity is taken at the latest positions X^n.
- *   R11 Eq. 23: xdot_0 is interpolated after the fluid update, at X^n.
+ *   R11 Eq. 23: the tentative velocity xdot_0(t) is the fluid velocity at time t, the U of
+ *       step 1 (interpolated at X^n before the fluid update), as the Verlet form
+ *       x(t + dt) = x(t) + v(t) dt + a(t) dt^2 / 2 has it. (Interpolating it after the
+ *       update instead makes the step-1 forcing u_v - U grow with the fluid's acceleration
+ *       at the marker, and the coupled step is then unstable even with no membrane force.)
  *   R12 viscous stress tau = rho nu (grad u + grad u^T), pressure p = rho / 3.
  *   R15 Taylor D from the eigenvalues of the polygon's area second-moment tensor.
  *   R23 Capsule-capsule repulsion (Section 3.4, Eq. 27): a vertex feels every vertex of
@@ -928,15 +938,21 @@ static void dynamic_step(orc_sim* s) {
     size_t N = (size_t)L->nx * (size_t)L->ny;
     memset(s->fibnew, 0, 2 * N * sizeof(double));
     sim_repulsion(s);   /* Eq. 27 at X^n, part of the total force of step 7 */
-    /* 1-3: U = I(u^n) with half of the last spread force, F_l = (U_b - U)/dt, spread */
+    /* 1-3: U = I(u^n) of the populations before any IB force (R1d), F_l = (U_b - U)/dt,
+     * spread. U is also the tentative velocity of step 8 (R11). */
+    double** Ucap = (double**)malloc((s->ncaps > 0 ? s->ncaps : 1) * sizeof(double*));
     for (int c = 0; c < s->ncaps; c++) {
         orc_capsule* k = &s->caps[c];
         int n = k->n;
         double* F = (double*)malloc(2 * n * sizeof(double));
+        double* U = (double*)malloc(2 * n * sizeof(double));
+        Ucap[c] = U;
         for (int v = 0; v < n; v++) {
             double o[8];
-            if (orc_interp(L, s->f, s->fib, k->X[2 * v], k->X[2 * v + 1], o))
+            if (orc_interp(L, s->f, NULL, k->X[2 * v], k->X[2 * v + 1], o))
                 s->status = ORC_ERR_SUPPORT;
+            U[2 * v] = o[0];
+            U[2 * v + 1] = o[1];
             if (k->rigid) {
                 /* desired velocity: the rigid-body motion (R27) */
                 k->uv[2 * v] = k->body[3] - k->body[5] * (k->X[2 * v + 1] - k->body[1]);
@@ -970,7 +986,7 @@ static void dynamic_step(orc_sim* s) {
         orc_capsule* k = &s->caps[c];
         int n = k->n;
         if (k->rigid) {
-            if (orc_rigid_load(L, s->f, s->fib, k->X, n, k->body[0], k->body[1], k->load, k->Fext))
+            if (orc_rigid_load(L, s->f, NULL, k->X, n, k->body[0], k->body[1], k->load, k->Fext))
                 s->status = ORC_ERR_SUPPORT;
             for (int v = 0; v < n; v++) {   /* Eq. 27 on the markers (R28) */
                 k->load[0] += k->Fpp[2 * v];
@@ -984,27 +1000,22 @@ static void dynamic_step(orc_sim* s) {
             k->age++;
             continue;
         }
-        double* xdot0 = (double*)malloc(2 * n * sizeof(double));
         double* Ftot = (double*)malloc(2 * n * sizeof(double));
         double* Xnew = (double*)malloc(2 * n * sizeof(double));
-        for (int v = 0; v < n; v++) {
-            double o[8];
-            if (orc_interp(L, s->f, s->fib, k->X[2 * v], k->X[2 * v + 1], o))
-                s->status = ORC_ERR_SUPPORT;
-            xdot0[2 * v] = o[0];
-            xdot0[2 * v + 1] = o[1];
-        }
-        if (orc_tractions(L, s->f, s->fib, k->X, n, k->Fext)) s->status = ORC_ERR_SUPPORT;
+        /* 7: probe tractions on the updated populations (R1d), internal forces at X^n */
+        if (orc_tractions(L, s->f, NULL, k->X, n, k->Fext)) s->status = ORC_ERR_SUPPORT;
         orc_membrane_force(k->X, n, k->L0, k->th0, k->A0, k->ks, k->kb, k->ka, k->Fint);
         for (int m = 0; m < 2 * n; m++) Ftot[m] = k->Fint[m] + k->Fext[m] + k->Fpp[m];
-        orc_dynamic_advance(2 * n, k->X, k->Xm1, xdot0, Ftot, k->m, Xnew, k->uv);
+        /* 8: Eq. 23 with the tentative velocity U of step 1 (R11), Eq. 24 */
+        orc_dynamic_advance(2 * n, k->X, k->Xm1, Ucap[c], Ftot, k->m, Xnew, k->uv);
         memcpy(k->Xm1, k->X, 2 * n * sizeof(double));
         memcpy(k->X, Xnew, 2 * n * sizeof(double));
         k->age++;
-        free(xdot0);
         free(Ftot);
         free(Xnew);
     }
+    for (int c = 0; c < s->ncaps; c++) free(Ucap[c]);
+    free(Ucap);
 }
 
 /* scheme: 0 = Kinematic, 1 = Dynamic. Returns the sticky status. */

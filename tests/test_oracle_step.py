@@ -169,7 +169,7 @@ def test_dynamic_step_follows_steps_1_to_8():
     s = _sim(L, [(ref, ks, kb, ka, m)])
     s.init_fields(rho, ux, uy)
     s.step(3, o.DYNAMIC)
-    f, fib_prev = s.populations(), s.force_field()
+    f = s.populations()
     X, uv, _, _ = s.read_capsule(0)
     X, uv = X.reshape(-1, 2), uv.reshape(-1, 2)
     s2 = _sim(L, [(ref, ks, kb, ka, m)])
@@ -178,14 +178,15 @@ def test_dynamic_step_follows_steps_1_to_8():
     Xm1 = s2.read_capsule(0)[0].reshape(-1, 2)
     s.step(1, o.DYNAMIC)
     n = len(X)
-    U = np.array([o.interp(L, f, fib_prev, px, py)[0][:2] for px, py in X])   # Eq. 8
+    # Eq. 8 on the populations before any IB force (reading R1d): half of g only
+    U = np.array([o.interp(L, f, None, px, py)[0][:2] for px, py in X])
     F = uv - U                                                                # step 1
     fib = np.zeros((2, L.ny, L.nx))
     for v in range(n):                                                        # steps 2-3
         cl = 0.5 * (np.hypot(*(X[v] - X[v - 1])) + np.hypot(*(X[(v + 1) % n] - X[v])))
         o.spread(L, X[v, 0], X[v, 1], F[v, 0], F[v, 1], cl, fib)
     f1 = o.collide_stream(L, f, fib)                                          # steps 4-6
-    xd0 = np.array([o.interp(L, f1, fib, px, py)[0][:2] for px, py in X])
+    xd0 = U                      # tentative velocity of Eq. 23: U of step 1 (reading R11)
     nu = (0.8 - 0.5) / 3
     Fext = np.zeros_like(X)                                                   # Eq. 15-16
     for l in range(n):
@@ -194,8 +195,8 @@ def test_dynamic_step_follows_steps_1_to_8():
         ln = np.hypot(*d)
         npl = np.array([d[1], -d[0]]) / ln
         c = 0.5 * (a + b)
-        op = o.interp(L, f1, fib, *(c + 1.2 * npl))[0]
-        om = o.interp(L, f1, fib, *(c - 1.2 * npl))[0]
+        op = o.interp(L, f1, None, *(c + 1.2 * npl))[0]      # probes: reading R1d
+        om = o.interp(L, f1, None, *(c - 1.2 * npl))[0]
         gp = op[4:].reshape(2, 2); gm = om[4:].reshape(2, 2)
         tp = op[2] * nu * (gp + gp.T); tm = om[2] * nu * (gm + gm.T)
         Fl = -(op[3] - om[3]) * npl * ln + (tp - tm) @ npl * ln
