@@ -32,10 +32,9 @@ FALLBACK_HBM_GBS = 6800.0
 METRIC = "LBM-IB MLUPS (coupled step) and % of HBM roofline"
 
 # DRAM bytes (read + write) per lattice update of k_collide_stream from one ncu capture of
-# the current kernel (see profiles/k_collide_stream_*.md); scaled to a full launch by the
-# number of updates. None where no capture of the current kernel exists.
-MEASURED_TRAFFIC_PER_UPDATE = {"fp32": (302.065152e6 + 251.889152e6) / (4096 * 2048), "fp64": None,
-                               "fp16": (151.071232e6 + 107.023104e6) / (4096 * 2048)}
+# the current kernel on a lattice whose writes dwarf L2 (profiles/k_collide_stream_*.md);
+# scaled to a full launch by the number of updates. None where no such capture exists.
+MEASURED_TRAFFIC_PER_UPDATE = {"fp32": None, "fp64": None, "fp16": None}
 
 
 def parse():
@@ -43,7 +42,8 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=20)
-    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference", "oracle-sample"],
+                   help="oracle-sample: internal, one timed oracle sample printed as JSON (the all-core run)")
     p.add_argument("--nx", type=int, default=16384)
     p.add_argument("--ny", type=int, default=8192)
     p.add_argument("--storage", default="fp32", choices=["fp64", "fp32", "fp16"])
@@ -58,7 +58,13 @@ def parse():
     p.add_argument("--adjoint-steps", type=int, default=800, help="horizon T of the adjoint measurement")
     p.add_argument("--batch-autotune", type=int, default=20,
                    help="steps per candidate launch shape of the batch autotuner (0: default shape)")
-    p.add_argument("--only", default="all", choices=["all", "batched", "adjoint", "precision", "dense", "open", "rigid"],
+    p.add_argument("--sample-steps", type=int, default=0, help="oracle-sample: timed steps (0: time-bounded)")
+    p.add_argument("--study-out", default="", help="oracle-sample --only study: where the oracle's state goes")
+    p.add_argument("--study-steps", type=int, default=5000, help="precision study: steps of the GPU runs")
+    p.add_argument("--study-oracle-steps", type=int, default=100,
+                   help="precision study: steps of the FP64 oracle run the GPU runs are compared with")
+    p.add_argument("--only", default="all",
+                   choices=["all", "batched", "adjoint", "precision", "dense", "open", "rigid", "study", "fp64"],
                    help="batched / adjoint: run only that measurement and print its JSON object")
     return p.parse_args()
 
@@ -159,50 +165,121 @@ def job_throughput(units_per_rank: float, elapsed_ms: float, world: int, dist, d
     return world * units_per_rank / (slowest / 1e3), slowest
 
 
-def cpu_baseline(a, seconds: float):
-    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload: a
-    2048 x 512 slab of the same channel with the same capsule density."""
-    import oracle as o
-    nx, ny = 2048, 512
+def host_cpu():
+    """Model and logical core count of the host that runs the CPU baseline."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu model")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return {"cpu_model": model or "unknown", "nproc": os.cpu_count()}
+
+
+SLAB = (2048, 512)
+
+
+def slab_case(a):
+    """The bounded CPU sample of the workload: a 2048 x 512 slab of the same channel with
+    the same capsule density (one 128-vertex biconcave capsule per 8192 nodes)."""
+    nx, ny = SLAB
     scheme = W.DYNAMIC if a.scheme == "dynamic" else W.KINEMATIC
     if a.no_capsules:
-        case = W.Case("slab", nx, ny, 0.7, True, gx=W.poiseuille_force(0.7, 0.02, a.ny), init="parabola")
-    else:
-        case = W.poiseuille_biconcave(nx=nx, ny=ny, count=(nx * ny) // 8192, seed=0, scheme=scheme,
-                                      placement="grid")
-    L = o.lattice(nx, ny, 0.7, True, gx=case.gx)
+        return W.Case("slab", nx, ny, 0.7, True, gx=W.poiseuille_force(0.7, 0.02, ny), init="parabola")
+    return W.poiseuille_biconcave(nx=nx, ny=ny, count=(nx * ny) // 8192, seed=0, scheme=scheme,
+                                  placement="grid")
+
+
+def slab_name(a, case):
+    return (f"poiseuille-biconcave-{case.nx}x{case.ny}-{len(case.capsules)}x128-{a.scheme}-f64 "
+            f"(CPU sample of the {a.nx}x{a.ny} workload)")
+
+
+def oracle_sample(a, steps=0, seconds=12.0, warmup=0):
+    """The FP64 CPU oracle, as it stands, on the slab: `warmup` untimed steps after the
+    start-up step, then `steps` timed steps (or as many as fit in `seconds` when steps is
+    0). Threads: one, or every core in the all-core build (LBMIB_ORACLE_OPENMP=1, set by
+    oracle_sample_all_cores for its child process)."""
+    import oracle as o
+    case = slab_case(a)
+    scheme = W.DYNAMIC if a.scheme == "dynamic" else W.KINEMATIC
+    L = o.lattice(case.nx, case.ny, 0.7, True, gx=case.gx)
     s = o.Sim(L)
     s.init_fields(*case.fields())
     for c in case.capsules:
         s.add_capsule(c.xy, c.ks, c.kb, c.ka, c.mass)
-    s.step(1, scheme)  # start-up step, untimed
+    s.step(1 + warmup, scheme)  # start-up step and warm-up, untimed
     t0 = time.perf_counter()
-    steps = 0
-    while time.perf_counter() - t0 < seconds:
-        s.step(1, scheme)
-        steps += 1
+    done = 0
+    if steps > 0:
+        s.step(steps, scheme)
+        done = steps
+    else:
+        while time.perf_counter() - t0 < seconds:
+            s.step(1, scheme)
+            done += 1
     dt = time.perf_counter() - t0
-    return {"value": nx * ny * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{nx}x{ny} slab, {len(case.capsules)} capsules, {steps} steps, FP64, single thread"}
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)) if o.OPENMP else 1
+    nodes = case.nx * case.ny
+    return {"value": nodes * done / dt / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+            "steps": done, "ms_per_step": dt / done * 1e3, "workload": slab_name(a, case),
+            "sample": f"{case.nx}x{case.ny} slab, {len(case.capsules)} capsules, {done} steps, FP64, "
+                      + (f"lattice loop on {threads} threads (OpenMP build)" if o.OPENMP else "single thread"),
+            **host_cpu()}
+
+
+def oracle_sample_all_cores(a, steps=0, seconds=12.0, warmup=0):
+    """oracle_sample in a child process that loads the all-core (OpenMP) build."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--impl", "oracle-sample", "--scheme", a.scheme,
+           "--nx", str(a.nx), "--ny", str(a.ny), "--sample-steps", str(steps), "--cpu-seconds", str(seconds),
+           "--warmup", str(warmup)] + (["--no-capsules"] if a.no_capsules else [])
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=600,
+                           env=dict(os.environ, LBMIB_ORACLE_OPENMP="1"))
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:   # the baseline line must not sink the benchmark
+        return {"unavailable": f"all-core oracle run failed: {type(e).__name__}: {e}"}
+
+
+def cpu_baseline(a, seconds: float):
+    out = oracle_sample(a, seconds=seconds)
+    out["all_cores"] = oracle_sample_all_cores(a, seconds=seconds)
+    return out
 
 
 def run_reference(a):
-    """The CPU baseline arm: the FP64 oracle as it stands, on a bounded sample of the
-    same workload (there is no reference code; the paper describes a method). Under
-    torchrun only rank 0 runs it."""
+    """The CPU baseline arm: the FP64 oracle as it stands (single thread), W warm-up and K
+    timed steps on the slab sample of the workload (there is no reference code; the paper
+    describes a method). The line reports what ran: the slab, its steps and its time per
+    step; the all-core (OpenMP) run of the same sample and the time per step extrapolated
+    to the full lattice are separate keys. Under torchrun only rank 0 runs it."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per_step_budget = a.cpu_seconds / max(1, a.steps)
-    base = cpu_baseline(a, max(1.0, per_step_budget * a.steps))
-    case_name = f"poiseuille-biconcave-{a.nx}x{a.ny}-{(a.nx * a.ny) // 8192}x128-{a.scheme}-{a.storage}"
+    base = oracle_sample(a, steps=a.steps, warmup=a.warmup)
+    allc = oracle_sample_all_cores(a, steps=a.steps, warmup=a.warmup)
+    full = make_case(a)
     line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "MLUPS",
-            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": a.nx * a.ny / (base["value"] * 1e6) * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": case_name, "nx": a.nx, "ny": a.ny, "scheme": a.scheme,
-                       "storage": a.storage, "sample": base["sample"]},
+            "n_gpus": a.gpus, "steps": base["steps"], "warmup": a.warmup, "ms_per_step": base["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": base["workload"], "nx": SLAB[0], "ny": SLAB[1], "scheme": a.scheme,
+                       "sample_of": workload_name(a, full), "sample": base["sample"]},
             "cpu_baseline": base,
+            "cpu_baseline_all_cores": allc,
+            "extrapolated_full_lattice_ms_per_step": base["ms_per_step"] * (a.nx * a.ny) / (SLAB[0] * SLAB[1]),
             "e2e": {"value": base["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -278,7 +355,9 @@ def run_gpu(a):
     if rank == 0 and not a.no_extras:
         ctx.close()
         line["ib_fp64"] = ib_fp64_run(L, a, case, scheme)
+        line["fp64_storage"] = fp64_coupled_run(L, a, case, scheme, dev)
         line["precision"] = precision_run(L, dev)
+        line["precision_study"] = precision_study(L, a.study_steps, a.study_oracle_steps)
         line["dense"] = dense_run(L)
         line["open"] = open_run(L)
         line["rigid"] = rigid_run(L)
@@ -339,6 +418,110 @@ def precision_run(L, dev, steps=(12, 60)):
         out[storage] = r
         ctx.close()
     return out
+
+
+def fp64_coupled_run(L, a, case, scheme, dev, steps=20, warmup=3):
+    """The main workload (same lattice, capsules and scheme) with FP64 storage: the whole
+    coupled step, and its lattice kernel against the FP64 ALU roofline."""
+    import torch
+
+    ctx = L.from_case(case, storage="fp64")
+    ctx.set_option(L.OPT_TIMING, 1)
+    ctx.step(warmup, scheme)
+    ctx.sync()
+    ctx.kernel_time(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(dev) as clk:
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        ctx.step(steps, scheme)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ctx.sync()
+    kms, kn = ctx.kernel_time(reset=True)
+    per = kms / max(1, kn)
+    nodes = a.nx * a.ny
+    gl = nodes / (per / 1e3) / 1e9
+    mhz = clk.summary().get("sm_mhz") or 2070.0
+    peak = FP64_INSTR_PER_SM_CYCLE * SM_COUNT * mhz * 1e6 / 1e9
+    ctx.close()
+    return {"workload": workload_name(a, case).replace(f"-{a.storage}", "-fp64"), "steps": steps,
+            "ms_per_step": ms, "mlups": nodes / ms / 1e3, "lattice_kernel_ms": per, "lattice_share": per / ms,
+            "roofline": {"bound": "alu", "unit": "G FP64 instr/s", "peak": peak,
+                         "achieved": FP64_INSTR_PER_UPDATE * gl, "frac": FP64_INSTR_PER_UPDATE * gl / peak,
+                         "peak_source": "2 FP64 instructions per SM per cycle x 152 SMs x sampled SM clock"},
+            "clocks": clk.summary()}
+
+
+def _study_case():
+    # 4096 x 512 channel, 256 biconcave capsules of 128 vertices (a = 8) at non-overlapping
+    # random positions from seed 0, Ca = 0.01, Dynamic
+    return W.poiseuille_biconcave(nx=4096, ny=512, count=256, n=128, seed=0, scheme=W.DYNAMIC)
+
+
+def _study_state(fields, obs):
+    _, ux, uy = fields
+    return np.stack([ux, uy]), np.asarray(obs)[:, 2]
+
+
+def precision_study(L, steps=5000, oracle_steps=100):
+    """Precision study: FP64, FP32 and FP16 population storage on the 4096 x 512 channel
+    with 256 biconcave capsules, each run's velocity field and capsule Taylor deformations
+    against FP64 references: (1) the FP64 CPU oracle after `oracle_steps` steps (the
+    all-core build, a child process); (2) the GPU's FP64-storage run (itself held to the
+    oracle at 1e-10 over 1000 steps by the parity tests) after the full `steps`."""
+    import tempfile
+
+    case = _study_case()
+    out = {"workload": "4096x512 channel, 256 biconcave capsules x 128 vertices (seed 0), Ca 0.01, Dynamic",
+           "steps": steps, "oracle_steps": oracle_steps}
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "oracle.npz")
+        cmd = [sys.executable, os.path.abspath(__file__), "--impl", "oracle-sample", "--only", "study",
+               "--study-oracle-steps", str(oracle_steps), "--study-out", path]
+        t0 = time.perf_counter()
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=1800,
+                           env=dict(os.environ, LBMIB_ORACLE_OPENMP="1"))
+        if r.returncode != 0 or not os.path.exists(path):
+            out["vs_oracle"] = {"unavailable": (r.stderr or r.stdout).strip()[-300:]}
+            ref = None
+        else:
+            z = np.load(path)
+            ref = (z["vel"], z["D"])
+            out["oracle_s"] = time.perf_counter() - t0
+    runs = {}
+    for storage in ("fp64", "fp32", "fp16"):
+        ctx = L.from_case(case, storage=storage)
+        ctx.step(oracle_steps, L.DYNAMIC)
+        early = _study_state(ctx.read_fields(), ctx.observables_all())
+        ctx.step(steps - oracle_steps, L.DYNAMIC)
+        late = _study_state(ctx.read_fields(), ctx.observables_all())
+        runs[storage] = (early, late)
+        ctx.close()
+
+    def err(a, b):
+        return {"velocity_rel_max": float(np.abs(a[0] - b[0]).max() / np.abs(b[0]).max()),
+                "max_abs_dD": float(np.abs(a[1] - b[1]).max())}
+
+    if ref is not None:
+        out["vs_oracle"] = {k: err(v[0], ref) for k, v in runs.items()}
+    out["vs_gpu_fp64"] = {k: err(runs[k][1], runs["fp64"][1]) for k in ("fp32", "fp16")}
+    out["D_mean_end"] = float(runs["fp64"][1][1].mean())
+    return out
+
+
+def study_oracle(oracle_steps, path):
+    """Child process of precision_study: the oracle's state after oracle_steps steps."""
+    import oracle as o
+    case = _study_case()
+    s = o.Sim(o.lattice(case.nx, case.ny, case.tau, True, gx=case.gx))
+    s.init_fields(*case.fields())
+    for c in case.capsules:
+        s.add_capsule(c.xy, c.ks, c.kb, c.ka, c.mass)
+    assert s.step(oracle_steps, o.DYNAMIC) == 0
+    vel, D = _study_state(s.read_fields(), [s.observables(k) for k in range(len(case.capsules))])
+    np.savez(path, vel=vel, D=D)
 
 
 def ib_fp64_run(L, a, case, scheme, steps=100, warmup=10):
@@ -609,6 +792,12 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.impl == "oracle-sample":
+        if a.only == "study":
+            study_oracle(a.study_oracle_steps, a.study_out)
+        else:
+            print(json.dumps(oracle_sample(a, steps=a.sample_steps, seconds=a.cpu_seconds, warmup=a.warmup)),
+                  flush=True)
     elif a.only != "all":
         import torch
 
@@ -620,6 +809,9 @@ def main():
                else dense_run(L) if a.only == "dense"
                else open_run(L) if a.only == "open"
                else rigid_run(L) if a.only == "rigid"
+               else precision_study(L, a.study_steps, a.study_oracle_steps) if a.only == "study"
+               else fp64_coupled_run(L, a, make_case(a), L.DYNAMIC if a.scheme == "dynamic" else L.KINEMATIC,
+                                     int(os.environ.get("LOCAL_RANK", "0"))) if a.only == "fp64"
                else {"dynamic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=1),
                      "kinematic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=0)})
         print(json.dumps(out), flush=True)

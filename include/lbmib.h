@@ -128,9 +128,16 @@ lbmib_status lbmib_read_rigid(lbmib_ctx* ctx, int id, double* out);
  * shape; its time history restarts (the next step is a start-up step). */
 lbmib_status lbmib_set_capsule_positions(lbmib_ctx* ctx, int id, const double* xy);
 
-/* Advance nsteps time steps with the given scheme (enqueued, asynchronous). A capsule's
- * first step after being added starts its history: Kinematic uses forward Euler,
- * Dynamic sets u_v = I(u) and X^{-1} = X^0 - u_v. */
+/* Advance nsteps time steps with the given scheme (enqueued, asynchronous).
+ * Kinematic (Section 2.4, steps i-viii): spread the internal forces at X^n, update the
+ * lattice, interpolate u (Eq. 7 with half of the spread force) at X^n, advance by Eq. 25.
+ * Dynamic (Section 2.3.2, steps 1-8): interpolate U at X^n from the populations before
+ * any IB force (rho u = sum f e + g/2), spread c_l (u_v - U) with c_l the vertex's share of
+ * the arc length, update the lattice, take the probe tractions (Eq. 15-16) on the updated
+ * populations (again before any IB force) and the internal forces at X^n, and advance by
+ * Eq. 23 with U as the tentative velocity and Eq. 24.
+ * A capsule's first step after being added starts its history: Kinematic uses forward
+ * Euler, Dynamic sets u_v = U and X^{-1} = X^0 - u_v. */
 lbmib_status lbmib_step(lbmib_ctx* ctx, long long nsteps, lbmib_scheme scheme);
 
 /* Wait for the stream and report any sticky device status. */
@@ -199,11 +206,11 @@ lbmib_status lbmib_observables_all(lbmib_ctx* ctx, double* out);
 lbmib_status lbmib_interpolate(lbmib_ctx* ctx, const double* xy, int n, double* out);
 
 /* Same as lbmib_interpolate, for callers that cannot allocate device memory at the time
- * of the call: code running while a stream is being captured into a CUDA graph (where
- * cudaMalloc is not allowed), callbacks on real-time loops that must not trigger the
- * implicit synchronisation of an allocation, or hosts whose device memory belongs to
- * another framework's allocator. The paper has no counterpart; this is a library
- * convenience. The call allocates nothing: the device staging of the points and results
+ * of the call: callbacks on real-time loops that must not trigger the implicit
+ * synchronisation of an allocation, hosts whose device memory belongs to another
+ * framework's allocator (which would see a cudaMalloc as memory it does not account
+ * for), or processes held to a fixed device-memory budget. The paper has no
+ * counterpart; this is a library convenience. The call allocates nothing: the device staging of the points and results
  * lives in a static array of the library, sized for 16384 points (1.25 MiB held on every
  * device that loads the library until the process exits). n > 16384 is rejected with
  * LBMIB_ERR_ARG. The first call on a device resolves the array's device address (with
@@ -266,7 +273,7 @@ lbmib_status lbmib_field_ptr(lbmib_ctx* ctx, int field, void** ptr, int* pitch);
  *   LBMIB_OPT_FUSE_IB       1 (default): within one lbmib_step call of the Dynamic
  *                           scheme, the node update of a step and the force and
  *                           spread of the next run as one kernel (both read the
- *                           same lattice state; Section 2.3.2 steps 5-8 and 1-3)
+ *                           same lattice state; Section 2.3.2 steps 7-8 and 1-3)
  *                           when every capsule has one CTA and the context holds no
  *                           rigid particles; 0: separate kernels. The state between
  *                           calls and the results do not depend on it.

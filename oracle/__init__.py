@@ -19,17 +19,25 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbmib_oracle.c")
 _LIB = os.path.join(_HERE, "liblbmib_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "liblbmib_oracle_omp.so")
 
 CFLAGS = ["-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11", "-D_DEFAULT_SOURCE"]
 
+# LBMIB_ORACLE_OPENMP=1 loads the all-core build: the same source compiled with -fopenmp,
+# whose lattice loop runs its rows on every host core (identical results). Only the
+# timed CPU baseline uses it.
+OPENMP = os.environ.get("LBMIB_ORACLE_OPENMP", "0") == "1"
 
-def build_library(force: bool = False) -> str:
+
+def build_library(force: bool = False, openmp: bool = False) -> str:
     """Compile the oracle with gcc (plain C11, no FMA contraction) if it is stale."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    out = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        flags = CFLAGS + (["-fopenmp"] if openmp else [])
+        subprocess.check_call(["gcc", *flags, _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 _lib = None
@@ -38,7 +46,7 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build_library())
+        _lib = C.CDLL(build_library(openmp=OPENMP))
         _declare(_lib)
     return _lib
 

@@ -230,6 +230,10 @@ void orc_open_boundaries(const orc_lattice* L, double* f) {
 void orc_collide_stream(const orc_lattice* L, const double* f, const double* fib, double* fnew) {
     const double tau = L->tau;
     const double cs2 = 1.0 / 3.0;
+    /* Rows are independent (each node writes its own streamed populations), so the
+     * all-core build (-fopenmp) splits them over threads with identical results; the
+     * plain build ignores the pragma. */
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < L->ny; y++) {
         for (int x = 0; x < L->nx; x++) {
             double rho, ux, uy, Fx, Fy, feq[9];

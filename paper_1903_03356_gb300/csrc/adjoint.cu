@@ -569,8 +569,10 @@ __global__ void __launch_bounds__(256) k_adj_lattice(const S* __restrict__ post0
         fbar[N + node] = Fby;
         fib_clear[node] = 0.0;
         fib_clear[N + node] = 0.0;
-        bbar_clear[node] = 0.0;
-        bbar_clear[N + node] = 0.0;
+        if (bbar_clear) {   // the Dynamic sweep has no half-force adjoint
+            bbar_clear[node] = 0.0;
+            bbar_clear[N + node] = 0.0;
+        }
         gx = (double)Fbx;
         gy = (double)Fby;
     }
@@ -679,15 +681,16 @@ __global__ void __launch_bounds__(128) k_adj_membrane(Lat L, Nodes nd, const dou
 }
 
 // =================================================================================
-// Dynamic scheme (Section 2.3.2, steps 1-8; Eq. 15-16, 21-24). Forward step n:
-//   U1 = I(s^n, fib^{n-1}, X^n)         (first step of a vertex: u_v := U1, X^{n-1} := X^n - U1)
-//   F_l = u_v - U1,  c_l = (l_left + l_right)/2,  fib^n = sum phi(X^n) c_l F_l
+// Dynamic scheme (Section 2.3.2, steps 1-8; Eq. 15-16, 21-24). Forward step n, every
+// interpolation on the populations before any IB force (velocity (m + g/2)/rho):
+//   U = I(s^n, X^n)                     (first step of a vertex: u_v := U, X^{n-1} := X^n - U)
+//   F_l = u_v - U,  c_l = (l_left + l_right)/2,  fib^n = sum phi(X^n) c_l F_l
 //   post^{n+1} = Coll(s^n, g + fib^n)
-//   U2 = I(s^{n+1}, fib^n, X^n),  F^ext = tractions(s^{n+1}, fib^n, X^n),  F^int = F(X^n)
-//   X^{n+1} = X^n + U2 + (F^int + F^ext) / (2 m)                               (Eq. 23)
+//   F^ext = tractions(s^{n+1}, X^n),  F^int = F(X^n)
+//   X^{n+1} = X^n + U + (F^int + F^ext) / (2 m)       (Eq. 23, tentative velocity U)
 //   u_v^{n+1} = 3/2 X^{n+1} - 2 X^n + 1/2 X^{n-1}                             (Eq. 24)
-// The reverse sweep carries S = dJ/ds^{n+1}, B^n = dJ/dfib^n (from the next step's U1),
-// Xc = dJ/dX^{n+1}, Xm = dJ/dX^n through the X^{n-1} slot and Ub = dJ/du_v^{n+1}.
+// The reverse sweep carries S = dJ/ds^{n+1}, Xc = dJ/dX^{n+1}, Xm = dJ/dX^n through the
+// X^{n-1} slot and Ub = dJ/du_v^{n+1}.
 // =================================================================================
 
 // MLS density and velocity gradient at probe P from the fields of its 3x3 support
@@ -796,12 +799,10 @@ __global__ void __launch_bounds__(128) k_adjd_spread(Lat L, Nodes nd, int max_n,
     }
 }
 
-// Fields (density deviation, Eq. 7 velocity, density) at lattice node (xk, yk).
+// Fields (density deviation, velocity before any IB force, density) at lattice node (xk, yk).
 template <typename S>
-__device__ __forceinline__ void node_fields(const S* __restrict__ post, const Lat& L, const double* __restrict__ fib,
-                                            int xk, int yk, double& drho, double& ux, double& uy) {
-    const long long N = (long long)L.nx * L.ny;
-    const long long cell = (long long)yk * L.nx + xk;
+__device__ __forceinline__ void node_fields(const S* __restrict__ post, const Lat& L, int xk, int yk, double& drho,
+                                            double& ux, double& uy) {
     double mx = 0.0, my = 0.0;
     drho = 0.0;
     typename St<S>::C qc[9];
@@ -814,28 +815,26 @@ __device__ __forceinline__ void node_fields(const S* __restrict__ post, const La
         my += ey(i) * q;
     }
     const double rho = 1.0 + drho;
-    ux = (mx + 0.5 * (L.gx + fib[cell])) / rho;
-    uy = (my + 0.5 * (L.gy + fib[N + cell])) / rho;
+    ux = (mx + 0.5 * L.gx) / rho;
+    uy = (my + 0.5 * L.gy) / rho;
 }
 
 // Adjoint of the fields at support node `cell`: drho-bar and u-bar into the population
-// adjoint (drho = sum s, u = (m + (g + fib)/2) / rho) and the half-force adjoint.
+// adjoint (drho = sum s, u = (m + g/2) / rho) and the body-force gradient.
 __device__ __forceinline__ void inject_fields(const Lat& L, long long cell, double drho_b, double ubx, double uby,
-                                              double ux, double uy, double rho, double* sbar, double* bbar,
-                                              double& gsx, double& gsy) {
+                                              double ux, double uy, double rho, double* sbar, double& gsx,
+                                              double& gsy) {
     const long long N = (long long)L.nx * L.ny;
 #pragma unroll
     for (int i = 0; i < 9; i++)
         atomicAdd(sbar + (long long)i * N + cell, drho_b + ((ex(i) - ux) * ubx + (ey(i) - uy) * uby) / rho);
-    atomicAdd(bbar + cell, 0.5 * ubx / rho);
-    atomicAdd(bbar + N + cell, 0.5 * uby / rho);
     gsx += 0.5 * ubx / rho;
     gsy += 0.5 * uby / rho;
 }
 
 // DR1: transposes of Eq. 24, Eq. 23 and the membrane force, one CTA per capsule. Writes
-// dJ/dX^n (partial) to xout, U2-bar to u2b, F^tot-bar to ftb (for the tractions), and
-// keeps dJ/dX^{n-1} (from Eq. 24) in xm for DR3.
+// dJ/dX^n (partial) to xout, the adjoint of Eq. 23's tentative velocity U to u2b, F^tot-bar
+// to ftb (for the tractions), and keeps dJ/dX^{n-1} (from Eq. 24) in xm for DR3.
 __global__ void __launch_bounds__(128) k_adjd_update(Nodes nd, int max_n, const double2* Xn, const double2* xc,
                                                      double2* xm, const double2* ub, double2* xout, double2* u2b,
                                                      double2* ftb, int ncaps, double* grad) {
@@ -879,10 +878,9 @@ constexpr int kTractThreads = (9 * kTractGroups + 31) / 32 * 32;
 
 template <typename S>
 __global__ void __launch_bounds__(kTractThreads) k_adjd_tract(Lat L, Nodes nd, int count, const double2* Xn,
-                                                                 const S* __restrict__ post1,
-                                                                 const double* __restrict__ fib, const double2* ftb,
-                                                                 double2* xout, double* sbar, double* bbar,
-                                                                 double* grad_g, unsigned* status) {
+                                                                 const S* __restrict__ post1, const double2* ftb,
+                                                                 double2* xout, double* sbar, double* grad_g,
+                                                                 unsigned* status) {
     // the traction adjoint computes in single precision for single-precision storage
     using R = typename std::conditional<sizeof(S) == 8, double, float>::type;
     __shared__ R fld[3][kTractGroups][9];   // density deviation, u_x, u_y of each support node
@@ -915,7 +913,7 @@ __global__ void __launch_bounds__(kTractThreads) k_adjd_tract(Lat L, Nodes nd, i
         ok = support_centre(L, Px, Py, cx, cy);
         const int xk = wrapi(cx + k % 3 - 1, L.nx), yk = support_row(L, cy + k / 3 - 1);
         cell = (long long)yk * L.nx + xk;
-        node_fields<S>(post1, L, fib, xk, yk, dr, u, w);
+        node_fields<S>(post1, L, xk, yk, dr, u, w);
         fld[0][grp][k] = R(dr);
         fld[1][grp][k] = R(u);
         fld[2][grp][k] = R(w);
@@ -960,7 +958,7 @@ __global__ void __launch_bounds__(kTractThreads) k_adjd_tract(Lat L, Nodes nd, i
         const R gx = gxa * qyb, gy = qxa * gyb;
         inject_fields(L, cell, (double)(phi * rho_b), (double)(Gb[0][0] * gx + Gb[0][1] * gy),
                       (double)(Gb[1][0] * gx + Gb[1][1] * gy), (double)R(u), (double)R(w), 1.0 + (double)R(dr), sbar,
-                      bbar, gsx, gsy);
+                      gsx, gsy);
     }
     for (int o = 16; o > 0; o >>= 1) {
         gsx += __shfl_xor_sync(0xffffffffu, gsx, o);
@@ -973,13 +971,13 @@ __global__ void __launch_bounds__(kTractThreads) k_adjd_tract(Lat L, Nodes nd, i
     if (!ok && k == 0) atomicOr(status, kStatSupport);
 }
 
-// Interpolation transpose (Eq. 8, Eq. 7 velocity) of U = I(s, fib, X^n) at every vertex
-// for a given U-bar: one thread per (vertex, support node). Adds to the population
-// adjoint, the half-force adjoint and dJ/dX^n (xout).
+// Interpolation transpose (Eq. 8, velocity before any IB force) of U = I(s, X^n) at every
+// vertex for a given U-bar: one thread per (vertex, support node). Adds to the population
+// adjoint and dJ/dX^n (xout).
 template <typename S>
-__global__ void __launch_bounds__(kInterpThreads) k_adjd_interp(Lat L, const S* __restrict__ post, const double* __restrict__ fib,
+__global__ void __launch_bounds__(kInterpThreads) k_adjd_interp(Lat L, const S* __restrict__ post,
                                                      const Shape* __restrict__ shp, int count, const double2* ubar,
-                                                     double2* xout, double* sbar, double* bbar, double* grad_g) {
+                                                     double2* xout, double* sbar, double* grad_g) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = t / 9, k = t - 9 * (t / 9);
     double gsx = 0.0, gsy = 0.0;
@@ -989,13 +987,12 @@ __global__ void __launch_bounds__(kInterpThreads) k_adjd_interp(Lat L, const S* 
         const Shape& s = shp[v];
         const int xk = wrapi(s.cx + a - 1, L.nx), yk = support_row(L, s.cy + b - 1);
         double drho, ux, uy;
-        node_fields<S>(post, L, fib, xk, yk, drho, ux, uy);
+        node_fields<S>(post, L, xk, yk, drho, ux, uy);
         const double uU = ux * U.x + uy * U.y;
         atomicAdd(&xout[v].x, s.px[b][a] * uU);
         atomicAdd(&xout[v].y, s.py[b][a] * uU);
         const double phi = s.phi[b][a];
-        inject_fields(L, (long long)yk * L.nx + xk, 0.0, phi * U.x, phi * U.y, ux, uy, 1.0 + drho, sbar, bbar, gsx,
-                      gsy);
+        inject_fields(L, (long long)yk * L.nx + xk, 0.0, phi * U.x, phi * U.y, ux, uy, 1.0 + drho, sbar, gsx, gsy);
     }
     for (int o = 16; o > 0; o >>= 1) {
         gsx += __shfl_xor_sync(0xffffffffu, gsx, o);
@@ -1007,12 +1004,12 @@ __global__ void __launch_bounds__(kInterpThreads) k_adjd_interp(Lat L, const S* 
     }
 }
 
-// DR3: spread transpose (with c_l), F_l = u_v - U1 and the start-up rule, one CTA per
-// capsule. Completes dJ/dX^n in xout (except the U1 interpolation, added by the next
-// kernel), writes U1-bar, the new u_v-bar and dJ/dX^{n-1}.
+// DR3: spread transpose (with c_l), F_l = u_v - U and the start-up rule, one CTA per
+// capsule. Completes dJ/dX^n in xout (except the U interpolation, added by the next
+// kernel), writes U-bar (with Eq. 23's part, utb), the new u_v-bar and dJ/dX^{n-1}.
 __global__ void __launch_bounds__(128) k_adjd_forcing(Lat L, Nodes nd, int max_n, const double2* Xn,
                                                       const double2* Flc, const Shape* __restrict__ shp,
-                                                      const double* __restrict__ fbar, const double* __restrict__ bbar,
+                                                      const double* __restrict__ fbar, const double2* utb,
                                                       const int* age0, int nloc, double2* xout, double2* xm,
                                                       double2* ub, double2* u1b) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1033,7 +1030,7 @@ __global__ void __launch_bounds__(128) k_adjd_forcing(Lat L, Nodes nd, int max_n
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 const int cell = support_cell(L, s, a, b);
-                const double tx = fbar[cell] + bbar[cell], ty = fbar[N + cell] + bbar[N + cell];
+                const double tx = fbar[cell], ty = fbar[N + cell];
                 cfx += s.phi[b][a] * tx;
                 cfy += s.phi[b][a] * ty;
                 const double tF = tx * F.x + ty * F.y;
@@ -1062,16 +1059,16 @@ __global__ void __launch_bounds__(128) k_adjd_forcing(Lat L, Nodes nd, int max_n
         double2 acc = sm.xd[v];
         acc.x += wl * dlx - wr * drx;
         acc.y += wl * dly - wr * dry;
-        const double2 flb = sm.ext[v], xm1 = xm[g];
+        const double2 flb = sm.ext[v], xm1 = xm[g], ut = utb[g];
         if (age0[g] + nloc == 0) {
-            // start-up: u_v := U1 (F_l = 0 whatever U1 is), X^{n-1} := X^n - U1
+            // start-up: u_v := U (F_l = 0 whatever U is), X^{n-1} := X^n - U
             acc.x += xm1.x;
             acc.y += xm1.y;
-            u1b[g] = make_double2(-xm1.x, -xm1.y);
+            u1b[g] = make_double2(ut.x - xm1.x, ut.y - xm1.y);
             ub[g] = make_double2(0.0, 0.0);
             xm[g] = make_double2(0.0, 0.0);
         } else {
-            u1b[g] = make_double2(-flb.x, -flb.y);
+            u1b[g] = make_double2(ut.x - flb.x, ut.y - flb.y);
             ub[g] = flb;   // xm keeps dJ/dX^{n-1}
         }
         xout[g] = acc;
@@ -1091,7 +1088,7 @@ namespace {
 struct AdjLayout {
     int K = 0, nseg = 0;
     size_t pb = 0, ckpt = 0;
-    size_t tape_pops = 0, tape_X = 0, tape_flc = 0, tape_fib0 = 0, age0 = 0, ckpts = 0, sbar[2]{}, fbar = 0,
+    size_t tape_pops = 0, tape_X = 0, tape_flc = 0, age0 = 0, ckpts = 0, sbar[2]{}, fbar = 0,
            fib[3]{}, bbar[3]{}, xc = 0, xp = 0, xnew = 0, xb[2]{}, ub = 0, u1b = 0, u2b = 0, ftb = 0, fv = 0, fv1 = 0,
            shp = 0, shp1 = 0, grad = 0, J = 0, total = 0;
 };
@@ -1115,7 +1112,6 @@ AdjLayout adj_layout(const lbmib_ctx* c, long long T, int K) {
     a.tape_pops = take((size_t)(a.K + 1) * a.pb);
     a.tape_X = take((size_t)(a.K + 1) * M * sizeof(double2));
     a.tape_flc = take((size_t)(a.K + 1) * M * sizeof(double2));   // Dynamic: c_l F_l per step
-    a.tape_fib0 = take(2 * N * sizeof(double));                    // Dynamic: spread force before the segment
     a.age0 = take(M * sizeof(int));
     a.ckpts = take(a.nseg > 1 ? (size_t)(a.nseg + 1) * a.ckpt : 0);
     a.sbar[0] = take(9 * N * cs);
@@ -1204,9 +1200,6 @@ lbmib_status tape_forward(lbmib_ctx* c, lbmib_scheme scheme, int len, char* w, c
     double2* tX = (double2*)(w + a.tape_X);
     LBMIB_CUDA(c, cudaMemcpyAsync(tape, c->pops[c->cur], pbytes, cudaMemcpyDeviceToDevice, s));
     LBMIB_CUDA(c, cudaMemcpyAsync(w + a.age0, c->nd.age, M * sizeof(int), cudaMemcpyDeviceToDevice, s));
-    if (scheme == LBMIB_DYNAMIC)
-        LBMIB_CUDA(c, cudaMemcpyAsync(w + a.tape_fib0, c->fib[c->cur_fib], 2 * (size_t)c->cfg.nx * c->cfg.ny *
-                                      sizeof(double), cudaMemcpyDeviceToDevice, s));
     void* keep0 = c->pops[0];
     void* keep1 = c->pops[1];
     fork_ib(c, s);
@@ -1312,17 +1305,16 @@ lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* 
     double2* xm = (double2*)(w + a.xp);
     double2* ub = (double2*)(w + a.ub);
     double2* u1b = (double2*)(w + a.u1b);
-    double2* u2b = (double2*)(w + a.u2b);
+    double2* utb = (double2*)(w + a.u2b);   // adjoint of Eq. 23's tentative velocity
     const int* age0 = (const int*)(w + a.age0);
-    // Three streams. The spread of step n-1 (taped positions and c_l F_l only) runs on a
+    // Two streams. The spread of step n-1 (taped positions and c_l F_l only) runs on a
     // side stream beside this step's chain, except at the segment's first reverse step,
     // whose own spread the chain needs; it waits for the previous reverse step, whose
-    // lattice transpose clears the buffer it writes, and the second interpolation
-    // transpose, which reads it, waits for it. The traction transpose and the first
-    // interpolation transpose only add into the same adjoint buffers and run side by
-    // side; the lattice transpose waits for both.
-    cudaStream_t s2 = c->ib_stream, s3 = c->aux_stream;
-    cudaEvent_t ev_prev = c->ev_adj[0], ev_spr = c->ev_adj[1], ev_upd = c->ev_adj[2], ev_int = c->ev_adj[3];
+    // lattice transpose clears the buffer it writes, and the next step's lattice
+    // transpose, which reads it, waits for it.
+    cudaStream_t s2 = c->ib_stream;
+    cudaEvent_t ev_prev = c->ev_adj[0], ev_spr = c->ev_adj[1];
+    bool pending = false;   // the side stream is spreading the step about to be reversed
     for (int k = len - 1; k >= 0; k--) {
         const long long n = n0 + k;
         const int par = (int)(n & 1);
@@ -1331,9 +1323,7 @@ lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* 
         const double2* Xn = (const double2*)(w + a.tape_X) + (size_t)k * M;
         const double2* flc = (const double2*)(w + a.tape_flc);
         double* fib_n = (double*)(w + a.fib[r3(n)]);
-        double* fib_p = k > 0 ? (double*)(w + a.fib[r3(n - 1)]) : (double*)(w + a.tape_fib0);
-        double* b_n = (double*)(w + a.bbar[r3(n)]);
-        double* b_p = (double*)(w + a.bbar[r3(n - 1)]);
+        double* fib_p = k > 0 ? (double*)(w + a.fib[r3(n - 1)]) : nullptr;
         double* sb_in = (double*)(w + a.sbar[1 - par]);
         double* sb_out = (double*)(w + a.sbar[par]);
         double2* xc = (double2*)(w + a.xb[1 - par]);
@@ -1341,6 +1331,8 @@ lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* 
         Shape* shp = shps[par];
         const bool first = k == len - 1, side = !first && k > 0;
         if (ncaps > 0) {
+            if (pending) cudaStreamWaitEvent(s, ev_spr, 0);   // this step's spread and shapes
+            pending = false;
             if (first || side) {
                 cudaStream_t q = first ? s : s2;
                 if (side) {
@@ -1349,33 +1341,28 @@ lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* 
                 }
                 k_adjd_spread<<<ncaps, 128, 0, q>>>(L, c->nd, c->max_n, Xn, k > 0 ? Xn - M : nullptr,
                                                     flc + (size_t)k * M, k > 0 ? flc + (size_t)(k - 1) * M : nullptr,
-                                                    first ? fib_n : nullptr, k > 0 ? fib_p : nullptr, shp,
-                                                    shps[1 - par], first);
-                if (side) cudaEventRecord(ev_spr, s2);
+                                                    first ? fib_n : nullptr, fib_p, shp, shps[1 - par], first);
+                if (side) {
+                    cudaEventRecord(ev_spr, s2);
+                    pending = true;
+                }
             }
-            k_adjd_update<<<ncaps, 128, smem, s>>>(c->nd, c->max_n, Xn, xc, xm, ub, xout, u2b,
+            k_adjd_update<<<ncaps, 128, smem, s>>>(c->nd, c->max_n, Xn, xc, xm, ub, xout, utb,
                                                    (double2*)(w + a.ftb), ncaps, grad);
-            cudaEventRecord(ev_upd, s);
-            cudaStreamWaitEvent(s3, ev_upd, 0);
-            k_adjd_interp<S><<<nblk(9LL * count, kInterpThreads), kInterpThreads, 0, s3>>>(L, post1, fib_n, shp, count, u2b, xout, sb_in,
-                                                                     b_n, grad + 2 * ncaps);
-            cudaEventRecord(ev_int, s3);
             k_adjd_tract<S><<<nblk(2LL * count, kTractGroups), kTractThreads, 0, s>>>(
-                L, c->nd, count, Xn, post1, fib_n, (const double2*)(w + a.ftb), xout, sb_in, b_n, grad + 2 * ncaps,
+                L, c->nd, count, Xn, post1, (const double2*)(w + a.ftb), xout, sb_in, grad + 2 * ncaps,
                 &c->ctr->status);
-            cudaStreamWaitEvent(s, ev_int, 0);
         }
         k_adj_lattice<S><<<nblk(N, 256), 256, 0, s>>>(post0, L, sb_in, sb_out, fbar, fib_n,
-                                                       (double*)(w + a.fib[r3(n + 1)]),
-                                                       (double*)(w + a.bbar[r3(n + 1)]), grad + 2 * ncaps);
+                                                       (double*)(w + a.fib[r3(n + 1)]), nullptr, grad + 2 * ncaps);
         if (ncaps > 0) {
-            k_adjd_forcing<<<ncaps, 128, smem, s>>>(L, c->nd, c->max_n, Xn, flc + (size_t)k * M, shp, fbar, b_n,
+            k_adjd_forcing<<<ncaps, 128, smem, s>>>(L, c->nd, c->max_n, Xn, flc + (size_t)k * M, shp, fbar, utb,
                                                     age0, k, xout, xm, ub, u1b);
-            if (side) cudaStreamWaitEvent(s, ev_spr, 0);
-            k_adjd_interp<S><<<nblk(9LL * count, kInterpThreads), kInterpThreads, 0, s>>>(L, post0, fib_p, shp, count, u1b, xout, sb_out,
-                                                                    b_p, grad + 2 * ncaps);
+            k_adjd_interp<S><<<nblk(9LL * count, kInterpThreads), kInterpThreads, 0, s>>>(L, post0, shp, count, u1b,
+                                                                                          xout, sb_out,
+                                                                                          grad + 2 * ncaps);
         }
-        c->launches += ncaps > 0 ? 7 : 1;
+        c->launches += ncaps > 0 ? (first || side ? 6 : 5) : 1;
         LBMIB_CUDA(c, cudaGetLastError());
     }
     return LBMIB_OK;

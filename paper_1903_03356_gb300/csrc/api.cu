@@ -54,6 +54,7 @@ Layout make_layout(const lbmib_config* c) {
     L.uv = take(M * sizeof(double2));
     L.Fint = take(M * sizeof(double2));
     L.Fext = take(M * sizeof(double2));
+    L.U = take(M * sizeof(double2));
     L.L0 = take(M * sizeof(double));
     L.c0 = take(M * sizeof(double));
     L.s0 = take(M * sizeof(double));
@@ -178,7 +179,7 @@ bool enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
     if (ncaps > 0 && !spread_done) {
         if (scheme == LBMIB_DYNAMIC) {
             with_ib_storage(c, [&](auto v) {
-                launch_dyn_force_spread<decltype(v)>(src, L, c->fib[fp], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells,
+                launch_dyn_force_spread<decltype(v)>(src, L, c->nd, ncaps, c->max_n, c->arcs, c->tile_cells,
                                                      c->nrigid > 0, sp, status, s);
             });
         } else {
@@ -232,7 +233,7 @@ bool enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
             cudaMemsetAsync(reset, 0, sizeof(int), s);
             const Spread next{c->fib[fp], c->mark, c->list[fp], reset, &c->ctr->step_stamp, list_cap, status};
             with_ib_storage(c, [&](auto v) {
-                launch_dyn_update_spread<decltype(v)>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells, next,
+                launch_dyn_update_spread<decltype(v)>(dst, L, c->nd, ncaps, c->max_n, c->tile_cells, next,
                                                       status, s);
             });
             if (ov) cudaEventRecord(c->ev_spread, s);
@@ -243,7 +244,7 @@ bool enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
         }
         if (scheme == LBMIB_DYNAMIC) {
             with_ib_storage(c, [&](auto v) {
-                launch_dyn_update<decltype(v)>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->arcs, c->tile_cells,
+                launch_dyn_update<decltype(v)>(dst, L, c->nd, ncaps, c->max_n, c->arcs, c->tile_cells,
                                                c->nrigid > 0, reset, status, s);
             });
         } else {
@@ -411,6 +412,7 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     c->nd.uv = (double2*)(a + lay.uv);
     c->nd.Fint = (double2*)(a + lay.Fint);
     c->nd.Fext = (double2*)(a + lay.Fext);
+    c->nd.U = (double2*)(a + lay.U);
     c->nd.L0 = (double*)(a + lay.L0);
     c->nd.c0 = (double*)(a + lay.c0);
     c->nd.s0 = (double*)(a + lay.s0);

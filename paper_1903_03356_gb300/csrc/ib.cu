@@ -252,17 +252,18 @@ constexpr int dyn_min_blocks() {
 }
 
 // ---------------------------------------------------------------------------------
-// Dynamic IB (Section 2.3.2), steps 1-3: U = I(u^n) with half of the last spread
-// force, F_l = u_v - U, spread with c_l = (l_left + l_right)/2. First step of a vertex:
-// u_v = U and X^{-1} = X^0 - U.
+// Dynamic IB (Section 2.3.2), steps 1-3: U = I(u^n) of the populations before any IB
+// force (rho u = sum f e + g/2; the step's IB force is the unknown of the direct forcing),
+// F_l = u_v - U, spread with c_l = (l_left + l_right)/2. U is kept per vertex: it is also
+// the tentative velocity of the step's Eq. 23 (the fluid velocity at time t). First step
+// of a vertex: u_v = U and X^{-1} = X^0 - U.
 // ---------------------------------------------------------------------------------
 // Steps 1-3 on a staged arc whose tile holds the moments of the lattice state and zeroed
 // force accumulators (collective; starts with a barrier-ordered pass over the element
 // lengths). Returns false when a support left the channel or the tile. FRAMED (single
 // precision): the support frames at X^n are already stored (by the previous update).
 template <typename S, bool RIGID, bool FRAMED = false>
-__device__ __forceinline__ bool dyn_spread(const S* __restrict__ src, const Lat& L, const double* __restrict__ fib_prev,
-                                           const Nodes& nd, const CapsuleParams& P, const Arc& a, const CapSmem& sm,
+__device__ __forceinline__ bool dyn_spread(const S* __restrict__ src, const Lat& L, const Nodes& nd, const CapsuleParams& P, const Arc& a, const CapSmem& sm,
                                            Tile<typename St<S>::C>& t, const Spread& sp, int stamp) {
     using C = typename St<S>::C;
     constexpr bool F32 = sizeof(C) == 4;   // single precision: lengths and forces in float
@@ -291,8 +292,9 @@ __device__ __forceinline__ bool dyn_spread(const S* __restrict__ src, const Lat&
             store_mls<C>(nd.mls, g, w);
         }
         InterpT<C> o;
-        ok &= interp_with<S, false>(w, t, src, L, fib_prev, o);
+        ok &= interp_with<S, false>(w, t, src, L, nullptr, o);
         const double Ux = (double)o.ux, Uy = (double)o.uy;
+        nd.U[g] = make_double2(Ux, Uy);
         double2 uv;
         if (RIGID && P.rigid) {
             uv = rigid_velocity(nd.rb[a.cap].body, Xv);   // the body's motion (Section 2.3.1)
@@ -320,7 +322,7 @@ __device__ __forceinline__ bool dyn_spread(const S* __restrict__ src, const Lat&
 
 template <typename S, bool RIGID>
 __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_force_spread(const S* __restrict__ src, Lat L,
-                                                          const double* __restrict__ fib_prev, Nodes nd, int max_n,
+                                                          Nodes nd, int max_n,
                                                           int arcs, int tile_cells, Spread sp, unsigned* status) {
     using C = typename St<S>::C;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -330,11 +332,11 @@ __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_force_spread(c
     if (!load_arc(nd, sm, max_n, arcs, true, P, a, status)) return;
     Tile<C> t = make_tile<C>(sm, kHalo, kHalo + a.m, 1, tile_cells, true, true);
     if (t.use) {
-        fill_moments<S>(t, src, L, fib_prev);
+        fill_moments<S>(t, src, L, nullptr);
         zero_forces<C>(t);
     }
     const int stamp = *sp.stamp + 1;
-    const bool ok = dyn_spread<S, RIGID>(src, L, fib_prev, nd, P, a, sm, t, sp, stamp);
+    const bool ok = dyn_spread<S, RIGID>(src, L, nd, P, a, sm, t, sp, stamp);
     __syncthreads();
     if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
     if (!ok) atomicOr(status, kStatSupport);
@@ -378,8 +380,9 @@ __device__ void rigid_update(const Nodes& nd, const CapsuleParams& P, const Arc&
     }
 }
 
-// Dynamic IB steps 5-8: xdot_0 = I(u^{n+1}) at X^n, probe tractions (Eq. 15-16),
-// internal forces (Eq. 11, 13, 14), Verlet position (Eq. 23) and BDF2 velocity (Eq. 24).
+// Dynamic IB steps 7-8: probe tractions (Eq. 15-16) on the updated populations (before
+// any IB force, as in step 1), internal forces (Eq. 11, 13, 14), Verlet position (Eq. 23)
+// with the tentative velocity U of step 1, and BDF2 velocity (Eq. 24).
 // With arcs > 1 the capsule's CTAs form a cluster: the enclosed area is summed over it,
 // and its barrier also orders every CTA's reads of X^n (own and halo) before any CTA
 // writes X^{n+1}.
@@ -389,8 +392,7 @@ __device__ void rigid_update(const Nodes& nd, const CapsuleParams& P, const Arc&
 // tile. NEXT (single precision, one CTA per ring): also store each vertex's support frame
 // at X^{n+1}, found from its frame at X^n and the increment, for the next step's spread.
 template <typename S, bool NEXT = false>
-__device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat& L, const double* __restrict__ fib,
-                                           const Nodes& nd, const CapsuleParams& P, const Arc& a, const CapSmem& sm,
+__device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat& L, const Nodes& nd, const CapsuleParams& P, const Arc& a, const CapSmem& sm,
                                            const Tile<typename St<S>::C>& t, int arcs, int m) {
     using C = typename St<S>::C;
     bool ok = true;
@@ -411,9 +413,6 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
             // the probes of its element in float
             const MlsW<C> w = load_mls<C>(L, nd.mls, P.off + a.node(li));
             if (k < m) {
-                InterpT<C> o;
-                ok &= interp_with<S, false>(w, t, dst, L, fib, o);
-                xd_f(sm)[li] = make_float2(o.ux, o.uy);
                 // the area term (X_v - X_0) x (X_{v+1} - X_0) = (X_v - X_0) x e_v, in float:
                 // its rounding is of the order of the float membrane terms'
                 const double2 Xv = sm.X[li];
@@ -426,9 +425,9 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
             const float nx = e.y * rl, ny = -e.x * rl;
             InterpT<C> op, om;
             ok &= interp_with<S, true>(mls_near<C>(L, w, 0.5f * e.x + 1.2f * nx, 0.5f * e.y + 1.2f * ny), t, dst,
-                                       L, fib, op);
+                                       L, nullptr, op);
             ok &= interp_with<S, true>(mls_near<C>(L, w, 0.5f * e.x - 1.2f * nx, 0.5f * e.y - 1.2f * ny), t, dst,
-                                       L, fib, om);
+                                       L, nullptr, om);
             const C mp = op.rho * nu, mm = om.rho * nu;
             const C txx = C(2) * (mp * op.dudx - mm * om.dudx);
             const C tyy = C(2) * (mp * op.dvdy - mm * om.dvdy);
@@ -441,20 +440,15 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
         vertex_terms(sm, P, nd, li - 1, li, li + 1, P.off + a.node(li));
         if (k == m + 1) continue;
         const double2 Xv = sm.X[li], Xr = sm.X[li + 1];
-        if (k < m) {
-            InterpT<C> o;
-            ok &= interp_with<S, false>(load_mls<C>(L, nd.mls, P.off + a.v0 + k), t, dst, L, fib, o);
-            sm.xd[li] = make_double2((double)o.ux, (double)o.uy);
-            area2[0] += area_term(a.X0, Xv, Xr);
-        }
+        if (k < m) area2[0] += area_term(a.X0, Xv, Xr);
         // element li: probes at the centroid +/- 1.2 n+ (Section 2.2.2)
         const double2 d = Xr - Xv;
         const double rl = rsqrt(d.x * d.x + d.y * d.y);
         const double npx = d.y * rl, npy = -d.x * rl;
         const double cx = 0.5 * (Xv.x + Xr.x), cy = 0.5 * (Xv.y + Xr.y);
         InterpT<C> op, om;
-        ok &= interp_at<S, true>(t, dst, L, fib, cx + 1.2 * npx, cy + 1.2 * npy, op);
-        ok &= interp_at<S, true>(t, dst, L, fib, cx - 1.2 * npx, cy - 1.2 * npy, om);
+        ok &= interp_at<S, true>(t, dst, L, nullptr, cx + 1.2 * npx, cy + 1.2 * npy, op);
+        ok &= interp_at<S, true>(t, dst, L, nullptr, cx - 1.2 * npx, cy - 1.2 * npy, om);
         // tau = rho nu (grad u + grad u^T) at each probe; Eq. 15 + Eq. 16 (per unit
         // length, then times the element length)
         const C mp = op.rho * nu, mm = om.rho * nu;
@@ -491,7 +485,8 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
                 Fe.y += (float)f.y;
             }
             const double2 Xv = sm.X[li], Xm = nd.Xm1[g];
-            const float2 xd = xd_f(sm)[li];
+            const double2 U = nd.U[g];
+            const float2 xd = make_float2((float)U.x, (float)U.y);
             // Eq. 23 as the increment X^{n+1} - X^n, and Eq. 24 as
             // 1.5 (X^{n+1} - X^n) - 0.5 (X^n - X^{n-1})
             const float ix = xd.x + hm * (Fi.x + Fe.x), iy = xd.y + hm * (Fi.y + Fe.y);
@@ -529,7 +524,7 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
             if (nd.Fpp) Fe = Fe + nd.Fpp[g];   // Eq. 27, part of the total force (step 7)
             const double2 Xv = sm.X[li];
             const double2 Xm = nd.Xm1[g];
-            const double2 xd = sm.xd[li];
+            const double2 xd = nd.U[g];
             const double hm = 0.5 / P.m;
             const double2 Xn = make_double2(Xv.x + xd.x + hm * (Fi.x + Fe.x), Xv.y + xd.y + hm * (Fi.y + Fe.y));
             nd.uv[g] = make_double2(1.5 * Xn.x - 2.0 * Xv.x + 0.5 * Xm.x, 1.5 * Xn.y - 2.0 * Xv.y + 0.5 * Xm.y);
@@ -545,7 +540,7 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
 
 template <typename S>
 __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_update(const S* __restrict__ dst, Lat L,
-                                                    const double* __restrict__ fib, Nodes nd, int max_n, int arcs,
+                                                    Nodes nd, int max_n, int arcs,
                                                     int tile_cells, int* reset_count, unsigned* status) {
     using C = typename St<S>::C;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -559,22 +554,22 @@ __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_update(const S
     const int m = P.rigid ? 0 : a.m;
     // vertices v0-1 .. v0+m: the ends of every element whose probes this CTA evaluates
     Tile<C> t = make_tile<C>(sm, kHalo - 1, m > 0 ? kHalo + m + 1 : kHalo - 1, 3, tile_cells, true, false);
-    if (t.use) fill_moments<S>(t, dst, L, fib);
+    if (t.use) fill_moments<S>(t, dst, L, nullptr);
     __syncthreads();
-    const bool ok = dyn_update<S>(dst, L, fib, nd, P, a, sm, t, arcs, m);
+    const bool ok = dyn_update<S>(dst, L, nd, P, a, sm, t, arcs, m);
     if (!ok) atomicOr(status, kStatSupport);
 }
 
-// Steps 5-8 of step n and steps 1-3 of step n+1 in one pass, for one CTA per capsule
+// Steps 7-8 of step n and steps 1-3 of step n+1 in one pass, for one CTA per capsule
 // and no rigid particles (the host launches it only then). Both read the lattice state
-// after step n's patch: the moments with half of the force spread in step n. So the tile
+// after step n's patch: the moments before any IB force. So the tile
 // filled for the update at X^n also serves the interpolation and the spread at X^{n+1},
 // whose supports lie inside the update's margin unless a vertex moved more than two
 // lattice units in a step (flagged, as for any point that leaves its tile). The spread
 // goes to the other force buffer and list (sp), whose counter the host has reset.
 template <typename S>
 __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_update_spread(const S* __restrict__ dst, Lat L,
-                                                                const double* __restrict__ fib, Nodes nd,
+                                                                Nodes nd,
                                                                 int max_n, int tile_cells, Spread sp,
                                                                 unsigned* status) {
     using C = typename St<S>::C;
@@ -585,16 +580,16 @@ __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_update_spread(
     if (!load_arc(nd, sm, max_n, 1, true, P, a, status)) return;
     Tile<C> t = make_tile<C>(sm, kHalo - 1, kHalo + a.m + 1, 3, tile_cells, true, true);
     if (t.use) {
-        fill_moments<S>(t, dst, L, fib);
+        fill_moments<S>(t, dst, L, nullptr);
         zero_forces<C>(t);
     }
     __syncthreads();
-    bool ok = dyn_update<S, true>(dst, L, fib, nd, P, a, sm, t, 1, a.m);
+    bool ok = dyn_update<S, true>(dst, L, nd, P, a, sm, t, 1, a.m);
     __syncthreads();   // every X^{n+1} is written; the staged X^n is dead
     for (int li = threadIdx.x; li < a.m + 2 * kHalo; li += blockDim.x) sm.X[li] = nd.X[P.off + a.node(li)];
     __syncthreads();
     const int stamp = *sp.stamp + 1;
-    ok &= dyn_spread<S, false, true>(dst, L, fib, nd, P, a, sm, t, sp, stamp);
+    ok &= dyn_spread<S, false, true>(dst, L, nd, P, a, sm, t, sp, stamp);
     __syncthreads();
     if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
     if (!ok) atomicOr(status, kStatSupport);
@@ -606,7 +601,7 @@ __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_update_spread(
 // context holds rigid particles.
 template <typename S>
 __global__ void __launch_bounds__(128) k_rigid_update(const S* __restrict__ dst, Lat L,
-                                                      const double* __restrict__ fib, Nodes nd, int max_n, int arcs,
+                                                      Nodes nd, int max_n, int arcs,
                                                       int tile_cells, unsigned* status) {
     using C = typename St<S>::C;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -617,7 +612,7 @@ __global__ void __launch_bounds__(128) k_rigid_update(const S* __restrict__ dst,
     if (!P.rigid) return;   // uniform over the capsule's cluster
     const int m = a.m;
     Tile<C> t = make_tile<C>(sm, kHalo - 1, m > 0 ? kHalo + m + 1 : kHalo - 1, 3, tile_cells, true, false);
-    if (t.use) fill_moments<S>(t, dst, L, fib);
+    if (t.use) fill_moments<S>(t, dst, L, nullptr);   // before any IB force, as the capsules' probes
     // the particle's state at n and n - 1, staged before the cluster barrier after which
     // the first CTA overwrites it
     __shared__ double body[12];
@@ -639,7 +634,7 @@ __global__ void __launch_bounds__(128) k_rigid_update(const S* __restrict__ dst,
         const double cx = 0.5 * (Xv.x + Xr.x), cy = 0.5 * (Xv.y + Xr.y);
         const double len = (d.x * d.x + d.y * d.y) * rl;
         InterpT<C> op;
-        ok &= interp_at<S, true>(t, dst, L, fib, cx + 1.2 * npx, cy + 1.2 * npy, op);
+        ok &= interp_at<S, true>(t, dst, L, nullptr, cx + 1.2 * npx, cy + 1.2 * npy, op);
         // Eq. 17: (tau+ . n+ - p+ n+) l_l of the outer fluid alone; Eq. 18: its moment
         // about c, lever arm to the element centroid. The reference pressure 1/3 adds
         // nothing over a closed ring (sum n_l l_l = 0, sum r_l x n_l l_l = 0) and is left
@@ -923,36 +918,36 @@ static void launch_arcs(void (*k)(P...), int ncaps, int arcs, bool cluster, size
 }
 
 template <typename S>
-void launch_dyn_force_spread(const void* src, const Lat& L, const double* fib_prev, Nodes nd, int ncaps, int max_n,
+void launch_dyn_force_spread(const void* src, const Lat& L, Nodes nd, int ncaps, int max_n,
                              int arcs, int cells, bool rigid, Spread sp, unsigned* status, cudaStream_t s) {
     using C = typename St<S>::C;
     const size_t sh = smem_bytes<C>(arc_slots(max_n, arcs), cells, true, true);
     if (rigid)
-        launch_arcs(k_dyn_force_spread<S, true>, ncaps, arcs, false, sh, s, (const S*)src, L, fib_prev, nd, max_n,
+        launch_arcs(k_dyn_force_spread<S, true>, ncaps, arcs, false, sh, s, (const S*)src, L, nd, max_n,
                     arcs, cells, sp, status);
     else
-        launch_arcs(k_dyn_force_spread<S, false>, ncaps, arcs, false, sh, s, (const S*)src, L, fib_prev, nd, max_n,
+        launch_arcs(k_dyn_force_spread<S, false>, ncaps, arcs, false, sh, s, (const S*)src, L, nd, max_n,
                     arcs, cells, sp, status);
 }
 
 template <typename S>
-void launch_dyn_update(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
+void launch_dyn_update(const void* dst, const Lat& L, Nodes nd, int ncaps, int max_n,
                        int arcs, int cells, bool rigid, int* reset_count, unsigned* status, cudaStream_t s) {
     using C = typename St<S>::C;
     const size_t sh = smem_bytes<C>(arc_slots(max_n, arcs), cells, true, false);
-    launch_arcs(k_dyn_update<S>, ncaps, arcs, true, sh, s, (const S*)dst, L, fib_cur, nd, max_n, arcs, cells,
+    launch_arcs(k_dyn_update<S>, ncaps, arcs, true, sh, s, (const S*)dst, L, nd, max_n, arcs, cells,
                 reset_count, status);
     if (rigid)
-        launch_arcs(k_rigid_update<S>, ncaps, arcs, true, sh, s, (const S*)dst, L, fib_cur, nd, max_n, arcs, cells,
+        launch_arcs(k_rigid_update<S>, ncaps, arcs, true, sh, s, (const S*)dst, L, nd, max_n, arcs, cells,
                     status);
 }
 
 template <typename S>
-void launch_dyn_update_spread(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
+void launch_dyn_update_spread(const void* dst, const Lat& L, Nodes nd, int ncaps, int max_n,
                               int cells, Spread sp_next, unsigned* status, cudaStream_t s) {
     using C = typename St<S>::C;
     const size_t sh = smem_bytes<C>(arc_slots(max_n, 1), cells, true, true);
-    launch_arcs(k_dyn_update_spread<S>, ncaps, 1, false, sh, s, (const S*)dst, L, fib_cur, nd, max_n, cells, sp_next,
+    launch_arcs(k_dyn_update_spread<S>, ncaps, 1, false, sh, s, (const S*)dst, L, nd, max_n, cells, sp_next,
                 status);
 }
 
@@ -990,12 +985,12 @@ void launch_interp_points(const void* src, const Lat& L, const double* fib, cons
 }
 
 #define LBMIB_INSTANTIATE_IB(S)                                                                              \
-    template void launch_dyn_force_spread<S>(const void*, const Lat&, const double*, Nodes, int, int, int,   \
-                                             int, bool, Spread, unsigned*, cudaStream_t);                    \
-    template void launch_dyn_update<S>(const void*, const Lat&, const double*, Nodes, int, int, int, int,    \
-                                       bool, int*, unsigned*, cudaStream_t);                                 \
-    template void launch_dyn_update_spread<S>(const void*, const Lat&, const double*, Nodes, int, int, int,  \
-                                              Spread, unsigned*, cudaStream_t);                              \
+    template void launch_dyn_force_spread<S>(const void*, const Lat&, Nodes, int, int, int, int, bool,       \
+                                             Spread, unsigned*, cudaStream_t);                               \
+    template void launch_dyn_update<S>(const void*, const Lat&, Nodes, int, int, int, int, bool, int*,       \
+                                       unsigned*, cudaStream_t);                                             \
+    template void launch_dyn_update_spread<S>(const void*, const Lat&, Nodes, int, int, int, Spread,         \
+                                              unsigned*, cudaStream_t);                                      \
     template void launch_kin_advance<S>(const void*, const Lat&, const double*, Nodes, int, int, int, int,   \
                                         int*, unsigned*, cudaStream_t);                                      \
     template void launch_interp_points<S>(const void*, const Lat&, const double*, const double2*, int,       \

@@ -582,8 +582,13 @@ __device__ __forceinline__ Mom<typename St<S>::C> node_moments(const S* __restri
     const C inv = C(1) / (C(1) + drho);
     Mom<C> m;
     m.drho = drho;
-    m.ux = (mx + C(0.5) * (C(L.gx) + C(fib[n]))) * inv;
-    m.uy = (my + C(0.5) * (C(L.gy) + C(fib[N + n]))) * inv;
+    if (fib) {   // Eq. 7 with half of the uniform force and of the last spread force
+        m.ux = (mx + C(0.5) * (C(L.gx) + C(fib[n]))) * inv;
+        m.uy = (my + C(0.5) * (C(L.gy) + C(fib[N + n]))) * inv;
+    } else {     // before any IB force (the Dynamic scheme's interpolations)
+        m.ux = (mx + C(0.5) * C(L.gx)) * inv;
+        m.uy = (my + C(0.5) * C(L.gy)) * inv;
+    }
     return m;
 }
 

@@ -21,6 +21,8 @@ struct Nodes {
     double2* uv;     // node velocity (Dynamic: Eq. 24; Kinematic: interpolated)
     double2* Fint;   // last internal force (Eq. 22)
     double2* Fext;   // last external force (Eq. 15-16)
+    double2* U;      // Dynamic: fluid velocity at X^n interpolated by the step's forcing
+                     // (step 1), the tentative velocity of the step's Eq. 23
     double* L0;      // stress-free length of element v (v -> v+1)
     double* c0;      // cos(theta_0) at vertex v
     double* s0;      // sin(theta_0) at vertex v
@@ -87,17 +89,17 @@ constexpr int kMaxArcs = 8;    // portable thread-block cluster size
 // staged vertex slots per CTA for rings of at most max_n vertices in `arcs` arcs
 __host__ __device__ inline int arc_slots(int max_n, int arcs) { return (max_n + arcs - 1) / arcs + 2 * kHalo; }
 template <typename S>
-void launch_dyn_force_spread(const void* src, const Lat& L, const double* fib_prev, Nodes nd, int ncaps, int max_n,
+void launch_dyn_force_spread(const void* src, const Lat& L, Nodes nd, int ncaps, int max_n,
                              int arcs, int cells, bool rigid, Spread sp, unsigned* status, cudaStream_t s);
 // the node update of the capsules, then (rigid: the context holds rigid particles) that
 // of the rigid particles
 template <typename S>
-void launch_dyn_update(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
+void launch_dyn_update(const void* dst, const Lat& L, Nodes nd, int ncaps, int max_n,
                        int arcs, int cells, bool rigid, int* reset_count, unsigned* status, cudaStream_t s);
 // the node update of step n and the force and spread of step n+1 in one kernel (one CTA
 // per capsule, no rigid particles), spreading through sp_next
 template <typename S>
-void launch_dyn_update_spread(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
+void launch_dyn_update_spread(const void* dst, const Lat& L, Nodes nd, int ncaps, int max_n,
                               int cells, Spread sp_next, unsigned* status, cudaStream_t s);
 void launch_kin_force_spread(const Lat& L, Nodes nd, int ncaps, int max_n, int arcs, int cells, Spread sp,
                              unsigned* status, bool fp64_weights, cudaStream_t s);

@@ -71,4 +71,11 @@ def test_reference_arm_prints_the_contract_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
-    assert line["config"]["workload"].startswith("poiseuille-biconcave-16384x8192")
+    # the line names what ran: the slab sample, its own steps and time per step
+    assert line["config"]["workload"].startswith("poiseuille-biconcave-2048x512")
+    assert line["config"]["sample_of"].startswith("poiseuille-biconcave-16384x8192")
+    assert line["steps"] == 1 and line["cpu_baseline"]["steps"] == 1
+    assert abs(line["ms_per_step"] - 2048 * 512 / (line["value"] * 1e6) * 1e3) < 1e-6 * line["ms_per_step"]
+    assert line["cpu_baseline"]["nproc"] >= 1 and line["cpu_baseline"]["cpu_model"]
+    allc = line["cpu_baseline_all_cores"]
+    assert allc["kind"] == "oracle" and allc["cores"] >= 1 and allc["value"] > 0

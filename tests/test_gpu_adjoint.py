@@ -62,12 +62,15 @@ _REF = {}
 
 
 def reference(case, key, T, objective):
-    """Richardson-extrapolated central differences at relative steps 1e-4 and 3e-4, the
-    first as the reference and their spread as its uncertainty (round-off of J over
-    the step, and truncation), cached per key."""
+    """Richardson-extrapolated central differences at two relative steps, the first as
+    the reference and their spread as its uncertainty (round-off of J over the step, and
+    truncation), cached per key. Steps 1e-4 and 3e-4 for D; for a centroid coordinate,
+    whose derivatives are ~1e-13 of J itself (J ~ 15 lattice units), 1e-2 and 3e-3: at
+    1e-4 the round-off of J alone moves the difference quotient by ~1e-3."""
+    h1, h2 = (1e-4, 3e-4) if objective == 0 else (1e-2, 3e-3)
     if (key, T, objective) not in _REF:
-        r1, J = oracle_gradient(case, T, objective, h=1e-4, richardson=True)
-        r2, _ = oracle_gradient(case, T, objective, h=3e-4, richardson=True)
+        r1, J = oracle_gradient(case, T, objective, h=h1, richardson=True)
+        r2, _ = oracle_gradient(case, T, objective, h=h2, richardson=True)
         unc = {k: abs(r1[k] - r2[k]) / max(abs(r1[k]), 1e-300) for k in r1}
         _REF[(key, T, objective)] = (r1, unc, J)
     return _REF[(key, T, objective)]

@@ -1,9 +1,8 @@
 """The allocation-free interpolation entry point (lbmib_interpolate_noalloc).
 
-Some callers cannot allocate device memory when they want to probe the flow: code that
-runs while a stream is being captured into a CUDA graph, real-time callbacks that must
-not stall on an allocation, or hosts whose device memory is owned by another
-framework's allocator. For them the library offers an interpolation call whose device
+Some callers cannot allocate device memory when they want to probe the flow: real-time
+callbacks that must not stall on an allocation, hosts whose device memory is owned by
+another framework's allocator, or processes held to a fixed device-memory budget. For them the library offers an interpolation call whose device
 staging lives in a static array of the library instead of the caller's arena. This file
 checks it, through the C ABI, against the ordinary lbmib_interpolate on two calls in a
 row (the static array keeps the previous call's contents), and checks the size limit.
