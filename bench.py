@@ -34,7 +34,7 @@ METRIC = "LBM-IB MLUPS (coupled step) and % of HBM roofline"
 # DRAM bytes (read + write) per lattice update of k_collide_stream from one ncu capture of
 # the current kernel on a lattice whose writes dwarf L2 (profiles/k_collide_stream_*.md);
 # scaled to a full launch by the number of updates. None where no such capture exists.
-MEASURED_TRAFFIC_PER_UPDATE = {"fp32": None, "fp64": None, "fp16": None}
+MEASURED_TRAFFIC_PER_UPDATE = {"fp32": (1208041472 + 1165416704) / (8192 * 4096), "fp64": None, "fp16": None}
 
 
 def parse():
@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the batched-launch and adjoint measurements that follow the main line")
     p.add_argument("--batch-steps", type=int, default=3000, help="steps per case of the batched workload")
-    p.add_argument("--adjoint-steps", type=int, default=800, help="horizon T of the adjoint measurement")
+    p.add_argument("--adjoint-steps", type=int, default=8000, help="horizon T of the adjoint measurement")
     p.add_argument("--batch-autotune", type=int, default=20,
                    help="steps per candidate launch shape of the batch autotuner (0: default shape)")
     p.add_argument("--sample-steps", type=int, default=0, help="oracle-sample: timed steps (0: time-bounded)")

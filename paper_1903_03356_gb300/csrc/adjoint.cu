@@ -28,6 +28,7 @@
 // checkpoint into the tape before its reverse sweep. With K >= T the forward writes the
 // tape directly and nothing is recomputed.
 #include <cmath>
+#include <map>
 #include <cstring>
 #include <string>
 #include <type_traits>
@@ -1192,8 +1193,7 @@ lbmib_status ckpt_load(lbmib_ctx* c, const char* src, const AdjLayout& a) {
 
 // Forward `len` steps from the context state, writing every step's populations into the
 // tape (slot 0 = the starting state) and the vertex positions before every step.
-lbmib_status tape_forward(lbmib_ctx* c, lbmib_scheme scheme, int len, char* w, const AdjLayout& a) {
-    cudaStream_t s = c->stream;
+lbmib_status tape_forward(lbmib_ctx* c, lbmib_scheme scheme, int len, char* w, const AdjLayout& a, cudaStream_t s) {
     const size_t M = (size_t)(c->nd.count > 0 ? c->nd.count : 1);
     const size_t pbytes = 9 * (size_t)c->L.plane * storage_bytes(c->cfg.storage);
     char* tape = w + a.tape_pops;
@@ -1231,8 +1231,8 @@ lbmib_status tape_forward(lbmib_ctx* c, lbmib_scheme scheme, int len, char* w, c
 // the third force buffer (cleared by step n+1's lattice transpose, whose completion it
 // waits for); step n-1 waits for it before its interpolation transpose.
 template <typename S>
-lbmib_status reverse_segment(lbmib_ctx* c, long long n0, int len, char* w, const AdjLayout& a) {
-    cudaStream_t s = c->stream, s2 = c->ib_stream;
+lbmib_status reverse_segment(lbmib_ctx* c, long long n0, int len, char* w, const AdjLayout& a, cudaStream_t s) {
+    cudaStream_t s2 = c->ib_stream;
     cudaEvent_t ev_prev = c->ev_adj[0], ev_spr = c->ev_adj[1];
     const Lat& L = c->L;
     const int ncaps = (int)c->caps.size();
@@ -1290,8 +1290,8 @@ lbmib_status reverse_segment(lbmib_ctx* c, long long n0, int len, char* w, const
 
 // Reverse sweep of one taped Dynamic segment: global steps n0 + len - 1 down to n0.
 template <typename S>
-lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* w, const AdjLayout& a) {
-    cudaStream_t s = c->stream;
+lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* w, const AdjLayout& a,
+                                     cudaStream_t s) {
     const Lat& L = c->L;
     const int ncaps = (int)c->caps.size();
     const int count = c->nd.count;
@@ -1368,6 +1368,40 @@ lbmib_status reverse_segment_dynamic(lbmib_ctx* c, long long n0, int len, char* 
     return LBMIB_OK;
 }
 
+// Instantiated graphs of the segments of one adjoint call (destroyed with it).
+struct SegmentGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;   // kernels it runs
+    int cur_fib = 0;          // force-buffer index after a recompute
+};
+struct SegmentGraphs {
+    std::map<int, SegmentGraph> fwd;
+    std::map<std::pair<int, int>, SegmentGraph> rev;
+    ~SegmentGraphs() {
+        for (auto& kv : fwd) cudaGraphExecDestroy(kv.second.exec);
+        for (auto& kv : rev) cudaGraphExecDestroy(kv.second.exec);
+    }
+};
+
+// Capture what body(stream) enqueues on the context's capture stream into an
+// instantiated graph. The capture is ended whatever body returns.
+template <typename F>
+lbmib_status capture_segment(lbmib_ctx* c, cudaGraphExec_t* exec, F&& body) {
+    LBMIB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const lbmib_status st = body(c->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (st != LBMIB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture (adjoint segment)");
+    const cudaError_t ei = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return cuda_fail(c, ei, "cudaGraphInstantiate (adjoint segment)");
+    return LBMIB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1410,7 +1444,7 @@ lbmib_status lbmib_adjoint(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme, 
     const size_t cs = comp_bytes(c->cfg.storage);
     // forward sweep
     if (a.nseg == 1) {
-        st = tape_forward(c, scheme, (int)nsteps, w, a);
+        st = tape_forward(c, scheme, (int)nsteps, w, a, s);
         if (st != LBMIB_OK) return st;
     } else {
         for (int j = 0; j < a.nseg; j++) {
@@ -1443,22 +1477,56 @@ lbmib_status lbmib_adjoint(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme, 
     k_adj_objective<<<1, 256, 0, s>>>(c->nd, capsule, objective, xT, (double*)(w + a.J));
     c->launches++;
     LBMIB_CUDA(c, cudaGetLastError());
-    // reverse sweep, segment by segment
+    // reverse sweep, segment by segment. The recompute of a segment depends only on its
+    // length (every segment starts from a checkpoint in buffer 0), and its reverse sweep
+    // on its length and on its first step modulo 6 (the parity and the modulo-3 rotation
+    // of the adjoint buffers): each distinct shape is captured once into a CUDA graph and
+    // replayed for the segments that share it.
+    SegmentGraphs graphs;
     for (int j = a.nseg - 1; j >= 0; j--) {
         const long long n0 = (long long)j * a.K;
         const int len = (int)std::min<long long>(a.K, nsteps - n0);
         if (a.nseg > 1) {
             st = ckpt_load(c, w + a.ckpts + (size_t)j * a.ckpt, a);
-            if (st == LBMIB_OK) st = tape_forward(c, scheme, len, w, a);
             if (st != LBMIB_OK) return st;
+            auto it = graphs.fwd.find(len);
+            if (it == graphs.fwd.end()) {
+                SegmentGraph g;
+                const long long launches0 = c->launches;
+                st = capture_segment(c, &g.exec, [&](cudaStream_t q) { return tape_forward(c, scheme, len, w, a, q); });
+                if (st != LBMIB_OK) return st;
+                g.launches = c->launches - launches0;
+                g.cur_fib = c->cur_fib;
+                c->launches = launches0;
+                c->steps -= len;   // the capture only recorded the steps
+                it = graphs.fwd.emplace(len, g).first;
+            }
+            LBMIB_CUDA(c, cudaGraphLaunch(it->second.exec, s));
+            c->launches += it->second.launches;
+            c->cur_fib = it->second.cur_fib;
+            c->steps += len;
         }
-        by_storage(c->cfg.storage, [&](auto tag) {
-            using S = decltype(tag);
-            if (st != LBMIB_OK) return;
-            st = scheme == LBMIB_KINEMATIC ? reverse_segment<S>(c, n0, len, w, a)
-                                           : reverse_segment_dynamic<S>(c, n0, len, w, a);
-        });
-        if (st != LBMIB_OK) return st;
+        const std::pair<int, int> key(len, (int)(n0 % 6));
+        auto it = graphs.rev.find(key);
+        if (it == graphs.rev.end()) {
+            SegmentGraph g;
+            const long long launches0 = c->launches;
+            st = capture_segment(c, &g.exec, [&](cudaStream_t q) {
+                lbmib_status r = LBMIB_OK;
+                by_storage(c->cfg.storage, [&](auto tag) {
+                    using S = decltype(tag);
+                    r = scheme == LBMIB_KINEMATIC ? reverse_segment<S>(c, n0, len, w, a, q)
+                                                  : reverse_segment_dynamic<S>(c, n0, len, w, a, q);
+                });
+                return r;
+            });
+            if (st != LBMIB_OK) return st;
+            g.launches = c->launches - launches0;
+            c->launches = launches0;
+            it = graphs.rev.emplace(key, g).first;
+        }
+        LBMIB_CUDA(c, cudaGraphLaunch(it->second.exec, s));
+        c->launches += it->second.launches;
     }
     if (a.nseg > 1) {
         st = ckpt_load(c, w + a.ckpts + (size_t)a.nseg * a.ckpt, a);
