@@ -31,6 +31,7 @@
 #include <map>
 #include <cstring>
 #include <string>
+#include <tuple>
 #include <type_traits>
 #include <vector>
 
@@ -1089,7 +1090,7 @@ namespace {
 struct AdjLayout {
     int K = 0, nseg = 0;
     size_t pb = 0, ckpt = 0;
-    size_t tape_pops = 0, tape_X = 0, tape_flc = 0, age0 = 0, ckpts = 0, sbar[2]{}, fbar = 0,
+    size_t tape_pops = 0, tape_X = 0, tape_flc = 0, age0 = 0, tape2_pops = 0, tape2_X = 0, tape2_flc = 0, age02 = 0, ckpts = 0, sbar[2]{}, fbar = 0,
            fib[3]{}, bbar[3]{}, xc = 0, xp = 0, xnew = 0, xb[2]{}, ub = 0, u1b = 0, u2b = 0, ftb = 0, fv = 0, fv1 = 0,
            shp = 0, shp1 = 0, grad = 0, J = 0, total = 0;
 };
@@ -1114,6 +1115,13 @@ AdjLayout adj_layout(const lbmib_ctx* c, long long T, int K) {
     a.tape_X = take((size_t)(a.K + 1) * M * sizeof(double2));
     a.tape_flc = take((size_t)(a.K + 1) * M * sizeof(double2));   // Dynamic: c_l F_l per step
     a.age0 = take(M * sizeof(int));
+    if (a.nseg > 1) {
+        // a second tape: the recompute of one segment runs while the previous is reversed
+        a.tape2_pops = take((size_t)(a.K + 1) * a.pb);
+        a.tape2_X = take((size_t)(a.K + 1) * M * sizeof(double2));
+        a.tape2_flc = take((size_t)(a.K + 1) * M * sizeof(double2));
+        a.age02 = take(M * sizeof(int));
+    }
     a.ckpts = take(a.nseg > 1 ? (size_t)(a.nseg + 1) * a.ckpt : 0);
     a.sbar[0] = take(9 * N * cs);
     a.sbar[1] = take(9 * N * cs);
@@ -1164,10 +1172,9 @@ lbmib_status ckpt_save(lbmib_ctx* c, char* dst, const AdjLayout& a) {
     return LBMIB_OK;
 }
 
-lbmib_status ckpt_load(lbmib_ctx* c, const char* src, const AdjLayout& a) {
+lbmib_status ckpt_load(lbmib_ctx* c, const char* src, const AdjLayout& a, cudaStream_t s) {
     const size_t N = (size_t)c->cfg.nx * c->cfg.ny;
     const size_t M = (size_t)(c->nd.count > 0 ? c->nd.count : 1);
-    cudaStream_t s = c->stream;
     c->cur = 0;
     c->cur_fib = 0;
     const char* p = src;
@@ -1177,7 +1184,10 @@ lbmib_status ckpt_load(lbmib_ctx* c, const char* src, const AdjLayout& a) {
     LBMIB_CUDA(c, cudaMemcpyAsync(c->fib[0], p, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     LBMIB_CUDA(c, cudaMemsetAsync(c->fib[1], 0, 2 * N * sizeof(double), s));
     p += up(2 * N * sizeof(double), kAlign);
-    LBMIB_CUDA(c, cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
+    // list counts and step stamp restart; the sticky status word is kept (a reverse sweep
+    // may run beside this load and flag into it)
+    LBMIB_CUDA(c, cudaMemsetAsync(&c->ctr->count[0], 0, 2 * sizeof(int), s));
+    LBMIB_CUDA(c, cudaMemsetAsync(&c->ctr->step_stamp, 0, sizeof(int), s));
     LBMIB_CUDA(c, cudaMemcpyAsync(&c->ctr->count[0], p, sizeof(int), cudaMemcpyDeviceToDevice, s));
     LBMIB_CUDA(c, cudaMemcpyAsync(c->list[0], p + 16, 9 * M * sizeof(int), cudaMemcpyDeviceToDevice, s));
     p += up(9 * M * sizeof(int) + 16, kAlign);
@@ -1375,11 +1385,25 @@ struct SegmentGraph {
     int cur_fib = 0;          // force-buffer index after a recompute
 };
 struct SegmentGraphs {
-    std::map<int, SegmentGraph> fwd;
-    std::map<std::pair<int, int>, SegmentGraph> rev;
+    std::map<std::pair<int, int>, SegmentGraph> fwd;
+    std::map<std::tuple<int, int, int>, SegmentGraph> rev;
     ~SegmentGraphs() {
         for (auto& kv : fwd) cudaGraphExecDestroy(kv.second.exec);
         for (auto& kv : rev) cudaGraphExecDestroy(kv.second.exec);
+    }
+};
+
+// Events ordering the two tapes between the recompute and reverse streams.
+struct Events {
+    cudaEvent_t fdone[2]{}, rdone[2]{}, fork{};
+    bool ok = true;
+    Events() {
+        for (cudaEvent_t* e : {&fdone[0], &fdone[1], &rdone[0], &rdone[1], &fork})
+            ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    }
+    ~Events() {
+        for (cudaEvent_t e : {fdone[0], fdone[1], rdone[0], rdone[1], fork})
+            if (e) cudaEventDestroy(e);
     }
 };
 
@@ -1477,46 +1501,80 @@ lbmib_status lbmib_adjoint(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme, 
     k_adj_objective<<<1, 256, 0, s>>>(c->nd, capsule, objective, xT, (double*)(w + a.J));
     c->launches++;
     LBMIB_CUDA(c, cudaGetLastError());
-    // reverse sweep, segment by segment. The recompute of a segment depends only on its
-    // length (every segment starts from a checkpoint in buffer 0), and its reverse sweep
-    // on its length and on its first step modulo 6 (the parity and the modulo-3 rotation
-    // of the adjoint buffers): each distinct shape is captured once into a CUDA graph and
-    // replayed for the segments that share it.
+    // reverse sweep, segment by segment. With checkpoints, segment j - 1 is recomputed
+    // into the other tape on a second stream while segment j is reversed (the reverse
+    // sweep reads only its tape, the adjoint buffers and the constant capsule data; the
+    // recompute only the context's working state and its tape). The recompute of a segment
+    // depends only on its length and tape, and its reverse sweep on its length, tape and
+    // first step modulo 6 (the parity and the modulo-3 rotation of the adjoint buffers):
+    // each distinct shape is captured once into a CUDA graph and replayed for the segments
+    // that share it.
     SegmentGraphs graphs;
+    AdjLayout alt = a;
+    alt.tape_pops = a.tape2_pops;
+    alt.tape_X = a.tape2_X;
+    alt.tape_flc = a.tape2_flc;
+    alt.age0 = a.age02;
+    auto tape_of = [&](int j) -> const AdjLayout& { return (j & 1) ? alt : a; };
+    cudaStream_t sf = c->aux_stream;
+    Events ev;
+    if (!ev.ok) return fail(c, LBMIB_ERR_CUDA, "lbmib_adjoint: cudaEventCreateWithFlags failed");
+    auto recompute = [&](int j) -> lbmib_status {
+        const int b = j & 1;
+        const int len = (int)std::min<long long>(a.K, nsteps - (long long)j * a.K);
+        if (j + 2 <= a.nseg - 1) LBMIB_CUDA(c, cudaStreamWaitEvent(sf, ev.rdone[b], 0));   // tape b free
+        lbmib_status r = ckpt_load(c, w + a.ckpts + (size_t)j * a.ckpt, tape_of(j), sf);
+        if (r != LBMIB_OK) return r;
+        const std::pair<int, int> key(len, b);
+        auto it = graphs.fwd.find(key);
+        if (it == graphs.fwd.end()) {
+            SegmentGraph g;
+            const long long launches0 = c->launches;
+            r = capture_segment(c, &g.exec,
+                                [&](cudaStream_t q) { return tape_forward(c, scheme, len, w, tape_of(j), q); });
+            if (r != LBMIB_OK) return r;
+            g.launches = c->launches - launches0;
+            g.cur_fib = c->cur_fib;
+            c->launches = launches0;
+            c->steps -= len;   // the capture only recorded the steps
+            it = graphs.fwd.emplace(key, g).first;
+        }
+        LBMIB_CUDA(c, cudaGraphLaunch(it->second.exec, sf));
+        LBMIB_CUDA(c, cudaEventRecord(ev.fdone[b], sf));
+        c->launches += it->second.launches;
+        c->cur_fib = it->second.cur_fib;
+        c->steps += len;
+        return LBMIB_OK;
+    };
+    if (a.nseg > 1) {
+        LBMIB_CUDA(c, cudaEventRecord(ev.fork, s));   // the objective and the cleared buffers
+        LBMIB_CUDA(c, cudaStreamWaitEvent(sf, ev.fork, 0));
+        st = recompute(a.nseg - 1);
+        if (st != LBMIB_OK) return st;
+    }
     for (int j = a.nseg - 1; j >= 0; j--) {
         const long long n0 = (long long)j * a.K;
         const int len = (int)std::min<long long>(a.K, nsteps - n0);
+        const int b = j & 1;
         if (a.nseg > 1) {
-            st = ckpt_load(c, w + a.ckpts + (size_t)j * a.ckpt, a);
-            if (st != LBMIB_OK) return st;
-            auto it = graphs.fwd.find(len);
-            if (it == graphs.fwd.end()) {
-                SegmentGraph g;
-                const long long launches0 = c->launches;
-                st = capture_segment(c, &g.exec, [&](cudaStream_t q) { return tape_forward(c, scheme, len, w, a, q); });
+            if (j > 0) {
+                st = recompute(j - 1);
                 if (st != LBMIB_OK) return st;
-                g.launches = c->launches - launches0;
-                g.cur_fib = c->cur_fib;
-                c->launches = launches0;
-                c->steps -= len;   // the capture only recorded the steps
-                it = graphs.fwd.emplace(len, g).first;
             }
-            LBMIB_CUDA(c, cudaGraphLaunch(it->second.exec, s));
-            c->launches += it->second.launches;
-            c->cur_fib = it->second.cur_fib;
-            c->steps += len;
+            LBMIB_CUDA(c, cudaStreamWaitEvent(s, ev.fdone[b], 0));
         }
-        const std::pair<int, int> key(len, (int)(n0 % 6));
+        const std::tuple<int, int, int> key(len, (int)(n0 % 6), a.nseg > 1 ? b : 0);
         auto it = graphs.rev.find(key);
         if (it == graphs.rev.end()) {
             SegmentGraph g;
             const long long launches0 = c->launches;
+            const AdjLayout& t = a.nseg > 1 ? tape_of(j) : a;
             st = capture_segment(c, &g.exec, [&](cudaStream_t q) {
                 lbmib_status r = LBMIB_OK;
                 by_storage(c->cfg.storage, [&](auto tag) {
                     using S = decltype(tag);
-                    r = scheme == LBMIB_KINEMATIC ? reverse_segment<S>(c, n0, len, w, a, q)
-                                                  : reverse_segment_dynamic<S>(c, n0, len, w, a, q);
+                    r = scheme == LBMIB_KINEMATIC ? reverse_segment<S>(c, n0, len, w, t, q)
+                                                  : reverse_segment_dynamic<S>(c, n0, len, w, t, q);
                 });
                 return r;
             });
@@ -1526,10 +1584,15 @@ lbmib_status lbmib_adjoint(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme, 
             it = graphs.rev.emplace(key, g).first;
         }
         LBMIB_CUDA(c, cudaGraphLaunch(it->second.exec, s));
+        if (a.nseg > 1) LBMIB_CUDA(c, cudaEventRecord(ev.rdone[b], s));
         c->launches += it->second.launches;
     }
+    if (a.nseg > 1) {   // join the recompute stream before the context state is restored
+        LBMIB_CUDA(c, cudaEventRecord(ev.fork, sf));
+        LBMIB_CUDA(c, cudaStreamWaitEvent(s, ev.fork, 0));
+    }
     if (a.nseg > 1) {
-        st = ckpt_load(c, w + a.ckpts + (size_t)a.nseg * a.ckpt, a);
+        st = ckpt_load(c, w + a.ckpts + (size_t)a.nseg * a.ckpt, a, s);
         if (st != LBMIB_OK) return st;
         c->steps = steps_end;
     }

@@ -267,45 +267,57 @@ __device__ __forceinline__ bool dyn_spread(const S* __restrict__ src, const Lat&
                                            Tile<typename St<S>::C>& t, const Spread& sp, int stamp) {
     using C = typename St<S>::C;
     constexpr bool F32 = sizeof(C) == 4;   // single precision: lengths and forces in float
-    // lengths of the elements on both sides of every own vertex (c_l of reading R4)
+    // lengths of the elements on both sides of every own vertex (c_l of reading R4). FRAMED
+    // (single precision, right after this CTA's node update): the staged slots still hold
+    // X^n, with the float edge vectors of X^n and the float increments X^{n+1} - X^n, so
+    // the edges of X^{n+1} are e + (d_{v+1} - d_v) in float, to the float rounding of the
+    // double differences they replace.
     for (int e = threadIdx.x; e < (a.m > 0 ? a.m + 1 : 0); e += blockDim.x) {
         const int li = kHalo - 1 + e;
-        const double2 d = sm.X[li + 1] - sm.X[li];
-        if constexpr (F32) {
-            const float dx = (float)d.x, dy = (float)d.y;
+        if constexpr (FRAMED && F32) {
+            const float2 ev = ring_f(sm)[li].e, d0 = xd_f(sm)[li], d1 = xd_f(sm)[li + 1];
+            const float dx = ev.x + (d1.x - d0.x), dy = ev.y + (d1.y - d0.y);
             len_f(sm)[li] = sqrtf(dx * dx + dy * dy);
         } else {
-            sm.sst[li] = sqrt(d.x * d.x + d.y * d.y);
+            const double2 d = sm.X[li + 1] - sm.X[li];
+            if constexpr (F32) {
+                const float dx = (float)d.x, dy = (float)d.y;
+                len_f(sm)[li] = sqrtf(dx * dx + dy * dy);
+            } else {
+                sm.sst[li] = sqrt(d.x * d.x + d.y * d.y);
+            }
         }
     }
     __syncthreads();
     bool ok = true;
     for (int k = threadIdx.x; k < a.m; k += blockDim.x) {
         const int li = kHalo + k, g = P.off + a.v0 + k;
-        const double2 Xv = sm.X[li];
         // shape functions at X^n: used for U, for the spread, and by this step's update
         MlsW<C> w;
         if constexpr (FRAMED && sizeof(C) == 4) {
             w = load_mls<C>(L, nd.mls, g);
         } else {
+            const double2 Xv = sm.X[li];
             w = mls_setup<C>(L, Xv.x, Xv.y);
             store_mls<C>(nd.mls, g, w);
         }
         InterpT<C> o;
         ok &= interp_with<S, false>(w, t, src, L, nullptr, o);
-        const double Ux = (double)o.ux, Uy = (double)o.uy;
-        nd.U[g] = make_double2(Ux, Uy);
+        // U as computed: float for single precision, double otherwise
+        if constexpr (F32) u_f(nd)[g] = make_float2(o.ux, o.uy);
+        else nd.U[g] = make_double2((double)o.ux, (double)o.uy);
         double2 uv;
         if (RIGID && P.rigid) {
-            uv = rigid_velocity(nd.rb[a.cap].body, Xv);   // the body's motion (Section 2.3.1)
+            uv = rigid_velocity(nd.rb[a.cap].body, sm.X[li]);   // the body's motion (Section 2.3.1)
         } else {
             uv = nd.uv[g];
-            if (nd.age[g] == 0) {
-                uv = make_double2(Ux, Uy);
+            if (!FRAMED && nd.age[g] == 0) {   // a vertex's first step (never a fused one)
+                uv = make_double2((double)o.ux, (double)o.uy);
                 nd.uv[g] = uv;
-                nd.Xm1[g] = Xv - uv;
+                nd.Xm1[g] = sm.X[li] - uv;
             }
         }
+        const double Ux = (double)o.ux, Uy = (double)o.uy;
         if constexpr (F32) {
             const float cl = 0.5f * (len_f(sm)[li - 1] + len_f(sm)[li]);
             const float Fx = (float)uv.x - o.ux, Fy = (float)uv.y - o.uy;
@@ -476,6 +488,9 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
         const float hm = 0.5f / (float)P.m;
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
             const int li = kHalo + k, g = P.off + a.v0 + k;
+            // the vertex's global inputs first, so that their latency overlaps the force terms
+            const double2 Xm = nd.Xm1[g];
+            const float2 xd = u_f(nd)[g];   // tentative velocity U of step 1 (Eq. 23)
             const float2 Fi = internal_force_f(sm, li - 1, li, li + 1, fa);
             const float2 e0 = ext_f(sm)[li], e1 = ext_f(sm)[li - 1];
             float2 Fe = make_float2(0.5f * (e0.x + e1.x), 0.5f * (e0.y + e1.y));
@@ -484,9 +499,7 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
                 Fe.x += (float)f.x;
                 Fe.y += (float)f.y;
             }
-            const double2 Xv = sm.X[li], Xm = nd.Xm1[g];
-            const double2 U = nd.U[g];
-            const float2 xd = make_float2((float)U.x, (float)U.y);
+            const double2 Xv = sm.X[li];
             // Eq. 23 as the increment X^{n+1} - X^n, and Eq. 24 as
             // 1.5 (X^{n+1} - X^n) - 0.5 (X^n - X^{n-1})
             const float ix = xd.x + hm * (Fi.x + Fe.x), iy = xd.y + hm * (Fi.y + Fe.y);
@@ -511,9 +524,14 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
                     f.d0x = __int_as_float(0x7fc00000);
                 }
                 reinterpret_cast<MlsFrame*>(nd.mls)[g] = f;
+                // the increment for the next step's element lengths (the slot's tentative
+                // velocity is dead by now). The last forces are not stored: a fused update
+                // never ends a call, and the update that does stores them.
+                xd_f(sm)[li] = make_float2(ix, iy);
+            } else {
+                nd.Fint[g] = make_double2(Fi.x, Fi.y);
+                nd.Fext[g] = make_double2(Fe.x, Fe.y);
             }
-            nd.Fint[g] = make_double2(Fi.x, Fi.y);
-            nd.Fext[g] = make_double2(Fe.x, Fe.y);
             nd.age[g] += 1;
         }
     } else {
@@ -585,8 +603,16 @@ __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_update_spread(
     }
     __syncthreads();
     bool ok = dyn_update<S, true>(dst, L, nd, P, a, sm, t, 1, a.m);
-    __syncthreads();   // every X^{n+1} is written; the staged X^n is dead
-    for (int li = threadIdx.x; li < a.m + 2 * kHalo; li += blockDim.x) sm.X[li] = nd.X[P.off + a.node(li)];
+    __syncthreads();   // every X^{n+1} is written (single precision: every increment staged)
+    if constexpr (sizeof(C) == 4) {
+        // the halo slots of the whole ring repeat its last and first vertex
+        if (threadIdx.x == 0) {
+            xd_f(sm)[kHalo - 1] = xd_f(sm)[kHalo + a.m - 1];
+            xd_f(sm)[kHalo + a.m] = xd_f(sm)[kHalo];
+        }
+    } else {
+        for (int li = threadIdx.x; li < a.m + 2 * kHalo; li += blockDim.x) sm.X[li] = nd.X[P.off + a.node(li)];
+    }
     __syncthreads();
     const int stamp = *sp.stamp + 1;
     ok &= dyn_spread<S, false, true>(dst, L, nd, P, a, sm, t, sp, stamp);

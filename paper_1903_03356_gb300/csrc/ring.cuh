@@ -190,6 +190,8 @@ __device__ __forceinline__ RingF* ring_f(const CapSmem& sm) { return reinterpret
 __device__ __forceinline__ float2* ext_f(const CapSmem& sm) { return reinterpret_cast<float2*>(sm.ext); }
 __device__ __forceinline__ float2* xd_f(const CapSmem& sm) { return reinterpret_cast<float2*>(sm.xd); }
 __device__ __forceinline__ float* len_f(const CapSmem& sm) { return reinterpret_cast<float*>(sm.sst); }
+// the Dynamic scheme's per-vertex U as float in single precision (the first half of its slots)
+__device__ __forceinline__ float2* u_f(const Nodes& nd) { return reinterpret_cast<float2*>(nd.U); }
 
 // vertex_terms in single precision (the same Eq. 11 and Eq. 13 terms).
 __device__ __forceinline__ void vertex_terms_f(const CapSmem& sm, const CapsuleParams& P, const Nodes& nd, int vl,

@@ -1,5 +1,5 @@
 """The Dynamic node update of a step fused with the force and spread of the next
-(Section 2.3.2 steps 5-8 and 1-3 read the same lattice state): against the separate
+(Section 2.3.2 steps 7-8 and 1-3 read the same lattice state): against the separate
 kernels, against the oracle, through graphs and direct launches, across call boundaries,
 and in the launch count it reports.
 """
