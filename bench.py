@@ -64,7 +64,8 @@ def parse():
     p.add_argument("--study-oracle-steps", type=int, default=100,
                    help="precision study: steps of the FP64 oracle run the GPU runs are compared with")
     p.add_argument("--only", default="all",
-                   choices=["all", "batched", "adjoint", "precision", "dense", "open", "rigid", "study", "fp64"],
+                   choices=["all", "batched", "adjoint", "precision", "dense", "open", "rigid", "study", "fp64",
+                            "poiseuille"],
                    help="batched / adjoint: run only that measurement and print its JSON object")
     return p.parse_args()
 
@@ -358,6 +359,7 @@ def run_gpu(a):
         line["fp64_storage"] = fp64_coupled_run(L, a, case, scheme, dev)
         line["precision"] = precision_run(L, dev)
         line["precision_study"] = precision_study(L, a.study_steps, a.study_oracle_steps)
+        line["poiseuille_runs"] = poiseuille_runs(L)
         line["dense"] = dense_run(L)
         line["open"] = open_run(L)
         line["rigid"] = rigid_run(L)
@@ -452,6 +454,45 @@ def fp64_coupled_run(L, a, case, scheme, dev, steps=20, warmup=3):
                          "achieved": FP64_INSTR_PER_UPDATE * gl, "frac": FP64_INSTR_PER_UPDATE * gl / peak,
                          "peak_source": "2 FP64 instructions per SM per cycle x 152 SMs x sampled SM clock"},
             "clocks": clk.summary()}
+
+
+def poiseuille_runs(L, steps=20000, every=2000):
+    """Dynamic against Kinematic IB for an inertial circular capsule in plane Poiseuille
+    flow: 600 x 120 channel, tau 0.7, body force for a centre-line velocity of 0.02,
+    radius 12 with 96 vertices starting at y = 0.3 H, density ratio 1 and 5 (Kinematic:
+    1 only), Ca 1e-3, 1e-2, 1e-1, FP64 and FP32 storage, `steps` steps: the centroid
+    trajectory and Taylor D every `every` steps, and each FP32 run's largest departure
+    from its FP64 run."""
+    import torch
+
+    out = {"workload": "600x120 Poiseuille channel, circular capsule r 12 (96 vertices) at 0.3 H, tau 0.7, "
+                       "u_max 0.02", "steps": steps, "every": every, "runs": []}
+    t0 = time.perf_counter()
+    for scheme, ratios in ((L.DYNAMIC, (1.0, 5.0)), (L.KINEMATIC, (1.0,))):
+        for ratio in ratios:
+            for ca in (1e-3, 1e-2, 1e-1):
+                case = W.poiseuille_capsule(ca=ca, density_ratio=ratio, scheme=scheme, steps=steps)
+                traj = {}
+                for storage in ("fp64", "fp32"):
+                    ctx = L.from_case(case, storage=storage)
+                    rows = []
+                    for _ in range(steps // every):
+                        ctx.step(every, scheme)
+                        o = ctx.observables(0)
+                        rows.append([float(o[3]), float(o[4]), float(o[2])])   # x_c, y_c, D
+                    ctx.close()
+                    traj[storage] = np.array(rows)
+                d64, d32 = traj["fp64"], traj["fp32"]
+                out["runs"].append({
+                    "scheme": "dynamic" if scheme == L.DYNAMIC else "kinematic", "density_ratio": ratio, "ca": ca,
+                    "k_s": case.capsules[0].ks, "k_b": case.capsules[0].kb,
+                    "fp64": {"x_c": d64[:, 0].round(4).tolist(), "y_c": d64[:, 1].round(5).tolist(),
+                             "D": d64[:, 2].round(6).tolist()},
+                    "fp32_max_dev": {"y_c": float(np.abs(d32[:, 1] - d64[:, 1]).max()),
+                                     "D": float(np.abs(d32[:, 2] - d64[:, 2]).max())}})
+    torch.cuda.synchronize()
+    out["wall_s"] = time.perf_counter() - t0
+    return out
 
 
 def _study_case():
@@ -810,6 +851,7 @@ def main():
                else open_run(L) if a.only == "open"
                else rigid_run(L) if a.only == "rigid"
                else precision_study(L, a.study_steps, a.study_oracle_steps) if a.only == "study"
+               else poiseuille_runs(L) if a.only == "poiseuille"
                else fp64_coupled_run(L, a, make_case(a), L.DYNAMIC if a.scheme == "dynamic" else L.KINEMATIC,
                                      int(os.environ.get("LOCAL_RANK", "0"))) if a.only == "fp64"
                else {"dynamic": adjoint_run(L, a.storage, a.adjoint_steps, scheme=1),

@@ -167,12 +167,39 @@ __device__ void run_case(const BatchDev& d, int c, int nsteps, const CapSmem& sm
             if (t.use && (t.w > L.nx || (!L.walls && t.h > L.ny))) t.use = false;
             ok &= t.use;
             if (t.use) zero_forces<C>(t);
-            double area2[1] = {0.0};
-            for (int v = threadIdx.x; v < n; v += blockDim.x) area2[0] += ring_terms(sm, P, d.nd, v);
-            block_reduce<1, false>(area2, sm.red);
-            const double A = 0.5 * area2[0];
+            // membrane terms (Eq. 11, 13, 14): in float for single-precision storage, as in
+            // the single-case IB kernels (positions and the update stay double)
+            constexpr bool F32 = sizeof(C) == 4;
+            float fa = 0.0f;
+            double A = 0.0;
+            if constexpr (F32) {
+                for (int v = threadIdx.x; v < n; v += blockDim.x)
+                    vertex_terms_f(sm, P, d.nd, v == 0 ? n - 1 : v - 1, v, v + 1 == n ? 0 : v + 1, off + v);
+                __syncthreads();
+                float area2[1] = {0.0f};
+                const double2 X0 = sm.X[0];
+                for (int v = threadIdx.x; v < n; v += blockDim.x) {
+                    const double2 Xv = sm.X[v];
+                    const float2 e = ring_f(sm)[v].e;
+                    area2[0] += (float)(Xv.x - X0.x) * e.y - (float)(Xv.y - X0.y) * e.x;
+                }
+                block_reduce<1, false>(area2, sm.red);
+                // Eq. 14 factor k_a (1 - A/A0) p_ref / 2 from the difference A0 - A
+                fa = (float)P.ka * (((float)P.A0 - 0.5f * area2[0]) / (6.0f * (float)P.A0));
+            } else {
+                double area2[1] = {0.0};
+                for (int v = threadIdx.x; v < n; v += blockDim.x) area2[0] += ring_terms(sm, P, d.nd, v);
+                block_reduce<1, false>(area2, sm.red);
+                A = 0.5 * area2[0];
+            }
             for (int v = threadIdx.x; v < n; v += blockDim.x) {
-                const double2 F = node_internal_force(sm, P, v, A);
+                double2 F;
+                if constexpr (F32) {
+                    const float2 Ff = internal_force_f(sm, v == 0 ? n - 1 : v - 1, v, v + 1 == n ? 0 : v + 1, fa);
+                    F = make_double2(Ff.x, Ff.y);
+                } else {
+                    F = node_internal_force(sm, P, v, A);
+                }
                 if (t.use) {
                     const MlsW<C> m = mls_setup<C>(L, sm.X[v].x, sm.X[v].y);
                     ok &= m.ok && t.holds(m.cx, m.cy);

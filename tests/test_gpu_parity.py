@@ -237,6 +237,26 @@ def test_fp16_storage_error_is_reported(L):
     assert err < 5e-2
 
 
+def test_fp16_dynamic_coupled_step_error_is_reported(L):
+    # FP16 storage (shifted values times 2^10 in half precision, collision in FP32) on the
+    # Dynamic biconcave suspension: its error against the FP64 oracle is reported. The
+    # bound follows from the storage: half an FP16 ulp of the scaled shifted populations
+    # (up to ~7 for u ~ 0.02: 2e-3, i.e. 2e-6 in f) per step, repeated the same way on a
+    # near-steady flow, is ~4e-4 in f and ~1e-2 of u_max after 200 steps.
+    case = W.poiseuille_biconcave(nx=300, ny=96, count=6, n=64, seed=0, scheme=o.DYNAMIC)
+    ctx = L.from_case(case, storage="fp16")
+    s = oracle_sim(case)
+    ctx.step(200, o.DYNAMIC)
+    assert s.step(200, o.DYNAMIC) == 0
+    _, u_g, v_g = ctx.read_fields()
+    _, u_o, v_o = s.read_fields()
+    err = rel(np.stack([u_g, v_g]), np.stack([u_o, v_o]))
+    dD = max(abs(ctx.observables(k)[2] - s.observables(k)[2]) for k in range(len(case.capsules)))
+    print(f"fp16 dynamic 200 steps: velocity rel err {err:.3e}, max |dD| {dD:.3e}")
+    assert err < 1e-2
+    assert dD < 1e-3
+
+
 @pytest.mark.parametrize("nx,ny,walls", [(301, 37, True), (512, 20, False), (256, 64, True)])
 def test_packed_fp16_kernel_equals_the_scalar_fp16_kernel(L, nx, ny, walls):
     # the 8-nodes-per-thread FP16 lattice kernel (default) against the 4-per-thread one:
