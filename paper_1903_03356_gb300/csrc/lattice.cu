@@ -419,19 +419,38 @@ __global__ void __launch_bounds__(256) k_patch(const S* __restrict__ src, S* __r
         nc = nc > capacity ? capacity : nc;
         np = np > capacity ? capacity : np;
     }
-    for (int k = t0; k < nc; k += stride) {
-        const int cell = list_c[k];
-        if (cell < 0 || (long long)cell >= N) {
-            atomicOr(&ctr->status, kStatCell);
-            continue;
-        }
-        const int y = cell / L.nx, x = cell - y * L.nx;
-        C s[9];
-        pull_all<S>(src, L, x, y, s);
-        const C usq = collide<C>(s, C(L.gx + fib_c[cell]), C(L.gy + fib_c[N + cell]), C(L.omega));
-        if (!(usq < C(0.09))) atomicOr(&ctr->status, kStatUnstable);
+    // two list entries per thread and pass, all their pulls issued before either is
+    // collided: twice the loads in flight of one node per thread (the kernel waits on
+    // memory latency, not bandwidth)
+    for (int k = t0; k < nc; k += 2 * stride) {
+        int cell[2] = {list_c[k], k + stride < nc ? list_c[k + stride] : -1};
+        bool use[2];
 #pragma unroll
-        for (int i = 0; i < 9; i++) St<S>::st(dst + (long long)i * L.plane + (long long)y * L.pitch + x, s[i], L);
+        for (int q = 0; q < 2; q++) {
+            use[q] = cell[q] >= 0 && (long long)cell[q] < N;
+            if (!use[q] && (q == 0 || k + stride < nc)) atomicOr(&ctr->status, kStatCell);
+            if (!use[q]) cell[q] = 0;
+        }
+        int y[2], x[2];
+        C s[2][9];
+        double fx[2], fy[2];
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            y[q] = cell[q] / L.nx;
+            x[q] = cell[q] - y[q] * L.nx;
+            pull_all<S>(src, L, x[q], y[q], s[q]);
+            fx[q] = fib_c[cell[q]];
+            fy[q] = fib_c[N + cell[q]];
+        }
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            if (!use[q]) continue;
+            const C usq = collide<C>(s[q], C(L.gx + fx[q]), C(L.gy + fy[q]), C(L.omega));
+            if (!(usq < C(0.09))) atomicOr(&ctr->status, kStatUnstable);
+#pragma unroll
+            for (int i = 0; i < 9; i++)
+                St<S>::st(dst + (long long)i * L.plane + (long long)y[q] * L.pitch + x[q], s[q][i], L);
+        }
     }
     for (int k = t0; k < np; k += stride) {
         const int cell = list_p[k];
@@ -604,10 +623,11 @@ void launch_collide_stream(const void* src, void* dst, const Lat& L, unsigned* s
 template <typename S>
 void launch_patch(const void* src, void* dst, const Lat& L, const double* fib_c, const int* list_c,
                   double* fib_p, const int* list_p, DevCounters* ctr, int c, int capacity, cudaStream_t s) {
-    // a grid-stride loop over the touched list, whose length only the device knows: up to
-    // 16384 blocks, about one node per thread on the benchmark (4096 blocks: 0.1 % slower)
-    int grid = (int)blocks_for(capacity > 0 ? capacity : 1, 256);
-    if (grid > 16384) grid = 16384;
+    // a grid-stride loop over the touched list, whose length only the device knows, two
+    // entries per thread and pass: up to 6144 blocks of 256, one pass for the 2.9e6
+    // touched nodes of the 16384 x 8192 benchmark
+    int grid = (int)blocks_for(capacity > 0 ? (capacity + 1) / 2 : 1, 256);
+    if (grid > 6144) grid = 6144;
     k_patch<S><<<grid, 256, 0, s>>>((const S*)src, (S*)dst, L, fib_c, list_c, fib_p, list_p, ctr, c, capacity);
 }
 
