@@ -1519,6 +1519,15 @@ lbmib_status lbmib_adjoint(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme, 
     cudaStream_t sf = c->aux_stream;
     Events ev;
     if (!ev.ok) return fail(c, LBMIB_ERR_CUDA, "lbmib_adjoint: cudaEventCreateWithFlags failed");
+    // how many segments share each shape: only a shape used more than once is captured
+    std::map<std::pair<int, int>, int> fwd_uses;
+    std::map<std::tuple<int, int, int>, int> rev_uses;
+    for (int j = 0; j < a.nseg; j++) {
+        const long long n0 = (long long)j * a.K;
+        const int len = (int)std::min<long long>(a.K, nsteps - n0);
+        if (j < a.nseg) fwd_uses[std::make_pair(len, j & 1)]++;
+        rev_uses[std::make_tuple(len, (int)(n0 % 6), a.nseg > 1 ? (j & 1) : 0)]++;
+    }
     auto recompute = [&](int j) -> lbmib_status {
         const int b = j & 1;
         const int len = (int)std::min<long long>(a.K, nsteps - (long long)j * a.K);
@@ -1526,6 +1535,12 @@ lbmib_status lbmib_adjoint(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme, 
         lbmib_status r = ckpt_load(c, w + a.ckpts + (size_t)j * a.ckpt, tape_of(j), sf);
         if (r != LBMIB_OK) return r;
         const std::pair<int, int> key(len, b);
+        if (fwd_uses[key] <= 1) {   // a shape recomputed once is enqueued directly
+            r = tape_forward(c, scheme, len, w, tape_of(j), sf);
+            if (r != LBMIB_OK) return r;
+            LBMIB_CUDA(c, cudaEventRecord(ev.fdone[b], sf));
+            return LBMIB_OK;
+        }
         auto it = graphs.fwd.find(key);
         if (it == graphs.fwd.end()) {
             SegmentGraph g;
@@ -1564,11 +1579,21 @@ lbmib_status lbmib_adjoint(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme, 
             LBMIB_CUDA(c, cudaStreamWaitEvent(s, ev.fdone[b], 0));
         }
         const std::tuple<int, int, int> key(len, (int)(n0 % 6), a.nseg > 1 ? b : 0);
+        const AdjLayout& t = a.nseg > 1 ? tape_of(j) : a;
+        if (rev_uses[key] <= 1) {   // a shape reversed once is enqueued directly
+            by_storage(c->cfg.storage, [&](auto tag) {
+                using S = decltype(tag);
+                st = scheme == LBMIB_KINEMATIC ? reverse_segment<S>(c, n0, len, w, t, s)
+                                               : reverse_segment_dynamic<S>(c, n0, len, w, t, s);
+            });
+            if (st != LBMIB_OK) return st;
+            if (a.nseg > 1) LBMIB_CUDA(c, cudaEventRecord(ev.rdone[b], s));
+            continue;
+        }
         auto it = graphs.rev.find(key);
         if (it == graphs.rev.end()) {
             SegmentGraph g;
             const long long launches0 = c->launches;
-            const AdjLayout& t = a.nseg > 1 ? tape_of(j) : a;
             st = capture_segment(c, &g.exec, [&](cudaStream_t q) {
                 lbmib_status r = LBMIB_OK;
                 by_storage(c->cfg.storage, [&](auto tag) {
