@@ -1525,7 +1525,7 @@ lbmib_status lbmib_adjoint(lbmib_ctx* c, long long nsteps, lbmib_scheme scheme, 
     for (int j = 0; j < a.nseg; j++) {
         const long long n0 = (long long)j * a.K;
         const int len = (int)std::min<long long>(a.K, nsteps - n0);
-        if (j < a.nseg) fwd_uses[std::make_pair(len, j & 1)]++;
+        fwd_uses[std::make_pair(len, j & 1)]++;
         rev_uses[std::make_tuple(len, (int)(n0 % 6), a.nseg > 1 ? (j & 1) : 0)]++;
     }
     auto recompute = [&](int j) -> lbmib_status {

@@ -424,7 +424,7 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
             // the vertex's shape functions at X^n (stored by this step's spread kernel) place
             // the probes of its element in float
             const MlsW<C> w = load_mls<C>(L, nd.mls, P.off + a.node(li));
-            if (k < m) {
+            if (k < m && P.ka != 0.0) {
                 // the area term (X_v - X_0) x (X_{v+1} - X_0) = (X_v - X_0) x e_v, in float:
                 // its rounding is of the order of the float membrane terms'
                 const double2 Xv = sm.X[li];
@@ -474,8 +474,12 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
                                   (double)(-dp * ny + txy * nx + tyy * ny) * len);
     }
     if constexpr (F32) {
-        block_reduce<1, false>(area2f, sm.red);
-        area2[0] = area2f[0];
+        if (P.ka != 0.0) {   // the enclosed area enters only Eq. 14's term, k_a (1 - A/A0)
+            block_reduce<1, false>(area2f, sm.red);
+            area2[0] = area2f[0];
+        } else {
+            __syncthreads();   // the staged terms and tractions, before the neighbours read them
+        }
     } else {
         block_reduce<1, false>(area2, sm.red);
     }

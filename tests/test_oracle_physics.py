@@ -42,3 +42,19 @@ def test_capsule_in_couette_flow_migrates_towards_the_centre_line():
     yc = obs[:, 4]
     assert np.all(np.diff(yc) > 0)
     assert yc[-1] - 14.37 > 0.5 and yc[-1] < 0.5 * case.ny
+
+
+def test_dynamic_capsules_in_couette_flow_migrate_towards_the_centre_line():
+    # Section 3.5: in a linear (Couette) flow capsules of any membrane mass reach 0.5 H.
+    # With the Dynamic scheme, density ratios 1 and 2, started at 0.3 H: the centroid rises
+    # steadily over 6000 steps (after the start-up interval) and the heavier capsule lags.
+    rise = {}
+    for ratio in (1.0, 2.0):
+        case = W.shear_capsule(nx=80, ny=48, radius=6.0, n=40, ca=0.05, scheme=o.DYNAMIC, centre=(40.1, 14.37),
+                               shear_rate=4e-4, density_ratio=ratio)
+        yc = run(case, o.DYNAMIC, 6000, every=1500)[:, 4]
+        assert np.all(np.diff(yc) > 0)
+        assert yc[-1] < 0.5 * case.ny
+        rise[ratio] = yc[-1] - 14.37
+    assert rise[1.0] > 0.2 and rise[2.0] > 0.15
+    assert rise[2.0] < rise[1.0]
