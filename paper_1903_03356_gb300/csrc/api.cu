@@ -464,8 +464,7 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->ib_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking);
-    for (cudaEvent_t* ev : {&c->ev_fork, &c->ev_spread, &c->ev_patch, &c->ev_join, &c->ev_adj[0], &c->ev_adj[1],
-                            &c->ev_adj[2], &c->ev_adj[3]})
+    for (cudaEvent_t* ev : {&c->ev_fork, &c->ev_spread, &c->ev_patch, &c->ev_join, &c->ev_adj[0], &c->ev_adj[1]})
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         lbmib_destroy(c);
@@ -509,8 +508,7 @@ void lbmib_destroy(lbmib_ctx* c) {
             cudaStreamSynchronize(*q);
             cudaStreamDestroy(*q);
         }
-    for (cudaEvent_t ev : {c->ev_fork, c->ev_spread, c->ev_patch, c->ev_join, c->ev_adj[0], c->ev_adj[1],
-                           c->ev_adj[2], c->ev_adj[3]})
+    for (cudaEvent_t ev : {c->ev_fork, c->ev_spread, c->ev_patch, c->ev_join, c->ev_adj[0], c->ev_adj[1]})
         if (ev) cudaEventDestroy(ev);
     delete c;
 }

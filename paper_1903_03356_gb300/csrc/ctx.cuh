@@ -43,9 +43,10 @@ struct lbmib_ctx {
     cudaStream_t ib_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_spread = nullptr, ev_patch = nullptr, ev_join = nullptr;
     int overlap = -1;   // 1 on, 0 off, -1 automatic (on while the capsules cannot fill the GPU)
-    // a third stream and events for the reverse sweep's independent kernels
+    // the adjoint's third stream (a segment's recompute beside the previous segment's
+    // reverse sweep) and the events of the reverse sweep's side-stream spread
     cudaStream_t aux_stream = nullptr;
-    cudaEvent_t ev_adj[4]{};
+    cudaEvent_t ev_adj[2]{};
     // capsule-capsule repulsion (Eq. 27); rep_rc = 0: off
     double rep_rc = 0.0, rep_coeff = 0.0;
     lbmib::RepGrid rep{};
