@@ -44,7 +44,6 @@ Layout make_layout(const lbmib_config* c) {
     L.pops[1] = take(9 * (size_t)L.plane * s);
     L.fib[0] = take(2 * N * sizeof(double));
     L.fib[1] = take(2 * N * sizeof(double));
-    L.mark = take(N * sizeof(int));
     L.list[0] = take(9 * M * sizeof(int));
     L.list[1] = take(9 * M * sizeof(int));
     L.ctr = take(sizeof(DevCounters));
@@ -170,7 +169,7 @@ bool enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
     const int fp = cur_fib;      // last spread force
     unsigned* status = &c->ctr->status;
     const int list_cap = 9 * (c->cfg.max_nodes > 0 ? c->cfg.max_nodes : 1);
-    Spread sp{c->fib[fc], c->mark, c->list[fc], &c->ctr->count[fc], &c->ctr->step_stamp, list_cap, status};
+    Spread sp{c->fib[fc], c->list[fc], &c->ctr->count[fc], list_cap, status};
     const lbmib_storage st = c->cfg.storage;
     if (ncaps > 1 && c->rep_rc > 0.0) {
         launch_repulsion(L, c->nd, ncaps, c->max_n, c->arcs, c->rep, status, s);
@@ -231,7 +230,7 @@ bool enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
             // the next step spreads into the buffer and list this step's patch has just
             // cleared and read: reset their counter first (the fused kernel appends to it)
             cudaMemsetAsync(reset, 0, sizeof(int), s);
-            const Spread next{c->fib[fp], c->mark, c->list[fp], reset, &c->ctr->step_stamp, list_cap, status};
+            const Spread next{c->fib[fp], c->list[fp], reset, list_cap, status};
             with_ib_storage(c, [&](auto v) {
                 launch_dyn_update_spread<decltype(v)>(dst, L, c->nd, ncaps, c->max_n, c->tile_cells, next,
                                                       status, s);
@@ -402,7 +401,6 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     c->pops[1] = a + lay.pops[1];
     c->fib[0] = (double*)(a + lay.fib[0]);
     c->fib[1] = (double*)(a + lay.fib[1]);
-    c->mark = (int*)(a + lay.mark);
     c->list[0] = (int*)(a + lay.list[0]);
     c->list[1] = (int*)(a + lay.list[1]);
     c->ctr = (DevCounters*)(a + lay.ctr);
@@ -474,7 +472,6 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     const size_t N = (size_t)cfg->nx * cfg->ny;
     e = cudaMemsetAsync(c->fib[0], 0, 2 * N * sizeof(double), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->fib[1], 0, 2 * N * sizeof(double), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->mark, 0, N * sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream);
     if (e != cudaSuccess) {
         lbmib_destroy(c);
@@ -966,8 +963,6 @@ lbmib_status lbmib_load_state(lbmib_ctx* c, const void* buf, size_t bytes) {
     LBMIB_CUDA(c, cudaMemcpy(c->nd.age, p, M * sizeof(int), cudaMemcpyHostToDevice));
     p += M * sizeof(int);
     LBMIB_CUDA(c, cudaMemcpy(c->nd.rb, p, c->caps.size() * sizeof(RigidBody), cudaMemcpyHostToDevice));
-    // fresh stamps: no cell carries a stamp that a coming step will use
-    LBMIB_CUDA(c, cudaMemset(c->mark, 0, N * sizeof(int)));
     DevCounters ctr{};
     ctr.count[0] = h.count;
     LBMIB_CUDA(c, cudaMemcpy(c->ctr, &ctr, sizeof(ctr), cudaMemcpyHostToDevice));

@@ -32,47 +32,60 @@ namespace lbmib {
 
 size_t capsule_smem_bytes(int max_n) { return ring_smem_bytes(max_n); }
 
-// Fill the moment tile from the populations (nine pulls per node, row by row).
+// Fill the moment tile from the populations (nine pulls per node, row by row), two
+// nodes per thread and pass with both nodes' pulls issued before either is reduced: the
+// fill waits on memory latency, and this halves its round trips.
 template <typename S>
 __device__ void fill_moments(Tile<typename St<S>::C>& t, const S* __restrict__ src, const Lat& L,
                              const double* __restrict__ fib) {
     using C = typename St<S>::C;
     const int cells = t.w * t.h;
-    for (int k = threadIdx.x; k < cells; k += blockDim.x) {
-        const int j = k / t.w, i = k - j * t.w;
-        const Mom<C> m = node_moments<S>(src, L, fib, wrapi(t.x0 + i, L.nx), support_row(L, t.y0 + j));
-        t.drho[k] = m.drho;
-        t.ux[k] = m.ux;
-        t.uy[k] = m.uy;
+    for (int k = threadIdx.x; k < cells; k += 2 * blockDim.x) {
+        const int k1 = k + blockDim.x;
+        const int j0 = k / t.w, i0 = k - j0 * t.w;
+        const int k1c = k1 < cells ? k1 : k;   // a missing second node repeats the first
+        const int j1 = k1c / t.w, i1 = k1c - j1 * t.w;
+        const Mom<C> m0 = node_moments<S>(src, L, fib, wrapi(t.x0 + i0, L.nx), support_row(L, t.y0 + j0));
+        const Mom<C> m1 = node_moments<S>(src, L, fib, wrapi(t.x0 + i1, L.nx), support_row(L, t.y0 + j1));
+        t.drho[k] = m0.drho;
+        t.ux[k] = m0.ux;
+        t.uy[k] = m0.uy;
+        if (k1 < cells) {
+            t.drho[k1] = m1.drho;
+            t.ux[k1] = m1.ux;
+            t.uy[k1] = m1.uy;
+        }
     }
 }
 
-__device__ __forceinline__ void touch(const Spread& sp, int cell, int stamp) {
-    if (atomicExch(&sp.mark[cell], stamp) != stamp) {
-        const int p = atomicAdd(sp.count, 1);
-        if (p < sp.capacity) sp.list[p] = cell;
-        else atomicOr(sp.status, kStatList);
-    }
+__device__ __forceinline__ void touch(const Spread& sp, int cell) {
+    const int p = atomicAdd(sp.count, 1);
+    if (p < sp.capacity) sp.list[p] = cell;
+    else atomicOr(sp.status, kStatList);
 }
 
 // Add the force tile to the lattice force field and record the touched nodes. The
-// nodes new to this step's list are collected in shared memory first and appended with
-// one global reservation per capsule, so that the list counter is not a hot spot.
+// tile's nonzero nodes are collected in shared memory first and appended with one global
+// reservation per capsule, so that the list counter is not a hot spot, and nothing in
+// the loop waits on a global round trip (the force adds are fire-and-forget). A node
+// that the tiles of several capsules cover is listed once by each: the patch then
+// redoes its collision, and clears its force, more than once, with the same result, and
+// the list still holds at most 9 entries per vertex.
 // Collective (all threads); the moment arrays are dead by now and hold the scratch.
 template <typename C>
-__device__ void flush_forces(const Tile<C>& t, const Lat& L, const Spread& sp, int stamp, int* s_count) {
+__device__ void flush_forces(const Tile<C>& t, const Lat& L, const Spread& sp, int* s_count) {
     const long long N = (long long)L.nx * L.ny;
     const int cells = t.w * t.h;
     if (threadIdx.x == 0) *s_count = 0;
     __syncthreads();
     for (int k = threadIdx.x; k < cells; k += blockDim.x) {
-        const double fx = (double)t.fx[k], fy = (double)t.fy[k];
-        if (fx == 0.0 && fy == 0.0) continue;
+        const C cx = t.fx[k], cy = t.fy[k];   // zero test before the widening (exact either way)
+        if (cx == C(0) && cy == C(0)) continue;
         const int j = k / t.w, i = k - j * t.w;
         const int cell = support_row(L, t.y0 + j) * L.nx + wrapi(t.x0 + i, L.nx);
-        atomicAdd(sp.fib + cell, fx);
-        atomicAdd(sp.fib + N + cell, fy);
-        if (atomicExch(&sp.mark[cell], stamp) != stamp) t.cells[atomicAdd(s_count, 1)] = cell;
+        atomicAdd(sp.fib + cell, (double)cx);
+        atomicAdd(sp.fib + N + cell, (double)cy);
+        t.cells[atomicAdd(s_count, 1)] = cell;
     }
     __syncthreads();
     const int nnew = *s_count;
@@ -122,7 +135,7 @@ __device__ __forceinline__ bool interp_at(const Tile<typename St<S>::C>& t, cons
 // Spread c * F with the shape functions m (step 3 / step iii): into the force tile, or
 // straight into the lattice field when the capsule has no tile.
 template <typename C>
-__device__ __forceinline__ bool spread_with(const MlsW<C>& m, Tile<C>& t, const Lat& L, const Spread& sp, int stamp,
+__device__ __forceinline__ bool spread_with(const MlsW<C>& m, Tile<C>& t, const Lat& L, const Spread& sp,
                                             C Fx, C Fy, C c) {
     const long long N = (long long)L.nx * L.ny;
     const bool in_tile = t.holds(m.cx, m.cy);
@@ -141,7 +154,7 @@ __device__ __forceinline__ bool spread_with(const MlsW<C>& m, Tile<C>& t, const 
                 const int cell = support_row(L, m.cy + b - 1) * L.nx + wrapi(m.cx + a - 1, L.nx);
                 atomicAdd(sp.fib + cell, w * (double)Fx);
                 atomicAdd(sp.fib + N + cell, w * (double)Fy);
-                touch(sp, cell, stamp);
+                touch(sp, cell);
             }
         }
     }
@@ -264,7 +277,7 @@ constexpr int dyn_min_blocks() {
 // precision): the support frames at X^n are already stored (by the previous update).
 template <typename S, bool RIGID, bool FRAMED = false>
 __device__ __forceinline__ bool dyn_spread(const S* __restrict__ src, const Lat& L, const Nodes& nd, const CapsuleParams& P, const Arc& a, const CapSmem& sm,
-                                           Tile<typename St<S>::C>& t, const Spread& sp, int stamp) {
+                                           Tile<typename St<S>::C>& t, const Spread& sp) {
     using C = typename St<S>::C;
     constexpr bool F32 = sizeof(C) == 4;   // single precision: lengths and forces in float
     // lengths of the elements on both sides of every own vertex (c_l of reading R4). FRAMED
@@ -294,8 +307,10 @@ __device__ __forceinline__ bool dyn_spread(const S* __restrict__ src, const Lat&
         const int li = kHalo + k, g = P.off + a.v0 + k;
         // shape functions at X^n: used for U, for the spread, and by this step's update
         MlsW<C> w;
-        if constexpr (FRAMED && sizeof(C) == 4) {
-            w = load_mls<C>(L, nd.mls, g);
+        if constexpr (FRAMED && sizeof(C) == 4) {   // the frame the update of this CTA left
+            const int2 fc = frame_c_f(sm)[li];
+            const float2 fd = frame_d_f(sm)[li];
+            w = mls_from_frame<C>(L, MlsFrame{fc.x, fc.y, fd.x, fd.y});
         } else {
             const double2 Xv = sm.X[li];
             w = mls_setup<C>(L, Xv.x, Xv.y);
@@ -309,6 +324,9 @@ __device__ __forceinline__ bool dyn_spread(const S* __restrict__ src, const Lat&
         double2 uv;
         if (RIGID && P.rigid) {
             uv = rigid_velocity(nd.rb[a.cap].body, sm.X[li]);   // the body's motion (Section 2.3.1)
+        } else if (FRAMED && F32) {
+            const float2 u = uv_next_f(sm)[li];   // the update of this CTA left it (float is all F needs)
+            uv = make_double2(u.x, u.y);
         } else {
             uv = nd.uv[g];
             if (!FRAMED && nd.age[g] == 0) {   // a vertex's first step (never a fused one)
@@ -322,11 +340,11 @@ __device__ __forceinline__ bool dyn_spread(const S* __restrict__ src, const Lat&
             const float cl = 0.5f * (len_f(sm)[li - 1] + len_f(sm)[li]);
             const float Fx = (float)uv.x - o.ux, Fy = (float)uv.y - o.uy;
             if (nd.Flc) nd.Flc[g] = make_double2((double)(cl * Fx), (double)(cl * Fy));
-            ok &= spread_with<C>(w, t, L, sp, stamp, Fx, Fy, cl);
+            ok &= spread_with<C>(w, t, L, sp, Fx, Fy, cl);
         } else {
             const double cl = 0.5 * (sm.sst[li - 1] + sm.sst[li]);
             if (nd.Flc) nd.Flc[g] = make_double2(cl * (uv.x - Ux), cl * (uv.y - Uy));
-            ok &= spread_with<C>(w, t, L, sp, stamp, uv.x - Ux, uv.y - Uy, cl);
+            ok &= spread_with<C>(w, t, L, sp, uv.x - Ux, uv.y - Uy, cl);
         }
     }
     return ok;
@@ -347,10 +365,9 @@ __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_force_spread(c
         fill_moments<S>(t, src, L, nullptr);
         zero_forces<C>(t);
     }
-    const int stamp = *sp.stamp + 1;
-    const bool ok = dyn_spread<S, RIGID>(src, L, nd, P, a, sm, t, sp, stamp);
+    const bool ok = dyn_spread<S, RIGID>(src, L, nd, P, a, sm, t, sp);
     __syncthreads();
-    if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
+    if (t.use) flush_forces<C>(t, L, sp, reinterpret_cast<int*>(sm.red));
     if (!ok) atomicOr(status, kStatSupport);
 }
 
@@ -508,7 +525,8 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
             // 1.5 (X^{n+1} - X^n) - 0.5 (X^n - X^{n-1})
             const float ix = xd.x + hm * (Fi.x + Fe.x), iy = xd.y + hm * (Fi.y + Fe.y);
             const double dx = (double)ix, dy = (double)iy;
-            nd.uv[g] = make_double2(1.5 * dx - 0.5 * (Xv.x - Xm.x), 1.5 * dy - 0.5 * (Xv.y - Xm.y));
+            const double2 uvn = make_double2(1.5 * dx - 0.5 * (Xv.x - Xm.x), 1.5 * dy - 0.5 * (Xv.y - Xm.y));
+            nd.uv[g] = uvn;
             nd.Xm1[g] = Xv;
             const double2 Xn = make_double2(Xv.x + dx, Xv.y + dy);
             nd.X[g] = Xn;
@@ -528,6 +546,10 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
                     f.d0x = __int_as_float(0x7fc00000);
                 }
                 reinterpret_cast<MlsFrame*>(nd.mls)[g] = f;
+                // for the spread of the same CTA (only the float velocity enters its force)
+                uv_next_f(sm)[li] = make_float2((float)uvn.x, (float)uvn.y);
+                frame_c_f(sm)[li] = make_int2(f.cx, f.cy);
+                frame_d_f(sm)[li] = make_float2(f.d0x, f.d0y);
                 // the increment for the next step's element lengths (the slot's tentative
                 // velocity is dead by now). The last forces are not stored: a fused update
                 // never ends a call, and the update that does stores them.
@@ -618,10 +640,9 @@ __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_update_spread(
         for (int li = threadIdx.x; li < a.m + 2 * kHalo; li += blockDim.x) sm.X[li] = nd.X[P.off + a.node(li)];
     }
     __syncthreads();
-    const int stamp = *sp.stamp + 1;
-    ok &= dyn_spread<S, false, true>(dst, L, nd, P, a, sm, t, sp, stamp);
+    ok &= dyn_spread<S, false, true>(dst, L, nd, P, a, sm, t, sp);
     __syncthreads();
-    if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
+    if (t.use) flush_forces<C>(t, L, sp, reinterpret_cast<int*>(sm.red));
     if (!ok) atomicOr(status, kStatSupport);
 }
 
@@ -725,7 +746,6 @@ __global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int m
     block_reduce<1, false>(area2, sm.red);  // also orders the tile zeroing before the spread
     if (m == a.n) copy_halo_terms(sm, m, false);
     const double A = 0.5 * cluster_total(area2[0], arcs);
-    const int stamp = *sp.stamp + 1;
     bool ok = true;
     for (int k = threadIdx.x; k < m; k += blockDim.x) {
         const int li = kHalo + k, g = P.off + a.v0 + k;
@@ -735,10 +755,10 @@ __global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int m
         nd.Fext[g] = make_double2(0.0, 0.0);
         const MlsW<C> w = mls_setup<C>(L, sm.X[li].x, sm.X[li].y);
         store_mls<C>(nd.mls, g, w);
-        ok &= spread_with<C>(w, t, L, sp, stamp, F.x + Fp.x, F.y + Fp.y, 1.0);
+        ok &= spread_with<C>(w, t, L, sp, F.x + Fp.x, F.y + Fp.y, 1.0);
     }
     __syncthreads();
-    if (t.use) flush_forces<C>(t, L, sp, stamp, reinterpret_cast<int*>(sm.red));
+    if (t.use) flush_forces<C>(t, L, sp, reinterpret_cast<int*>(sm.red));
     if (!ok) atomicOr(status, kStatSupport);
 }
 

@@ -401,8 +401,9 @@ __global__ void __launch_bounds__(128) k_ragged_h(const __half* __restrict__ src
 
 // Forced-node patch: redo the collision of every node in the current touched-cell list
 // with the total force g + f_ib (Eq. 4-5), reading the same input as k_collide_stream.
-// Also clears the previous force buffer at the previous list (its last reader has run)
-// and advances the touched-cell stamp.
+// Also clears the previous force buffer at the previous list (its last reader has run).
+// A node listed more than once (covered by several capsules' tiles) is redone and
+// cleared each time, with the same values.
 template <typename S>
 __global__ void __launch_bounds__(256) k_patch(const S* __restrict__ src, S* __restrict__ dst, Lat L,
                                                const double* __restrict__ fib_c, const int* __restrict__ list_c,
@@ -461,7 +462,6 @@ __global__ void __launch_bounds__(256) k_patch(const S* __restrict__ src, S* __r
         fib_p[cell] = 0.0;
         fib_p[N + cell] = 0.0;
     }
-    if (t0 == 0) ctr->step_stamp += 1;
 }
 
 // Start-up: post-collision populations whose pull gives the Eq. 2 equilibrium of the

@@ -455,18 +455,23 @@ __device__ __forceinline__ void store_mls(void* base, long long g, const MlsW<C>
     }
 }
 
+// The single-precision shape functions rebuilt from a stored frame.
+template <typename C>
+__device__ __forceinline__ MlsW<C> mls_from_frame(const Lat& L, const MlsFrame& f) {
+    const bool sane = !isnan(f.d0x);
+    const int cx = sane ? f.cx : 0, cy = sane ? f.cy : 0;
+    MlsW<C> m = mls_weights<C>(cx, cy, sane ? C(f.d0x) : C(0), sane ? C(f.d0y) : C(0),
+                               sane && support_inside(L, cx, cy));
+    m.sane = sane;
+    return m;
+}
+
 template <typename C>
 __device__ __forceinline__ MlsW<C> load_mls(const Lat& L, const void* base, long long g) {
     if constexpr (sizeof(C) == 8) {
         return reinterpret_cast<const MlsW<C>*>(base)[g];
     } else {
-        const MlsFrame f = reinterpret_cast<const MlsFrame*>(base)[g];
-        const bool sane = !isnan(f.d0x);
-        const int cx = sane ? f.cx : 0, cy = sane ? f.cy : 0;
-        MlsW<C> m = mls_weights<C>(cx, cy, sane ? C(f.d0x) : C(0), sane ? C(f.d0y) : C(0),
-                                   sane && support_inside(L, cx, cy));
-        m.sane = sane;
-        return m;
+        return mls_from_frame<C>(L, reinterpret_cast<const MlsFrame*>(base)[g]);
     }
 }
 
@@ -582,12 +587,13 @@ __device__ __forceinline__ Mom<typename St<S>::C> node_moments(const S* __restri
     const C inv = C(1) / (C(1) + drho);
     Mom<C> m;
     m.drho = drho;
+    const C gx = lat_c<C>(L.gx, L.gxf), gy = lat_c<C>(L.gy, L.gyf);   // C(g), rounded once on the host
     if (fib) {   // Eq. 7 with half of the uniform force and of the last spread force
-        m.ux = (mx + C(0.5) * (C(L.gx) + C(fib[n]))) * inv;
-        m.uy = (my + C(0.5) * (C(L.gy) + C(fib[N + n]))) * inv;
+        m.ux = (mx + C(0.5) * (gx + C(fib[n]))) * inv;
+        m.uy = (my + C(0.5) * (gy + C(fib[N + n]))) * inv;
     } else {     // before any IB force (the Dynamic scheme's interpolations)
-        m.ux = (mx + C(0.5) * C(L.gx)) * inv;
-        m.uy = (my + C(0.5) * C(L.gy)) * inv;
+        m.ux = (mx + C(0.5) * gx) * inv;
+        m.uy = (my + C(0.5) * gy) * inv;
     }
     return m;
 }
@@ -660,8 +666,7 @@ enum : unsigned {
 struct DevCounters {
     int count[2];          // touched-cell list lengths (force buffers 0 and 1)
     unsigned status;       // sticky status bits
-    int step_stamp;        // incremented once per coupled step (touched-cell stamps)
-    int pad[4];
+    int pad[5];
 };
 
 // Per-capsule parameters (device and host mirror).

@@ -55,10 +55,8 @@ constexpr int kRepSlots = 16;
 // Touched-cell bookkeeping for the spread of one step.
 struct Spread {
     double* fib;     // force buffer written this step (fx[N] then fy[N])
-    int* mark;       // per-cell stamp of the last step that touched it
     int* list;       // unique touched cells of this step
     int* count;      // length of list
-    const int* stamp;  // stamp source (DevCounters::step_stamp, + 1 is this step's stamp)
     int capacity;    // entries the list can hold
     unsigned* status;
 };

@@ -192,6 +192,17 @@ __device__ __forceinline__ float2* xd_f(const CapSmem& sm) { return reinterpret_
 __device__ __forceinline__ float* len_f(const CapSmem& sm) { return reinterpret_cast<float*>(sm.sst); }
 // the Dynamic scheme's per-vertex U as float in single precision (the first half of its slots)
 __device__ __forceinline__ float2* u_f(const Nodes& nd) { return reinterpret_cast<float2*>(nd.U); }
+// What the fused single-precision update hands to the next step's spread in the same CTA
+// (so that the spread reloads nothing from global memory): the new vertex velocity in
+// float in the double slots of sm.bs, which the float terms leave unused, and the new
+// support frame split over the unused second halves of the ext and xd arrays.
+__device__ __forceinline__ float2* uv_next_f(const CapSmem& sm) { return reinterpret_cast<float2*>(sm.bs); }
+__device__ __forceinline__ int2* frame_c_f(const CapSmem& sm) {
+    return reinterpret_cast<int2*>(sm.ext) + (sm.xd - sm.ext);
+}
+__device__ __forceinline__ float2* frame_d_f(const CapSmem& sm) {
+    return reinterpret_cast<float2*>(sm.xd) + (sm.bdl - sm.xd);
+}
 
 // vertex_terms in single precision (the same Eq. 11 and Eq. 13 terms).
 __device__ __forceinline__ void vertex_terms_f(const CapSmem& sm, const CapsuleParams& P, const Nodes& nd, int vl,
