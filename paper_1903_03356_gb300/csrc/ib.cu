@@ -264,6 +264,22 @@ constexpr int dyn_min_blocks() {
     return sizeof(typename St<S>::C) == 4 ? 6 : 1;
 }
 
+// An odd step coprime to m, about a quarter of m (1 for short arcs): j -> j * hop mod m
+// visits every vertex once and puts consecutive j far apart on the ring.
+__device__ __forceinline__ int ring_hop(int m) {
+    if (m < 64) return 1;
+    for (int h = (m / 4) | 1; h < m / 2; h += 2) {
+        int a = h, b = m;
+        while (b) {
+            const int r = a % b;
+            a = b;
+            b = r;
+        }
+        if (a == 1) return h;
+    }
+    return 1;
+}
+
 // ---------------------------------------------------------------------------------
 // Dynamic IB (Section 2.3.2), steps 1-3: U = I(u^n) of the populations before any IB
 // force (rho u = sum f e + g/2; the step's IB force is the unknown of the direct forcing),
@@ -303,7 +319,12 @@ __device__ __forceinline__ bool dyn_spread(const S* __restrict__ src, const Lat&
     }
     __syncthreads();
     bool ok = true;
-    for (int k = threadIdx.x; k < a.m; k += blockDim.x) {
+    // the lanes of a warp take vertices `hop` apart on the ring (a bijection of 0..m-1):
+    // their 3x3 supports then rarely share a tile cell, and the shared-memory atomics of
+    // the spread rarely collide within an instruction
+    const int hop = ring_hop(a.m);
+    for (int j = threadIdx.x; j < a.m; j += blockDim.x) {
+        const int k = (int)((long long)j * hop % a.m);
         const int li = kHalo + k, g = P.off + a.v0 + k;
         // shape functions at X^n: used for U, for the spread, and by this step's update
         MlsW<C> w;
