@@ -32,6 +32,10 @@ namespace lbmib {
 
 size_t capsule_smem_bytes(int max_n) { return ring_smem_bytes(max_n); }
 
+// Reduction scratch of the 128-thread capsule kernels (4 warps x 8 doubles): smaller
+// scratch lets seven CTAs share a multiprocessor's shared memory.
+constexpr int kRedIB = 4 * 8;
+
 // Fill the moment tile from the populations (nine pulls per node, row by row), two
 // nodes per thread and pass with both nodes' pulls issued before either is reduced: the
 // fill waits on memory latency, and this halves its round trips.
@@ -261,7 +265,7 @@ __device__ __forceinline__ void copy_halo_terms(const CapSmem& sm, int m, bool e
 // that pipe fed), the register file's own limit in double, which would spill at 6.
 template <typename S>
 constexpr int dyn_min_blocks() {
-    return sizeof(typename St<S>::C) == 4 ? 6 : 1;
+    return sizeof(typename St<S>::C) == 4 ? 7 : 1;
 }
 
 // An odd step coprime to m, about a quarter of m (1 for short arcs): j -> j * hop mod m
@@ -377,7 +381,7 @@ __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_force_spread(c
                                                           int arcs, int tile_cells, Spread sp, unsigned* status) {
     using C = typename St<S>::C;
     extern __shared__ __align__(16) unsigned char smem[];
-    const CapSmem sm = carve(smem, arc_slots(max_n, arcs));
+    const CapSmem sm = carve(smem, arc_slots(max_n, arcs), kRedIB);
     CapsuleParams P;
     Arc a;
     if (!load_arc(nd, sm, max_n, arcs, true, P, a, status)) return;
@@ -609,7 +613,7 @@ __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_update(const S
                                                     int tile_cells, int* reset_count, unsigned* status) {
     using C = typename St<S>::C;
     extern __shared__ __align__(16) unsigned char smem[];
-    const CapSmem sm = carve(smem, arc_slots(max_n, arcs));
+    const CapSmem sm = carve(smem, arc_slots(max_n, arcs), kRedIB);
     if (blockIdx.x == 0 && threadIdx.x == 0 && reset_count) *reset_count = 0;
     CapsuleParams P;
     Arc a;
@@ -639,7 +643,7 @@ __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_dyn_update_spread(
                                                                 unsigned* status) {
     using C = typename St<S>::C;
     extern __shared__ __align__(16) unsigned char smem[];
-    const CapSmem sm = carve(smem, arc_slots(max_n, 1));
+    const CapSmem sm = carve(smem, arc_slots(max_n, 1), kRedIB);
     CapsuleParams P;
     Arc a;
     if (!load_arc(nd, sm, max_n, 1, true, P, a, status)) return;
@@ -677,7 +681,7 @@ __global__ void __launch_bounds__(128) k_rigid_update(const S* __restrict__ dst,
                                                       int tile_cells, unsigned* status) {
     using C = typename St<S>::C;
     extern __shared__ __align__(16) unsigned char smem[];
-    const CapSmem sm = carve(smem, arc_slots(max_n, arcs));
+    const CapSmem sm = carve(smem, arc_slots(max_n, arcs), kRedIB);
     CapsuleParams P;
     Arc a;
     if (!load_arc(nd, sm, max_n, arcs, true, P, a, status)) return;
@@ -749,7 +753,7 @@ template <typename C>
 __global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int max_n, int arcs, int tile_cells,
                                                           Spread sp, unsigned* status) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const CapSmem sm = carve(smem, arc_slots(max_n, arcs));
+    const CapSmem sm = carve(smem, arc_slots(max_n, arcs), kRedIB);
     CapsuleParams P;
     Arc a;
     if (!load_arc(nd, sm, max_n, arcs, true, P, a, status)) return;
@@ -792,7 +796,7 @@ __global__ void __launch_bounds__(128) k_kin_advance(const S* __restrict__ dst, 
                                                      int tile_cells, int* reset_count, unsigned* status) {
     using C = typename St<S>::C;
     extern __shared__ __align__(16) unsigned char smem[];
-    const CapSmem sm = carve(smem, arc_slots(max_n, arcs));
+    const CapSmem sm = carve(smem, arc_slots(max_n, arcs), kRedIB);
     if (blockIdx.x == 0 && threadIdx.x == 0 && reset_count) *reset_count = 0;
     CapsuleParams P;
     Arc a;
@@ -904,7 +908,7 @@ static size_t tile_bytes(int cells, bool moments, bool forces) {
 
 template <typename C>
 static size_t smem_bytes(int slots, int cells, bool moments, bool forces) {
-    return ring_smem_bytes(slots) + tile_bytes<C>(cells, moments, forces);
+    return ring_smem_bytes(slots, kRedIB) + tile_bytes<C>(cells, moments, forces);
 }
 
 int tile_budget(int slots, double extent, bool tight) {
@@ -913,7 +917,7 @@ int tile_budget(int slots, double extent, bool tight) {
     const double side = extent + 8.0;
     long long cells = (long long)((tight ? 1.0 : 1.5) * side * side);
     if (cells < 256) cells = 256;
-    const size_t free_b = kSmemLimit - ring_smem_bytes(slots);
+    const size_t free_b = kSmemLimit - ring_smem_bytes(slots, kRedIB);
     const long long cap = (long long)(free_b / (3 * sizeof(double) + 2 * sizeof(double)));
     if (cells > cap) cells = cap;
     return (int)cells;

@@ -16,15 +16,17 @@ struct CapSmem {
     double* bs;     // k_b sin(theta_v - theta_v0) at vertex v            (Eq. 13)
     double2* bdl;   // d(theta_v)/dX_{v-1}
     double2* bdr;   // d(theta_v)/dX_{v+1}
-    double* red;    // reduction scratch (32 * 8 doubles)
+    double* red;    // reduction scratch (8 doubles per warp of the block)
     unsigned char* tile;  // moment / force tile
 };
 
-inline size_t ring_smem_bytes(int max_n) {
-    return (size_t)max_n * (5 * sizeof(double2) + 2 * sizeof(double)) + 32 * 8 * sizeof(double);
+// red_doubles: the reduction scratch, 8 doubles per warp of the launch (the default
+// covers blocks of up to 1024 threads)
+inline size_t ring_smem_bytes(int max_n, int red_doubles = 32 * 8) {
+    return (size_t)max_n * (5 * sizeof(double2) + 2 * sizeof(double)) + (size_t)red_doubles * sizeof(double);
 }
 
-__device__ __forceinline__ CapSmem carve(unsigned char* base, int max_n) {
+__device__ __forceinline__ CapSmem carve(unsigned char* base, int max_n, int red_doubles = 32 * 8) {
     CapSmem s;
     s.X = reinterpret_cast<double2*>(base);
     s.ext = s.X + max_n;
@@ -34,13 +36,13 @@ __device__ __forceinline__ CapSmem carve(unsigned char* base, int max_n) {
     s.sst = reinterpret_cast<double*>(s.bdr + max_n);
     s.bs = s.sst + max_n;
     s.red = s.bs + max_n;
-    s.tile = reinterpret_cast<unsigned char*>(s.red + 32 * 8);
+    s.tile = reinterpret_cast<unsigned char*>(s.red + red_doubles);
     return s;
 }
 
 // Reduction of K doubles or floats over the block (blockDim.x a multiple of 32, <= 1024);
 // MIN selects minimum instead of sum. Every thread receives the results. `red_` is the
-// block's double scratch (32 * 8 doubles).
+// block's double scratch (8 doubles per warp).
 template <int K, bool MIN, typename T>
 __device__ void block_reduce(T (&v)[K], double* red_) {
     T* red = reinterpret_cast<T*>(red_);
