@@ -265,7 +265,7 @@ __device__ __forceinline__ void copy_halo_terms(const CapSmem& sm, int m, bool e
 // that pipe fed), the register file's own limit in double, which would spill at 6.
 template <typename S>
 constexpr int dyn_min_blocks() {
-    return sizeof(typename St<S>::C) == 4 ? 7 : 1;
+    return sizeof(typename St<S>::C) == 4 ? 8 : 1;
 }
 
 // An odd step coprime to m, about a quarter of m (1 for short arcs): j -> j * hop mod m
@@ -915,7 +915,7 @@ int tile_budget(int slots, double extent, bool tight) {
     // a square of side `extent` plus the probes and supports (3 nodes each side); for a
     // whole ring 1.5 x that, room for any rotation and for deformation
     const double side = extent + 8.0;
-    long long cells = (long long)((tight ? 1.0 : 1.5) * side * side);
+    long long cells = (long long)((tight ? 1.0 : 1.15) * side * side);
     if (cells < 256) cells = 256;
     const size_t free_b = kSmemLimit - ring_smem_bytes(slots, kRedIB);
     const long long cap = (long long)(free_b / (3 * sizeof(double) + 2 * sizeof(double)));
