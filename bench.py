@@ -812,21 +812,34 @@ def e2e_run(a, case, L, scheme, dev):
     ncap = len(case.capsules)
     obs = torch.empty((max(ncap, 1), 8), dtype=torch.float64).pin_memory()
     ctx = L.from_case(case, storage=a.storage)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    L.lbmib_init_fields(ctx.h, *[p.numpy() for p in pin])
-    L.lbmib_step(ctx.h, a.steps, scheme)
-    L.lbmib_read_fields(ctx.h, *[o.numpy() for o in out])
-    if ncap:
-        L.lbmib_observables_all(ctx.h, obs.numpy())
-    L.lbmib_sync(ctx.h)
-    dt = time.perf_counter() - t0
+
+    def once():
+        torch.cuda.synchronize()
+        t = [time.perf_counter()]
+        L.lbmib_init_fields(ctx.h, *[p.numpy() for p in pin])
+        t.append(time.perf_counter())
+        L.lbmib_step(ctx.h, a.steps, scheme)
+        L.lbmib_sync(ctx.h)
+        t.append(time.perf_counter())
+        L.lbmib_read_fields(ctx.h, *[o.numpy() for o in out])
+        if ncap:
+            L.lbmib_observables_all(ctx.h, obs.numpy())
+        L.lbmib_sync(ctx.h)
+        t.append(time.perf_counter())
+        return t
+
+    once()   # untimed pass: the step graphs are captured on the first call of a context
+    t = once()
+    dt = t[-1] - t[0]
     ctx.close()
     h2d = 3 * N * 8
     d2h = 3 * N * 8 + 8 * 8 * ncap
     return {"value": N * a.steps / dt / 1e6, "unit": "MLUPS",
             "h2d_bytes_per_step": h2d / a.steps, "d2h_bytes_per_step": d2h / a.steps,
-            "note": "init_fields + step + read_fields + observables_all, host-pinned buffers"}
+            "ms": {"init_fields": 1e3 * (t[1] - t[0]), "steps": 1e3 * (t[2] - t[1]),
+                   "read_back": 1e3 * (t[3] - t[2])},
+            "note": ("init_fields + step + read_fields + observables_all, host-pinned buffers; the "
+                     "second of two passes on one context (the first captures the step graphs)")}
 
 
 def main():
