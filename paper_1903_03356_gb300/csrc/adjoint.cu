@@ -1184,9 +1184,10 @@ lbmib_status ckpt_load(lbmib_ctx* c, const char* src, const AdjLayout& a, cudaSt
     LBMIB_CUDA(c, cudaMemcpyAsync(c->fib[0], p, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     LBMIB_CUDA(c, cudaMemsetAsync(c->fib[1], 0, 2 * N * sizeof(double), s));
     p += up(2 * N * sizeof(double), kAlign);
-    // list counts restart; the sticky status word is kept (a reverse sweep may run beside
-    // this load and flag into it)
+    // list counts and claim stamps restart; the sticky status word is kept (a reverse
+    // sweep may run beside this load and flag into it)
     LBMIB_CUDA(c, cudaMemsetAsync(&c->ctr->count[0], 0, 2 * sizeof(int), s));
+    LBMIB_CUDA(c, cudaMemsetAsync(&c->ctr->step_stamp, 0, 2 * sizeof(int), s));
     LBMIB_CUDA(c, cudaMemcpyAsync(&c->ctr->count[0], p, sizeof(int), cudaMemcpyDeviceToDevice, s));
     LBMIB_CUDA(c, cudaMemcpyAsync(c->list[0], p + 16, 9 * M * sizeof(int), cudaMemcpyDeviceToDevice, s));
     p += up(9 * M * sizeof(int) + 16, kAlign);
@@ -1196,6 +1197,7 @@ lbmib_status ckpt_load(lbmib_ctx* c, const char* src, const AdjLayout& a, cudaSt
         p += up(M * sizeof(double2), kAlign);
     }
     LBMIB_CUDA(c, cudaMemcpyAsync(c->nd.age, p, M * sizeof(int), cudaMemcpyDeviceToDevice, s));
+    LBMIB_CUDA(c, cudaMemsetAsync(c->mark, 0, N * sizeof(int), s));
     return LBMIB_OK;
 }
 

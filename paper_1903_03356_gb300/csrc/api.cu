@@ -44,6 +44,7 @@ Layout make_layout(const lbmib_config* c) {
     L.pops[1] = take(9 * (size_t)L.plane * s);
     L.fib[0] = take(2 * N * sizeof(double));
     L.fib[1] = take(2 * N * sizeof(double));
+    L.mark = take(N * sizeof(int));
     L.list[0] = take(9 * M * sizeof(int));
     L.list[1] = take(9 * M * sizeof(int));
     L.ctr = take(sizeof(DevCounters));
@@ -216,11 +217,14 @@ bool enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
         const int cap = list_cap;
         if (ov) cudaStreamWaitEvent(s_lat, c->ev_spread, 0);
         if (st == LBMIB_FP64)
-            launch_patch<double>(src, dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->ctr, fc, cap, s_lat);
+            launch_patch<double>(dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->mark, c->ctr, fc, cap,
+                                   s_lat);
         else if (st == LBMIB_FP32)
-            launch_patch<float>(src, dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->ctr, fc, cap, s_lat);
+            launch_patch<float>(dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->mark, c->ctr, fc, cap,
+                                   s_lat);
         else
-            launch_patch<__half>(src, dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->ctr, fc, cap, s_lat);
+            launch_patch<__half>(dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->mark, c->ctr, fc, cap,
+                                   s_lat);
         if (ov) {
             cudaEventRecord(c->ev_patch, s_lat);
             cudaStreamWaitEvent(s, c->ev_patch, 0);
@@ -401,6 +405,7 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     c->pops[1] = a + lay.pops[1];
     c->fib[0] = (double*)(a + lay.fib[0]);
     c->fib[1] = (double*)(a + lay.fib[1]);
+    c->mark = (int*)(a + lay.mark);
     c->list[0] = (int*)(a + lay.list[0]);
     c->list[1] = (int*)(a + lay.list[1]);
     c->ctr = (DevCounters*)(a + lay.ctr);
@@ -472,6 +477,7 @@ lbmib_status lbmib_create(const lbmib_config* cfg, void* d_arena, size_t arena_b
     const size_t N = (size_t)cfg->nx * cfg->ny;
     e = cudaMemsetAsync(c->fib[0], 0, 2 * N * sizeof(double), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->fib[1], 0, 2 * N * sizeof(double), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->mark, 0, N * sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), c->stream);
     if (e != cudaSuccess) {
         lbmib_destroy(c);
@@ -963,6 +969,8 @@ lbmib_status lbmib_load_state(lbmib_ctx* c, const void* buf, size_t bytes) {
     LBMIB_CUDA(c, cudaMemcpy(c->nd.age, p, M * sizeof(int), cudaMemcpyHostToDevice));
     p += M * sizeof(int);
     LBMIB_CUDA(c, cudaMemcpy(c->nd.rb, p, c->caps.size() * sizeof(RigidBody), cudaMemcpyHostToDevice));
+    // fresh claims: no node carries a stamp that a coming patch will use
+    LBMIB_CUDA(c, cudaMemset(c->mark, 0, N * sizeof(int)));
     DevCounters ctr{};
     ctr.count[0] = h.count;
     LBMIB_CUDA(c, cudaMemcpy(c->ctr, &ctr, sizeof(ctr), cudaMemcpyHostToDevice));

@@ -20,7 +20,7 @@ inline size_t storage_bytes(lbmib_storage s) { return s == LBMIB_FP64 ? 8 : (s =
 
 // Offsets of the context's buffers inside the caller's arena.
 struct Layout {
-    size_t pops[2], fib[2], list[2], ctr, scratch;
+    size_t pops[2], fib[2], mark, list[2], ctr, scratch;
     size_t X, Xm1, uv, Fint, Fext, U, L0, c0, s0, age, capid, mls, caps, obs, pts, pts_out;
     size_t Fpp, rep_box, rep_cellof, rep_count, rep_slot, u_in, rb, R0;
     int rep_buckets;
@@ -54,6 +54,7 @@ struct lbmib_ctx {
     char* arena = nullptr;
     void* pops[2]{};
     double* fib[2]{};
+    int* mark = nullptr;   // per node: the claim stamp of the last patch that forced it
     int* list[2]{};
     lbmib::DevCounters* ctr = nullptr;
     double* scratch = nullptr;

@@ -399,20 +399,25 @@ __global__ void __launch_bounds__(128) k_ragged_h(const __half* __restrict__ src
     if (ragged_chunk_h(src, dst, L, L.nx / 8 * 8, y, L.gxf, L.gyf, L.omegaf)) atomicOr(status, kStatUnstable);
 }
 
-// Forced-node patch: redo the collision of every node in the current touched-cell list
-// with the total force g + f_ib (Eq. 4-5), reading the same input as k_collide_stream.
-// Also clears the previous force buffer at the previous list (its last reader has run).
-// A node listed more than once (covered by several capsules' tiles) is redone and
-// cleared each time, with the same values.
+// Forced-node patch: the nodes of the current touched-cell list collide with the total
+// force g + f_ib (Eq. 4-5) instead of g. The lattice update has just written their
+// unforced post-collision populations in place, and those determine the forced ones
+// (force_node: the mass and momentum of the unforced collision give rho and u), so the
+// patch reads and writes each node's own nine slots and nothing else of the lattice. A
+// node that several capsules' tiles cover is listed more than once: the first thread to
+// claim it (an atomic exchange of this launch's stamp, issued with the loads) patches it,
+// the others leave it. The last block to finish advances the stamp. Also clears the
+// previous force buffer at the previous list (its last reader has run).
 template <typename S>
-__global__ void __launch_bounds__(256) k_patch(const S* __restrict__ src, S* __restrict__ dst, Lat L,
-                                               const double* __restrict__ fib_c, const int* __restrict__ list_c,
-                                               double* __restrict__ fib_p, const int* __restrict__ list_p,
+__global__ void __launch_bounds__(256) k_patch(S* __restrict__ dst, Lat L, const double* __restrict__ fib_c,
+                                               const int* __restrict__ list_c, double* __restrict__ fib_p,
+                                               const int* __restrict__ list_p, int* __restrict__ mark,
                                                DevCounters* ctr, int c, int capacity) {
     using C = typename St<S>::C;
     const long long N = (long long)L.nx * L.ny;
     int nc = ctr->count[c];
     int np = ctr->count[1 - c];
+    const int stamp = ctr->step_stamp + 1;
     const int stride = gridDim.x * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
     if (nc > capacity || np > capacity) {
@@ -420,9 +425,9 @@ __global__ void __launch_bounds__(256) k_patch(const S* __restrict__ src, S* __r
         nc = nc > capacity ? capacity : nc;
         np = np > capacity ? capacity : np;
     }
-    // two list entries per thread and pass, all their pulls issued before either is
-    // collided: twice the loads in flight of one node per thread (the kernel waits on
-    // memory latency, not bandwidth)
+    const C gx = lat_c<C>(L.gx, L.gxf), gy = lat_c<C>(L.gy, L.gyf), om = lat_c<C>(L.omega, L.omegaf);
+    // two list entries per thread and pass, all their loads and claims issued before
+    // either is used (the kernel waits on memory latency, not bandwidth)
     for (int k = t0; k < nc; k += 2 * stride) {
         int cell[2] = {list_c[k], k + stride < nc ? list_c[k + stride] : -1};
         bool use[2];
@@ -432,25 +437,27 @@ __global__ void __launch_bounds__(256) k_patch(const S* __restrict__ src, S* __r
             if (!use[q] && (q == 0 || k + stride < nc)) atomicOr(&ctr->status, kStatCell);
             if (!use[q]) cell[q] = 0;
         }
-        int y[2], x[2];
+        long long at[2];
         C s[2][9];
         double fx[2], fy[2];
+        int old[2];
 #pragma unroll
         for (int q = 0; q < 2; q++) {
-            y[q] = cell[q] / L.nx;
-            x[q] = cell[q] - y[q] * L.nx;
-            pull_all<S>(src, L, x[q], y[q], s[q]);
+            const int y = cell[q] / L.nx;
+            at[q] = (long long)y * L.pitch + (cell[q] - y * L.nx);
+            old[q] = use[q] ? atomicExch(mark + cell[q], stamp) : stamp;
+#pragma unroll
+            for (int i = 0; i < 9; i++) s[q][i] = St<S>::ld(dst + (long long)i * L.plane + at[q], L);
             fx[q] = fib_c[cell[q]];
             fy[q] = fib_c[N + cell[q]];
         }
 #pragma unroll
         for (int q = 0; q < 2; q++) {
-            if (!use[q]) continue;
-            const C usq = collide<C>(s[q], C(L.gx + fx[q]), C(L.gy + fy[q]), C(L.omega));
+            if (!use[q] || old[q] == stamp) continue;   // not a cell, or claimed by another entry
+            const C usq = force_node<C>(s[q], gx, gy, C(L.gx + fx[q]), C(L.gy + fy[q]), om);
             if (!(usq < C(0.09))) atomicOr(&ctr->status, kStatUnstable);
 #pragma unroll
-            for (int i = 0; i < 9; i++)
-                St<S>::st(dst + (long long)i * L.plane + (long long)y[q] * L.pitch + x[q], s[q][i], L);
+            for (int i = 0; i < 9; i++) St<S>::st(dst + (long long)i * L.plane + at[q], s[q][i], L);
         }
     }
     for (int k = t0; k < np; k += stride) {
@@ -461,6 +468,15 @@ __global__ void __launch_bounds__(256) k_patch(const S* __restrict__ src, S* __r
         }
         fib_p[cell] = 0.0;
         fib_p[N + cell] = 0.0;
+    }
+    // the stamp stays fixed until every block has read it: the last block advances it
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctr->patch_blocks, 1) == (int)gridDim.x - 1) {
+            ctr->patch_blocks = 0;
+            ctr->step_stamp = stamp;
+        }
     }
 }
 
@@ -621,14 +637,14 @@ void launch_collide_stream(const void* src, void* dst, const Lat& L, unsigned* s
 }
 
 template <typename S>
-void launch_patch(const void* src, void* dst, const Lat& L, const double* fib_c, const int* list_c,
-                  double* fib_p, const int* list_p, DevCounters* ctr, int c, int capacity, cudaStream_t s) {
+void launch_patch(void* dst, const Lat& L, const double* fib_c, const int* list_c, double* fib_p,
+                  const int* list_p, int* mark, DevCounters* ctr, int c, int capacity, cudaStream_t s) {
     // a grid-stride loop over the touched list, whose length only the device knows, two
     // entries per thread and pass: up to 6144 blocks of 256, one pass for the 2.9e6
     // touched nodes of the 16384 x 8192 benchmark
     int grid = (int)blocks_for(capacity > 0 ? (capacity + 1) / 2 : 1, 256);
     if (grid > 6144) grid = 6144;
-    k_patch<S><<<grid, 256, 0, s>>>((const S*)src, (S*)dst, L, fib_c, list_c, fib_p, list_p, ctr, c, capacity);
+    k_patch<S><<<grid, 256, 0, s>>>((S*)dst, L, fib_c, list_c, fib_p, list_p, mark, ctr, c, capacity);
 }
 
 template <typename S>
@@ -655,8 +671,8 @@ void launch_populations(const void* src, const Lat& L, const OpenBC& ob, int i0,
 
 #define LBMIB_INSTANTIATE_LATTICE(S)                                                                  \
     template void launch_collide_stream<S>(const void*, void*, const Lat&, unsigned*, int, cudaStream_t); \
-    template void launch_patch<S>(const void*, void*, const Lat&, const double*, const int*, double*, \
-                                  const int*, DevCounters*, int, int, cudaStream_t);                  \
+    template void launch_patch<S>(void*, const Lat&, const double*, const int*, double*, const int*,   \
+                                  int*, DevCounters*, int, int, cudaStream_t);                        \
     template void launch_open_columns<S>(const void*, void*, const Lat&, const OpenBC&, unsigned*,     \
                                          cudaStream_t);                                               \
     template void launch_init<S>(void*, const Lat&, const double*, const double*, const double*,      \

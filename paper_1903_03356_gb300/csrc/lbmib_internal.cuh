@@ -284,6 +284,46 @@ __device__ __forceinline__ C collide(C s[9], C Fx, C Fy, C omega) {
     return usq;
 }
 
+// The forced post-collision populations of a node from its unforced ones (in place).
+// collide() is keep * s + E(drho, u, F), where only E, the equilibrium and Guo parts,
+// depends on the force, and the unforced collision kept the mass and added g to the
+// momentum: so drho = sum s* and m = sum s* e - g, and the force g + f_ib gives
+// s* + E(drho, u', F) - E(drho, u, g), u = (m + g/2)/rho, u' = (m + F/2)/rho, with
+// rounding apart the populations collide() gives for F. (gx, gy) is the uniform force the
+// unforced collision used, (Fx, Fy) the total. Returns u'^2 for the stability check.
+template <typename C>
+__device__ __forceinline__ C force_node(C s[9], C gx, C gy, C Fx, C Fy, C omega) {
+    C drho, px, py;
+    moments<C>(s, drho, px, py);
+    const C mx = px - gx, my = py - gy;
+    const C rho = C(1) + drho;
+    const C inv = C(1) / rho;
+    const C ux0 = (mx + C(0.5) * gx) * inv, uy0 = (my + C(0.5) * gy) * inv;
+    const C ux = (mx + C(0.5) * Fx) * inv, uy = (my + C(0.5) * Fy) * inv;
+    const C usq0 = ux0 * ux0 + uy0 * uy0, usq = ux * ux + uy * uy;
+    const C fpre = C(1) - C(0.5) * omega;
+    const C uF30 = C(3) * (ux0 * gx + uy0 * gy), uF3 = C(3) * (ux * Fx + uy * Fy);
+    s[0] += wgt<C>(0) * (omega * rho * (C(1.5) * (usq0 - usq)) - fpre * (uF3 - uF30));
+#pragma unroll
+    for (int i : {1, 2, 5, 6}) {
+        const int j = opp(i);
+        const C eu0 = C(ex(i)) * ux0 + C(ey(i)) * uy0, eu = C(ex(i)) * ux + C(ey(i)) * uy;
+        const C eg = C(ex(i)) * gx + C(ey(i)) * gy, eF = C(ex(i)) * Fx + C(ey(i)) * Fy;
+        const C w = wgt<C>(i);
+        const C even = w * (omega * rho * (C(4.5) * (eu * eu - eu0 * eu0) - C(1.5) * (usq - usq0)) +
+                            fpre * ((C(9) * eu * eF - uF3) - (C(9) * eu0 * eg - uF30)));
+        const C odd = C(3) * w * (omega * rho * (eu - eu0) + fpre * (eF - eg));
+        s[i] += even + odd;
+        s[j] += even - odd;
+    }
+    if constexpr (sizeof(C) < 8) {   // the conservation reset of collide()
+        s[1] = s[3] + ((mx + Fx) - ((s[5] - s[6]) + (s[8] - s[7])));
+        s[2] = s[4] + ((my + Fy) - ((s[5] + s[6]) - (s[7] + s[8])));
+        s[0] = drho - (((s[1] + s[2]) + (s[3] + s[4])) + ((s[5] + s[6]) + (s[7] + s[8])));
+    }
+    return usq;
+}
+
 // Two single-precision lanes in one instruction (packed FP32 add, sub, mul and fma of
 // sm_100 and later): the single-precision lattice kernels update lattice nodes in pairs.
 // Each lane rounds as the scalar instruction would.
@@ -666,7 +706,9 @@ enum : unsigned {
 struct DevCounters {
     int count[2];          // touched-cell list lengths (force buffers 0 and 1)
     unsigned status;       // sticky status bits
-    int pad[5];
+    int step_stamp;        // the patch's claim stamp (advanced by the last patch block to finish)
+    int patch_blocks;      // patch blocks finished in the current launch
+    int pad[3];
 };
 
 // Per-capsule parameters (device and host mirror).
