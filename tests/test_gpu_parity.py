@@ -181,7 +181,9 @@ def test_benchmarked_launch_shape_fp32_matches_oracle_after_1000_steps(L):
     # scheme, one CTA per capsule (ARCS = 1) with each node update fused with the next
     # step's force and spread (FUSE_IB, one lbmib_step call), single-precision MLS,
     # membrane and traction arithmetic, 128-vertex biconcave rings at the benchmark's
-    # capsule density (one per 8192 lattice nodes: 64 on 1024 x 512).
+    # capsule density (one per 8192 lattice nodes: 64 on 1024 x 512), every kernel on the
+    # context stream as with the benchmark's 16384 capsules (OVERLAP 0; the automatic
+    # setting would overlap 64 capsules).
     #
     # Velocity bound: this channel is nearly steady (started on its parabola, body force
     # 4e-8 per step), so each step rounds the stored FP32 populations (|f - w| up to
@@ -199,6 +201,7 @@ def test_benchmarked_launch_shape_fp32_matches_oracle_after_1000_steps(L):
         ctx = L.from_case(case, storage="fp32")
         ctx.set_option(L.OPT_ARCS, 1)
         ctx.set_option(L.OPT_FUSE_IB, 1)
+        ctx.set_option(L.OPT_OVERLAP, 0)
         ctx.set_option(L.OPT_IB_FP64, ib64)
         ctx.step(1000, o.DYNAMIC)
         _, u, v = ctx.read_fields()
