@@ -72,9 +72,9 @@ __device__ __forceinline__ void touch(const Spread& sp, int cell) {
 // tile's nonzero nodes are collected in shared memory first and appended with one global
 // reservation per capsule, so that the list counter is not a hot spot, and nothing in
 // the loop waits on a global round trip (the force adds are fire-and-forget). A node
-// that the tiles of several capsules cover is listed once by each: the patch then
-// redoes its collision, and clears its force, more than once, with the same result, and
-// the list still holds at most 9 entries per vertex.
+// that the tiles of several capsules cover is listed once by each: the patch forces it
+// once (its first entry claims it) and clears its force once per entry, and the list
+// still holds at most 9 entries per vertex.
 // Collective (all threads); the moment arrays are dead by now and hold the scratch.
 template <typename C>
 __device__ void flush_forces(const Tile<C>& t, const Lat& L, const Spread& sp, int* s_count) {
