@@ -307,6 +307,7 @@ def run_gpu(a):
     ctx.step(a.warmup, scheme)
     ctx.sync()
     ctx.kernel_time(reset=True)
+    ctx.ib_kernel_time(reset=True)
     launches0 = ctx.launch_count
 
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -321,6 +322,7 @@ def run_gpu(a):
     elapsed_ms = start.elapsed_time(end)
     ctx.sync()
     k1_ms, k1_n = ctx.kernel_time(reset=True)
+    p_ms, ib_ms, ib_n, listed = ctx.ib_kernel_time(reset=True)
     launches = ctx.launch_count - launches0
     rate, elapsed_ms = job_throughput(N * a.steps, elapsed_ms, world, dist, torch.device("cuda", dev))
     mlups = rate / 1e6
@@ -350,6 +352,24 @@ def run_gpu(a):
         "clocks": clk.summary(),
         "setup_s": setup_s,
     }
+    if ib_n:
+        # per listed node the patch reads and writes the node's 9 populations and reads its
+        # force, and clears the last step's force and reads both lists' entries and its claim
+        p_bytes = listed * (bpu + 16 + 16 + 4 + 4 + 4)
+        p_avg = p_ms / ib_n
+        line["ib_kernels"] = {
+            "steps_timed": ib_n, "listed_nodes": listed,
+            "patch_ms": p_avg, "patch_share": p_ms / elapsed_ms,
+            "patch_achieved_GBps": p_bytes / (p_avg / 1e3) / 1e9,
+            "patch_frac": p_bytes / (p_avg / 1e3) / 1e9 / hbm,
+            "ib_update_ms": ib_ms / ib_n, "ib_update_share": ib_ms / elapsed_ms,
+            "note": ("CUDA events on the context stream around each step's patch (k_patch) and "
+                     "immersed-boundary node update (k_dyn_update_spread: the update fused with the "
+                     "next step's force and spread, with the list-counter reset before it); the "
+                     "patch's algorithmic bytes per listed node are its 9 populations read and "
+                     "written, the 16-byte force read, the last force cleared and three 4-byte "
+                     "list and claim words"),
+        }
 
     if not a.no_e2e:
         line["e2e"] = e2e_run(a, case, L, scheme, dev)

@@ -302,6 +302,16 @@ lbmib_status lbmib_set_option(lbmib_ctx* ctx, int option, long long value);
 lbmib_status lbmib_kernel_time(lbmib_ctx* ctx, double* total_ms, long long* launches,
                                int reset);
 
+/* Timing of the forced-node patch and of the immersed-boundary node update (with the
+ * next step's force and spread when fused) since the last reset, from CUDA events
+ * recorded while LBMIB_OPT_TIMING is on, in the steps whose kernels all ran on the
+ * context stream (no overlap, closed channel): total milliseconds of each and the
+ * number of steps timed; `listed` is the length of the last spread's touched-node list
+ * (a node covered by several capsules' tiles counts once per tile). Any pointer may be
+ * null. reset != 0 clears the record. Synchronises. */
+lbmib_status lbmib_ib_kernel_time(lbmib_ctx* ctx, double* patch_ms, double* ib_ms, long long* steps,
+                                  long long* listed, int reset);
+
 /* Number of kernels this context has launched (graph replays count their kernels). */
 long long lbmib_launch_count(const lbmib_ctx* ctx);
 

@@ -229,6 +229,23 @@ bool enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
             cudaEventRecord(c->ev_patch, s_lat);
             cudaStreamWaitEvent(s, c->ev_patch, 0);
         }
+        // patch and IB node-update times (one stream only: with overlap the IB kernels run
+        // beside the next lattice update)
+        const bool time_ib = timed && !ov && !L.inflow;
+        cudaEvent_t ep = nullptr, ei = nullptr;
+        if (time_ib) {
+            if (c->ev_ib_free.empty()) {
+                cudaEvent_t a, b;
+                cudaEventCreate(&a);
+                cudaEventCreate(&b);
+                c->ev_ib_free.push_back({a, b});
+            }
+            ep = c->ev_ib_free.back().first;
+            ei = c->ev_ib_free.back().second;
+            c->ev_ib_free.pop_back();
+            c->ev_ib.push_back({c->ev_used - 1, ep, ei});
+            cudaEventRecord(ep, s_lat);
+        }
         int* reset = &c->ctr->count[fp];
         if (scheme == LBMIB_DYNAMIC && fuse_next && fusable(c)) {
             // the next step spreads into the buffer and list this step's patch has just
@@ -240,6 +257,7 @@ bool enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
                                                       status, s);
             });
             if (ov) cudaEventRecord(c->ev_spread, s);
+            if (time_ib) cudaEventRecord(ei, s);
             c->launches += 2;
             cur_fib = fc;
             cur = 1 - cur;
@@ -256,6 +274,7 @@ bool enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
                                                 reset, status, s);
             });
         }
+        if (time_ib) cudaEventRecord(ei, s);
         c->launches += 2;
         cur_fib = fc;
     }
@@ -502,6 +521,11 @@ void lbmib_destroy(lbmib_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_graphs(c);
     for (auto& p : c->ev_pool) {
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    for (const auto& e : c->ev_ib) c->ev_ib_free.push_back({e.patch_end, e.ib_end});
+    for (auto& p : c->ev_ib_free) {
         cudaEventDestroy(p.first);
         cudaEventDestroy(p.second);
     }
@@ -1027,9 +1051,20 @@ lbmib_status lbmib_set_option(lbmib_ctx* c, int option, long long value) {
     return LBMIB_OK;
 }
 
-lbmib_status lbmib_kernel_time(lbmib_ctx* c, double* total_ms, long long* launches, int reset) {
-    if (!c) return LBMIB_ERR_ARG;
+// Fold the recorded events into the totals (the lattice pairs, then the IB events that
+// refer to them) and recycle them.
+static lbmib_status fold_timing(lbmib_ctx* c) {
     LBMIB_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (const auto& e : c->ev_ib) {
+        float mp = 0.0f, mi = 0.0f;
+        LBMIB_CUDA(c, cudaEventElapsedTime(&mp, c->ev_pool[e.lat].second, e.patch_end));
+        LBMIB_CUDA(c, cudaEventElapsedTime(&mi, e.patch_end, e.ib_end));
+        c->timed_patch_ms += mp;
+        c->timed_ib_ms += mi;
+        c->timed_ib_steps++;
+        c->ev_ib_free.push_back({e.patch_end, e.ib_end});
+    }
+    c->ev_ib.clear();
     for (size_t k = 0; k < c->ev_used; k++) {
         float ms = 0.0f;
         LBMIB_CUDA(c, cudaEventElapsedTime(&ms, c->ev_pool[k].first, c->ev_pool[k].second));
@@ -1037,6 +1072,33 @@ lbmib_status lbmib_kernel_time(lbmib_ctx* c, double* total_ms, long long* launch
         c->timed_launches++;
     }
     c->ev_used = 0;
+    return LBMIB_OK;
+}
+
+lbmib_status lbmib_ib_kernel_time(lbmib_ctx* c, double* patch_ms, double* ib_ms, long long* steps,
+                                  long long* listed, int reset) {
+    if (!c) return LBMIB_ERR_ARG;
+    const lbmib_status st = fold_timing(c);
+    if (st != LBMIB_OK) return st;
+    if (patch_ms) *patch_ms = c->timed_patch_ms;
+    if (ib_ms) *ib_ms = c->timed_ib_ms;
+    if (steps) *steps = c->timed_ib_steps;
+    if (listed) {
+        int n = 0;
+        LBMIB_CUDA(c, cudaMemcpy(&n, &c->ctr->count[c->cur_fib], sizeof(int), cudaMemcpyDeviceToHost));
+        *listed = n;
+    }
+    if (reset) {
+        c->timed_patch_ms = c->timed_ib_ms = 0.0;
+        c->timed_ib_steps = 0;
+    }
+    return LBMIB_OK;
+}
+
+lbmib_status lbmib_kernel_time(lbmib_ctx* c, double* total_ms, long long* launches, int reset) {
+    if (!c) return LBMIB_ERR_ARG;
+    const lbmib_status st = fold_timing(c);
+    if (st != LBMIB_OK) return st;
     if (total_ms) *total_ms = c->timed_ms;
     if (launches) *launches = c->timed_launches;
     if (reset) {

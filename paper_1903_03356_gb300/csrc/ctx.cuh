@@ -93,6 +93,16 @@ struct lbmib_ctx {
     size_t ev_used = 0;
     double timed_ms = 0.0;
     long long timed_launches = 0;
+    // the steps' patch and IB node-update kernels, timed from the lattice kernel's end
+    // event (ev_pool[lat]) when every kernel of the step is on the lattice stream
+    struct IbEvents {
+        size_t lat;
+        cudaEvent_t patch_end, ib_end;
+    };
+    std::vector<IbEvents> ev_ib;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_ib_free;
+    double timed_patch_ms = 0.0, timed_ib_ms = 0.0;
+    long long timed_ib_steps = 0;
     std::string err;
 };
 

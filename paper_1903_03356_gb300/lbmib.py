@@ -87,6 +87,7 @@ _SIGS = {
     "lbmib_load_state": (C.c_int, [_vp, _vp, C.c_size_t]),
     "lbmib_set_option": (C.c_int, [_vp, C.c_int, C.c_longlong]),
     "lbmib_kernel_time": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
+    "lbmib_ib_kernel_time": (C.c_int, [_vp, _dp, _dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.c_int]),
     "lbmib_launch_count": (C.c_longlong, [_vp]),
     "lbmib_bytes_per_update": (C.c_double, [_vp]),
     "lbmib_set_repulsion": (C.c_int, [_vp, C.c_double, C.c_double]),
@@ -225,6 +226,14 @@ def lbmib_kernel_time(h, reset: bool = False):
     n = C.c_longlong()
     _check(h, _lib.lbmib_kernel_time(h, C.byref(ms), C.byref(n), int(reset)))
     return ms.value, n.value
+
+
+def lbmib_ib_kernel_time(h, reset: bool = False):
+    """(patch ms, IB update ms, steps timed, touched-list length of the last spread)."""
+    pm, im = C.c_double(), C.c_double()
+    n, listed = C.c_longlong(), C.c_longlong()
+    _check(h, _lib.lbmib_ib_kernel_time(h, C.byref(pm), C.byref(im), C.byref(n), C.byref(listed), int(reset)))
+    return pm.value, im.value, n.value, listed.value
 
 
 def lbmib_launch_count(h) -> int:
@@ -475,6 +484,9 @@ class Context:
 
     def kernel_time(self, reset=False):
         return lbmib_kernel_time(self.h, reset)
+
+    def ib_kernel_time(self, reset=False):
+        return lbmib_ib_kernel_time(self.h, reset)
 
     def adjoint(self, nsteps: int, objective: int = OBJ_TAYLOR_D, capsule: int = 0, ckpt_every: int = 200,
                 scheme: int = KINEMATIC):

@@ -313,6 +313,25 @@ def test_overlapped_streams_equal_a_single_stream(L, scheme):
         np.testing.assert_allclose(ctx.observables_all(), a.observables_all(), rtol=1e-12, atol=1e-13)
 
 
+def test_ib_kernel_time_reports_the_timed_steps(L):
+    # with every kernel on the context stream, each timed step records its patch and IB
+    # node update; with overlap none are recorded
+    case = W.poiseuille_biconcave(nx=512, ny=128, count=12, seed=3, scheme=o.DYNAMIC, steps=1)
+    ctx = L.from_case(case, storage="fp32")
+    ctx.set_option(L.OPT_OVERLAP, 0)
+    ctx.set_option(L.OPT_TIMING, 1)
+    ctx.step(7, o.DYNAMIC)
+    lat_ms, lat_n = ctx.kernel_time(reset=True)
+    p_ms, ib_ms, n, listed = ctx.ib_kernel_time(reset=True)
+    assert lat_n == 7 and n == 7
+    assert p_ms > 0 and ib_ms > 0 and lat_ms > 0
+    assert 9 <= listed <= 9 * sum(c.xy.shape[0] for c in case.capsules)
+    assert ctx.ib_kernel_time()[2] == 0   # reset
+    ctx.set_option(L.OPT_OVERLAP, 1)
+    ctx.step(3, o.DYNAMIC)
+    assert ctx.kernel_time()[1] == 3 and ctx.ib_kernel_time()[2] == 0
+
+
 def test_checkpoint_restart_matches_a_straight_run(L):
     case = _capsule_case(o.DYNAMIC)
     a = L.from_case(case, storage="fp64")
