@@ -640,7 +640,7 @@ template <typename S>
 void launch_patch(void* dst, const Lat& L, const double* fib_c, const int* list_c, double* fib_p,
                   const int* list_p, int* mark, DevCounters* ctr, int c, int capacity, cudaStream_t s) {
     // a grid-stride loop over the touched list, whose length only the device knows, two
-    // entries per thread and pass: up to 6144 blocks of 256, one pass for the 2.9e6
+    // entries per thread and pass: up to 6144 blocks of 256, one pass for the 2.2e6
     // touched nodes of the 16384 x 8192 benchmark
     int grid = (int)blocks_for(capacity > 0 ? (capacity + 1) / 2 : 1, 256);
     if (grid > 6144) grid = 6144;
