@@ -218,13 +218,13 @@ bool enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
         if (ov) cudaStreamWaitEvent(s_lat, c->ev_spread, 0);
         if (st == LBMIB_FP64)
             launch_patch<double>(dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->mark, c->ctr, fc, cap,
-                                   s_lat);
+                                   c->nd.count, s_lat);
         else if (st == LBMIB_FP32)
             launch_patch<float>(dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->mark, c->ctr, fc, cap,
-                                   s_lat);
+                                   c->nd.count, s_lat);
         else
             launch_patch<__half>(dst, L, c->fib[fc], c->list[fc], c->fib[fp], c->list[fp], c->mark, c->ctr, fc, cap,
-                                   s_lat);
+                                   c->nd.count, s_lat);
         if (ov) {
             cudaEventRecord(c->ev_patch, s_lat);
             cudaStreamWaitEvent(s, c->ev_patch, 0);

@@ -8,6 +8,7 @@
 // only the warp's edge lane issues one extra scalar load. Stores are aligned 16-byte
 // stores of the node's own slots, so the kernel moves exactly 9 loads + 9 stores of
 // the storage type per lattice update from HBM.
+#include <algorithm>
 #include <type_traits>
 
 #include "lbmib_kernels.cuh"
@@ -638,11 +639,14 @@ void launch_collide_stream(const void* src, void* dst, const Lat& L, unsigned* s
 
 template <typename S>
 void launch_patch(void* dst, const Lat& L, const double* fib_c, const int* list_c, double* fib_p,
-                  const int* list_p, int* mark, DevCounters* ctr, int c, int capacity, cudaStream_t s) {
+                  const int* list_p, int* mark, DevCounters* ctr, int c, int capacity, long long vertices,
+                  cudaStream_t s) {
     // a grid-stride loop over the touched list, whose length only the device knows, two
-    // entries per thread and pass: up to 6144 blocks of 256, one pass for the 2.2e6
-    // touched nodes of the 16384 x 8192 benchmark
-    int grid = (int)blocks_for(capacity > 0 ? (capacity + 1) / 2 : 1, 256);
+    // entries per thread and pass, sized for 1.1 entries per vertex (the 16384 x 8192
+    // benchmark lists 2.2e6 nodes for 2.1e6 vertices: one pass, and no idle blocks; a
+    // longer list takes more passes), at most 6144 blocks of 256
+    const long long want = (11 * (vertices > 0 ? vertices : 1) + 9) / 10;
+    int grid = (int)blocks_for((std::min<long long>(want, capacity > 0 ? capacity : 1) + 1) / 2, 256);
     if (grid > 6144) grid = 6144;
     k_patch<S><<<grid, 256, 0, s>>>((S*)dst, L, fib_c, list_c, fib_p, list_p, mark, ctr, c, capacity);
 }
@@ -672,7 +676,7 @@ void launch_populations(const void* src, const Lat& L, const OpenBC& ob, int i0,
 #define LBMIB_INSTANTIATE_LATTICE(S)                                                                  \
     template void launch_collide_stream<S>(const void*, void*, const Lat&, unsigned*, int, cudaStream_t); \
     template void launch_patch<S>(void*, const Lat&, const double*, const int*, double*, const int*,   \
-                                  int*, DevCounters*, int, int, cudaStream_t);                        \
+                                  int*, DevCounters*, int, int, long long, cudaStream_t);             \
     template void launch_open_columns<S>(const void*, void*, const Lat&, const OpenBC&, unsigned*,     \
                                          cudaStream_t);                                               \
     template void launch_init<S>(void*, const Lat&, const double*, const double*, const double*,      \

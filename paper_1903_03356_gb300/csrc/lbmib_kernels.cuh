@@ -68,7 +68,8 @@ void launch_collide_stream(const void* src, void* dst, const Lat& L, unsigned* s
 // force the listed nodes in place (their unforced post-collision populations in dst)
 template <typename S>
 void launch_patch(void* dst, const Lat& L, const double* fib_c, const int* list_c, double* fib_p,
-                  const int* list_p, int* mark, DevCounters* ctr, int c, int capacity, cudaStream_t s);
+                  const int* list_p, int* mark, DevCounters* ctr, int c, int capacity, long long vertices,
+                  cudaStream_t s);
 // open channel: Zou-He inlet and outlet columns, after launch_collide_stream on its output
 template <typename S>
 void launch_open_columns(const void* src, void* dst, const Lat& L, const OpenBC& ob, unsigned* status,
