@@ -313,6 +313,24 @@ def test_overlapped_streams_equal_a_single_stream(L, scheme):
         np.testing.assert_allclose(ctx.observables_all(), a.observables_all(), rtol=1e-12, atol=1e-13)
 
 
+def test_degenerate_step_calls(L):
+    # zero steps change nothing; negative counts and unknown schemes are rejected; without
+    # capsules the two schemes are the same lattice update
+    case = W.Case("channel", 301, 37, 0.7, True, gx=W.poiseuille_force(0.7, 0.02, 37), init="parabola")
+    a = L.from_case(case, storage="fp32")
+    f0 = a.read_populations()
+    a.step(0, o.DYNAMIC)
+    assert np.array_equal(a.read_populations(), f0)
+    for n, scheme in ((-1, o.DYNAMIC), (1, 7)):
+        with pytest.raises(L.LbmibError) as e:
+            a.step(n, scheme)
+        assert e.value.status == L.ERR_ARG
+    b = L.from_case(case, storage="fp32")
+    a.step(20, o.DYNAMIC)
+    b.step(20, o.KINEMATIC)
+    assert np.array_equal(a.read_populations(), b.read_populations())
+
+
 def test_ib_kernel_time_reports_the_timed_steps(L):
     # with every kernel on the context stream, each timed step records its patch and IB
     # node update; with overlap none are recorded
