@@ -747,11 +747,14 @@ __global__ void __launch_bounds__(128) k_rigid_update(const S* __restrict__ dst,
 // ---------------------------------------------------------------------------------
 // Kinematic IB (Section 2.4), steps i-iii: internal forces at X^n (Eq. 11, 13, 14) and
 // their spread with c_v = 1. With arcs > 1 the capsule's CTAs form a cluster that sums
-// the enclosed area.
+// the enclosed area. With float weights (single-precision storage) the membrane terms
+// are in float too, as in the Dynamic kernels (positions, their differences and the
+// strain's difference of squares stay double).
 // ---------------------------------------------------------------------------------
 template <typename C>
 __global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int max_n, int arcs, int tile_cells,
                                                           Spread sp, unsigned* status) {
+    constexpr bool F32 = sizeof(C) == 4;
     extern __shared__ __align__(16) unsigned char smem[];
     const CapSmem sm = carve(smem, arc_slots(max_n, arcs), kRedIB);
     CapsuleParams P;
@@ -761,20 +764,44 @@ __global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int m
     Tile<C> t = make_tile<C>(sm, kHalo, kHalo + m, 1, tile_cells, false, true);
     if (t.use) zero_forces<C>(t);
     double area2[1] = {0.0};
+    float area2f[1] = {0.0f};
     // own slots, then (split ring) the halo slots kHalo-1 and kHalo+m
     const bool split = m > 0 && m < a.n;   // an arc without vertices has no tasks
     for (int k = threadIdx.x; k < (split ? m + 2 : m); k += blockDim.x) {
         const int li = k < m ? kHalo + k : (k == m ? kHalo - 1 : kHalo + m);
-        vertex_terms(sm, P, nd, li - 1, li, li + 1, P.off + a.node(li));
-        if (k < m) area2[0] += area_term(a.X0, sm.X[li], sm.X[li + 1]);
+        if constexpr (F32) {
+            vertex_terms_f(sm, P, nd, li - 1, li, li + 1, P.off + a.node(li));
+            if (k < m) {
+                const double2 Xv = sm.X[li];
+                const float2 e = ring_f(sm)[li].e;
+                area2f[0] += (float)(Xv.x - a.X0.x) * e.y - (float)(Xv.y - a.X0.y) * e.x;
+            }
+        } else {
+            vertex_terms(sm, P, nd, li - 1, li, li + 1, P.off + a.node(li));
+            if (k < m) area2[0] += area_term(a.X0, sm.X[li], sm.X[li + 1]);
+        }
     }
-    block_reduce<1, false>(area2, sm.red);  // also orders the tile zeroing before the spread
-    if (m == a.n) copy_halo_terms(sm, m, false);
+    // the reductions also order the tile zeroing before the spread
+    if constexpr (F32) {
+        block_reduce<1, false>(area2f, sm.red);
+        area2[0] = area2f[0];
+    } else {
+        block_reduce<1, false>(area2, sm.red);
+    }
+    if (m == a.n) copy_halo_terms<F32>(sm, m, false);
     const double A = 0.5 * cluster_total(area2[0], arcs);
+    // Eq. 14 factor k_a (1 - A/A0) p_ref / 2 from the difference A0 - A (single precision)
+    const float fa = F32 ? (float)P.ka * ((float)(P.A0 - A) / (6.0f * (float)P.A0)) : 0.0f;
     bool ok = true;
     for (int k = threadIdx.x; k < m; k += blockDim.x) {
         const int li = kHalo + k, g = P.off + a.v0 + k;
-        const double2 F = internal_force(sm, P, li - 1, li, li + 1, A);
+        double2 F;
+        if constexpr (F32) {
+            const float2 f = internal_force_f(sm, li - 1, li, li + 1, fa);
+            F = make_double2(f.x, f.y);
+        } else {
+            F = internal_force(sm, P, li - 1, li, li + 1, A);
+        }
         nd.Fint[g] = F;
         const double2 Fp = nd.Fpp ? nd.Fpp[g] : make_double2(0.0, 0.0);   // Eq. 27
         nd.Fext[g] = make_double2(0.0, 0.0);
@@ -791,7 +818,7 @@ __global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int m
 // X^{n+1} = 2/3 (2 X^n - X^{n-1}/2 + xdot) (Eq. 25); forward Euler on a first step.
 // Every CTA reads and writes only its own vertices.
 template <typename S>
-__global__ void __launch_bounds__(128) k_kin_advance(const S* __restrict__ dst, Lat L,
+__global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_kin_advance(const S* __restrict__ dst, Lat L,
                                                      const double* __restrict__ fib, Nodes nd, int max_n, int arcs,
                                                      int tile_cells, int* reset_count, unsigned* status) {
     using C = typename St<S>::C;
