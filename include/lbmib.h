@@ -270,13 +270,15 @@ lbmib_status lbmib_field_ptr(lbmib_ctx* ctx, int field, void** ptr, int* pitch);
  *                           multiprocessors, otherwise min(8, multiprocessors /
  *                           capsules, vertices / 16). Results do not depend on it
  *                           beyond the order of the area sum.
- *   LBMIB_OPT_FUSE_IB       1 (default): within one lbmib_step call of the Dynamic
- *                           scheme, the node update of a step and the force and
- *                           spread of the next run as one kernel (both read the
- *                           same lattice state; Section 2.3.2 steps 7-8 and 1-3)
- *                           when every capsule has one CTA and the context holds no
- *                           rigid particles; 0: separate kernels. The state between
- *                           calls and the results do not depend on it.
+ *   LBMIB_OPT_FUSE_IB       1 (default): within one lbmib_step call, the node update
+ *                           of a step and the force and spread of the next run as one
+ *                           kernel when every capsule has one CTA and the context
+ *                           holds no rigid particles: the Dynamic scheme (both read
+ *                           the same lattice state; Section 2.3.2 steps 7-8 and 1-3),
+ *                           and the Kinematic one without repulsion (the advance,
+ *                           then the membrane forces at the new positions and their
+ *                           spread; Section 2.4); 0: separate kernels. The state
+ *                           between calls and the results do not depend on it.
  *   LBMIB_OPT_IB_FP64       1: with FP32 or FP16 storage the immersed-boundary kernels
  *                           gather in storage precision and do the MLS solve, the
  *                           membrane and traction forces and the node update in FP64

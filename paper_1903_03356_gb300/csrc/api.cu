@@ -263,6 +263,22 @@ bool enqueue_step(lbmib_ctx* c, lbmib_scheme scheme, int& cur, int& cur_fib, cud
             cur = 1 - cur;
             return true;
         }
+        if (scheme == LBMIB_KINEMATIC && fuse_next && fusable(c) && !(ncaps > 1 && c->rep_rc > 0.0)) {
+            // as above; the Kinematic spread also needs the repulsion at X^{n+1}, which the
+            // next step computes first: fused only without repulsion
+            cudaMemsetAsync(reset, 0, sizeof(int), s);
+            const Spread next{c->fib[fp], c->list[fp], reset, list_cap, status};
+            with_ib_storage(c, [&](auto v) {
+                launch_kin_advance_spread<decltype(v)>(dst, L, c->fib[fc], c->nd, ncaps, c->max_n, c->tile_cells,
+                                                       next, status, s);
+            });
+            if (ov) cudaEventRecord(c->ev_spread, s);
+            if (time_ib) cudaEventRecord(ei, s);
+            c->launches += 2;
+            cur_fib = fc;
+            cur = 1 - cur;
+            return true;
+        }
         if (scheme == LBMIB_DYNAMIC) {
             with_ib_storage(c, [&](auto v) {
                 launch_dyn_update<decltype(v)>(dst, L, c->nd, ncaps, c->max_n, c->arcs, c->tile_cells,

@@ -751,18 +751,15 @@ __global__ void __launch_bounds__(128) k_rigid_update(const S* __restrict__ dst,
 // are in float too, as in the Dynamic kernels (positions, their differences and the
 // strain's difference of squares stay double).
 // ---------------------------------------------------------------------------------
+// Steps i-iii on a staged arc whose force tile is zeroed (collective; a cluster over the
+// capsule's CTAs when arcs > 1): the membrane terms, the enclosed area, the internal
+// forces, the shape functions at the staged positions (stored for the node advance) and
+// the spread. Returns false when a support left the channel or the tile.
 template <typename C>
-__global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int max_n, int arcs, int tile_cells,
-                                                          Spread sp, unsigned* status) {
+__device__ __forceinline__ bool kin_spread(const Lat& L, const Nodes& nd, const CapsuleParams& P, const Arc& a,
+                                           const CapSmem& sm, Tile<C>& t, const Spread& sp, int arcs) {
     constexpr bool F32 = sizeof(C) == 4;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const CapSmem sm = carve(smem, arc_slots(max_n, arcs), kRedIB);
-    CapsuleParams P;
-    Arc a;
-    if (!load_arc(nd, sm, max_n, arcs, true, P, a, status)) return;
     const int m = a.m;
-    Tile<C> t = make_tile<C>(sm, kHalo, kHalo + m, 1, tile_cells, false, true);
-    if (t.use) zero_forces<C>(t);
     double area2[1] = {0.0};
     float area2f[1] = {0.0f};
     // own slots, then (split ring) the halo slots kHalo-1 and kHalo+m
@@ -809,6 +806,26 @@ __global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int m
         store_mls<C>(nd.mls, g, w);
         ok &= spread_with<C>(w, t, L, sp, F.x + Fp.x, F.y + Fp.y, 1.0);
     }
+    return ok;
+}
+
+// Kinematic IB (Section 2.4), steps i-iii: internal forces at X^n (Eq. 11, 13, 14) and
+// their spread with c_v = 1. With arcs > 1 the capsule's CTAs form a cluster that sums
+// the enclosed area. With float weights (single-precision storage) the membrane terms
+// are in float too, as in the Dynamic kernels (positions, their differences and the
+// strain's difference of squares stay double).
+// ---------------------------------------------------------------------------------
+template <typename C>
+__global__ void __launch_bounds__(128) k_kin_force_spread(Lat L, Nodes nd, int max_n, int arcs, int tile_cells,
+                                                          Spread sp, unsigned* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CapSmem sm = carve(smem, arc_slots(max_n, arcs), kRedIB);
+    CapsuleParams P;
+    Arc a;
+    if (!load_arc(nd, sm, max_n, arcs, true, P, a, status)) return;
+    Tile<C> t = make_tile<C>(sm, kHalo, kHalo + a.m, 1, tile_cells, false, true);
+    if (t.use) zero_forces<C>(t);
+    const bool ok = kin_spread<C>(L, nd, P, a, sm, t, sp, arcs);
     __syncthreads();
     if (t.use) flush_forces<C>(t, L, sp, reinterpret_cast<int*>(sm.red));
     if (!ok) atomicOr(status, kStatSupport);
@@ -852,6 +869,64 @@ __global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_kin_advance(const 
         nd.uv[g] = make_double2(Ux, Uy);
         nd.age[g] += 1;
     }
+    if (!ok) atomicOr(status, kStatSupport);
+}
+
+// Kinematic steps vii-viii of step n and steps i-iii of step n+1 in one pass, for one
+// CTA per capsule without rigid particles or repulsion (the host launches it only then):
+// the node advance at X^n as in k_kin_advance, X^{n+1} staged in place of X^n, then the
+// spread at X^{n+1} into the next force buffer and list (sp, whose counter the host has
+// reset). One tile serves both: the moments around X^n for the advance, the force
+// accumulators for the spread, whose supports at X^{n+1} lie inside its margin of three
+// nodes unless a vertex moved two lattice units in a step (flagged, as for any point that
+// leaves its tile).
+template <typename S>
+__global__ void __launch_bounds__(128, dyn_min_blocks<S>()) k_kin_advance_spread(const S* __restrict__ dst, Lat L,
+                                                                 const double* __restrict__ fib, Nodes nd,
+                                                                 int max_n, int tile_cells, Spread sp,
+                                                                 unsigned* status) {
+    using C = typename St<S>::C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CapSmem sm = carve(smem, arc_slots(max_n, 1), kRedIB);
+    CapsuleParams P;
+    Arc a;
+    if (!load_arc(nd, sm, max_n, 1, true, P, a, status)) return;
+    const int m = a.m;   // the whole ring
+    Tile<C> t = make_tile<C>(sm, kHalo - 1, kHalo + m + 1, 3, tile_cells, true, true);
+    if (t.use) {
+        fill_moments<S>(t, dst, L, fib);
+        zero_forces<C>(t);
+    }
+    __syncthreads();
+    bool ok = true;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        const int li = kHalo + k, g = P.off + a.v0 + k;
+        const double2 Xv = sm.X[li];
+        InterpT<C> o;
+        ok &= interp_with<S, false>(load_mls<C>(L, nd.mls, g), t, dst, L, fib, o);
+        const double Ux = (double)o.ux, Uy = (double)o.uy;
+        double2 Xn;
+        if (nd.age[g] == 0) {
+            Xn = make_double2(Xv.x + Ux, Xv.y + Uy);
+        } else {
+            const double2 Xm = nd.Xm1[g];
+            Xn = make_double2((2.0 / 3.0) * (2.0 * Xv.x - 0.5 * Xm.x + Ux),
+                              (2.0 / 3.0) * (2.0 * Xv.y - 0.5 * Xm.y + Uy));
+        }
+        nd.Xm1[g] = Xv;
+        nd.X[g] = Xn;
+        nd.uv[g] = make_double2(Ux, Uy);
+        nd.age[g] += 1;
+        sm.X[li] = Xn;   // only this thread reads the slot before the barrier
+    }
+    __syncthreads();
+    // the halo slots repeat the ring's last and first vertices at X^{n+1}
+    for (int h = threadIdx.x; h < 2 * kHalo; h += blockDim.x)
+        sm.X[h < kHalo ? h : m + h] = sm.X[h < kHalo ? m + h : h];
+    __syncthreads();
+    ok &= kin_spread<C>(L, nd, P, a, sm, t, sp, 1);
+    __syncthreads();
+    if (t.use) flush_forces<C>(t, L, sp, reinterpret_cast<int*>(sm.red));
     if (!ok) atomicOr(status, kStatSupport);
 }
 
@@ -989,6 +1064,11 @@ void set_capsule_smem_limits(int slots, int cells) {
     LBMIB_SMEM(k_dyn_update_spread<double>, double, true, true);
     LBMIB_SMEM(k_dyn_update_spread<float>, float, true, true);
     LBMIB_SMEM(k_dyn_update_spread<__half>, float, true, true);
+    LBMIB_SMEM(k_kin_advance_spread<double>, double, true, true);
+    LBMIB_SMEM(k_kin_advance_spread<float>, float, true, true);
+    LBMIB_SMEM(k_kin_advance_spread<__half>, float, true, true);
+    LBMIB_SMEM(k_kin_advance_spread<f32w>, double, true, true);
+    LBMIB_SMEM(k_kin_advance_spread<f16w>, double, true, true);
     LBMIB_SMEM(k_kin_advance<double>, double, true, false);
     LBMIB_SMEM(k_kin_advance<float>, float, true, false);
     LBMIB_SMEM(k_kin_advance<__half>, float, true, false);
@@ -1073,6 +1153,14 @@ void launch_kin_advance(const void* dst, const Lat& L, const double* fib_cur, No
                 (const S*)dst, L, fib_cur, nd, max_n, arcs, cells, reset_count, status);
 }
 
+template <typename S>
+void launch_kin_advance_spread(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
+                               int cells, Spread sp_next, unsigned* status, cudaStream_t s) {
+    using C = typename St<S>::C;
+    launch_arcs(k_kin_advance_spread<S>, ncaps, 1, false, smem_bytes<C>(arc_slots(max_n, 1), cells, true, true), s,
+                (const S*)dst, L, fib_cur, nd, max_n, cells, sp_next, status);
+}
+
 void launch_observables(Nodes nd, int ncaps, int max_n, double* out, cudaStream_t s) {
     // set here rather than with the other limits: contexts and batches of different ring
     // sizes share this kernel
@@ -1095,6 +1183,8 @@ void launch_interp_points(const void* src, const Lat& L, const double* fib, cons
                                               unsigned*, cudaStream_t);                                      \
     template void launch_kin_advance<S>(const void*, const Lat&, const double*, Nodes, int, int, int, int,   \
                                         int*, unsigned*, cudaStream_t);                                      \
+    template void launch_kin_advance_spread<S>(const void*, const Lat&, const double*, Nodes, int, int, int,  \
+                                               Spread, unsigned*, cudaStream_t);                             \
     template void launch_interp_points<S>(const void*, const Lat&, const double*, const double2*, int,       \
                                           double*, unsigned*, cudaStream_t);
 

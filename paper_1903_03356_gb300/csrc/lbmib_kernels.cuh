@@ -106,6 +106,11 @@ void launch_kin_force_spread(const Lat& L, Nodes nd, int ncaps, int max_n, int a
 template <typename S>
 void launch_kin_advance(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
                         int arcs, int cells, int* reset_count, unsigned* status, cudaStream_t s);
+// the Kinematic node advance of step n and the force and spread of step n+1 in one kernel
+// (one CTA per capsule, no rigid particles, no repulsion), spreading through sp_next
+template <typename S>
+void launch_kin_advance_spread(const void* dst, const Lat& L, const double* fib_cur, Nodes nd, int ncaps, int max_n,
+                               int cells, Spread sp_next, unsigned* status, cudaStream_t s);
 void launch_observables(Nodes nd, int ncaps, int max_n, double* out, cudaStream_t s);
 template <typename S>
 void launch_interp_points(const void* src, const Lat& L, const double* fib, const double2* pts, int n,

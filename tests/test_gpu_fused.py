@@ -1,7 +1,8 @@
-"""The Dynamic node update of a step fused with the force and spread of the next
-(Section 2.3.2 steps 7-8 and 1-3 read the same lattice state): against the separate
-kernels, against the oracle, through graphs and direct launches, across call boundaries,
-and in the launch count it reports.
+"""The node update of a step fused with the force and spread of the next: the Dynamic
+scheme (Section 2.3.2 steps 7-8 and 1-3 read the same lattice state) and the Kinematic
+one (Section 2.4: the advance of step n, then the membrane forces at X^{n+1} and their
+spread). Against the separate kernels, against the oracle, through graphs and direct
+launches, across call boundaries, and in the launch count it reports.
 """
 import numpy as np
 import pytest
@@ -118,3 +119,64 @@ def test_fuse_option_is_checked(L):
         with pytest.raises(L.LbmibError) as e:
             ctx.set_option(L.OPT_FUSE_IB, bad)
         assert e.value.status == L.ERR_ARG
+
+
+def kinematic_suspension():
+    return W.poiseuille_biconcave(nx=300, ny=96, count=6, n=64, seed=0, scheme=o.KINEMATIC)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+@pytest.mark.parametrize("graphs", [True, False])
+def test_fused_kinematic_steps_match_the_separate_kernels(L, storage, graphs):
+    case = kinematic_suspension()
+    a = context(L, case, storage, fuse=True, graphs=graphs)
+    b = context(L, case, storage, fuse=False, graphs=graphs)
+    a.step(70, L.KINEMATIC)
+    b.step(70, L.KINEMATIC)
+    pa, xa = state(a, len(case.capsules))
+    pb, xb = state(b, len(case.capsules))
+    print(f"kinematic {storage} graphs={graphs}: populations {np.abs(pa - pb).max():.2e}, "
+          f"positions {np.abs(xa - xb).max():.2e}")
+    np.testing.assert_allclose(pa, pb, rtol=0, atol=AGREE[storage])
+    np.testing.assert_allclose(xa, xb, rtol=0, atol=AGREE[storage] * 10)
+
+
+def test_fused_kinematic_steps_match_the_oracle(L):
+    case = kinematic_suspension()
+    ctx = context(L, case, "fp64", fuse=True)
+    s = o.Sim(o.lattice(case.nx, case.ny, case.tau, case.walls, case.u_bottom, case.u_top, case.gx, case.gy))
+    s.init_fields(*case.fields())
+    for c in case.capsules:
+        s.add_capsule(c.xy, c.ks, c.kb, c.ka, c.mass)
+    ctx.step(100, L.KINEMATIC)
+    assert s.step(100, o.KINEMATIC) == 0
+    _, u_g, v_g = ctx.read_fields()
+    _, u_o, v_o = s.read_fields()
+    err = max(np.abs(u_g - u_o).max(), np.abs(v_g - v_o).max()) / np.abs(u_o).max()
+    assert err < 1e-10
+    for k in range(len(case.capsules)):
+        assert np.abs(ctx.read_capsule(k)[0] - s.read_capsule(k)[0]).max() < 1e-9
+
+
+def test_fused_kinematic_call_boundaries_and_launch_count(L):
+    # one call against three, and against Dynamic steps in between; per fused step the
+    # lattice update, the patch and the advance with the next spread
+    case = kinematic_suspension()
+    a = context(L, case, "fp64", fuse=True)
+    b = context(L, case, "fp64", fuse=True)
+    a.step(30, L.KINEMATIC)
+    for n in (7, 1, 22):
+        b.step(n, L.KINEMATIC)
+    np.testing.assert_allclose(a.read_populations(), b.read_populations(), rtol=0, atol=1e-12)
+    c = context(L, case, "fp64", fuse=True)
+    d = context(L, case, "fp64", fuse=False)
+    for ctx in (c, d):
+        ctx.step(10, L.KINEMATIC)
+        ctx.step(1, L.DYNAMIC)
+        ctx.step(10, L.KINEMATIC)
+    np.testing.assert_allclose(c.read_populations(), d.read_populations(), rtol=0, atol=1e-12)
+    e = context(L, case, "fp32", fuse=True, graphs=False)
+    n0 = e.launch_count
+    e.step(37, L.KINEMATIC)
+    e.sync()
+    assert e.launch_count - n0 == 3 * 37 + 1
