@@ -247,7 +247,8 @@ lbmib_status lbmib_field_ptr(lbmib_ctx* ctx, int field, void** ptr, int* pitch);
  *                           0: launch kernels directly.
  *   LBMIB_OPT_TIMING        1: record CUDA events around every lattice-update launch
  *                           (forces direct launches); read with lbmib_kernel_time.
- *   LBMIB_OPT_GRAPH_STEPS   steps per captured graph (default 16).
+ *   LBMIB_OPT_GRAPH_STEPS   steps per captured graph (default 64; each graph opens with
+ *                           its own force and spread and closes with its own update).
  *   LBMIB_OPT_FP16_SCALE    log2 of the FP16 storage scale (default 10).
  *   LBMIB_OPT_LATTICE_VARIANT launch shape of the lattice-update kernel: bits 0-11 the
  *                           block size (128 or 256), bit 18 a 64-register cap (eight

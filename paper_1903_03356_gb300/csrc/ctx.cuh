@@ -80,7 +80,7 @@ struct lbmib_ctx {
     // options
     bool use_graphs = true;
     bool timing = false;
-    int graph_steps = 16;
+    int graph_steps = 64;
     int lattice_variant = 256;
     bool fuse_ib = true;
     bool ib_fp64 = false;     // IB arithmetic in FP64 over single-precision storage

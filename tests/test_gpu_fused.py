@@ -31,6 +31,7 @@ def context(L, case, storage, fuse, graphs=True):
     ctx.set_option(L.OPT_ARCS, 1)          # one CTA per capsule: the fusable launch shape
     ctx.set_option(L.OPT_FUSE_IB, 1 if fuse else 0)
     ctx.set_option(L.OPT_GRAPHS, 1 if graphs else 0)
+    ctx.set_option(L.OPT_GRAPH_STEPS, 16)   # graph boundaries inside the runs below
     return ctx
 
 
