@@ -790,7 +790,10 @@ __device__ __forceinline__ bool kin_spread(const Lat& L, const Nodes& nd, const 
     // Eq. 14 factor k_a (1 - A/A0) p_ref / 2 from the difference A0 - A (single precision)
     const float fa = F32 ? (float)P.ka * ((float)(P.A0 - A) / (6.0f * (float)P.A0)) : 0.0f;
     bool ok = true;
-    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    // the spread in ring-hop order (see dyn_spread): fewer colliding shared-memory atomics
+    const int hop = ring_hop(m);
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        const int k = (int)((long long)j * hop % m);
         const int li = kHalo + k, g = P.off + a.v0 + k;
         double2 F;
         if constexpr (F32) {
