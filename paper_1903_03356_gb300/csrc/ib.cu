@@ -550,7 +550,10 @@ __device__ __forceinline__ bool dyn_update(const S* __restrict__ dst, const Lat&
             // 1.5 (X^{n+1} - X^n) - 0.5 (X^n - X^{n-1})
             const float ix = xd.x + hm * (Fi.x + Fe.x), iy = xd.y + hm * (Fi.y + Fe.y);
             const double dx = (double)ix, dy = (double)iy;
-            const double2 uvn = make_double2(1.5 * dx - 0.5 * (Xv.x - Xm.x), 1.5 * dy - 0.5 * (Xv.y - Xm.y));
+            // the last increment X^n - X^{n-1} as the exact double difference, the rest in
+            // float (the velocity enters only the float force of the next spread)
+            const float px = (float)(Xv.x - Xm.x), py = (float)(Xv.y - Xm.y);
+            const double2 uvn = make_double2(1.5f * ix - 0.5f * px, 1.5f * iy - 0.5f * py);
             nd.uv[g] = uvn;
             nd.Xm1[g] = Xv;
             const double2 Xn = make_double2(Xv.x + dx, Xv.y + dy);
