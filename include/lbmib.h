@@ -284,7 +284,7 @@ lbmib_status lbmib_field_ptr(lbmib_ctx* ctx, int field, void** ptr, int* pitch);
  *                           gather in storage precision and do the MLS solve, the
  *                           membrane and traction forces and the node update in FP64
  *                           (slower: GB300's FP64 rate); 0 (default): they compute in
- *                           FP32 around FP64 positions, velocities and enclosed areas.
+ *                           FP32 around FP64 positions, stored velocities and enclosed areas.
  *                           No effect with FP64 storage.                             */
 enum {
     LBMIB_OPT_GRAPHS = 1,
